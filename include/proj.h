@@ -1,0 +1,232 @@
+/*
+ * proj.h - C ABI of the B300 (sm_103a) cone-beam projector library.
+ *
+ * Operations (paper: "Differentiable Forward and Back-Projector for Rigid
+ * Motion Estimation in X-ray Imaging"):
+ *   proj_set_volume         volume gradient grad mu by central differences
+ *                           (Sec. II-C.1), cached in the workspace;
+ *   proj_forward            ray-driven forward projection l = A(M) mu
+ *                           (Eq. forward, Sec. II-C.1);
+ *   proj_forward_pose_grad  dL/dtheta of a projection-domain loss, the
+ *                           12 channels of G_f projected in the same march
+ *                           (Eqs. for_grad, final_forward, for_int,
+ *                           dis_forward), fused with the loss residual;
+ *   proj_back               voxel-driven back-projection mu = A^T(M) l
+ *                           (Eq. back, Sec. II-C.2);
+ *   proj_back_pose_grad     dL/dtheta of an image-domain loss, the 12
+ *                           channels of G_b back-projected (Eqs. back_derive,
+ *                           final_back, back_int, dis_back);
+ *   proj_forward_adjoint    exact transpose of proj_forward (the "A^T" of
+ *                           Sec. II-C.2 for the ray-driven A).
+ *
+ * Conventions (the paper leaves them open; Table I fixes the symbols):
+ *   - World frame in mm; pose theta = (tx, ty, tz, gx, gy, gz) in mm and
+ *     rad; R = Rz(gz) Ry(gy) Rx(gx); a point r' of the object is seen at
+ *     r = R r' + t (M = [R | t]), so r' = R^T (r - t).
+ *   - Volume memory order [nz][ny][nx], FP32; voxel (i, j, k) centre in the
+ *     object frame = vol_offset + ((i-(nx-1)/2) vx, (j-(ny-1)/2) vy,
+ *     (k-(nz-1)/2) vz).  mu is zero outside the grid and the trilinear
+ *     interpolant mu~ uses zero padding.
+ *   - View v: source s, detector centre c, pixel-pitch vectors U (column
+ *     direction, |U| = pixel width) and V (row direction); pixel (iu, iv)
+ *     centre = c + (iu-(nu-1)/2) U + (iv-(nv-1)/2) V.  Images are
+ *     [nv][nu], FP32.  The projection matrix P of Eq. projmatrix is built
+ *     from these vectors in pixel-index units: P = [B^-1 | -B^-1 s],
+ *     B = [U | V | q00 - s].
+ *   - Ray of pixel i: r_k = s + k * step * e_i (e_i unit), k >= 0 integer;
+ *     l_i = step * sum over k whose object index coordinate lies in the
+ *     open box (-1, n)^3 of mu~(R^T (r_k - t)).
+ *   - Back-projection: mu_j = sum over instances of W * l~(d_j), d_j the
+ *     projection of R r'_j + t, l~ bilinear with zero padding, W = 1 or the
+ *     FDK distance weight (w'(0) / w'(r_j))^2; voxels with w' <= 0 get 0.
+ *   - Pose gradients are returned per pose: dL/dt in 1/mm, dL/dgamma in
+ *     1/rad.
+ *
+ * Instances.  A plan has n_views physical views (geometry) and n_pose
+ * poses.  An instance is one (view, pose) pair; every call processes all
+ * n_inst instances of the plan.  Registration of 64 candidates seen by 2
+ * views is n_views = 2, n_pose = 64, n_inst = 128; per-view motion
+ * (motion-compensated reconstruction) is n_pose = n_inst = n_views.
+ *
+ * Memory and streams.  Every pointer whose name starts with d_ is device
+ * memory owned by the caller; everything else is host memory read during
+ * the call.  The plan owns only small device tables (views, instance map)
+ * allocated at creation.  Calls never allocate: scratch space is the
+ * caller's workspace d_ws of at least proj_workspace_size() bytes, which
+ * must stay untouched between proj_set_volume and the calls that use the
+ * volume.  Every call is asynchronous on the caller's stream (NULL = legacy
+ * default stream); outputs are overwritten, never accumulated.  Calls on
+ * one plan and workspace must not overlap on the GPU.
+ *
+ * Errors.  Functions return PROJ_OK (0) or a negative code; the message of
+ * the last failure in the calling thread is in proj_last_error().  Argument
+ * checks run on the host before any launch and then nothing is launched.
+ * Conditions only the device can see (a non-finite pose) make the affected
+ * instances contribute zero and set a bit in a status word inside the
+ * workspace; proj_check() reads and clears it (it synchronises the stream).
+ */
+#ifndef PROJ_H
+#define PROJ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *proj_stream;
+
+enum {
+  PROJ_OK = 0,
+  PROJ_E_ARG = -1,         /* invalid argument (null, size, index, value) */
+  PROJ_E_CUDA = -2,        /* a CUDA runtime call or launch failed */
+  PROJ_E_WORKSPACE = -3,   /* workspace missing, too small or misaligned */
+  PROJ_E_UNSUPPORTED = -4, /* operation not enabled in the plan's flags */
+  PROJ_E_DEVICE = -5       /* device-side status bit set (see proj_check) */
+};
+
+/* Loss modes of proj_forward_pose_grad. */
+enum {
+  PROJ_LOSS_RESIDUAL = 0, /* d_ref = dL/dl per instance [n_inst][nv][nu] */
+  PROJ_LOSS_L2 = 1,       /* d_ref = target per view [n_views][nv][nu];
+                             L_pose = sum over its instances of sum (l-b)^2
+                             (Eq. forward_loss) */
+  PROJ_LOSS_NCC = 2       /* d_ref = target per view; L_pose = -mean over its
+                             instances of the Pearson NCC of l and b over
+                             the whole image (Sec. II-D.3) */
+};
+
+/* Back-projection weights. */
+enum {
+  PROJ_W_NONE = 0,      /* W = 1 */
+  PROJ_W_FDK = 1,       /* W = (w'(0)/w'(r))^2; gradients include l~ grad W */
+  PROJ_W_FDK_CONST = 2  /* same W; gradients treat W as constant */
+};
+
+/* Operations a plan must support (sizes its workspace). */
+enum {
+  PROJ_OP_FORWARD = 1,
+  PROJ_OP_FORWARD_GRAD = 2,
+  PROJ_OP_BACK = 4,
+  PROJ_OP_BACK_GRAD = 8,
+  PROJ_OP_ADJOINT = 16,
+  PROJ_OP_ALL = 31
+};
+
+/* Device status bits (proj_check). */
+enum {
+  PROJ_STATUS_BAD_POSE = 1 /* a pose had a non-finite entry */
+};
+
+typedef struct {
+  int nx, ny, nz;        /* volume size in voxels, each >= 1 */
+  double vx, vy, vz;     /* voxel pitch, mm, > 0 */
+  double vol_offset[3];  /* object-frame position of the volume centre, mm */
+  int nu, nv;            /* detector columns and rows, each >= 1 */
+  int n_views;           /* >= 1 */
+  const double *views;   /* host [n_views][12]: s, c, U, V (mm) */
+  double step;           /* ray step along the world ray, mm, > 0 */
+} proj_geometry;
+
+typedef struct proj_plan_s *proj_plan;
+
+/* Create a plan on the current CUDA device.
+ *   geom       geometry, copied (views included); not referenced later.
+ *   n_pose     number of poses, >= 1.
+ *   n_inst     number of instances, >= 1.
+ *   inst_view  host [n_inst], view of each instance in [0, n_views).
+ *   inst_pose  host [n_inst], pose of each instance in [0, n_pose).
+ *   ops        OR of PROJ_OP_* the plan must support.
+ *   out        receives the plan.
+ * Errors: PROJ_E_ARG (bad sizes, indices, non-finite or degenerate
+ * geometry, singular detector basis), PROJ_E_CUDA (table allocation). */
+int proj_plan_create(const proj_geometry *geom, int n_pose, int n_inst, const int *inst_view,
+                     const int *inst_pose, int ops, proj_plan *out);
+
+/* Free a plan and its device tables (synchronous).  NULL is a no-op. */
+int proj_plan_destroy(proj_plan plan);
+
+/* Bytes of workspace the plan needs (multiple of 256; base must be
+ * 256-byte aligned). */
+int proj_workspace_size(proj_plan plan, size_t *bytes);
+
+/* Prepare the volume for the ray-driven calls (Sec. II-C.1: grad mu by
+ * central differences of the zero-padded volume): writes a zero-bordered
+ * copy of mu and, when PROJ_OP_FORWARD_GRAD is enabled, a float4
+ * (mu, d mu/dx', d mu/dy', d mu/dz') volume (per mm, object frame) on the
+ * index grid [-1, n]^3 into the workspace.
+ *   d_mu  [nz][ny][nx] FP32.
+ * Must run before proj_forward / proj_forward_pose_grad; stays valid until
+ * the workspace is reused for another volume. */
+int proj_set_volume(proj_plan plan, const float *d_mu, void *d_ws, size_t ws_bytes, proj_stream stream);
+
+/* Forward projection of the volume last set (Eq. forward).
+ *   d_pose  [n_pose][6] FP32.
+ *   d_proj  out [n_inst][nv][nu] FP32. */
+int proj_forward(proj_plan plan, const float *d_pose, float *d_proj, void *d_ws, size_t ws_bytes,
+                 proj_stream stream);
+
+/* Pose gradient of a projection-domain loss (Eqs. for_grad, final_forward,
+ * dis_forward).  One march per ray accumulates l_i and the 12 sums of G_f
+ * (grad mu interpolated from the central-difference grid at every sample);
+ * the loss residual weights each ray at its end; nothing per channel is
+ * written to memory.
+ *   loss        PROJ_LOSS_*.
+ *   d_ref       RESIDUAL: dL/dl [n_inst][nv][nu]; L2 / NCC: target images
+ *               [n_views][nv][nu].
+ *   d_grad      out [n_pose][6] FP32, dL/dtheta.
+ *   d_loss      out [n_pose] FP32 or NULL (RESIDUAL writes 0).
+ *   d_proj      out [n_inst][nv][nu] FP32 projections, or NULL. */
+int proj_forward_pose_grad(proj_plan plan, const float *d_pose, int loss, const float *d_ref, float *d_grad,
+                           float *d_loss, float *d_proj, void *d_ws, size_t ws_bytes, proj_stream stream);
+
+/* Voxel-driven back-projection (Eq. back) of one image per instance.
+ *   d_proj  [n_inst][nv][nu] FP32.
+ *   weight  PROJ_W_NONE or PROJ_W_FDK (FDK_CONST behaves as FDK here).
+ *   d_vol   out [nz][ny][nx] FP32 (sum over all instances). */
+int proj_back(proj_plan plan, const float *d_proj, const float *d_pose, int weight, float *d_vol, void *d_ws,
+              size_t ws_bytes, proj_stream stream);
+
+/* Pose gradient of an image-domain loss through the back-projector
+ * (Eqs. back_derive, final_back, back_int, dis_back): grad_d l by central
+ * differences of each image interpolated at the projected voxel, the
+ * projection Jacobian, and the FDK weight derivative for PROJ_W_FDK.
+ *   d_proj      [n_inst][nv][nu] FP32 images that were back-projected.
+ *   weight      PROJ_W_*.
+ *   d_vol_resid dL/dmu [nz][ny][nx] FP32.
+ *   d_grad      out [n_pose][6] FP32. */
+int proj_back_pose_grad(proj_plan plan, const float *d_proj, const float *d_pose, int weight,
+                        const float *d_vol_resid, float *d_grad, void *d_ws, size_t ws_bytes,
+                        proj_stream stream);
+
+/* Exact transpose of proj_forward for the given poses: each sample spreads
+ * step * y_i over its 8 trilinear corners.
+ *   d_y    [n_inst][nv][nu] FP32.
+ *   d_vol  out [nz][ny][nx] FP32. */
+int proj_forward_adjoint(proj_plan plan, const float *d_y, const float *d_pose, float *d_vol, void *d_ws,
+                         size_t ws_bytes, proj_stream stream);
+
+/* Synchronise the stream, read and clear the workspace status word.
+ * *status receives the PROJ_STATUS_* bits (may be NULL).  Returns PROJ_OK,
+ * PROJ_E_DEVICE when a bit was set, or PROJ_E_CUDA. */
+int proj_check(proj_plan plan, void *d_ws, size_t ws_bytes, proj_stream stream, int *status);
+
+/* Ray samples |K_i| per instance for the given poses, counted on the
+ * device by the same clipping and sample test the march kernels use (for
+ * reporting samples/s).
+ *   d_count  out [n_inst] int64. */
+int proj_count_samples(proj_plan plan, const float *d_pose, long long *d_count, void *d_ws, size_t ws_bytes,
+                       proj_stream stream);
+
+/* Message of the last error in this thread ("" if none). */
+const char *proj_last_error(void);
+
+/* Library version string. */
+const char *proj_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PROJ_H */

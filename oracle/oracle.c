@@ -30,8 +30,9 @@
  *  - Back-projection pose gradient (Eq. back_derive / final_back / back_int
  *    / dis_back): grad_d l = bilinear interpolation of central-difference
  *    detector images on the extended grid (analytic) or the exact derivative
- *    of l~ (exact); the FDK weight contributes l~ * grad W unless the
- *    paper-literal constant-weight variant is requested.
+ *    of l~ (exact), both taken on the open support (-1,nu) x (-1,nv) of l~;
+ *    the FDK weight contributes l~ * grad W unless the paper-literal
+ *    constant-weight variant is requested.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -427,10 +428,14 @@ static void det_grad_grid(const double *img, const or_geom *g, int iu, int iv, d
   out[1] = 0.5 * (pix(img, g, iu, iv + 1) - pix(img, g, iu, iv - 1));
 }
 
+/* Detector gradient at (u, v).  Like the forward samples, which are kept in
+ * the open index box where mu~ lives, it is taken only on the open support
+ * (-1, nu) x (-1, nv) of l~ and is zero elsewhere. */
 static void det_gradient_at(const double *img, const or_geom *g, double u, double v, int mode, double out[2]) {
   int i0 = (int)floor(u), j0 = (int)floor(v);
   double au = u - i0, av = v - j0;
   out[0] = out[1] = 0.0;
+  if (!(u > -1.0 && u < g->nu && v > -1.0 && v < g->nv)) return;
   for (int c = 0; c < 4; ++c) {
     int di = c & 1, dj = (c >> 1) & 1;
     double wu = di ? au : 1 - au, wv = dj ? av : 1 - av;
