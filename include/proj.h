@@ -54,7 +54,8 @@
  * allocated at creation.  Calls never allocate: scratch space is the
  * caller's workspace d_ws of at least proj_workspace_size() bytes, which
  * must stay untouched between proj_set_volume and the calls that use the
- * volume.  Every call is asynchronous on the caller's stream (NULL = legacy
+ * volume.  Its first 256 bytes hold the device status word: zero them once
+ * after allocating the workspace.  Every call is asynchronous on the caller's stream (NULL = legacy
  * default stream); outputs are overwritten, never accumulated.  Calls on
  * one plan and workspace must not overlap on the GPU.
  *

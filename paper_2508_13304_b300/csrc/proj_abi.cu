@@ -1,0 +1,407 @@
+// C ABI of the projector library (declared in include/proj.h): plan
+// creation, host-side argument validation, workspace layout and the
+// launch sequence of each operation.  No entry point allocates device
+// memory except proj_plan_create (the plan's small tables).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "proj_internal.cuh"
+
+using namespace projk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(PROJ_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+}  // namespace
+
+struct proj_plan_s {
+  Geo geo;
+  int n_views, n_pose, n_inst, ops;
+  int device;
+  int n_tiles;        // ray tiles per instance
+  int bp_blocks;      // blocks of the back-projection gradient kernel
+  std::vector<double> views;
+  std::vector<int> inst_view, inst_pose;
+  // device tables owned by the plan
+  double* d_views = nullptr;
+  int* d_inst_view = nullptr;
+  int* d_inst_pose = nullptr;
+  int* d_pose_ptr = nullptr;
+  int* d_pose_idx = nullptr;
+  // workspace layout (byte offsets; 0 = buffer absent, the status word sits at 0)
+  size_t off_status = 0, off_inst = 0, off_ptab = 0, off_vol1 = 0, off_vol4 = 0, off_part_f = 0, off_det4 = 0,
+         off_part_b = 0, off_acc = 0, ws_bytes = 0;
+};
+
+namespace {
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+struct WsView {
+  int* status = nullptr;
+  InstTable* inst = nullptr;
+  PoseTable* ptab = nullptr;
+  float* vol1 = nullptr;
+  float4* vol4 = nullptr;
+  float* part_f = nullptr;
+  float4* det4 = nullptr;
+  float* part_b = nullptr;
+  float* acc = nullptr;
+};
+
+int check_ws(const proj_plan_s* p, void* d_ws, size_t ws_bytes, WsView* w) {
+  if (!d_ws) return fail(PROJ_E_WORKSPACE, "workspace pointer is NULL");
+  if (reinterpret_cast<uintptr_t>(d_ws) % kAlign) return fail(PROJ_E_WORKSPACE, "workspace is not 256-byte aligned");
+  if (ws_bytes < p->ws_bytes)
+    return fail(PROJ_E_WORKSPACE, "workspace has %zu bytes, plan needs %zu", ws_bytes, p->ws_bytes);
+  char* b = static_cast<char*>(d_ws);
+  w->status = reinterpret_cast<int*>(b + p->off_status);
+  w->inst = reinterpret_cast<InstTable*>(b + p->off_inst);
+  w->ptab = reinterpret_cast<PoseTable*>(b + p->off_ptab);
+  w->vol1 = p->off_vol1 ? reinterpret_cast<float*>(b + p->off_vol1) : nullptr;
+  w->vol4 = p->off_vol4 ? reinterpret_cast<float4*>(b + p->off_vol4) : nullptr;
+  w->part_f = p->off_part_f ? reinterpret_cast<float*>(b + p->off_part_f) : nullptr;
+  w->det4 = p->off_det4 ? reinterpret_cast<float4*>(b + p->off_det4) : nullptr;
+  w->part_b = p->off_part_b ? reinterpret_cast<float*>(b + p->off_part_b) : nullptr;
+  w->acc = p->off_acc ? reinterpret_cast<float*>(b + p->off_acc) : nullptr;
+  return PROJ_OK;
+}
+
+int need_op(const proj_plan_s* p, int op, const char* name) {
+  if (!(p->ops & op)) return fail(PROJ_E_UNSUPPORTED, "%s: operation not enabled when the plan was created", name);
+  return PROJ_OK;
+}
+
+int setup(const proj_plan_s* p, const float* d_pose, const WsView& w, cudaStream_t s) {
+  cudaError_t e = launch_setup(d_pose, p->n_pose, p->d_views, p->d_inst_view, p->d_inst_pose, p->n_inst, p->geo,
+                               w.inst, w.ptab, w.status, s);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "pose set-up launch");
+}
+
+int check_device(const proj_plan_s* p) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != p->device) return fail(PROJ_E_ARG, "current device %d differs from the plan's device %d", dev, p->device);
+  return PROJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* proj_last_error(void) { return g_last_error.c_str(); }
+
+const char* proj_version(void) { return "b300-diffproj 0.1 (sm_103a)"; }
+
+int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const int* inst_view, const int* inst_pose,
+                     int ops, proj_plan* out) {
+  g_last_error.clear();
+  if (!out) return fail(PROJ_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (!geom) return fail(PROJ_E_ARG, "geometry is NULL");
+  const proj_geometry& G = *geom;
+  if (G.nx < 1 || G.ny < 1 || G.nz < 1) return fail(PROJ_E_ARG, "volume size %d x %d x %d", G.nx, G.ny, G.nz);
+  if (G.nu < 1 || G.nv < 1) return fail(PROJ_E_ARG, "detector size %d x %d", G.nu, G.nv);
+  const long long npad = (long long)(G.nx + 2) * (G.ny + 2) * (G.nz + 2);
+  if (npad >= (1LL << 31)) return fail(PROJ_E_ARG, "volume too large (padded voxel count %lld >= 2^31)", npad);
+  if ((long long)(G.nu + 2) * (G.nv + 2) >= (1LL << 31)) return fail(PROJ_E_ARG, "detector too large");
+  if (!finite_pos(G.vx) || !finite_pos(G.vy) || !finite_pos(G.vz))
+    return fail(PROJ_E_ARG, "voxel pitch must be finite and > 0");
+  if (!finite_pos(G.step)) return fail(PROJ_E_ARG, "ray step must be finite and > 0");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(G.vol_offset[a])) return fail(PROJ_E_ARG, "volume offset must be finite");
+  if (G.n_views < 1 || !G.views) return fail(PROJ_E_ARG, "need n_views >= 1 and a view table");
+  if (n_pose < 1) return fail(PROJ_E_ARG, "n_pose must be >= 1");
+  if (n_inst < 1 || !inst_view || !inst_pose) return fail(PROJ_E_ARG, "need n_inst >= 1 and instance maps");
+  if (ops <= 0 || (ops & ~PROJ_OP_ALL)) return fail(PROJ_E_ARG, "ops must be a non-empty OR of PROJ_OP_*");
+  for (int v = 0; v < G.n_views; ++v) {
+    const double* w = G.views + 12 * v;
+    for (int a = 0; a < 12; ++a)
+      if (!std::isfinite(w[a])) return fail(PROJ_E_ARG, "view %d has a non-finite entry", v);
+    // detector basis B = [U | V | q00 - s] must be invertible
+    double q00[3], B[9];
+    for (int a = 0; a < 3; ++a) {
+      q00[a] = w[3 + a] - 0.5 * (G.nu - 1) * w[6 + a] - 0.5 * (G.nv - 1) * w[9 + a];
+      B[3 * a] = w[6 + a];
+      B[3 * a + 1] = w[9 + a];
+      B[3 * a + 2] = q00[a] - w[a];
+    }
+    const double det = B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) +
+                       B[2] * (B[3] * B[7] - B[4] * B[6]);
+    const double scale = std::sqrt(B[0] * B[0] + B[3] * B[3] + B[6] * B[6]) *
+                         std::sqrt(B[1] * B[1] + B[4] * B[4] + B[7] * B[7]) *
+                         std::sqrt(B[2] * B[2] + B[5] * B[5] + B[8] * B[8]);
+    if (!(std::fabs(det) > 1e-12 * scale)) return fail(PROJ_E_ARG, "view %d: singular detector basis", v);
+  }
+  for (int i = 0; i < n_inst; ++i) {
+    if (inst_view[i] < 0 || inst_view[i] >= G.n_views)
+      return fail(PROJ_E_ARG, "instance %d: view %d out of range [0, %d)", i, inst_view[i], G.n_views);
+    if (inst_pose[i] < 0 || inst_pose[i] >= n_pose)
+      return fail(PROJ_E_ARG, "instance %d: pose %d out of range [0, %d)", i, inst_pose[i], n_pose);
+  }
+
+  proj_plan_s* p = new proj_plan_s();
+  Geo& g = p->geo;
+  g.nx = G.nx;
+  g.ny = G.ny;
+  g.nz = G.nz;
+  g.px = G.nx + 2;
+  g.py = G.ny + 2;
+  g.pz = G.nz + 2;
+  g.vx = (float)G.vx;
+  g.vy = (float)G.vy;
+  g.vz = (float)G.vz;
+  g.hx = 0.5f * (G.nx + 1);
+  g.hy = 0.5f * (G.ny + 1);
+  g.hz = 0.5f * (G.nz + 1);
+  g.cx = 0.5f * (G.nx - 1);
+  g.cy = 0.5f * (G.ny - 1);
+  g.cz = 0.5f * (G.nz - 1);
+  g.offx = (float)G.vol_offset[0];
+  g.offy = (float)G.vol_offset[1];
+  g.offz = (float)G.vol_offset[2];
+  g.nu = G.nu;
+  g.nv = G.nv;
+  g.step = (float)G.step;
+  p->n_views = G.n_views;
+  p->n_pose = n_pose;
+  p->n_inst = n_inst;
+  p->ops = ops;
+  p->views.assign(G.views, G.views + 12 * (size_t)G.n_views);
+  p->inst_view.assign(inst_view, inst_view + n_inst);
+  p->inst_pose.assign(inst_pose, inst_pose + n_inst);
+  p->n_tiles = ceil_div(G.nu, kTileU) * ceil_div(G.nv, kTileV);
+
+  // CSR list of instances per pose (ascending instance order).
+  std::vector<int> ptr(n_pose + 1, 0), idx(n_inst);
+  for (int i = 0; i < n_inst; ++i) ptr[inst_pose[i] + 1]++;
+  for (int q = 0; q < n_pose; ++q) ptr[q + 1] += ptr[q];
+  {
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (int i = 0; i < n_inst; ++i) idx[fill[inst_pose[i]]++] = i;
+  }
+
+  cudaError_t e = cudaGetDevice(&p->device);
+  int n_sm = 148;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "device query");
+  }
+  {
+    const long long items = (long long)ceil_div(G.nx, kBpX) * ceil_div(G.ny, kBpY) * ceil_div(G.nz, kZChunk);
+    const long long cap = (long long)n_sm * kBpGradBlocksPerSM;
+    p->bp_blocks = (int)(items < cap ? items : cap);
+  }
+
+  // Workspace layout.
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  p->off_status = take(sizeof(int));
+  p->off_inst = take(sizeof(InstTable) * (size_t)n_inst);
+  p->off_ptab = take(sizeof(PoseTable) * (size_t)n_pose);
+  const size_t npad_sz = (size_t)npad;
+  p->off_vol1 = (ops & PROJ_OP_FORWARD) ? take(sizeof(float) * npad_sz) : 0;
+  p->off_vol4 = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float4) * npad_sz) : 0;
+  p->off_part_f = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float) * kRec * (size_t)n_inst * p->n_tiles) : 0;
+  p->off_det4 = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float4) * (size_t)n_inst * (G.nu + 2) * (G.nv + 2)) : 0;
+  p->off_part_b = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float) * 12 * (size_t)n_inst * p->bp_blocks) : 0;
+  p->off_acc = (ops & PROJ_OP_ADJOINT) ? take(sizeof(float) * npad_sz) : 0;
+  p->ws_bytes = off;
+
+  e = cudaMalloc(&p->d_views, sizeof(double) * p->views.size());
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_inst_view, sizeof(int) * n_inst);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_inst_pose, sizeof(int) * n_inst);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_pose_ptr, sizeof(int) * (n_pose + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_pose_idx, sizeof(int) * n_inst);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_views, p->views.data(), sizeof(double) * p->views.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_inst_view, inst_view, sizeof(int) * n_inst, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_inst_pose, inst_pose, sizeof(int) * n_inst, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_pose_ptr, ptr.data(), sizeof(int) * (n_pose + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_pose_idx, idx.data(), sizeof(int) * n_inst, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    proj_plan_destroy(p);
+    return cuda_fail(e, "plan table allocation");
+  }
+  *out = p;
+  return PROJ_OK;
+}
+
+int proj_plan_destroy(proj_plan p) {
+  if (!p) return PROJ_OK;
+  cudaFree(p->d_views);
+  cudaFree(p->d_inst_view);
+  cudaFree(p->d_inst_pose);
+  cudaFree(p->d_pose_ptr);
+  cudaFree(p->d_pose_idx);
+  delete p;
+  return PROJ_OK;
+}
+
+int proj_workspace_size(proj_plan p, size_t* bytes) {
+  if (!p || !bytes) return fail(PROJ_E_ARG, "plan or bytes is NULL");
+  *bytes = p->ws_bytes;
+  return PROJ_OK;
+}
+
+int proj_set_volume(proj_plan p, const float* d_mu, void* d_ws, size_t ws_bytes, proj_stream stream) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_mu) return fail(PROJ_E_ARG, "d_mu is NULL");
+  if (!(p->ops & (PROJ_OP_FORWARD | PROJ_OP_FORWARD_GRAD)))
+    return fail(PROJ_E_UNSUPPORTED, "proj_set_volume: no ray-driven operation enabled");
+  WsView w;
+  int rc = check_ws(p, d_ws, ws_bytes, &w);
+  if (rc) return rc;
+  if ((rc = check_device(p))) return rc;
+  cudaError_t e = launch_volume_prep(d_mu, p->geo, w.vol1, w.vol4, (cudaStream_t)stream);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "volume preparation launch");
+}
+
+int proj_forward(proj_plan p, const float* d_pose, float* d_proj, void* d_ws, size_t ws_bytes, proj_stream stream) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_pose || !d_proj) return fail(PROJ_E_ARG, "proj_forward: NULL pose or output");
+  int rc = need_op(p, PROJ_OP_FORWARD, "proj_forward");
+  if (rc) return rc;
+  WsView w;
+  if ((rc = check_ws(p, d_ws, ws_bytes, &w))) return rc;
+  if ((rc = check_device(p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = setup(p, d_pose, w, s))) return rc;
+  cudaError_t e = launch_forward(w.inst, p->n_inst, p->geo, w.vol1, d_proj, s);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "forward launch");
+}
+
+int proj_count_samples(proj_plan p, const float* d_pose, long long* d_count, void* d_ws, size_t ws_bytes,
+                       proj_stream stream) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_pose || !d_count) return fail(PROJ_E_ARG, "proj_count_samples: NULL pose or output");
+  WsView w;
+  int rc = check_ws(p, d_ws, ws_bytes, &w);
+  if (rc) return rc;
+  if ((rc = check_device(p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = setup(p, d_pose, w, s))) return rc;
+  cudaError_t e = launch_count(w.inst, p->n_inst, p->geo, d_count, s);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "count launch");
+}
+
+int proj_forward_pose_grad(proj_plan p, const float* d_pose, int loss, const float* d_ref, float* d_grad,
+                           float* d_loss, float* d_proj, void* d_ws, size_t ws_bytes, proj_stream stream) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_pose || !d_ref || !d_grad) return fail(PROJ_E_ARG, "proj_forward_pose_grad: NULL pose, reference or grad");
+  if (loss != PROJ_LOSS_RESIDUAL && loss != PROJ_LOSS_L2 && loss != PROJ_LOSS_NCC)
+    return fail(PROJ_E_ARG, "unknown loss mode %d", loss);
+  int rc = need_op(p, PROJ_OP_FORWARD_GRAD, "proj_forward_pose_grad");
+  if (rc) return rc;
+  WsView w;
+  if ((rc = check_ws(p, d_ws, ws_bytes, &w))) return rc;
+  if ((rc = check_device(p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = setup(p, d_pose, w, s))) return rc;
+  cudaError_t e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, loss, d_ref, d_proj, w.part_f, s);
+  if (e != cudaSuccess) return cuda_fail(e, "forward pose-gradient launch");
+  e = launch_forward_grad_reduce(w.inst, w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_tiles, p->geo, loss,
+                                 w.part_f, d_grad, d_loss, s);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "forward pose-gradient reduction launch");
+}
+
+int proj_back(proj_plan p, const float* d_proj, const float* d_pose, int weight, float* d_vol, void* d_ws,
+              size_t ws_bytes, proj_stream stream) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_proj || !d_pose || !d_vol) return fail(PROJ_E_ARG, "proj_back: NULL input or output");
+  if (weight != PROJ_W_NONE && weight != PROJ_W_FDK && weight != PROJ_W_FDK_CONST)
+    return fail(PROJ_E_ARG, "unknown weight %d", weight);
+  int rc = need_op(p, PROJ_OP_BACK, "proj_back");
+  if (rc) return rc;
+  WsView w;
+  if ((rc = check_ws(p, d_ws, ws_bytes, &w))) return rc;
+  if ((rc = check_device(p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = setup(p, d_pose, w, s))) return rc;
+  cudaError_t e = launch_back(w.inst, p->n_inst, p->geo, weight, d_proj, d_vol, s);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "back-projection launch");
+}
+
+int proj_back_pose_grad(proj_plan p, const float* d_proj, const float* d_pose, int weight, const float* d_vol_resid,
+                        float* d_grad, void* d_ws, size_t ws_bytes, proj_stream stream) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_proj || !d_pose || !d_vol_resid || !d_grad) return fail(PROJ_E_ARG, "proj_back_pose_grad: NULL argument");
+  if (weight != PROJ_W_NONE && weight != PROJ_W_FDK && weight != PROJ_W_FDK_CONST)
+    return fail(PROJ_E_ARG, "unknown weight %d", weight);
+  int rc = need_op(p, PROJ_OP_BACK_GRAD, "proj_back_pose_grad");
+  if (rc) return rc;
+  WsView w;
+  if ((rc = check_ws(p, d_ws, ws_bytes, &w))) return rc;
+  if ((rc = check_device(p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = setup(p, d_pose, w, s))) return rc;
+  cudaError_t e = launch_detector_prep(d_proj, p->n_inst, p->geo, w.det4, s);
+  if (e != cudaSuccess) return cuda_fail(e, "detector-gradient launch");
+  e = launch_back_grad(w.inst, p->n_inst, p->geo, weight, w.det4, d_vol_resid, w.part_b, p->bp_blocks, s);
+  if (e != cudaSuccess) return cuda_fail(e, "back-projection gradient launch");
+  e = launch_back_grad_reduce(w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_inst, p->bp_blocks, p->geo,
+                              w.part_b, d_grad, s);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "back-projection gradient reduction launch");
+}
+
+int proj_forward_adjoint(proj_plan p, const float* d_y, const float* d_pose, float* d_vol, void* d_ws,
+                         size_t ws_bytes, proj_stream stream) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_y || !d_pose || !d_vol) return fail(PROJ_E_ARG, "proj_forward_adjoint: NULL argument");
+  int rc = need_op(p, PROJ_OP_ADJOINT, "proj_forward_adjoint");
+  if (rc) return rc;
+  WsView w;
+  if ((rc = check_ws(p, d_ws, ws_bytes, &w))) return rc;
+  if ((rc = check_device(p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = setup(p, d_pose, w, s))) return rc;
+  cudaError_t e = launch_forward_adjoint(w.inst, p->n_inst, p->geo, d_y, w.acc, d_vol, s);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "forward adjoint launch");
+}
+
+int proj_check(proj_plan p, void* d_ws, size_t ws_bytes, proj_stream stream, int* status) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  WsView w;
+  int rc = check_ws(p, d_ws, ws_bytes, &w);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, w.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.status, 0, sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (status) *status = h;
+  if (h) return fail(PROJ_E_DEVICE, "device status bits 0x%x", h);
+  return PROJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,287 @@
+// Voxel-driven kernels: back-projection (Eq. back, Sec. II-C.2), the
+// detector-gradient stencil (grad_d l by central differences) and the
+// back-projection pose gradient (Eqs. back_derive, final_back, back_int,
+// dis_back) with a deterministic two-stage reduction.
+//
+// Layout: a 256-thread block covers 32 (x) x 8 (y) voxel columns and
+// kZChunk voxels along z; each warp is one row of 32 x-adjacent columns, so
+// their projections are adjacent on the detector.  Each thread projects its
+// voxels with the instance's 3x4 matrix Q (centred voxel index -> (u',v',w')),
+// one FMA chain per voxel.
+#include "proj_internal.cuh"
+
+namespace projk {
+
+namespace {
+
+__device__ __forceinline__ float lerp(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+__device__ __forceinline__ float pix(const float* __restrict__ img, int nu, int nv, int iu, int iv) {
+  return (iu >= 0 && iu < nu && iv >= 0 && iv < nv) ? __ldg(img + (size_t)iv * nu + iu) : 0.f;
+}
+
+// ---------------------------------------------------------------- K4
+// (l, d_u l, d_v l, 0) on the extended grid [-1, nu] x [-1, nv], stored
+// padded as [n_inst][nv+2][nu+2].
+__global__ void k_detector_prep(const float* __restrict__ proj, int n_inst, Geo g, float4* __restrict__ det4) {
+  const int qu = g.nu + 2, qv = g.nv + 2;
+  const long long n = (long long)n_inst * qu * qv;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int iu = (int)(p % qu) - 1;
+    const int iv = (int)((p / qu) % qv) - 1;
+    const int in = (int)(p / ((long long)qu * qv));
+    const float* img = proj + (size_t)in * g.nu * g.nv;
+    const float l = pix(img, g.nu, g.nv, iu, iv);
+    const float du = 0.5f * (pix(img, g.nu, g.nv, iu + 1, iv) - pix(img, g.nu, g.nv, iu - 1, iv));
+    const float dv = 0.5f * (pix(img, g.nu, g.nv, iu, iv + 1) - pix(img, g.nu, g.nv, iu, iv - 1));
+    det4[p] = make_float4(l, du, dv, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------- K5
+
+__global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict__ inst, int n_inst, Geo g,
+                                                     int weight, const float* __restrict__ proj,
+                                                     float* __restrict__ vol) {
+  const int ix = blockIdx.x * kBpX + (threadIdx.x & 31);
+  const int iy = blockIdx.y * kBpY + (threadIdx.x >> 5);
+  const int iz0 = blockIdx.z * kZChunk;
+  if (ix >= g.nx || iy >= g.ny) return;
+  const float fx = (float)ix - g.cx, fy = (float)iy - g.cy;
+  float acc[kZChunk];
+#pragma unroll
+  for (int z = 0; z < kZChunk; ++z) acc[z] = 0.f;
+  const float fu = (float)g.nu, fvv = (float)g.nv;
+  for (int n = 0; n < n_inst; ++n) {
+    const InstTable& T = inst[n];
+    if (!T.valid) continue;
+    const float bu = fmaf(T.Q[3], fy, fmaf(T.Q[0], fx, T.Q[9]));
+    const float bv = fmaf(T.Q[4], fy, fmaf(T.Q[1], fx, T.Q[10]));
+    const float bw = fmaf(T.Q[5], fy, fmaf(T.Q[2], fx, T.Q[11]));
+    const float qz0 = T.Q[6], qz1 = T.Q[7], qz2 = T.Q[8], w0 = T.w0;
+    const float* img = proj + (size_t)n * g.nu * g.nv;
+#pragma unroll
+    for (int z = 0; z < kZChunk; ++z) {
+      const float fz = (float)(iz0 + z) - g.cz;
+      const float hw = fmaf(qz2, fz, bw);
+      if (!(hw > 0.f)) continue;
+      const float rw = 1.0f / hw;
+      const float u = fmaf(qz0, fz, bu) * rw, v = fmaf(qz1, fz, bv) * rw;
+      if (!(u > -1.f && u < fu && v > -1.f && v < fvv)) continue;
+      const float flu = floorf(u), flv = floorf(v);
+      const int i0 = (int)flu, j0 = (int)flv;
+      const float au = u - flu, av = v - flv;
+      const float c0 = lerp(pix(img, g.nu, g.nv, i0, j0), pix(img, g.nu, g.nv, i0 + 1, j0), au);
+      const float c1 = lerp(pix(img, g.nu, g.nv, i0, j0 + 1), pix(img, g.nu, g.nv, i0 + 1, j0 + 1), au);
+      float val = lerp(c0, c1, av);
+      if (weight != PROJ_W_NONE) {
+        const float r = w0 * rw;
+        val *= r * r;
+      }
+      acc[z] += val;
+    }
+  }
+#pragma unroll
+  for (int z = 0; z < kZChunk; ++z)
+    if (iz0 + z < g.nz) vol[((size_t)(iz0 + z) * g.ny + iy) * g.nx + ix] = acc[z];
+}
+
+// ---------------------------------------------------------------- K6
+//
+// Per voxel j and instance n: rho = W rw (D_u P0 + D_v P1 - s P2) with rw =
+// 1/w', s = D_u u + D_v v (+ 2 l~ for the FDK weight derivative), P0..P2 the
+// rows of P's left 3x3: this is W (grad_d l) J_p + l~ grad W, the per-mm
+// derivative of mu_j with respect to the moved voxel position.  With wj =
+// dL/dmu_j the 12 sums wj rho and wj rho f~^T (f~ = centred voxel index)
+// give dL/dM of the instance.  Each warp keeps its own slot per instance in
+// shared memory, so the block sum and the later grid sum run in a fixed
+// order.
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kBpThreads) k_back_grad(const InstTable* __restrict__ inst, int n_inst, Geo g,
+                                                          int weight, const float4* __restrict__ det4,
+                                                          const float* __restrict__ wvol, float* __restrict__ part,
+                                                          int items_x, int items_y, int items_z) {
+  __shared__ float sacc[kBpThreads / 32][kBpInstChunk][12];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n_items = items_x * items_y * items_z;
+  const int qu = g.nu + 2;
+  const size_t det_stride = (size_t)(g.nu + 2) * (g.nv + 2);
+  const float fu = (float)g.nu, fvv = (float)g.nv;
+  for (int n0 = 0; n0 < n_inst; n0 += kBpInstChunk) {
+    const int nc = min(kBpInstChunk, n_inst - n0);
+    for (int e = threadIdx.x; e < (kBpThreads / 32) * kBpInstChunk * 12; e += kBpThreads)
+      (&sacc[0][0][0])[e] = 0.f;
+    __syncthreads();
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+      const int bx = item % items_x, by = (item / items_x) % items_y, bz = item / (items_x * items_y);
+      const int ix = bx * kBpX + lane, iy = by * kBpY + warp, iz0 = bz * kZChunk;
+      const bool col = ix < g.nx && iy < g.ny;
+      float wj[kZChunk];
+#pragma unroll
+      for (int z = 0; z < kZChunk; ++z)
+        wj[z] = (col && iz0 + z < g.nz) ? __ldg(wvol + ((size_t)(iz0 + z) * g.ny + iy) * g.nx + ix) : 0.f;
+      const float fx = (float)ix - g.cx, fy = (float)iy - g.cy;
+      for (int i = 0; i < nc; ++i) {
+        const InstTable& T = inst[n0 + i];
+        float a[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) a[q] = 0.f;
+        if (T.valid) {
+          const float bu = fmaf(T.Q[3], fy, fmaf(T.Q[0], fx, T.Q[9]));
+          const float bv = fmaf(T.Q[4], fy, fmaf(T.Q[1], fx, T.Q[10]));
+          const float bw = fmaf(T.Q[5], fy, fmaf(T.Q[2], fx, T.Q[11]));
+          const float4* img = det4 + (size_t)(n0 + i) * det_stride;
+#pragma unroll
+          for (int z = 0; z < kZChunk; ++z) {
+            if (wj[z] == 0.f) continue;
+            const float fz = (float)(iz0 + z) - g.cz;
+            const float hw = fmaf(T.Q[8], fz, bw);
+            if (!(hw > 0.f)) continue;
+            const float rw = 1.0f / hw;
+            const float u = fmaf(T.Q[6], fz, bu) * rw, v = fmaf(T.Q[7], fz, bv) * rw;
+            if (!(u > -1.f && u < fu && v > -1.f && v < fvv)) continue;
+            // padded coordinates: pixel index + 1, corner clamped to [0, n]
+            const float up = u + 1.f, vp = v + 1.f;
+            const int i0 = min(max(__float2int_rd(up), 0), g.nu);
+            const int j0 = min(max(__float2int_rd(vp), 0), g.nv);
+            const float au = up - (float)i0, av = vp - (float)j0;
+            const float4* p0 = img + (size_t)j0 * qu + i0;
+            const float4 c00 = __ldg(p0), c10 = __ldg(p0 + 1), c01 = __ldg(p0 + qu), c11 = __ldg(p0 + qu + 1);
+            const float L = lerp(lerp(c00.x, c10.x, au), lerp(c01.x, c11.x, au), av);
+            const float Du = lerp(lerp(c00.y, c10.y, au), lerp(c01.y, c11.y, au), av);
+            const float Dv = lerp(lerp(c00.z, c10.z, au), lerp(c01.z, c11.z, au), av);
+            float W = 1.f;
+            float s = fmaf(Du, u, Dv * v);
+            if (weight != PROJ_W_NONE) {
+              const float r = T.w0 * rw;
+              W = r * r;
+              if (weight == PROJ_W_FDK) s = fmaf(2.f, L, s);
+            }
+            const float f = W * rw * wj[z];
+            const float r0 = f * (fmaf(Du, T.P3[0], Dv * T.P3[3]) - s * T.P3[6]);
+            const float r1 = f * (fmaf(Du, T.P3[1], Dv * T.P3[4]) - s * T.P3[7]);
+            const float r2 = f * (fmaf(Du, T.P3[2], Dv * T.P3[5]) - s * T.P3[8]);
+            a[0] += r0;
+            a[1] += r1;
+            a[2] += r2;
+            a[3] = fmaf(r0, fx, a[3]);
+            a[4] = fmaf(r0, fy, a[4]);
+            a[5] = fmaf(r0, fz, a[5]);
+            a[6] = fmaf(r1, fx, a[6]);
+            a[7] = fmaf(r1, fy, a[7]);
+            a[8] = fmaf(r1, fz, a[8]);
+            a[9] = fmaf(r2, fx, a[9]);
+            a[10] = fmaf(r2, fy, a[10]);
+            a[11] = fmaf(r2, fz, a[11]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          const float s = warp_sum(a[q]);
+          if (lane == 0) sacc[warp][i][q] += s;
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * 12; e += kBpThreads) {
+      float s = 0.f;
+      for (int w = 0; w < kBpThreads / 32; ++w) s += sacc[w][e / 12][e % 12];
+      part[((size_t)blockIdx.x * n_inst + n0 + e / 12) * 12 + e % 12] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// Per pose: FP64 sum over blocks (fixed order) of its instances' records,
+// conversion to dL/dM and contraction with dM/dtheta.
+__global__ void k_back_grad_reduce(const PoseTable* __restrict__ ptab, const int* __restrict__ pose_ptr,
+                                   const int* __restrict__ pose_idx, int n_inst, int n_blocks, Geo g,
+                                   const float* __restrict__ part, float* __restrict__ grad) {
+  constexpr int kGroups = 20;
+  __shared__ double sp[kGroups][12];
+  __shared__ double acc[12];
+  const int p = blockIdx.x, t = threadIdx.x;
+  if (t < 12) acc[t] = 0.0;
+  __syncthreads();
+  for (int e = pose_ptr[p]; e < pose_ptr[p + 1]; ++e) {
+    const int n = pose_idx[e];
+    if (t < kGroups * 12) {
+      const int q = t % 12, grp = t / 12;
+      double s = 0.0;
+      for (int b = grp; b < n_blocks; b += kGroups) s += (double)part[((size_t)b * n_inst + n) * 12 + q];
+      sp[grp][q] = s;
+    }
+    __syncthreads();
+    if (t < 12) {
+      double s = 0.0;
+      for (int grp = 0; grp < kGroups; ++grp) s += sp[grp][t];
+      acc[t] += s;
+    }
+    __syncthreads();
+  }
+  if (t != 0) return;
+  const PoseTable& P = ptab[p];
+  float* out = grad + 6 * p;
+  if (!P.valid) {
+    for (int q = 0; q < 6; ++q) out[q] = 0.f;
+    return;
+  }
+  // acc[0..2] = A0_a = sum w rho_a ; acc[3 + 3a + b] = sum w rho_a f~_b.
+  const double off[3] = {g.offx, g.offy, g.offz};
+  const double vox[3] = {g.vx, g.vy, g.vz};
+  double gM[12];
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) gM[4 * a + b] = off[b] * acc[a] + vox[b] * acc[3 + 3 * a + b];
+    gM[4 * a + 3] = acc[a];
+  }
+  for (int a = 0; a < 3; ++a) out[a] = (float)gM[4 * a + 3];
+  for (int j = 0; j < 3; ++j) {
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) s += gM[4 * a + b] * P.dR[9 * j + 3 * a + b];
+    out[3 + j] = (float)s;
+  }
+}
+
+int elementwise_grid(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 148LL * 64 ? (b < 1 ? 1 : b) : 148LL * 64);
+}
+
+}  // namespace
+
+cudaError_t launch_detector_prep(const float* d_proj, int n_inst, Geo geo, float4* d_det4, cudaStream_t s) {
+  const long long n = (long long)n_inst * (geo.nu + 2) * (geo.nv + 2);
+  k_detector_prep<<<elementwise_grid(n), 256, 0, s>>>(d_proj, n_inst, geo, d_det4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_back(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float* d_proj,
+                        float* d_vol, cudaStream_t s) {
+  dim3 grid(ceil_div(geo.nx, kBpX), ceil_div(geo.ny, kBpY), ceil_div(geo.nz, kZChunk));
+  k_back<<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_proj, d_vol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_back_grad(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float4* d_det4,
+                             const float* d_wvol, float* d_part, int n_blocks, cudaStream_t s) {
+  const int ix = ceil_div(geo.nx, kBpX), iy = ceil_div(geo.ny, kBpY), iz = ceil_div(geo.nz, kZChunk);
+  k_back_grad<<<n_blocks, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_det4, d_wvol, d_part, ix, iy, iz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_back_grad_reduce(const PoseTable* d_ptab, int n_pose, const int* d_pose_ptr,
+                                    const int* d_pose_idx, int n_inst, int n_blocks, Geo geo, const float* d_part,
+                                    float* d_grad, cudaStream_t s) {
+  k_back_grad_reduce<<<n_pose, 256, 0, s>>>(d_ptab, d_pose_ptr, d_pose_idx, n_inst, n_blocks, geo, d_part, d_grad);
+  return cudaGetLastError();
+}
+
+}  // namespace projk

@@ -1,0 +1,495 @@
+// Ray-driven kernels: volume preparation (grad mu by central differences,
+// Sec. II-C.1), forward projection (Eq. forward), the fused forward pose
+// gradient (Eqs. for_grad, final_forward, for_int, dis_forward) with its
+// deterministic reduction, the exact transpose of the forward projector and
+// a sample counter.
+//
+// March layout: one thread per detector ray; a 256-thread block owns a
+// 16 x 16 pixel tile of one instance and each warp an 8 x 4 sub-tile, so
+// the 32 rays of a warp stay within a few voxels of each other at equal
+// sample index k and their 8-corner gathers share cache lines.  Samples are
+// anchored at world arc length k * step from the source (k integer), so a
+// projection is a continuous function of the pose.
+#include "proj_internal.cuh"
+
+namespace projk {
+
+namespace {
+
+__device__ __forceinline__ float lerp(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+__device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t) {
+  return make_float4(lerp(a.x, b.x, t), lerp(a.y, b.y, t), lerp(a.z, b.z, t), lerp(a.w, b.w, t));
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Pixel of this thread inside the block's tile; false when outside the
+// detector (ragged tiles).
+__device__ __forceinline__ bool tile_pixel(int tile, int tiles_u, const Geo& g, int& iu, int& iv) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tu = tile % tiles_u, tv = tile / tiles_u;
+  iu = tu * kTileU + (w & 1) * 8 + (lane & 7);
+  iv = tv * kTileV + (w >> 1) * 4 + (lane >> 3);
+  return iu < g.nu && iv < g.nv;
+}
+
+struct Ray {
+  float ax, ay, az;  // padded index coordinates of the source (sample k = 0)
+  float dx, dy, dz;  // index units per step
+  int k0, k1;        // inclusive sample range inside the open box
+};
+
+// Ray through the centre of pixel (iu, iv) of instance T, clipped to the
+// open index box (-1, n)^3 (centred: |f~| < (n+1)/2).  Returns false when
+// the ray misses the box.
+__device__ __forceinline__ bool ray_setup(const InstTable& T, const Geo& g, int iu, int iv, Ray& r) {
+  const float fu = (float)iu, fv = (float)iv;
+  const float dx = fmaf(fv, T.Vo[0], fmaf(fu, T.Uo[0], T.C0[0]));
+  const float dy = fmaf(fv, T.Vo[1], fmaf(fu, T.Uo[1], T.C0[1]));
+  const float dz = fmaf(fv, T.Vo[2], fmaf(fu, T.Uo[2], T.C0[2]));
+  const float sc = g.step * rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+  r.dx = dx * sc / g.vx;
+  r.dy = dy * sc / g.vy;
+  r.dz = dz * sc / g.vz;
+  float lo = 0.f, hi = 3.0e8f;
+  const float A[3] = {T.A[0], T.A[1], T.A[2]};
+  const float D[3] = {r.dx, r.dy, r.dz};
+  const float H[3] = {g.hx, g.hy, g.hz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (fabsf(D[a]) > 1e-20f) {
+      const float inv = 1.0f / D[a];
+      const float t1 = (-H[a] - A[a]) * inv, t2 = (H[a] - A[a]) * inv;
+      lo = fmaxf(lo, fminf(t1, t2));
+      hi = fminf(hi, fmaxf(t1, t2));
+    } else if (!(fabsf(A[a]) < H[a])) {
+      return false;
+    }
+  }
+  if (!(hi >= lo)) return false;
+  r.k0 = (int)ceilf(lo);
+  r.k1 = (int)floorf(hi);
+  r.ax = A[0] + g.cx + 1.0f;
+  r.ay = A[1] + g.cy + 1.0f;
+  r.az = A[2] + g.cz + 1.0f;
+  return r.k1 >= r.k0;
+}
+
+// Cell of padded index point (fx, fy, fz): lower corner clamped to
+// [0, n] so the 8 corners stay inside the (n+2)^3 padded array; fractions
+// are taken from the clamped corner so that a point marginally outside the
+// box (rounding) interpolates towards the zero border.
+struct Cell {
+  int idx;
+  float ax, ay, az;
+};
+
+__device__ __forceinline__ Cell locate(float fx, float fy, float fz, const Geo& g) {
+  const int ix = min(max(__float2int_rd(fx), 0), g.nx);
+  const int iy = min(max(__float2int_rd(fy), 0), g.ny);
+  const int iz = min(max(__float2int_rd(fz), 0), g.nz);
+  Cell c;
+  c.ax = fx - (float)ix;
+  c.ay = fy - (float)iy;
+  c.az = fz - (float)iz;
+  c.idx = (iz * g.py + iy) * g.px + ix;
+  return c;
+}
+
+// ---------------------------------------------------------------- K1
+
+__global__ void k_volume_prep(const float* __restrict__ mu, Geo g, float* __restrict__ vol1,
+                              float4* __restrict__ vol4) {
+  const long long n = (long long)g.px * g.py * g.pz;
+  const float sx = 0.5f / g.vx, sy = 0.5f / g.vy, sz = 0.5f / g.vz;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(p % g.px) - 1;
+    const int j = (int)((p / g.px) % g.py) - 1;
+    const int k = (int)(p / ((long long)g.px * g.py)) - 1;
+    auto at = [&](int a, int b, int c) -> float {
+      return (a >= 0 && a < g.nx && b >= 0 && b < g.ny && c >= 0 && c < g.nz)
+                 ? __ldg(mu + ((size_t)c * g.ny + b) * g.nx + a)
+                 : 0.0f;
+    };
+    const float m = at(i, j, k);
+    if (vol1) vol1[p] = m;
+    if (vol4) {
+      const float gx = (at(i + 1, j, k) - at(i - 1, j, k)) * sx;
+      const float gy = (at(i, j + 1, k) - at(i, j - 1, k)) * sy;
+      const float gz = (at(i, j, k + 1) - at(i, j, k - 1)) * sz;
+      vol4[p] = make_float4(m, gx, gy, gz);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- K2
+
+__global__ void __launch_bounds__(kMarchThreads) k_forward(const InstTable* __restrict__ inst, int n_tiles,
+                                                           int tiles_u, Geo g, const float* __restrict__ vol,
+                                                           float* __restrict__ proj) {
+  const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
+  int iu, iv;
+  if (!tile_pixel(tile, tiles_u, g, iu, iv)) return;
+  const InstTable& T = inst[n];
+  float acc = 0.f;
+  Ray r;
+  if (T.valid && ray_setup(T, g, iu, iv, r)) {
+    const int pxy = g.px * g.py;
+    for (int k = r.k0; k <= r.k1; ++k) {
+      const float kf = (float)k;
+      const Cell c = locate(fmaf(kf, r.dx, r.ax), fmaf(kf, r.dy, r.ay), fmaf(kf, r.dz, r.az), g);
+      const float* p0 = vol + c.idx;
+      const float v000 = __ldg(p0), v100 = __ldg(p0 + 1);
+      const float v010 = __ldg(p0 + g.px), v110 = __ldg(p0 + g.px + 1);
+      const float v001 = __ldg(p0 + pxy), v101 = __ldg(p0 + pxy + 1);
+      const float v011 = __ldg(p0 + pxy + g.px), v111 = __ldg(p0 + pxy + g.px + 1);
+      const float c0 = lerp(lerp(v000, v100, c.ax), lerp(v010, v110, c.ax), c.ay);
+      const float c1 = lerp(lerp(v001, v101, c.ax), lerp(v011, v111, c.ax), c.ay);
+      acc += lerp(c0, c1, c.az);
+    }
+  }
+  proj[((size_t)n * g.nv + iv) * g.nu + iu] = g.step * acc;
+}
+
+// ---------------------------------------------------------------- count
+
+__global__ void k_count(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g,
+                        unsigned long long* __restrict__ count) {
+  const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
+  int iu, iv;
+  unsigned long long c = 0;
+  Ray r;
+  if (tile_pixel(tile, tiles_u, g, iu, iv) && inst[n].valid && ray_setup(inst[n], g, iu, iv, r))
+    c = (unsigned long long)(r.k1 - r.k0 + 1);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count + n, c);
+}
+
+// ---------------------------------------------------------------- K3
+//
+// Per ray: a = sum_k mu~, S0 = sum_k g, S1[b][c] = sum_k g_b f~_c with
+// g = interpolated central-difference gradient (per mm) and f~ the centred
+// index coordinate of the sample.  Since r - t = R r' and r' = off + f~ vox,
+// step * (S0, S1) determine the ray's dl/dM exactly (contraction in the
+// reduction kernel).  At the end of the ray the loss residual weights the
+// 12 sums; a warp/block reduction writes one record per tile.
+
+template <int LOSS>
+__global__ void __launch_bounds__(kMarchThreads)
+    k_forward_grad(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g,
+                   const float4* __restrict__ vol, const float* __restrict__ ref, float* __restrict__ proj,
+                   float* __restrict__ part) {
+  __shared__ float red[kMarchThreads / 32][kRec];
+  const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
+  int iu, iv;
+  const bool on_det = tile_pixel(tile, tiles_u, g, iu, iv);
+  const InstTable& T = inst[n];
+  float a = 0.f;
+  float s0[3] = {0.f, 0.f, 0.f};
+  float s1[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  Ray r;
+  if (on_det && T.valid && ray_setup(T, g, iu, iv, r)) {
+    const int pxy = g.px * g.py;
+    const float ox = g.cx + 1.0f, oy = g.cy + 1.0f, oz = g.cz + 1.0f;
+    for (int k = r.k0; k <= r.k1; ++k) {
+      const float kf = (float)k;
+      const float fx = fmaf(kf, r.dx, r.ax), fy = fmaf(kf, r.dy, r.ay), fz = fmaf(kf, r.dz, r.az);
+      const Cell c = locate(fx, fy, fz, g);
+      const float4* p0 = vol + c.idx;
+      const float4 v000 = __ldg(p0), v100 = __ldg(p0 + 1);
+      const float4 v010 = __ldg(p0 + g.px), v110 = __ldg(p0 + g.px + 1);
+      const float4 v001 = __ldg(p0 + pxy), v101 = __ldg(p0 + pxy + 1);
+      const float4 v011 = __ldg(p0 + pxy + g.px), v111 = __ldg(p0 + pxy + g.px + 1);
+      const float4 c0 = lerp4(lerp4(v000, v100, c.ax), lerp4(v010, v110, c.ax), c.ay);
+      const float4 c1 = lerp4(lerp4(v001, v101, c.ax), lerp4(v011, v111, c.ax), c.ay);
+      const float4 v = lerp4(c0, c1, c.az);
+      const float cx = fx - ox, cy = fy - oy, cz = fz - oz;
+      a += v.x;
+      s0[0] += v.y;
+      s0[1] += v.z;
+      s0[2] += v.w;
+      s1[0] = fmaf(v.y, cx, s1[0]);
+      s1[1] = fmaf(v.y, cy, s1[1]);
+      s1[2] = fmaf(v.y, cz, s1[2]);
+      s1[3] = fmaf(v.z, cx, s1[3]);
+      s1[4] = fmaf(v.z, cy, s1[4]);
+      s1[5] = fmaf(v.z, cz, s1[5]);
+      s1[6] = fmaf(v.w, cx, s1[6]);
+      s1[7] = fmaf(v.w, cy, s1[7]);
+      s1[8] = fmaf(v.w, cz, s1[8]);
+    }
+  }
+  const float l = g.step * a;
+  const size_t pix = (size_t)iv * g.nu + iu;
+  if (on_det && proj) proj[(size_t)n * g.nu * g.nv + pix] = l;
+
+  float G[12];
+  G[0] = g.step * s0[0];
+  G[1] = g.step * s0[1];
+  G[2] = g.step * s0[2];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) G[3 + q] = g.step * s1[q];
+
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (LOSS == PROJ_LOSS_NCC) {
+    const float b = on_det ? __ldg(ref + (size_t)T.view * g.nu * g.nv + pix) : 0.f;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const float s = warp_sum(G[q]);
+      const float sa = warp_sum(l * G[q]);
+      const float sb = warp_sum(b * G[q]);
+      if (lane == 0) {
+        red[w][kRecG + q] = s;
+        red[w][kRecAG + q] = sa;
+        red[w][kRecBG + q] = sb;
+      }
+    }
+    const float m0 = warp_sum(on_det ? l : 0.f), m1 = warp_sum(on_det ? l * l : 0.f);
+    const float m2 = warp_sum(on_det ? l * b : 0.f), m3 = warp_sum(b), m4 = warp_sum(b * b);
+    if (lane == 0) {
+      red[w][kRecMom + 0] = m0;
+      red[w][kRecMom + 1] = m1;
+      red[w][kRecMom + 2] = m2;
+      red[w][kRecMom + 3] = m3;
+      red[w][kRecMom + 4] = m4;
+    }
+  } else {
+    float wt = 0.f, lossv = 0.f;
+    if (on_det) {
+      if (LOSS == PROJ_LOSS_RESIDUAL) {
+        wt = __ldg(ref + (size_t)n * g.nu * g.nv + pix);
+      } else {
+        const float d = l - __ldg(ref + (size_t)T.view * g.nu * g.nv + pix);
+        wt = 2.0f * d;
+        lossv = d * d;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const float s = warp_sum(wt * G[q]);
+      if (lane == 0) red[w][kRecG + q] = s;
+    }
+    const float ls = warp_sum(lossv);
+    if (lane == 0) red[w][kRecLoss] = ls;
+  }
+  __syncthreads();
+  const int nrec = (LOSS == PROJ_LOSS_NCC) ? (kRecMom + 5) : (kRecLoss + 1);
+  if (threadIdx.x < kRec) {
+    float s = 0.f;
+    if ((int)threadIdx.x < nrec)
+      for (int ww = 0; ww < kMarchThreads / 32; ++ww) s += red[ww][threadIdx.x];
+    part[((size_t)n * n_tiles + tile) * kRec + threadIdx.x] = s;
+  }
+}
+
+// Per pose: sum the tile records of each of its instances in FP64 (fixed
+// order), apply the loss, convert the accumulator sums to dL/dM and
+// contract with dM/dtheta.
+__global__ void k_forward_grad_reduce(const InstTable* __restrict__ inst, const PoseTable* __restrict__ ptab,
+                                      const int* __restrict__ pose_ptr, const int* __restrict__ pose_idx,
+                                      int n_tiles, Geo g, int loss, const float* __restrict__ part,
+                                      float* __restrict__ grad, float* __restrict__ loss_out) {
+  constexpr int kGroups = 5;
+  __shared__ double sp[kGroups][kRec];
+  __shared__ double rec[kRec];
+  const int p = blockIdx.x;
+  const int t = threadIdx.x;
+  double acc[12];
+  double L = 0.0;
+  for (int q = 0; q < 12; ++q) acc[q] = 0.0;
+  const int e0 = pose_ptr[p], e1 = pose_ptr[p + 1];
+  const double np = (double)(e1 - e0);
+  for (int e = e0; e < e1; ++e) {
+    const int n = pose_idx[e];
+    if (t < kGroups * kRec) {
+      const int q = t % kRec, grp = t / kRec;
+      double s = 0.0;
+      for (int tile = grp; tile < n_tiles; tile += kGroups) s += (double)part[((size_t)n * n_tiles + tile) * kRec + q];
+      sp[grp][q] = s;
+    }
+    __syncthreads();
+    if (t < kRec) {
+      double s = 0.0;
+      for (int grp = 0; grp < kGroups; ++grp) s += sp[grp][t];
+      rec[t] = s;
+    }
+    __syncthreads();
+    if (t == 0 && inst[n].valid) {
+      if (loss == PROJ_LOSS_NCC) {
+        const double N = (double)g.nu * g.nv;
+        const double ma = rec[kRecMom] / N, mb = rec[kRecMom + 3] / N;
+        const double A = rec[kRecMom + 2] - N * ma * mb;
+        const double Va = rec[kRecMom + 1] - N * ma * ma;
+        const double Vb = rec[kRecMom + 4] - N * mb * mb;
+        if (Va > 0.0 && Vb > 0.0) {
+          const double r = 1.0 / sqrt(Va * Vb);
+          const double c2 = A * r / Va;
+          for (int q = 0; q < 12; ++q) {
+            const double gq = r * (rec[kRecBG + q] - mb * rec[kRecG + q]) -
+                              c2 * (rec[kRecAG + q] - ma * rec[kRecG + q]);
+            acc[q] -= gq / np;
+          }
+          L -= A * r / np;
+        }
+      } else {
+        for (int q = 0; q < 12; ++q) acc[q] += rec[kRecG + q];
+        if (loss == PROJ_LOSS_L2) L += rec[kRecLoss];
+      }
+    }
+    __syncthreads();
+  }
+  if (t != 0) return;
+  const PoseTable& P = ptab[p];
+  float* out = grad + 6 * p;
+  if (!P.valid) {
+    for (int q = 0; q < 6; ++q) out[q] = 0.f;
+    if (loss_out) loss_out[p] = 0.f;
+    return;
+  }
+  // acc[0..2] = S0_b, acc[3 + 3b + c] = sum g_b f~_c.  T[b][c] = sum g_b r'_c.
+  const double off[3] = {g.offx, g.offy, g.offz};
+  const double vox[3] = {g.vx, g.vy, g.vz};
+  double Tm[9];
+  for (int b = 0; b < 3; ++b)
+    for (int c = 0; c < 3; ++c) Tm[3 * b + c] = off[c] * acc[b] + vox[c] * acc[3 + 3 * b + c];
+  double gM[12];
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) {
+      double s = 0.0;
+      for (int c = 0; c < 3; ++c) s += P.R[3 * a + c] * Tm[3 * b + c];
+      gM[4 * a + b] = s;
+    }
+    gM[4 * a + 3] = -(P.R[3 * a] * acc[0] + P.R[3 * a + 1] * acc[1] + P.R[3 * a + 2] * acc[2]);
+  }
+  for (int a = 0; a < 3; ++a) out[a] = (float)gM[4 * a + 3];
+  for (int j = 0; j < 3; ++j) {
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) s += gM[4 * a + b] * P.dR[9 * j + 3 * a + b];
+    out[3 + j] = (float)s;
+  }
+  if (loss_out) loss_out[p] = (float)L;
+}
+
+// ---------------------------------------------------------------- K7
+
+__global__ void __launch_bounds__(kMarchThreads) k_forward_adjoint(const InstTable* __restrict__ inst, int n_tiles,
+                                                                   int tiles_u, Geo g, const float* __restrict__ y,
+                                                                   float* __restrict__ acc) {
+  const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
+  int iu, iv;
+  if (!tile_pixel(tile, tiles_u, g, iu, iv)) return;
+  const InstTable& T = inst[n];
+  const float yi = g.step * __ldg(y + ((size_t)n * g.nv + iv) * g.nu + iu);
+  Ray r;
+  if (yi == 0.f || !T.valid || !ray_setup(T, g, iu, iv, r)) return;
+  const int pxy = g.px * g.py;
+  for (int k = r.k0; k <= r.k1; ++k) {
+    const float kf = (float)k;
+    const Cell c = locate(fmaf(kf, r.dx, r.ax), fmaf(kf, r.dy, r.ay), fmaf(kf, r.dz, r.az), g);
+    float* p0 = acc + c.idx;
+    const float bx = 1.f - c.ax, by = 1.f - c.ay, bz = 1.f - c.az;
+    atomicAdd(p0, yi * bx * by * bz);
+    atomicAdd(p0 + 1, yi * c.ax * by * bz);
+    atomicAdd(p0 + g.px, yi * bx * c.ay * bz);
+    atomicAdd(p0 + g.px + 1, yi * c.ax * c.ay * bz);
+    atomicAdd(p0 + pxy, yi * bx * by * c.az);
+    atomicAdd(p0 + pxy + 1, yi * c.ax * by * c.az);
+    atomicAdd(p0 + pxy + g.px, yi * bx * c.ay * c.az);
+    atomicAdd(p0 + pxy + g.px + 1, yi * c.ax * c.ay * c.az);
+  }
+}
+
+// Interior of the padded accumulation volume -> [nz][ny][nx].
+__global__ void k_unpad(const float* __restrict__ acc, Geo g, float* __restrict__ vol) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(p % g.nx), j = (int)((p / g.nx) % g.ny), k = (int)(p / ((long long)g.nx * g.ny));
+    vol[p] = acc[((size_t)(k + 1) * g.py + (j + 1)) * g.px + (i + 1)];
+  }
+}
+
+int tiles_u_of(const Geo& g) { return ceil_div(g.nu, kTileU); }
+int tiles_of(const Geo& g) { return ceil_div(g.nu, kTileU) * ceil_div(g.nv, kTileV); }
+
+int elementwise_grid(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 148LL * 64 ? (b < 1 ? 1 : b) : 148LL * 64);
+}
+
+}  // namespace
+
+cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float* d_vol1, float4* d_vol4, cudaStream_t s) {
+  const long long n = (long long)geo.px * geo.py * geo.pz;
+  k_volume_prep<<<elementwise_grid(n), 256, 0, s>>>(d_mu, geo, d_vol1, d_vol4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const float* d_vol1, float* d_proj,
+                           cudaStream_t s) {
+  const int nt = tiles_of(geo);
+  k_forward<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo, d_vol1, d_proj);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long* d_count, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(long long) * n_inst, s);
+  if (e != cudaSuccess) return e;
+  const int nt = tiles_of(geo);
+  k_count<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo,
+                                                reinterpret_cast<unsigned long long*>(d_count));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4, int loss,
+                                const float* d_ref, float* d_proj, float* d_part, cudaStream_t s) {
+  const int nt = tiles_of(geo), tu = tiles_u_of(geo);
+  const int grid = n_inst * nt;
+  switch (loss) {
+    case PROJ_LOSS_RESIDUAL:
+      k_forward_grad<PROJ_LOSS_RESIDUAL><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_ref, d_proj,
+                                                                        d_part);
+      break;
+    case PROJ_LOSS_L2:
+      k_forward_grad<PROJ_LOSS_L2><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_ref, d_proj, d_part);
+      break;
+    default:
+      k_forward_grad<PROJ_LOSS_NCC><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_ref, d_proj,
+                                                                   d_part);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward_grad_reduce(const InstTable* d_inst, const PoseTable* d_ptab, int n_pose,
+                                       const int* d_pose_ptr, const int* d_pose_idx, int n_tiles, Geo geo,
+                                       int loss, const float* d_part, float* d_grad, float* d_loss,
+                                       cudaStream_t s) {
+  k_forward_grad_reduce<<<n_pose, 256, 0, s>>>(d_inst, d_ptab, d_pose_ptr, d_pose_idx, n_tiles, geo, loss, d_part,
+                                               d_grad, d_loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward_adjoint(const InstTable* d_inst, int n_inst, Geo geo, const float* d_y, float* d_acc,
+                                   float* d_vol, cudaStream_t s) {
+  const long long npad = (long long)geo.px * geo.py * geo.pz;
+  cudaError_t e = cudaMemsetAsync(d_acc, 0, sizeof(float) * npad, s);
+  if (e != cudaSuccess) return e;
+  const int nt = tiles_of(geo);
+  k_forward_adjoint<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo, d_y, d_acc);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long n = (long long)geo.nx * geo.ny * geo.nz;
+  k_unpad<<<elementwise_grid(n), 256, 0, s>>>(d_acc, geo, d_vol);
+  return cudaGetLastError();
+}
+
+}  // namespace projk

@@ -1,0 +1,107 @@
+// Internal declarations of the sm_103a projector library (not part of the
+// C ABI).  Device tables are rebuilt from the poses by the set-up kernel at
+// the start of every call, in FP64, and stored in FP32 for the march and
+// back-projection kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/proj.h"
+
+namespace projk {
+
+// Per-instance table (one (view, pose) pair), written by k_setup.
+//   Ray-driven kernels: object-frame centred index coordinates of sample k
+//   of pixel (iu, iv) are  f~_k = A + k * D,  D = (step / |d|) * d / vox,
+//   d = C0 + iu * Uo + iv * Vo  (object-frame mm, R^T applied).
+//   Voxel-driven kernels: (u', v', w') = Q[0:3] f~x + Q[3:6] f~y + Q[6:9] f~z
+//   + Q[9:12] for a voxel at centred index f~ (Q = P [R | t] T_obj, stored
+//   column by column), P3 = left 3x3 of P (row major) for the projection
+//   Jacobian, w0 = w' of the world origin (FDK weight).
+struct InstTable {
+  float A[3];
+  float C0[3];
+  float Uo[3];
+  float Vo[3];
+  float Q[12];
+  float P3[9];
+  float w0;
+  int view;
+  int pose;
+  int valid;
+  int pad[3];
+};
+static_assert(sizeof(InstTable) == 40 * 4, "InstTable layout");
+
+// Per-pose table in FP64: R (row major), t, dR/dg_j (j = x, y, z).
+struct PoseTable {
+  double R[9];
+  double t[3];
+  double dR[27];
+  int valid;
+  int pad;
+};
+static_assert(sizeof(PoseTable) % 8 == 0, "PoseTable layout");
+
+// Static geometry shared by all kernels of a plan (passed by value).
+struct Geo {
+  int nx, ny, nz;       // voxels
+  int px, py, pz;       // padded sizes (n + 2)
+  float vx, vy, vz;     // voxel pitch, mm
+  float hx, hy, hz;     // half extent of the open box in centred index units: (n+1)/2
+  float cx, cy, cz;     // (n-1)/2
+  float offx, offy, offz;
+  int nu, nv;
+  float step;
+};
+
+// Record of one K3 block (ray tile) partial: see kRec* offsets.
+constexpr int kRec = 48;
+constexpr int kRecG = 0;      // 12: sum of w * G   (RESIDUAL, L2)  or sum G (NCC)
+constexpr int kRecLoss = 12;  // L2 loss partial
+constexpr int kRecAG = 12;    // NCC: 12 sums l * G
+constexpr int kRecBG = 24;    // NCC: 12 sums b * G
+constexpr int kRecMom = 36;   // NCC: sum l, l^2, l b, b, b^2
+
+// Ray tile of the march kernels: 16 x 16 pixels, 8 warps of 8 x 4.
+constexpr int kTileU = 16;
+constexpr int kTileV = 16;
+constexpr int kMarchThreads = 256;
+
+// Voxel-driven kernels: 32 x 8 columns per block, kZChunk voxels along z.
+constexpr int kBpX = 32;
+constexpr int kBpY = 8;
+constexpr int kZChunk = 8;
+constexpr int kBpThreads = kBpX * kBpY;
+constexpr int kBpInstChunk = 32;   // instances per pass of the BP gradient
+constexpr int kBpGradBlocksPerSM = 4;
+
+// Launchers (defined in the .cu files; return cudaError_t of the launch).
+cudaError_t launch_setup(const float* d_pose, int n_pose, const double* d_views, const int* d_inst_view,
+                         const int* d_inst_pose, int n_inst, Geo geo, InstTable* d_inst, PoseTable* d_ptab,
+                         int* d_status, cudaStream_t s);
+cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float* d_vol1, float4* d_vol4, cudaStream_t s);
+cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const float* d_vol1, float* d_proj,
+                           cudaStream_t s);
+cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long* d_count, cudaStream_t s);
+cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4, int loss,
+                                const float* d_ref, float* d_proj, float* d_part, cudaStream_t s);
+cudaError_t launch_forward_grad_reduce(const InstTable* d_inst, const PoseTable* d_ptab, int n_pose,
+                                       const int* d_pose_ptr, const int* d_pose_idx, int n_tiles, Geo geo,
+                                       int loss, const float* d_part, float* d_grad, float* d_loss,
+                                       cudaStream_t s);
+cudaError_t launch_forward_adjoint(const InstTable* d_inst, int n_inst, Geo geo, const float* d_y,
+                                   float* d_acc, float* d_vol, cudaStream_t s);
+cudaError_t launch_detector_prep(const float* d_proj, int n_inst, Geo geo, float4* d_det4, cudaStream_t s);
+cudaError_t launch_back(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float* d_proj,
+                        float* d_vol, cudaStream_t s);
+cudaError_t launch_back_grad(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float4* d_det4,
+                             const float* d_wvol, float* d_part, int n_blocks, cudaStream_t s);
+cudaError_t launch_back_grad_reduce(const PoseTable* d_ptab, int n_pose, const int* d_pose_ptr,
+                                    const int* d_pose_idx, int n_inst, int n_blocks, Geo geo, const float* d_part,
+                                    float* d_grad, cudaStream_t s);
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace projk
