@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark of the batched 2D/3D registration step.
+
+Workload (synthetic, seeded): a 256^3 FP32 phantom at 0.8 mm (ten ellipsoids
+plus two high-contrast cylinders), two views 90 deg apart on 384 x 384
+detectors at 0.8 mm, SAD 800 / SDD 1200 mm, ray step 0.4 mm, 64 candidate
+poses (rot +-15 deg, trans +-20 mm).  One step = prepare the volume
+(grad mu stencil) + the fused NCC pose-gradient march of all 64 x 2 view
+instances + the deterministic reduction: 64 pose-gradient evaluations.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "pose-gradient evals/s & ray-samples/s, batched vs plain, at ≤1e-3 grad err"
+UNIT = "pose-gradient evals/s"
+FLOP_PER_SAMPLE = 118     # algorithmic FP32 work of one fused-march sample
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-cand", type=int, default=64)
+    ap.add_argument("--cpu-sample", type=int, default=2, help="candidates timed on the CPU oracle")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n_cand):
+    w = synth.workload_registration(n_cand=n_cand)
+    w["mu"] = np.ascontiguousarray(w["mu"], dtype=np.float32)
+    w["poses"] = np.ascontiguousarray(w["poses"], dtype=np.float32)
+    w["pose_true"] = np.ascontiguousarray(w["pose_true"], dtype=np.float32)
+    return w
+
+
+def instance_maps(n_cand, n_views):
+    iv = np.tile(np.arange(n_views, dtype=np.int32), n_cand)
+    ip = np.repeat(np.arange(n_cand, dtype=np.int32), n_views)
+    return iv, ip
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for r in csv.reader(f):
+                r = [x.strip() for x in r]
+                if len(r) >= 9 and r[0] == str(self.gpu):
+                    rows.append(r)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        smax = max(float(r[2]) for r in rows)
+        hot = [s for s in sm if s > 0.3 * smax] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(hot), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+
+def cpu_oracle_eval(w, cands, target=None):
+    """Oracle NCC loss and gradient for the given candidates; returns
+    (grads, seconds, threads).  Target rendered by the oracle when absent."""
+    import oracle
+    g = w["geom"]
+    iv = np.arange(g.n_views)
+    ip = np.zeros(g.n_views, dtype=np.int32)
+    mu = w["mu"].astype(np.float64)
+    if target is None:
+        target = oracle.forward(g, mu, w["pose_true"].astype(np.float64), iv, ip)
+    grads = []
+    t0 = time.perf_counter()
+    for c in cands:
+        pose = w["poses"][c].astype(np.float64)
+        proj = oracle.forward(g, mu, pose, iv, ip)
+        _, wts = oracle.pose_loss_weights("ncc", proj, target, iv, ip, 1)
+        gth, _ = oracle.forward_grad(g, mu, pose, wts, iv, ip)
+        grads.append(gth[0])
+    dt = time.perf_counter() - t0
+    return np.array(grads), dt, oracle.max_threads(), target
+
+
+def reference_arm(args):
+    """FP64 oracle on the host cores, each step a bounded sample (one
+    candidate) of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.n_cand)
+    _, _, threads, target = cpu_oracle_eval(w, [], None)
+    times = []
+    for s in range(args.warmup + args.steps):
+        _, dt, _, _ = cpu_oracle_eval(w, [s % args.n_cand], target)
+        if s >= args.warmup:
+            times.append(dt)
+    per = sum(times) / len(times)
+    v = 1.0 / per
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "1 of %d candidates per step (2 views 384^2, 256^3)" % args.n_cand},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args):
+    return {"workload": "batched 2D/3D registration: 256^3 @0.8 mm, 2 views 384^2 @0.8 mm, %d candidate poses, "
+                        "NCC loss + pose gradient fused" % args.n_cand,
+            "volume": [256, 256, 256], "detector": [384, 384], "views": 2, "candidates": args.n_cand,
+            "step_mm": 0.4, "loss": "ncc",
+            "timing": "per-step CUDA events on the launching stream; L2 flushed (256 MiB write) between steps",
+            "parallelism": "independent candidates per rank (no collective)" if args.gpus > 1 else "single GPU"}
+
+
+# ------------------------------------------------------------------ main arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import paper_2508_13304_b300 as pb
+    from paper_2508_13304_b300 import build
+    build.build()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    w = workload(args.n_cand)
+    g = w["geom"]
+    iv, ip = instance_maps(args.n_cand, g.n_views)
+    P = pb.Projector(g, n_pose=args.n_cand, inst_view=iv, inst_pose=ip,
+                     ops=pb.PROJ_OP_FORWARD | pb.PROJ_OP_FORWARD_GRAD)
+    mu_d = torch.from_numpy(w["mu"]).to(dev)
+    pose_d = torch.from_numpy(w["poses"]).to(dev)
+    # target projections at the true pose, rendered once by the forward projector (input data only)
+    Pt = pb.Projector(g, n_pose=1, inst_view=np.arange(g.n_views), inst_pose=np.zeros(g.n_views, np.int32),
+                      ops=pb.PROJ_OP_FORWARD)
+    Pt.set_volume(mu_d)
+    target_d = Pt.forward(torch.from_numpy(w["pose_true"]).to(dev)).contiguous()
+    grad_d = torch.empty((args.n_cand, 6), device=dev)
+    loss_d = torch.empty((args.n_cand,), device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    samples = int(P.count_samples(pose_d).sum().item())
+    pb.proj_enable_kernel_timing(P.plan)
+
+    def step():
+        pb.proj_set_volume(P.plan, mu_d, P.ws)
+        pb.proj_forward_pose_grad(P.plan, pose_d, pb.PROJ_LOSS_NCC, target_d, grad_d, loss_d, None, P.ws)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms, kern_ms = [], []
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            kern_ms.append(pb.proj_kernel_time_ms(P.plan))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.n_cand * args.steps / (total_ms * 1e-3)
+    k_ms = sum(kern_ms) / len(kern_ms)
+    clk = clocks.summary()
+    grad_h = grad_d.cpu().numpy().astype(np.float64)
+
+    # -------------------------------------------------------------- plain path
+    plain = None
+    if not args.no_plain:
+        P1 = pb.Projector(g, n_pose=1, inst_view=np.arange(g.n_views), inst_pose=np.zeros(g.n_views, np.int32),
+                          ops=pb.PROJ_OP_FORWARD_GRAD)
+        g1 = torch.empty((1, 6), device=dev)
+        l1 = torch.empty((1,), device=dev)
+        singles = [pose_d[c:c + 1].contiguous() for c in range(args.n_cand)]
+
+        def plain_step():
+            pb.proj_set_volume(P1.plan, mu_d, P1.ws)
+            for c in range(args.n_cand):
+                pb.proj_forward_pose_grad(P1.plan, singles[c], pb.PROJ_LOSS_NCC, target_d, g1, l1, None, P1.ws)
+
+        plain_step()
+        torch.cuda.synchronize()
+        pms = []
+        for _ in range(max(2, args.steps // 3)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plain_step()
+            e1.record(stream)
+            e1.synchronize()
+            pms.append(e0.elapsed_time(e1))
+        pm = sum(pms) / len(pms)
+        plain = {"value": args.n_cand / (pm * 1e-3), "unit": UNIT, "ms_per_step": pm,
+                 "what": "64 sequential single-candidate calls (2 instances each), same kernels"}
+
+    # -------------------------------------------------------------- end to end
+    mu_h = torch.from_numpy(w["mu"]).pin_memory()
+    pose_h = torch.from_numpy(w["poses"]).pin_memory()
+    target_h = target_d.cpu().pin_memory()
+    grad_o = torch.empty((args.n_cand, 6)).pin_memory()
+    loss_o = torch.empty((args.n_cand,)).pin_memory()
+    mu_e = torch.empty_like(mu_d)
+    pose_e = torch.empty_like(pose_d)
+    target_e = torch.empty_like(target_d)
+
+    def e2e_step():
+        mu_e.copy_(mu_h, non_blocking=True)
+        target_e.copy_(target_h, non_blocking=True)
+        pose_e.copy_(pose_h, non_blocking=True)
+        pb.proj_set_volume(P.plan, mu_e, P.ws)
+        pb.proj_forward_pose_grad(P.plan, pose_e, pb.PROJ_LOSS_NCC, target_e, grad_d, loss_d, None, P.ws)
+        grad_o.copy_(grad_d, non_blocking=True)
+        loss_o.copy_(loss_d, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    ems = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        ems.append(e0.elapsed_time(e1))
+    em = sum(ems) / len(ems)
+    h2d = mu_h.numel() * 4 + target_h.numel() * 4 + pose_h.numel() * 4
+    d2h = grad_o.numel() * 4 + loss_o.numel() * 4
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    alu_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12       # FP32 FMA lanes x 2 FLOP x max clock
+    achieved = samples * FLOP_PER_SAMPLE / (k_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(args),
+        "ray_samples_per_s": world * samples * args.steps / (total_ms * 1e-3),
+        "rays_per_s": world * args.n_cand * g.n_views * g.nu * g.nv * args.steps / (total_ms * 1e-3),
+        "samples_per_step": samples,
+        "kernel_ms": k_ms,
+        "plain": plain,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "kernel": "k_forward_grad<NCC> (fused pose-gradient march)",
+                     "peak_from": "FP32 FMA: %d SMs x 128 lanes x 2 FLOP x %.0f MHz" % (n_sm, sm_max),
+                     "flop_per_sample": FLOP_PER_SAMPLE},
+        "e2e": {"value": args.n_cand / (em * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": em},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+        "wall_s_timed_region": wall,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        cands = list(range(min(args.cpu_sample, args.n_cand)))
+        og, dt, threads, _ = cpu_oracle_eval(w, cands)
+        err = 0.0
+        for i, c in enumerate(cands):
+            for blk in (slice(0, 3), slice(3, 6)):
+                err = max(err, float(np.linalg.norm(grad_h[c, blk] - og[i, blk]) / np.linalg.norm(og[i, blk])))
+        line["cpu_baseline"] = {"value": len(cands) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": "%d of %d candidates (2 views 384^2, 256^3), NCC forward + gradient"
+                                          % (len(cands), args.n_cand)}
+        line["grad_rel_err_vs_oracle"] = err
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -220,6 +220,16 @@ int proj_check(proj_plan plan, void *d_ws, size_t ws_bytes, proj_stream stream, 
 int proj_count_samples(proj_plan plan, const float *d_pose, long long *d_count, void *d_ws, size_t ws_bytes,
                        proj_stream stream);
 
+/* Kernel timing for benchmarks.  While enabled, every call records two
+ * CUDA events on its stream, immediately before and after its main kernel
+ * (the march of proj_forward / proj_forward_pose_grad /
+ * proj_forward_adjoint, the voxel kernel of proj_back /
+ * proj_back_pose_grad); proj_kernel_time_ms waits for the second event and
+ * returns the elapsed time of the last call's main kernel.  The events are
+ * created by the first enable (not on the compute path). */
+int proj_enable_kernel_timing(proj_plan plan, int enable);
+int proj_kernel_time_ms(proj_plan plan, float *ms);
+
 /* Message of the last error in this thread ("" if none). */
 const char *proj_last_error(void);
 

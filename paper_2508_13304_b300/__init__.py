@@ -1,0 +1,345 @@
+"""Python binding of the sm_103a cone-beam projector library (libproj.so).
+
+The functions below carry the names of the C ABI in include/proj.h and only
+marshal arguments: torch CUDA tensors become device pointers, the current
+torch stream becomes the cudaStream_t, and a non-zero status becomes a
+``ProjError``.  Every step of the computation runs in the library's CUDA
+kernels; there is no CPU fallback.  ``Projector`` bundles a plan with a
+torch-allocated workspace for convenience.
+
+Importing this package does not load the library; the first call does, and
+raises ``RuntimeError`` if libproj.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libproj.so")
+
+# Constants of include/proj.h.
+PROJ_OK, PROJ_E_ARG, PROJ_E_CUDA, PROJ_E_WORKSPACE, PROJ_E_UNSUPPORTED, PROJ_E_DEVICE = 0, -1, -2, -3, -4, -5
+PROJ_LOSS_RESIDUAL, PROJ_LOSS_L2, PROJ_LOSS_NCC = 0, 1, 2
+PROJ_W_NONE, PROJ_W_FDK, PROJ_W_FDK_CONST = 0, 1, 2
+PROJ_OP_FORWARD, PROJ_OP_FORWARD_GRAD, PROJ_OP_BACK, PROJ_OP_BACK_GRAD, PROJ_OP_ADJOINT = 1, 2, 4, 8, 16
+PROJ_OP_ALL = 31
+PROJ_STATUS_BAD_POSE = 1
+
+
+class ProjError(RuntimeError):
+    """A library call returned a non-zero status."""
+
+    def __init__(self, code, msg):
+        super().__init__("proj error %d: %s" % (code, msg))
+        self.code = code
+
+
+class proj_geometry(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("vx", ctypes.c_double), ("vy", ctypes.c_double), ("vz", ctypes.c_double),
+                ("vol_offset", ctypes.c_double * 3),
+                ("nu", ctypes.c_int), ("nv", ctypes.c_int), ("n_views", ctypes.c_int),
+                ("views", ctypes.POINTER(ctypes.c_double)),
+                ("step", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_SZ = ctypes.c_size_t
+_I = ctypes.c_int
+_SIGS = {
+    "proj_plan_create": [ctypes.POINTER(proj_geometry), _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _I,
+                         ctypes.POINTER(_P)],
+    "proj_plan_destroy": [_P],
+    "proj_workspace_size": [_P, ctypes.POINTER(_SZ)],
+    "proj_set_volume": [_P, _P, _P, _SZ, _P],
+    "proj_forward": [_P, _P, _P, _P, _SZ, _P],
+    "proj_forward_pose_grad": [_P, _P, _I, _P, _P, _P, _P, _P, _SZ, _P],
+    "proj_back": [_P, _P, _P, _I, _P, _P, _SZ, _P],
+    "proj_back_pose_grad": [_P, _P, _P, _I, _P, _P, _P, _SZ, _P],
+    "proj_forward_adjoint": [_P, _P, _P, _P, _P, _SZ, _P],
+    "proj_check": [_P, _P, _SZ, _P, ctypes.POINTER(_I)],
+    "proj_count_samples": [_P, _P, _P, _P, _SZ, _P],
+    "proj_enable_kernel_timing": [_P, _I],
+    "proj_kernel_time_ms": [_P, ctypes.POINTER(ctypes.c_float)],
+    "proj_last_error": [],
+    "proj_version": [],
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libproj.so (loaded on first use)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libproj.so is not built; run python -m paper_2508_13304_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name in ("proj_last_error", "proj_version") else ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def proj_last_error() -> str:
+    return lib().proj_last_error().decode()
+
+
+def proj_version() -> str:
+    return lib().proj_version().decode()
+
+
+def _check(rc):
+    if rc != PROJ_OK:
+        raise ProjError(rc, proj_last_error())
+    return rc
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor", allow_none=False):
+    """Device pointer of a contiguous CUDA tensor (argument checks only)."""
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError("%s is required" % name)
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Plan:
+    """Handle of a proj_plan plus the host-side sizes the binding checks."""
+
+    def __init__(self, handle, geom, n_pose, inst_view, inst_pose, ops):
+        self.handle = handle
+        self.geom = geom
+        self.n_pose = n_pose
+        self.inst_view = np.asarray(inst_view, dtype=np.int32)
+        self.inst_pose = np.asarray(inst_pose, dtype=np.int32)
+        self.n_inst = len(self.inst_view)
+        self.ops = ops
+
+    @property
+    def vol_numel(self):
+        return self.geom.nx * self.geom.ny * self.geom.nz
+
+    @property
+    def img_numel(self):
+        return self.geom.nu * self.geom.nv
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.proj_plan_destroy(self.handle)
+            self.handle = None
+
+
+def make_geometry(geom):
+    """proj_geometry from any object with the fields nx..step (views as a
+    [n_views][12] array); returns (struct, views array kept alive)."""
+    views = np.ascontiguousarray(geom.views, dtype=np.float64).reshape(-1, 12)
+    off = tuple(getattr(geom, "off", (0.0, 0.0, 0.0)))
+    g = proj_geometry(int(geom.nx), int(geom.ny), int(geom.nz), float(geom.vx), float(geom.vy), float(geom.vz),
+                      (ctypes.c_double * 3)(*off), int(geom.nu), int(geom.nv), views.shape[0],
+                      views.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(geom.step))
+    return g, views
+
+
+def proj_plan_create(geom, n_pose, inst_view, inst_pose, ops=PROJ_OP_ALL) -> Plan:
+    g, views = make_geometry(geom)
+    iv = np.ascontiguousarray(inst_view, dtype=np.int32)
+    ip = np.ascontiguousarray(inst_pose, dtype=np.int32)
+    if iv.shape != ip.shape:
+        raise ValueError("inst_view and inst_pose differ in length")
+    h = ctypes.c_void_p()
+    _check(lib().proj_plan_create(ctypes.byref(g), int(n_pose), int(iv.size),
+                                  iv.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                  ip.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(ops), ctypes.byref(h)))
+    del views
+    return Plan(h, geom, int(n_pose), iv, ip, ops)
+
+
+def proj_plan_destroy(plan: Plan):
+    if plan.handle:
+        _check(lib().proj_plan_destroy(plan.handle))
+        plan.handle = None
+
+
+def proj_workspace_size(plan: Plan) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().proj_workspace_size(plan.handle, ctypes.byref(n)))
+    return int(n.value)
+
+
+def _ws(ws):
+    return _ptr(ws, name="workspace"), ws.numel() * ws.element_size()
+
+
+def proj_set_volume(plan: Plan, mu, ws, stream=None):
+    import torch
+    p, nb = _ws(ws)
+    _check(lib().proj_set_volume(plan.handle, _ptr(mu, torch.float32, plan.vol_numel, "mu"), p, nb,
+                                 _stream(stream)))
+
+
+def proj_forward(plan: Plan, pose, proj, ws, stream=None):
+    import torch
+    p, nb = _ws(ws)
+    _check(lib().proj_forward(plan.handle, _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"),
+                              _ptr(proj, torch.float32, plan.n_inst * plan.img_numel, "proj"), p, nb,
+                              _stream(stream)))
+
+
+def proj_forward_pose_grad(plan: Plan, pose, loss, ref, grad, loss_out=None, proj_out=None, ws=None,
+                           stream=None):
+    import torch
+    p, nb = _ws(ws)
+    n_ref = (plan.n_inst if loss == PROJ_LOSS_RESIDUAL else plan.geom.n_views) * plan.img_numel
+    _check(lib().proj_forward_pose_grad(
+        plan.handle, _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"), int(loss),
+        _ptr(ref, torch.float32, n_ref, "ref"), _ptr(grad, torch.float32, 6 * plan.n_pose, "grad"),
+        _ptr(loss_out, torch.float32, plan.n_pose, "loss", allow_none=True),
+        _ptr(proj_out, torch.float32, plan.n_inst * plan.img_numel, "proj", allow_none=True), p, nb,
+        _stream(stream)))
+
+
+def proj_back(plan: Plan, proj, pose, weight, vol, ws, stream=None):
+    import torch
+    p, nb = _ws(ws)
+    _check(lib().proj_back(plan.handle, _ptr(proj, torch.float32, plan.n_inst * plan.img_numel, "proj"),
+                           _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"), int(weight),
+                           _ptr(vol, torch.float32, plan.vol_numel, "vol"), p, nb, _stream(stream)))
+
+
+def proj_back_pose_grad(plan: Plan, proj, pose, weight, vol_resid, grad, ws, stream=None):
+    import torch
+    p, nb = _ws(ws)
+    _check(lib().proj_back_pose_grad(plan.handle, _ptr(proj, torch.float32, plan.n_inst * plan.img_numel, "proj"),
+                                     _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"), int(weight),
+                                     _ptr(vol_resid, torch.float32, plan.vol_numel, "vol_resid"),
+                                     _ptr(grad, torch.float32, 6 * plan.n_pose, "grad"), p, nb, _stream(stream)))
+
+
+def proj_forward_adjoint(plan: Plan, y, pose, vol, ws, stream=None):
+    import torch
+    p, nb = _ws(ws)
+    _check(lib().proj_forward_adjoint(plan.handle, _ptr(y, torch.float32, plan.n_inst * plan.img_numel, "y"),
+                                      _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"),
+                                      _ptr(vol, torch.float32, plan.vol_numel, "vol"), p, nb, _stream(stream)))
+
+
+def proj_count_samples(plan: Plan, pose, count, ws, stream=None):
+    import torch
+    p, nb = _ws(ws)
+    _check(lib().proj_count_samples(plan.handle, _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"),
+                                    _ptr(count, torch.int64, plan.n_inst, "count"), p, nb, _stream(stream)))
+
+
+def proj_check(plan: Plan, ws, stream=None) -> int:
+    """Synchronise, read and clear the device status bits (0 = clean)."""
+    p, nb = _ws(ws)
+    st = ctypes.c_int(0)
+    rc = lib().proj_check(plan.handle, p, nb, _stream(stream), ctypes.byref(st))
+    if rc not in (PROJ_OK, PROJ_E_DEVICE):
+        _check(rc)
+    return int(st.value)
+
+
+def proj_enable_kernel_timing(plan: Plan, enable=True):
+    _check(lib().proj_enable_kernel_timing(plan.handle, 1 if enable else 0))
+
+
+def proj_kernel_time_ms(plan: Plan) -> float:
+    ms = ctypes.c_float()
+    _check(lib().proj_kernel_time_ms(plan.handle, ctypes.byref(ms)))
+    return float(ms.value)
+
+
+class Projector:
+    """A plan plus its workspace (a zero-filled torch uint8 tensor on the
+    current CUDA device); methods allocate their outputs with torch."""
+
+    def __init__(self, geom, n_pose=1, inst_view=None, inst_pose=None, ops=PROJ_OP_ALL, device=None):
+        import torch
+        if inst_view is None:
+            inst_view = np.arange(geom.views.shape[0])
+        if inst_pose is None:
+            inst_pose = np.zeros(len(inst_view), dtype=np.int32) if n_pose == 1 else np.arange(len(inst_view))
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self.plan = proj_plan_create(geom, n_pose, inst_view, inst_pose, ops)
+            self.ws = torch.zeros(proj_workspace_size(self.plan), dtype=torch.uint8, device=self.device)
+        self.geom = geom
+
+    @property
+    def n_inst(self):
+        return self.plan.n_inst
+
+    def _t(self, x, dtype=None):
+        import torch
+        return torch.as_tensor(x, dtype=dtype or torch.float32, device=self.device).contiguous()
+
+    def set_volume(self, mu):
+        proj_set_volume(self.plan, self._t(mu), self.ws)
+
+    def forward(self, pose, out=None):
+        import torch
+        g = self.geom
+        out = out if out is not None else torch.empty((self.n_inst, g.nv, g.nu), device=self.device)
+        proj_forward(self.plan, self._t(pose), out, self.ws)
+        return out
+
+    def forward_pose_grad(self, pose, loss, ref, want_proj=False):
+        import torch
+        g = self.geom
+        grad = torch.empty((self.plan.n_pose, 6), device=self.device)
+        lossv = torch.empty((self.plan.n_pose,), device=self.device)
+        proj = torch.empty((self.n_inst, g.nv, g.nu), device=self.device) if want_proj else None
+        proj_forward_pose_grad(self.plan, self._t(pose), loss, self._t(ref), grad, lossv, proj, self.ws)
+        return (grad, lossv, proj) if want_proj else (grad, lossv)
+
+    def back(self, proj, pose, weight=PROJ_W_NONE):
+        import torch
+        g = self.geom
+        vol = torch.empty((g.nz, g.ny, g.nx), device=self.device)
+        proj_back(self.plan, self._t(proj), self._t(pose), weight, vol, self.ws)
+        return vol
+
+    def back_pose_grad(self, proj, pose, vol_resid, weight=PROJ_W_NONE):
+        import torch
+        grad = torch.empty((self.plan.n_pose, 6), device=self.device)
+        proj_back_pose_grad(self.plan, self._t(proj), self._t(pose), weight, self._t(vol_resid), grad, self.ws)
+        return grad
+
+    def forward_adjoint(self, y, pose):
+        import torch
+        g = self.geom
+        vol = torch.empty((g.nz, g.ny, g.nx), device=self.device)
+        proj_forward_adjoint(self.plan, self._t(y), self._t(pose), vol, self.ws)
+        return vol
+
+    def count_samples(self, pose):
+        import torch
+        c = torch.empty((self.n_inst,), dtype=torch.int64, device=self.device)
+        proj_count_samples(self.plan, self._t(pose), c, self.ws)
+        return c
+
+    def check(self):
+        return proj_check(self.plan, self.ws)

@@ -51,6 +51,9 @@ struct proj_plan_s {
   int* d_inst_pose = nullptr;
   int* d_pose_ptr = nullptr;
   int* d_pose_idx = nullptr;
+  // optional timing of the main kernel of each call
+  bool timing = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // workspace layout (byte offsets; 0 = buffer absent, the status word sits at 0)
   size_t off_status = 0, off_inst = 0, off_ptab = 0, off_vol1 = 0, off_vol4 = 0, off_part_f = 0, off_det4 = 0,
          off_part_b = 0, off_acc = 0, ws_bytes = 0;
@@ -99,6 +102,10 @@ int setup(const proj_plan_s* p, const float* d_pose, const WsView& w, cudaStream
   cudaError_t e = launch_setup(d_pose, p->n_pose, p->d_views, p->d_inst_view, p->d_inst_pose, p->n_inst, p->geo,
                                w.inst, w.ptab, w.status, s);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "pose set-up launch");
+}
+
+void mark(const proj_plan_s* p, bool before, cudaStream_t s) {
+  if (p->timing) cudaEventRecord(before ? p->ev0 : p->ev1, s);
 }
 
 int check_device(const proj_plan_s* p) {
@@ -258,6 +265,8 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
 
 int proj_plan_destroy(proj_plan p) {
   if (!p) return PROJ_OK;
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
   cudaFree(p->d_views);
   cudaFree(p->d_inst_view);
   cudaFree(p->d_inst_pose);
@@ -296,7 +305,9 @@ int proj_forward(proj_plan p, const float* d_pose, float* d_proj, void* d_ws, si
   if ((rc = check_device(p))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = setup(p, d_pose, w, s))) return rc;
+  mark(p, true, s);
   cudaError_t e = launch_forward(w.inst, p->n_inst, p->geo, w.vol1, d_proj, s);
+  mark(p, false, s);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "forward launch");
 }
 
@@ -327,7 +338,9 @@ int proj_forward_pose_grad(proj_plan p, const float* d_pose, int loss, const flo
   if ((rc = check_device(p))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = setup(p, d_pose, w, s))) return rc;
+  mark(p, true, s);
   cudaError_t e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, loss, d_ref, d_proj, w.part_f, s);
+  mark(p, false, s);
   if (e != cudaSuccess) return cuda_fail(e, "forward pose-gradient launch");
   e = launch_forward_grad_reduce(w.inst, w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_tiles, p->geo, loss,
                                  w.part_f, d_grad, d_loss, s);
@@ -347,7 +360,9 @@ int proj_back(proj_plan p, const float* d_proj, const float* d_pose, int weight,
   if ((rc = check_device(p))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = setup(p, d_pose, w, s))) return rc;
+  mark(p, true, s);
   cudaError_t e = launch_back(w.inst, p->n_inst, p->geo, weight, d_proj, d_vol, s);
+  mark(p, false, s);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "back-projection launch");
 }
 
@@ -366,7 +381,9 @@ int proj_back_pose_grad(proj_plan p, const float* d_proj, const float* d_pose, i
   if ((rc = setup(p, d_pose, w, s))) return rc;
   cudaError_t e = launch_detector_prep(d_proj, p->n_inst, p->geo, w.det4, s);
   if (e != cudaSuccess) return cuda_fail(e, "detector-gradient launch");
+  mark(p, true, s);
   e = launch_back_grad(w.inst, p->n_inst, p->geo, weight, w.det4, d_vol_resid, w.part_b, p->bp_blocks, s);
+  mark(p, false, s);
   if (e != cudaSuccess) return cuda_fail(e, "back-projection gradient launch");
   e = launch_back_grad_reduce(w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_inst, p->bp_blocks, p->geo,
                               w.part_b, d_grad, s);
@@ -384,8 +401,29 @@ int proj_forward_adjoint(proj_plan p, const float* d_y, const float* d_pose, flo
   if ((rc = check_device(p))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = setup(p, d_pose, w, s))) return rc;
+  mark(p, true, s);
   cudaError_t e = launch_forward_adjoint(w.inst, p->n_inst, p->geo, d_y, w.acc, d_vol, s);
+  mark(p, false, s);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "forward adjoint launch");
+}
+
+int proj_enable_kernel_timing(proj_plan p, int enable) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (enable && !p->ev0) {
+    cudaError_t e = cudaEventCreate(&p->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);
+    if (e != cudaSuccess) return cuda_fail(e, "timing event creation");
+  }
+  p->timing = enable != 0;
+  return PROJ_OK;
+}
+
+int proj_kernel_time_ms(proj_plan p, float* ms) {
+  if (!p || !ms) return fail(PROJ_E_ARG, "plan or ms is NULL");
+  if (!p->ev0) return fail(PROJ_E_UNSUPPORTED, "kernel timing was never enabled");
+  cudaError_t e = cudaEventSynchronize(p->ev1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, p->ev0, p->ev1);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "kernel timing");
 }
 
 int proj_check(proj_plan p, void* d_ws, size_t ws_bytes, proj_stream stream, int* status) {
