@@ -230,6 +230,32 @@ int proj_count_samples(proj_plan plan, const float *d_pose, long long *d_count, 
 int proj_enable_kernel_timing(proj_plan plan, int enable);
 int proj_kernel_time_ms(proj_plan plan, float *ms);
 
+/* Forward pose gradient that allocates nothing (the paper has no
+ * counterpart; this is a library facility).
+ *
+ * For callers that cannot allocate device memory - a plug-in whose host
+ * application owns every allocation, a real-time loop whose memory is frozen
+ * after start-up, code whose allocator is not CUDA's - and so can create
+ * neither a plan nor a workspace.  The caller passes only inputs and outputs;
+ * the geometry and instance maps are host data as in proj_plan_create.  All
+ * scratch (tables, the prepared (mu, grad mu) volume, reduction records) is
+ * one static device array of 5.5 MiB inside the library, which every GPU that
+ * loads the library keeps until the process exits.
+ *   Limits: (nx+2)(ny+2)(nz+2) <= 66^3 (a 64^3 volume), n_inst, n_pose and
+ *   n_views <= 64 each, n_inst x ceil(nu/16) x ceil(nv/16) <= 4096;
+ *   larger sizes return PROJ_E_ARG with a message saying which limit.
+ *   d_mu   [nz][ny][nx] FP32; d_pose, loss, d_ref, d_grad, d_loss as in
+ *          proj_forward_pose_grad (d_loss may be NULL).
+ * The result equals proj_forward_pose_grad's for the same inputs.  The first
+ * call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.
+ * Every call on a device shares the one array and overwrites it, so calls
+ * that overlap on the GPU (other streams or threads) race: serialise them.
+ * Non-finite poses give zero gradients (no status word is kept). */
+int proj_forward_pose_grad_static(const proj_geometry *geom, int n_pose, int n_inst, const int *inst_view,
+                                  const int *inst_pose, const float *d_mu, const float *d_pose, int loss,
+                                  const float *d_ref, float *d_grad, float *d_loss, proj_stream stream);
+
 /* Message of the last error in this thread ("" if none). */
 const char *proj_last_error(void);
 

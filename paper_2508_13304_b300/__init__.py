@@ -62,6 +62,8 @@ _SIGS = {
     "proj_forward_adjoint": [_P, _P, _P, _P, _P, _SZ, _P],
     "proj_check": [_P, _P, _SZ, _P, ctypes.POINTER(_I)],
     "proj_count_samples": [_P, _P, _P, _P, _SZ, _P],
+    "proj_forward_pose_grad_static": [ctypes.POINTER(proj_geometry), _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                      _P, _P, _I, _P, _P, _P, _P],
     "proj_enable_kernel_timing": [_P, _I],
     "proj_kernel_time_ms": [_P, ctypes.POINTER(ctypes.c_float)],
     "proj_last_error": [],
@@ -260,6 +262,28 @@ def proj_check(plan: Plan, ws, stream=None) -> int:
     if rc not in (PROJ_OK, PROJ_E_DEVICE):
         _check(rc)
     return int(st.value)
+
+
+def proj_forward_pose_grad_static(geom, n_pose, inst_view, inst_pose, mu, pose, loss, ref, grad, loss_out=None,
+                                  stream=None):
+    """Allocation-free forward pose gradient (no plan, no workspace): for
+    callers that cannot allocate device memory.  Sizes are limited by the
+    library's static scratch (a 64^3 volume, 64 instances / poses / views)."""
+    import torch
+    g, views = make_geometry(geom)
+    iv = np.ascontiguousarray(inst_view, dtype=np.int32)
+    ip = np.ascontiguousarray(inst_pose, dtype=np.int32)
+    if iv.shape != ip.shape:
+        raise ValueError("inst_view and inst_pose differ in length")
+    n_img = int(geom.nu) * int(geom.nv)
+    n_ref = (iv.size if loss == PROJ_LOSS_RESIDUAL else views.shape[0]) * n_img
+    _check(lib().proj_forward_pose_grad_static(
+        ctypes.byref(g), int(n_pose), int(iv.size), iv.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+        ip.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+        _ptr(mu, torch.float32, int(geom.nx) * int(geom.ny) * int(geom.nz), "mu"),
+        _ptr(pose, torch.float32, 6 * int(n_pose), "pose"), int(loss), _ptr(ref, torch.float32, n_ref, "ref"),
+        _ptr(grad, torch.float32, 6 * int(n_pose), "grad"),
+        _ptr(loss_out, torch.float32, int(n_pose), "loss", allow_none=True), _stream(stream)))
 
 
 def proj_enable_kernel_timing(plan: Plan, enable=True):

@@ -37,6 +37,8 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 }  // namespace
 
+void projk::record_error(const char* msg) { g_last_error = msg; }
+
 struct proj_plan_s {
   Geo geo;
   int n_views, n_pose, n_inst, ops;

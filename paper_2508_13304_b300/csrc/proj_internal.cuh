@@ -102,6 +102,9 @@ cudaError_t launch_back_grad_reduce(const PoseTable* d_ptab, int n_pose, const i
                                     const int* d_pose_idx, int n_inst, int n_blocks, Geo geo, const float* d_part,
                                     float* d_grad, cudaStream_t s);
 
+// Sets the calling thread's message returned by proj_last_error().
+void record_error(const char* msg);
+
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace projk
