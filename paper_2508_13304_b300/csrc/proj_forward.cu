@@ -5,7 +5,7 @@
 // a sample counter.
 //
 // March layout: one thread per detector ray; a 256-thread block owns a
-// 16 x 16 pixel tile of one instance and each warp an 8 x 4 sub-tile, so
+// 16 x 16 pixel tile of one instance and each warp a 4 x 8 sub-tile, so
 // the 32 rays of a warp stay within a few voxels of each other at equal
 // sample index k and their 8-corner gathers share cache lines.  Samples are
 // anchored at world arc length k * step from the source (k integer), so a
@@ -29,12 +29,14 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // Pixel of this thread inside the block's tile; false when outside the
-// detector (ragged tiles).
+// detector (ragged tiles).  Each warp takes a 4 x 8 pixel sub-tile, so each
+// quarter-warp (the 8 lanes served together by the L1 data pipe for 16-byte
+// loads) is a compact 4 x 2 patch of rays whose gathers share cache lines.
 __device__ __forceinline__ bool tile_pixel(int tile, int tiles_u, const Geo& g, int& iu, int& iv) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int tu = tile % tiles_u, tv = tile / tiles_u;
-  iu = tu * kTileU + (w & 1) * 8 + (lane & 7);
-  iv = tv * kTileV + (w >> 1) * 4 + (lane >> 3);
+  iu = tu * kTileU + (w & 3) * 4 + (lane & 3);
+  iv = tv * kTileV + (w >> 2) * 8 + (lane >> 2);
   return iu < g.nu && iv < g.nv;
 }
 

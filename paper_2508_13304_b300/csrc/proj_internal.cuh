@@ -64,7 +64,7 @@ constexpr int kRecAG = 12;    // NCC: 12 sums l * G
 constexpr int kRecBG = 24;    // NCC: 12 sums b * G
 constexpr int kRecMom = 36;   // NCC: sum l, l^2, l b, b, b^2
 
-// Ray tile of the march kernels: 16 x 16 pixels, 8 warps of 8 x 4.
+// Ray tile of the march kernels: 16 x 16 pixels, 8 warps of 4 x 8.
 constexpr int kTileU = 16;
 constexpr int kTileV = 16;
 constexpr int kMarchThreads = 256;
