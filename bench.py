@@ -33,7 +33,14 @@ import synth  # noqa: E402
 METRIC = "pose-gradient evals/s & ray-samples/s, batched vs plain, at ≤1e-3 grad err"
 UNIT = "pose-gradient evals/s"
 FLOP_PER_SAMPLE = 118     # algorithmic FP32 work of one fused-march sample
+L1_BYTES_PER_SAMPLE = 128  # 8 trilinear corners x float4 (mu, grad mu) delivered to registers
+L1_BYTES_PER_CLK_SM = 128  # L1 data-pipe width per SM per clock
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one fused-march launch on this workload: the
+# ncu capture of the 8-instance case (profiles/k_forward_grad_ncc_...md,
+# 1.934 GB) scaled by 128/8 instances, since every instance re-streams the
+# volume.  Set to None whenever the kernel changes until it is re-measured.
+TRAFFIC_PER_LAUNCH = 30.9e9
 
 
 def parse():
@@ -46,6 +53,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=2, help="candidates timed on the CPU oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the other kernels' measurements")
     return ap.parse_args()
 
 
@@ -174,6 +182,65 @@ def config_dict(args):
             "parallelism": "independent candidates per rank (no collective)" if args.gpus > 1 else "single GPU"}
 
 
+# ------------------------------------------------------------------ other kernels
+
+def _timed(fn, plan, pb, flush, reps=3):
+    """Median main-kernel time (ms) of fn() over reps, L2 flushed before each."""
+    fn()
+    ks = []
+    for _ in range(reps):
+        flush.zero_()
+        fn()
+        ks.append(pb.proj_kernel_time_ms(plan))
+    return float(np.median(ks))
+
+
+def secondary(pb, torch, dev, w, mu_d, flush):
+    """Main-kernel times of the other calls on full-size configurations."""
+    out = {}
+    g = w["geom"]
+    # forward projection (DRR batch) and its exact transpose: the 128 registration instances
+    nc = len(w["poses"])
+    iv, ip = instance_maps(nc, g.n_views)
+    P = pb.Projector(g, n_pose=nc, inst_view=iv, inst_pose=ip, ops=pb.PROJ_OP_FORWARD | pb.PROJ_OP_ADJOINT)
+    pb.proj_enable_kernel_timing(P.plan)
+    P.set_volume(mu_d)
+    pose = torch.from_numpy(w["poses"]).to(dev)
+    proj = torch.empty((P.n_inst, g.nv, g.nu), device=dev)
+    samples = int(P.count_samples(pose).sum().item())
+    ms = _timed(lambda: pb.proj_forward(P.plan, pose, proj, P.ws), P.plan, pb, flush)
+    out["forward"] = {"kernel": "k_forward", "config": "256^3, %d view instances of 384^2" % P.n_inst, "kernel_ms": ms,
+                      "rays_per_s": P.n_inst * g.nu * g.nv / (ms * 1e-3), "ray_samples_per_s": samples / (ms * 1e-3)}
+    vol = torch.empty_like(mu_d)
+    ms = _timed(lambda: pb.proj_forward_adjoint(P.plan, proj, pose, vol, P.ws), P.plan, pb, flush)
+    out["forward_adjoint"] = {"kernel": "k_forward_adjoint", "config": "256^3, %d view instances of 384^2" % P.n_inst,
+                              "kernel_ms": ms, "ray_samples_per_s": samples / (ms * 1e-3)}
+    del P
+    # FDK-weighted back-projection and its pose gradient: 360 views, 512^2, 256^3
+    gm = synth.Geometry(256, 256, 256, 0.8, 0.8, 0.8, 512, 512,
+                        synth.circular_views(360, synth.SAD, synth.SDD, 0.6, 0.6), 0.4)
+    rng = np.random.default_rng(1003)
+    motion = torch.from_numpy(synth.smooth_motion(rng, 360, 2.0, 3.0).astype(np.float32)).to(dev)
+    Pb = pb.Projector(gm, n_pose=360, inst_view=np.arange(360), inst_pose=np.arange(360),
+                      ops=pb.PROJ_OP_BACK | pb.PROJ_OP_BACK_GRAD)
+    pb.proj_enable_kernel_timing(Pb.plan)
+    img = torch.rand((360, 512, 512), device=dev)
+    volb = torch.empty((256, 256, 256), device=dev)
+    wvol = torch.randn((256, 256, 256), device=dev)
+    gradb = torch.empty((360, 6), device=dev)
+    vv = 360 * 256 ** 3
+    ms = _timed(lambda: pb.proj_back(Pb.plan, img, motion, pb.PROJ_W_FDK, volb, Pb.ws), Pb.plan, pb, flush)
+    out["back"] = {"kernel": "k_back", "config": "256^3, 360 views of 512^2, FDK weight", "kernel_ms": ms,
+                   "voxel_view_updates_per_s": vv / (ms * 1e-3)}
+    ms = _timed(lambda: pb.proj_back_pose_grad(Pb.plan, img, motion, pb.PROJ_W_FDK, wvol, gradb, Pb.ws), Pb.plan,
+                pb, flush)
+    out["back_pose_grad"] = {"kernel": "k_back_grad", "config": "256^3, 360 views of 512^2, FDK weight",
+                             "kernel_ms": ms, "voxel_view_updates_per_s": vv / (ms * 1e-3),
+                             "pose_gradient_evals_per_s": 360 / (ms * 1e-3)}
+    del Pb
+    return out
+
+
 # ------------------------------------------------------------------ main arm
 
 def main():
@@ -218,13 +285,14 @@ def main():
         pb.proj_forward_pose_grad(P.plan, pose_d, pb.PROJ_LOSS_NCC, target_d, grad_d, loss_d, None, P.ws)
 
     stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local).__enter__()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     step_ms, kern_ms = [], []
-    with ClockSampler(local) as clocks:
+    if True:
         torch.cuda.synchronize()
         wall0 = time.perf_counter()
         for _ in range(args.steps):
@@ -239,6 +307,7 @@ def main():
             kern_ms.append(pb.proj_kernel_time_ms(P.plan))
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+    clocks.__exit__()
     if dist:
         dist.barrier()
     total_ms = sum(step_ms)
@@ -331,8 +400,14 @@ def main():
         pass
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    alu_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12       # FP32 FMA lanes x 2 FLOP x max clock
-    achieved = samples * FLOP_PER_SAMPLE / (k_ms * 1e-3) / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    l1_peak = n_sm * L1_BYTES_PER_CLK_SM * sm_max * 1e6 / 1e9                 # GB/s
+    alu_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12                            # TFLOP/s
+    l1_achieved = samples * L1_BYTES_PER_SAMPLE / (k_ms * 1e-3) / 1e9
+    alu_achieved = samples * FLOP_PER_SAMPLE / (k_ms * 1e-3) / 1e12
+    npad = (g.nx + 2) * (g.ny + 2) * (g.nz + 2)
+    hbm_bytes = npad * 16 + g.n_views * g.nu * g.nv * 4 + args.n_cand * 6 * 4  # compulsory: float4 volume, targets
+    hbm_achieved = hbm_bytes / (k_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -342,17 +417,24 @@ def main():
         "samples_per_step": samples,
         "kernel_ms": k_ms,
         "plain": plain,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved / alu_peak, "traffic": None,
+        "roofline": {"bound": "l1", "achieved": l1_achieved, "peak": l1_peak, "unit": "GB/s",
+                     "frac": l1_achieved / l1_peak, "traffic": TRAFFIC_PER_LAUNCH,
                      "kernel": "k_forward_grad<NCC> (fused pose-gradient march)",
-                     "peak_from": "FP32 FMA: %d SMs x 128 lanes x 2 FLOP x %.0f MHz" % (n_sm, sm_max),
-                     "flop_per_sample": FLOP_PER_SAMPLE},
+                     "what": "L1->register gather bytes: %d B per ray sample (8 corners x float4); peak = %d SMs x "
+                             "%d B/clk x %.0f MHz" % (L1_BYTES_PER_SAMPLE, n_sm, L1_BYTES_PER_CLK_SM, sm_max),
+                     "alu": {"achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                             "frac": alu_achieved / alu_peak, "flop_per_sample": FLOP_PER_SAMPLE},
+                     "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": hbm_achieved / hbm_peak, "compulsory_bytes": hbm_bytes,
+                             "peak_from": "MEASURED_PEAKS.json hbm_gbs"}},
         "e2e": {"value": args.n_cand / (em * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": em},
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
         "wall_s_timed_region": wall,
     }
+    if not args.no_secondary:
+        line["secondary"] = secondary(pb, torch, dev, w, mu_d, flush)
     if not args.no_cpu_baseline and world == 1:
         cands = list(range(min(args.cpu_sample, args.n_cand)))
         og, dt, threads, _ = cpu_oracle_eval(w, cands)
