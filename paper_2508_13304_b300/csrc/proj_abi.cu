@@ -44,7 +44,7 @@ struct proj_plan_s {
   int n_views, n_pose, n_inst, ops;
   int device;
   int n_tiles;        // ray tiles per instance
-  int bp_blocks;      // blocks of the back-projection gradient kernel
+  int bp_blocks;      // voxel bricks of the back-projection gradient (records per instance)
   std::vector<double> views;
   std::vector<int> inst_view, inst_pose;
   // device tables owned by the plan
@@ -221,11 +221,9 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
     delete p;
     return cuda_fail(e, "device query");
   }
-  {
-    const long long items = (long long)ceil_div(G.nx, kBpX) * ceil_div(G.ny, kBpY) * ceil_div(G.nz, kZChunk);
-    const long long cap = (long long)n_sm * kBpGradBlocksPerSM;
-    p->bp_blocks = (int)(items < cap ? items : cap);
-  }
+  // records of the back-projection gradient: one per voxel brick and instance
+  p->bp_blocks = ceil_div(G.nx, kGbX) * ceil_div(G.ny, kGbY) * ceil_div(G.nz, kGbZ);
+  (void)n_sm;
 
   // Workspace layout.
   size_t off = 0;

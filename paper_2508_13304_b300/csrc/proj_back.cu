@@ -69,12 +69,18 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
       const float rw = 1.0f / hw;
       const float u = fmaf(qz0, fz, bu) * rw, v = fmaf(qz1, fz, bv) * rw;
       if (!(u > -1.f && u < fu && v > -1.f && v < fvv)) continue;
+      // u in (-1, nu) and v in (-1, nv): the lower corner is in [-1, n-1],
+      // so only the four edges need a test (zero padding outside the image).
       const float flu = floorf(u), flv = floorf(v);
       const int i0 = (int)flu, j0 = (int)flv;
       const float au = u - flu, av = v - flv;
-      const float c0 = lerp(pix(img, g.nu, g.nv, i0, j0), pix(img, g.nu, g.nv, i0 + 1, j0), au);
-      const float c1 = lerp(pix(img, g.nu, g.nv, i0, j0 + 1), pix(img, g.nu, g.nv, i0 + 1, j0 + 1), au);
-      float val = lerp(c0, c1, av);
+      const bool xl = i0 >= 0, xh = i0 < g.nu - 1, yl = j0 >= 0, yh = j0 < g.nv - 1;
+      const int o = j0 * g.nu + i0;
+      const float v00 = (xl && yl) ? __ldg(img + o) : 0.f;
+      const float v10 = (xh && yl) ? __ldg(img + o + 1) : 0.f;
+      const float v01 = (xl && yh) ? __ldg(img + o + g.nu) : 0.f;
+      const float v11 = (xh && yh) ? __ldg(img + o + g.nu + 1) : 0.f;
+      float val = lerp(lerp(v00, v10, au), lerp(v01, v11, au), av);
       if (weight != PROJ_W_NONE) {
         const float r = w0 * rw;
         val *= r * r;
@@ -94,9 +100,17 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
 // rows of P's left 3x3: this is W (grad_d l) J_p + l~ grad W, the per-mm
 // derivative of mu_j with respect to the moved voxel position.  With wj =
 // dL/dmu_j the 12 sums wj rho and wj rho f~^T (f~ = centred voxel index)
-// give dL/dM of the instance.  Each warp keeps its own slot per instance in
-// shared memory, so the block sum and the later grid sum run in a fixed
-// order.
+// give dL/dM of the instance.
+//
+// Work decomposition: a block owns one brick of kGbX x kGbY x kGbZ voxels
+// (one thread per (x, y) column holding its kGbZ residual weights in
+// registers) and a chunk of kGbViews consecutive instances; blocks of the same
+// chunk run together, so that chunk's detector stacks stay in L2.  The inner
+// loop over z is branch-free - a voxel that projects outside the image, lies
+// behind the source or has wj = 0 gets weight 0 and gathers from a clamped,
+// valid address - so the gathers of several voxels can be in flight at once.
+// Per (brick, instance) one block reduction (warp shuffles, then the 8 warps
+// in a fixed order) writes a record part[instance][brick][12].
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -104,102 +118,97 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-__global__ void __launch_bounds__(kBpThreads) k_back_grad(const InstTable* __restrict__ inst, int n_inst, Geo g,
-                                                          int weight, const float4* __restrict__ det4,
-                                                          const float* __restrict__ wvol, float* __restrict__ part,
-                                                          int items_x, int items_y, int items_z) {
-  __shared__ float sacc[kBpThreads / 32][kBpInstChunk][12];
+__global__ void __launch_bounds__(kBpThreads, 3)
+    k_back_grad(const InstTable* __restrict__ inst, int n_inst, Geo g, int weight, const float4* __restrict__ det4,
+                const float* __restrict__ wvol, float* __restrict__ part, int bricks_x, int bricks_y) {
+  __shared__ float sred[kBpThreads / 32][12];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int n_items = items_x * items_y * items_z;
+  const int n_bricks = gridDim.x;
+  const int brick = blockIdx.x;
+  const int bx = brick % bricks_x, by = (brick / bricks_x) % bricks_y, bz = brick / (bricks_x * bricks_y);
+  const int ix = bx * kGbX + lane, iy = by * kGbY + warp, iz0 = bz * kGbZ;
+  const bool col = ix < g.nx && iy < g.ny;
+  float wj[kGbZ];
+#pragma unroll
+  for (int z = 0; z < kGbZ; ++z)
+    wj[z] = (col && iz0 + z < g.nz) ? __ldg(wvol + ((size_t)(iz0 + z) * g.ny + iy) * g.nx + ix) : 0.f;
+  const float fx = (float)ix - g.cx, fy = (float)iy - g.cy;
   const int qu = g.nu + 2;
   const size_t det_stride = (size_t)(g.nu + 2) * (g.nv + 2);
   const float fu = (float)g.nu, fvv = (float)g.nv;
-  for (int n0 = 0; n0 < n_inst; n0 += kBpInstChunk) {
-    const int nc = min(kBpInstChunk, n_inst - n0);
-    for (int e = threadIdx.x; e < (kBpThreads / 32) * kBpInstChunk * 12; e += kBpThreads)
-      (&sacc[0][0][0])[e] = 0.f;
-    __syncthreads();
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-      const int bx = item % items_x, by = (item / items_x) % items_y, bz = item / (items_x * items_y);
-      const int ix = bx * kBpX + lane, iy = by * kBpY + warp, iz0 = bz * kZChunk;
-      const bool col = ix < g.nx && iy < g.ny;
-      float wj[kZChunk];
+  const int n0 = blockIdx.y * kGbViews, n1 = min(n_inst, n0 + kGbViews);
+  for (int n = n0; n < n1; ++n) {
+    const InstTable& T = inst[n];
+    float a[12];
 #pragma unroll
-      for (int z = 0; z < kZChunk; ++z)
-        wj[z] = (col && iz0 + z < g.nz) ? __ldg(wvol + ((size_t)(iz0 + z) * g.ny + iy) * g.nx + ix) : 0.f;
-      const float fx = (float)ix - g.cx, fy = (float)iy - g.cy;
-      for (int i = 0; i < nc; ++i) {
-        const InstTable& T = inst[n0 + i];
-        float a[12];
+    for (int q = 0; q < 12; ++q) a[q] = 0.f;
+    if (T.valid && col) {
+      const float4* img = det4 + (size_t)n * det_stride;
+      const float bu = fmaf(T.Q[3], fy, fmaf(T.Q[0], fx, T.Q[9]));
+      const float bv = fmaf(T.Q[4], fy, fmaf(T.Q[1], fx, T.Q[10]));
+      const float bw = fmaf(T.Q[5], fy, fmaf(T.Q[2], fx, T.Q[11]));
+      const float P0x = T.P3[0], P0y = T.P3[1], P0z = T.P3[2];
+      const float P1x = T.P3[3], P1y = T.P3[4], P1z = T.P3[5];
+      const float P2x = T.P3[6], P2y = T.P3[7], P2z = T.P3[8];
 #pragma unroll
-        for (int q = 0; q < 12; ++q) a[q] = 0.f;
-        if (T.valid) {
-          const float bu = fmaf(T.Q[3], fy, fmaf(T.Q[0], fx, T.Q[9]));
-          const float bv = fmaf(T.Q[4], fy, fmaf(T.Q[1], fx, T.Q[10]));
-          const float bw = fmaf(T.Q[5], fy, fmaf(T.Q[2], fx, T.Q[11]));
-          const float4* img = det4 + (size_t)(n0 + i) * det_stride;
-#pragma unroll
-          for (int z = 0; z < kZChunk; ++z) {
-            if (wj[z] == 0.f) continue;
-            const float fz = (float)(iz0 + z) - g.cz;
-            const float hw = fmaf(T.Q[8], fz, bw);
-            if (!(hw > 0.f)) continue;
-            const float rw = 1.0f / hw;
-            const float u = fmaf(T.Q[6], fz, bu) * rw, v = fmaf(T.Q[7], fz, bv) * rw;
-            if (!(u > -1.f && u < fu && v > -1.f && v < fvv)) continue;
-            // padded coordinates: pixel index + 1, corner clamped to [0, n]
-            const float up = u + 1.f, vp = v + 1.f;
-            const int i0 = min(max(__float2int_rd(up), 0), g.nu);
-            const int j0 = min(max(__float2int_rd(vp), 0), g.nv);
-            const float au = up - (float)i0, av = vp - (float)j0;
-            const float4* p0 = img + (size_t)j0 * qu + i0;
-            const float4 c00 = __ldg(p0), c10 = __ldg(p0 + 1), c01 = __ldg(p0 + qu), c11 = __ldg(p0 + qu + 1);
-            const float L = lerp(lerp(c00.x, c10.x, au), lerp(c01.x, c11.x, au), av);
-            const float Du = lerp(lerp(c00.y, c10.y, au), lerp(c01.y, c11.y, au), av);
-            const float Dv = lerp(lerp(c00.z, c10.z, au), lerp(c01.z, c11.z, au), av);
-            float W = 1.f;
-            float s = fmaf(Du, u, Dv * v);
-            if (weight != PROJ_W_NONE) {
-              const float r = T.w0 * rw;
-              W = r * r;
-              if (weight == PROJ_W_FDK) s = fmaf(2.f, L, s);
-            }
-            const float f = W * rw * wj[z];
-            const float r0 = f * (fmaf(Du, T.P3[0], Dv * T.P3[3]) - s * T.P3[6]);
-            const float r1 = f * (fmaf(Du, T.P3[1], Dv * T.P3[4]) - s * T.P3[7]);
-            const float r2 = f * (fmaf(Du, T.P3[2], Dv * T.P3[5]) - s * T.P3[8]);
-            a[0] += r0;
-            a[1] += r1;
-            a[2] += r2;
-            a[3] = fmaf(r0, fx, a[3]);
-            a[4] = fmaf(r0, fy, a[4]);
-            a[5] = fmaf(r0, fz, a[5]);
-            a[6] = fmaf(r1, fx, a[6]);
-            a[7] = fmaf(r1, fy, a[7]);
-            a[8] = fmaf(r1, fz, a[8]);
-            a[9] = fmaf(r2, fx, a[9]);
-            a[10] = fmaf(r2, fy, a[10]);
-            a[11] = fmaf(r2, fz, a[11]);
-          }
+      for (int z = 0; z < kGbZ; ++z) {
+        const float fz = (float)(iz0 + z) - g.cz;
+        const float hw = fmaf(T.Q[8], fz, bw);
+        const float rw = 1.0f / hw;
+        const float u0 = fmaf(T.Q[6], fz, bu) * rw, v0 = fmaf(T.Q[7], fz, bv) * rw;
+        const bool ok = wj[z] != 0.f && hw > 0.f && u0 > -1.f && u0 < fu && v0 > -1.f && v0 < fvv;
+        const float u = ok ? u0 : 0.f, v = ok ? v0 : 0.f;
+        // padded coordinates: pixel index + 1, corner clamped to [0, n]
+        const float up = u + 1.f, vp = v + 1.f;
+        const int i0 = min(max(__float2int_rd(up), 0), g.nu);
+        const int j0 = min(max(__float2int_rd(vp), 0), g.nv);
+        const float au = up - (float)i0, av = vp - (float)j0;
+        const float4* p0 = img + (j0 * qu + i0);
+        const float4 c00 = __ldg(p0), c10 = __ldg(p0 + 1), c01 = __ldg(p0 + qu), c11 = __ldg(p0 + qu + 1);
+        const float L = lerp(lerp(c00.x, c10.x, au), lerp(c01.x, c11.x, au), av);
+        const float Du = lerp(lerp(c00.y, c10.y, au), lerp(c01.y, c11.y, au), av);
+        const float Dv = lerp(lerp(c00.z, c10.z, au), lerp(c01.z, c11.z, au), av);
+        float W = 1.f;
+        float sv = fmaf(Du, u, Dv * v);
+        if (weight != PROJ_W_NONE) {
+          const float r = T.w0 * rw;
+          W = r * r;
+          if (weight == PROJ_W_FDK) sv = fmaf(2.f, L, sv);
         }
-#pragma unroll
-        for (int q = 0; q < 12; ++q) {
-          const float s = warp_sum(a[q]);
-          if (lane == 0) sacc[warp][i][q] += s;
-        }
+        const float f = ok ? W * rw * wj[z] : 0.f;
+        const float r0 = f * (fmaf(Du, P0x, Dv * P1x) - sv * P2x);
+        const float r1 = f * (fmaf(Du, P0y, Dv * P1y) - sv * P2y);
+        const float r2 = f * (fmaf(Du, P0z, Dv * P1z) - sv * P2z);
+        a[0] += r0;
+        a[1] += r1;
+        a[2] += r2;
+        a[3] = fmaf(r0, fx, a[3]);
+        a[4] = fmaf(r0, fy, a[4]);
+        a[5] = fmaf(r0, fz, a[5]);
+        a[6] = fmaf(r1, fx, a[6]);
+        a[7] = fmaf(r1, fy, a[7]);
+        a[8] = fmaf(r1, fz, a[8]);
+        a[9] = fmaf(r2, fx, a[9]);
+        a[10] = fmaf(r2, fy, a[10]);
+        a[11] = fmaf(r2, fz, a[11]);
       }
     }
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const float sq = warp_sum(a[q]);
+      if (lane == 0) sred[warp][q] = sq;
+    }
     __syncthreads();
-    for (int e = threadIdx.x; e < nc * 12; e += kBpThreads) {
-      float s = 0.f;
-      for (int w = 0; w < kBpThreads / 32; ++w) s += sacc[w][e / 12][e % 12];
-      part[((size_t)blockIdx.x * n_inst + n0 + e / 12) * 12 + e % 12] = s;
+    if (threadIdx.x < 12) {
+      float sq = 0.f;
+      for (int w = 0; w < kBpThreads / 32; ++w) sq += sred[w][threadIdx.x];
+      part[((size_t)n * n_bricks + brick) * 12 + threadIdx.x] = sq;
     }
     __syncthreads();
   }
 }
 
-// Per pose: FP64 sum over blocks (fixed order) of its instances' records,
+// Per pose: FP64 sum over bricks (fixed order) of its instances' records,
 // conversion to dL/dM and contraction with dM/dtheta.
 __global__ void k_back_grad_reduce(const PoseTable* __restrict__ ptab, const int* __restrict__ pose_ptr,
                                    const int* __restrict__ pose_idx, int n_inst, int n_blocks, Geo g,
@@ -215,7 +224,7 @@ __global__ void k_back_grad_reduce(const PoseTable* __restrict__ ptab, const int
     if (t < kGroups * 12) {
       const int q = t % 12, grp = t / 12;
       double s = 0.0;
-      for (int b = grp; b < n_blocks; b += kGroups) s += (double)part[((size_t)b * n_inst + n) * 12 + q];
+      for (int b = grp; b < n_blocks; b += kGroups) s += (double)part[((size_t)n * n_blocks + b) * 12 + q];
       sp[grp][q] = s;
     }
     __syncthreads();
@@ -272,8 +281,10 @@ cudaError_t launch_back(const InstTable* d_inst, int n_inst, Geo geo, int weight
 
 cudaError_t launch_back_grad(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float4* d_det4,
                              const float* d_wvol, float* d_part, int n_blocks, cudaStream_t s) {
-  const int ix = ceil_div(geo.nx, kBpX), iy = ceil_div(geo.ny, kBpY), iz = ceil_div(geo.nz, kZChunk);
-  k_back_grad<<<n_blocks, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_det4, d_wvol, d_part, ix, iy, iz);
+  const int bx = ceil_div(geo.nx, kGbX), by = ceil_div(geo.ny, kGbY), bz = ceil_div(geo.nz, kGbZ);
+  (void)n_blocks;  // = bx * by * bz, the record count per instance
+  dim3 grid(bx * by * bz, ceil_div(n_inst, kGbViews));
+  k_back_grad<<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_det4, d_wvol, d_part, bx, by);
   return cudaGetLastError();
 }
 

@@ -74,8 +74,11 @@ constexpr int kBpX = 32;
 constexpr int kBpY = 8;
 constexpr int kZChunk = 8;
 constexpr int kBpThreads = kBpX * kBpY;
-constexpr int kBpInstChunk = 32;   // instances per pass of the BP gradient
-constexpr int kBpGradBlocksPerSM = 4;
+// Back-projection gradient: bricks of 32 x 8 x 16 voxels, 8 instances per block.
+constexpr int kGbX = 32;
+constexpr int kGbY = 8;
+constexpr int kGbZ = 16;
+constexpr int kGbViews = 8;
 
 // Launchers (defined in the .cu files; return cudaError_t of the launch).
 cudaError_t launch_setup(const float* d_pose, int n_pose, const double* d_views, const int* d_inst_view,
