@@ -202,6 +202,31 @@ def back_grad(geom, proj, poses, wvol, inst_view=None, inst_pose=None,
     return gth, gM.reshape(c.n_pose, 3, 4)
 
 
+def forward_pixels(geom, mu, poses, pix, inst_view=None, inst_pose=None):
+    """Forward projection of selected rays only; pix = [m][3] (instance,
+    iu, iv).  Same definition as ``forward``."""
+    c = _Call(geom, poses, inst_view, inst_pose)
+    mu = _f64(mu)
+    pix = np.ascontiguousarray(pix, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros(pix.shape[0])
+    _load().or_forward_pixels(ctypes.byref(c.g), _dp(mu), _dp(c.poses), _ip(c.iv), _ip(c.ip),
+                              int(pix.shape[0]), _ip(pix), _dp(out))
+    return out
+
+
+def back_voxels(geom, proj, poses, vox, inst_view=None, inst_pose=None, weight=W_NONE):
+    """Back-projection at selected voxels only; vox = [m][3] (i, j, k).
+    Same definition as ``back``."""
+    c = _Call(geom, poses, inst_view, inst_pose)
+    proj = _f64(proj)
+    assert proj.shape == (c.n_inst, geom.nv, geom.nu)
+    vox = np.ascontiguousarray(vox, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros(vox.shape[0])
+    _load().or_back_voxels(ctypes.byref(c.g), _dp(proj), _dp(c.poses), c.n_inst, _ip(c.iv), _ip(c.ip),
+                           int(weight), int(vox.shape[0]), _ip(vox), _dp(out))
+    return out
+
+
 # ------------------------------------------------------------------ losses
 
 def l2_loss(a, b):

@@ -21,7 +21,11 @@
  *    G_f evaluated at every integration point; grad mu = trilinear
  *    interpolation of the central-difference grid of the zero-padded volume,
  *    defined on the extended index grid [-1, n]^3 (mode OR_GRAD_ANALYTIC),
- *    or the exact derivative of mu~ (mode OR_GRAD_EXACT).
+ *    or the exact derivative of mu~ (mode OR_GRAD_EXACT).  Each channel of
+ *    G_f is projected by the same ray march over the support of its own
+ *    interpolant: the open box (-2, n+1)^3 for the analytic gradient grid
+ *    (mu~ itself is zero outside (-1, n)^3), which keeps the gradient
+ *    continuous in the pose.
  *  - Back-projection (Eq. back, discretised as in Sec. II-C.2): voxel-driven
  *        mu_j = sum_inst W(r_j) * l~(p(R r'_j + t)),
  *    l~ bilinear with zero padding in pixel-index units; voxels with w' <= 0
@@ -29,10 +33,11 @@
  *    W = (w'(0) / w'(r))^2 with w'(0) the value at the world origin.
  *  - Back-projection pose gradient (Eq. back_derive / final_back / back_int
  *    / dis_back): grad_d l = bilinear interpolation of central-difference
- *    detector images on the extended grid (analytic) or the exact derivative
- *    of l~ (exact), both taken on the open support (-1,nu) x (-1,nv) of l~;
- *    the FDK weight contributes l~ * grad W unless the paper-literal
- *    constant-weight variant is requested.
+ *    detector images on the extended grid [-1,nu] x [-1,nv] with zero
+ *    padding (analytic; its interpolant lives on (-2,nu+1) x (-2,nv+1)) or
+ *    the exact derivative of l~ (exact); the FDK weight contributes
+ *    l~ * grad W unless the paper-literal constant-weight variant is
+ *    requested.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -216,9 +221,14 @@ static void world_to_index(const or_geom *g, const double R[9], const double t[3
   f[2] = (rp[2] - g->off[2]) / g->vz + 0.5 * (g->nz - 1);
 }
 
-static int inside_box(const or_geom *g, const double f[3]) {
-  return f[0] > -1.0 && f[0] < g->nx && f[1] > -1.0 && f[1] < g->ny && f[2] > -1.0 && f[2] < g->nz;
+/* Open box (-m, n - 1 + m)^3 in index coordinates: m = 1 is the support of
+ * mu~, m = 2 the support of the interpolated central-difference grid. */
+static int inside_box_m(const or_geom *g, const double f[3], int m) {
+  return f[0] > -m && f[0] < g->nx - 1 + m && f[1] > -m && f[1] < g->ny - 1 + m && f[2] > -m &&
+         f[2] < g->nz - 1 + m;
 }
+
+static int inside_box(const or_geom *g, const double f[3]) { return inside_box_m(g, f, 1); }
 
 /* Source and unit direction of the ray through the centre of pixel (iu,iv). */
 static void pixel_ray(const or_geom *g, const double *view, int iu, int iv, double s[3], double e[3]) {
@@ -234,10 +244,10 @@ static void pixel_ray(const or_geom *g, const double *view, int iu, int iv, doub
 }
 
 /* Range [k_lo, k_hi] of sample indices whose index coordinate can lie in the
- * open box; returns 0 when the ray misses.  Samples are re-tested one by one,
- * so this only bounds the loop. */
-static int sample_range(const or_geom *g, const double R[9], const double t[3], const double s[3],
-                        const double e[3], long *k_lo, long *k_hi) {
+ * open box (-m, n - 1 + m)^3; returns 0 when the ray misses.  Samples are
+ * re-tested one by one, so this only bounds the loop. */
+static int sample_range_m(const or_geom *g, const double R[9], const double t[3], const double s[3],
+                          const double e[3], int m, long *k_lo, long *k_hi) {
   double f0[3], f1[3], p1[3];
   world_to_index(g, R, t, s, f0);
   for (int a = 0; a < 3; ++a) p1[a] = s[a] + e[a];
@@ -247,10 +257,10 @@ static int sample_range(const or_geom *g, const double R[9], const double t[3], 
   for (int a = 0; a < 3; ++a) {
     double df = f1[a] - f0[a]; /* index units per mm of arc length */
     if (fabs(df) < 1e-300) {
-      if (!(f0[a] > -1.0 && f0[a] < n[a])) return 0;
+      if (!(f0[a] > -m && f0[a] < n[a] - 1 + m)) return 0;
       continue;
     }
-    double s1 = (-1.0 - f0[a]) / df, s2 = (n[a] - f0[a]) / df;
+    double s1 = (-(double)m - f0[a]) / df, s2 = (n[a] - 1 + m - f0[a]) / df;
     double a1 = s1 < s2 ? s1 : s2, a2 = s1 < s2 ? s2 : s1;
     if (a1 > lo) lo = a1;
     if (a2 < hi) hi = a2;
@@ -260,6 +270,11 @@ static int sample_range(const or_geom *g, const double R[9], const double t[3], 
   if (*k_lo < 0) *k_lo = 0;
   *k_hi = (long)ceil(hi / g->step) + 1;
   return 1;
+}
+
+static int sample_range(const or_geom *g, const double R[9], const double t[3], const double s[3],
+                        const double e[3], long *k_lo, long *k_hi) {
+  return sample_range_m(g, R, t, s, e, 1, k_lo, k_hi);
 }
 
 static void pose_of(const double *poses, int p, double R[9], double dR[27], double t[3]) {
@@ -339,12 +354,13 @@ void or_forward_grad(const or_geom *g, const double *mu, const double *poses, in
       double s[3], e[3];
       pixel_ray(g, view, iu, iv, s, e);
       long klo, khi;
-      if (wn[p] != 0.0 && sample_range(g, R, t, s, e, &klo, &khi)) {
+      const int m = (mode == OR_GRAD_ANALYTIC) ? 2 : 1;
+      if (wn[p] != 0.0 && sample_range_m(g, R, t, s, e, m, &klo, &khi)) {
         for (long k = klo; k <= khi; ++k) {
           double r[3], f[3], gr[3];
           for (int a = 0; a < 3; ++a) r[a] = s[a] + (double)k * g->step * e[a];
           world_to_index(g, R, t, r, f);
-          if (!inside_box(g, f)) continue;
+          if (!inside_box_m(g, f, m)) continue;
           gradient_at(mu, g, f, mode, gr);
           for (int a = 0; a < 3; ++a) {
             for (int b = 0; b < 3; ++b) acc[4 * a + b] += gr[b] * (r[a] - t[a]);
@@ -428,14 +444,13 @@ static void det_grad_grid(const double *img, const or_geom *g, int iu, int iv, d
   out[1] = 0.5 * (pix(img, g, iu, iv + 1) - pix(img, g, iu, iv - 1));
 }
 
-/* Detector gradient at (u, v).  Like the forward samples, which are kept in
- * the open index box where mu~ lives, it is taken only on the open support
- * (-1, nu) x (-1, nv) of l~ and is zero elsewhere. */
+/* Detector gradient at (u, v): the bilinear interpolant of the
+ * central-difference images (zero outside their grid [-1,nu] x [-1,nv]) or
+ * the exact derivative of l~. */
 static void det_gradient_at(const double *img, const or_geom *g, double u, double v, int mode, double out[2]) {
   int i0 = (int)floor(u), j0 = (int)floor(v);
   double au = u - i0, av = v - j0;
   out[0] = out[1] = 0.0;
-  if (!(u > -1.0 && u < g->nu && v > -1.0 && v < g->nv)) return;
   for (int c = 0; c < 4; ++c) {
     int di = c & 1, dj = (c >> 1) & 1;
     double wu = di ? au : 1 - au, wv = dj ? av : 1 - av;
@@ -586,5 +601,53 @@ void or_back_grad(const or_geom *g, const double *proj, const double *poses, int
     double R[9], dR[27], t[3];
     pose_of(poses, p, R, dR, t);
     contract_pose(gM + 12 * p, dR, gth + 6 * p);
+  }
+}
+
+/* ---------------------------------------------------------- sampled outputs */
+
+/* Forward projections of selected pixels only: pix[m] = (instance, iu, iv);
+ * out[m] = l of that ray (same definition as or_forward). */
+void or_forward_pixels(const or_geom *g, const double *mu, const double *poses, const int *inst_view,
+                       const int *inst_pose, int n_pix, const int *pix, double *out) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int m = 0; m < n_pix; ++m) {
+    const int n = pix[3 * m], iu = pix[3 * m + 1], iv = pix[3 * m + 2];
+    double R[9], t[3], s[3], e[3];
+    pose_of(poses, inst_pose[n], R, NULL, t);
+    pixel_ray(g, g->views + 12 * inst_view[n], iu, iv, s, e);
+    long klo, khi;
+    double acc = 0.0;
+    if (sample_range(g, R, t, s, e, &klo, &khi)) {
+      for (long k = klo; k <= khi; ++k) {
+        double r[3], f[3];
+        for (int a = 0; a < 3; ++a) r[a] = s[a] + (double)k * g->step * e[a];
+        world_to_index(g, R, t, r, f);
+        if (!inside_box(g, f)) continue;
+        acc += trilinear(mu, g, f);
+      }
+    }
+    out[m] = g->step * acc;
+  }
+}
+
+/* Back-projection at selected voxels only: vox[m] = (i, j, k); out[m] =
+ * sum over all instances (same definition as or_back). */
+void or_back_voxels(const or_geom *g, const double *proj, const double *poses, int n_inst, const int *inst_view,
+                    const int *inst_pose, int weight, int n_vox, const int *vox, double *out) {
+  const long npix = (long)g->nu * g->nv;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int m = 0; m < n_vox; ++m) {
+    double acc = 0.0;
+    for (int n = 0; n < n_inst; ++n) {
+      double R[9], t[3], P[12], rp[3], r[3], h[3];
+      pose_of(poses, inst_pose[n], R, NULL, t);
+      or_projection_matrix(g->views + 12 * inst_view[n], g->nu, g->nv, P);
+      voxel_world(g, R, t, vox[3 * m], vox[3 * m + 1], vox[3 * m + 2], rp, r);
+      apply_P(P, r, h);
+      if (!(h[2] > 0.0)) continue;
+      acc += distance_weight(P, h[2], weight) * bilinear(proj + (size_t)n * npix, g, h[0] / h[2], h[1] / h[2]);
+    }
+    out[m] = acc;
   }
 }

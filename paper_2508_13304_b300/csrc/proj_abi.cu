@@ -136,8 +136,9 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   if (G.nx < 1 || G.ny < 1 || G.nz < 1) return fail(PROJ_E_ARG, "volume size %d x %d x %d", G.nx, G.ny, G.nz);
   if (G.nu < 1 || G.nv < 1) return fail(PROJ_E_ARG, "detector size %d x %d", G.nu, G.nv);
   const long long npad = (long long)(G.nx + 2) * (G.ny + 2) * (G.nz + 2);
-  if (npad >= (1LL << 31)) return fail(PROJ_E_ARG, "volume too large (padded voxel count %lld >= 2^31)", npad);
-  if ((long long)(G.nu + 2) * (G.nv + 2) >= (1LL << 31)) return fail(PROJ_E_ARG, "detector too large");
+  const long long npad2 = (long long)(G.nx + 4) * (G.ny + 4) * (G.nz + 4);
+  if (npad2 >= (1LL << 31)) return fail(PROJ_E_ARG, "volume too large (padded voxel count %lld >= 2^31)", npad2);
+  if ((long long)(G.nu + 4) * (G.nv + 4) >= (1LL << 31)) return fail(PROJ_E_ARG, "detector too large");
   if (!finite_pos(G.vx) || !finite_pos(G.vy) || !finite_pos(G.vz))
     return fail(PROJ_E_ARG, "voxel pitch must be finite and > 0");
   if (!finite_pos(G.step)) return fail(PROJ_E_ARG, "ray step must be finite and > 0");
@@ -181,12 +182,18 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   g.px = G.nx + 2;
   g.py = G.ny + 2;
   g.pz = G.nz + 2;
+  g.qx = G.nx + 4;
+  g.qy = G.ny + 4;
+  g.qz = G.nz + 4;
   g.vx = (float)G.vx;
   g.vy = (float)G.vy;
   g.vz = (float)G.vz;
   g.hx = 0.5f * (G.nx + 1);
   g.hy = 0.5f * (G.ny + 1);
   g.hz = 0.5f * (G.nz + 1);
+  g.gx = 0.5f * (G.nx + 3);
+  g.gy = 0.5f * (G.ny + 3);
+  g.gz = 0.5f * (G.nz + 3);
   g.cx = 0.5f * (G.nx - 1);
   g.cy = 0.5f * (G.ny - 1);
   g.cz = 0.5f * (G.nz - 1);
@@ -237,9 +244,9 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   p->off_ptab = take(sizeof(PoseTable) * (size_t)n_pose);
   const size_t npad_sz = (size_t)npad;
   p->off_vol1 = (ops & PROJ_OP_FORWARD) ? take(sizeof(float) * npad_sz) : 0;
-  p->off_vol4 = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float4) * npad_sz) : 0;
+  p->off_vol4 = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float4) * (size_t)npad2) : 0;
   p->off_part_f = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float) * kRec * (size_t)n_inst * p->n_tiles) : 0;
-  p->off_det4 = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float4) * (size_t)n_inst * (G.nu + 2) * (G.nv + 2)) : 0;
+  p->off_det4 = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float4) * (size_t)n_inst * (G.nu + 4) * (G.nv + 4)) : 0;
   p->off_part_b = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float) * 12 * (size_t)n_inst * p->bp_blocks) : 0;
   p->off_acc = (ops & PROJ_OP_ADJOINT) ? take(sizeof(float) * npad_sz) : 0;
   p->ws_bytes = off;

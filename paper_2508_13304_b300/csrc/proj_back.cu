@@ -21,15 +21,16 @@ __device__ __forceinline__ float pix(const float* __restrict__ img, int nu, int 
 }
 
 // ---------------------------------------------------------------- K4
-// (l, d_u l, d_v l, 0) on the extended grid [-1, nu] x [-1, nv], stored
-// padded as [n_inst][nv+2][nu+2].
+// (l, d_u l, d_v l, 0) with a 2-pixel border, [n_inst][nv+4][nu+4]: the
+// central differences of the zero-padded image are non-zero up to one pixel
+// outside the image and zero on the outer border.
 __global__ void k_detector_prep(const float* __restrict__ proj, int n_inst, Geo g, float4* __restrict__ det4) {
-  const int qu = g.nu + 2, qv = g.nv + 2;
+  const int qu = g.nu + 4, qv = g.nv + 4;
   const long long n = (long long)n_inst * qu * qv;
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
-    const int iu = (int)(p % qu) - 1;
-    const int iv = (int)((p / qu) % qv) - 1;
+    const int iu = (int)(p % qu) - 2;
+    const int iv = (int)((p / qu) % qv) - 2;
     const int in = (int)(p / ((long long)qu * qv));
     const float* img = proj + (size_t)in * g.nu * g.nv;
     const float l = pix(img, g.nu, g.nv, iu, iv);
@@ -133,9 +134,9 @@ __global__ void __launch_bounds__(kBpThreads, 3)
   for (int z = 0; z < kGbZ; ++z)
     wj[z] = (col && iz0 + z < g.nz) ? __ldg(wvol + ((size_t)(iz0 + z) * g.ny + iy) * g.nx + ix) : 0.f;
   const float fx = (float)ix - g.cx, fy = (float)iy - g.cy;
-  const int qu = g.nu + 2;
-  const size_t det_stride = (size_t)(g.nu + 2) * (g.nv + 2);
-  const float fu = (float)g.nu, fvv = (float)g.nv;
+  const int qu = g.nu + 4;
+  const size_t det_stride = (size_t)(g.nu + 4) * (g.nv + 4);
+  const float fu = (float)g.nu + 1.f, fvv = (float)g.nv + 1.f;
   const int n0 = blockIdx.y * kGbViews, n1 = min(n_inst, n0 + kGbViews);
   for (int n = n0; n < n1; ++n) {
     const InstTable& T = inst[n];
@@ -156,12 +157,13 @@ __global__ void __launch_bounds__(kBpThreads, 3)
         const float hw = fmaf(T.Q[8], fz, bw);
         const float rw = 1.0f / hw;
         const float u0 = fmaf(T.Q[6], fz, bu) * rw, v0 = fmaf(T.Q[7], fz, bv) * rw;
-        const bool ok = wj[z] != 0.f && hw > 0.f && u0 > -1.f && u0 < fu && v0 > -1.f && v0 < fvv;
+        // support of the interpolated gradient images: (-2, nu+1) x (-2, nv+1)
+        const bool ok = wj[z] != 0.f && hw > 0.f && u0 > -2.f && u0 < fu && v0 > -2.f && v0 < fvv;
         const float u = ok ? u0 : 0.f, v = ok ? v0 : 0.f;
-        // padded coordinates: pixel index + 1, corner clamped to [0, n]
-        const float up = u + 1.f, vp = v + 1.f;
-        const int i0 = min(max(__float2int_rd(up), 0), g.nu);
-        const int j0 = min(max(__float2int_rd(vp), 0), g.nv);
+        // padded coordinates: pixel index + 2, corner clamped to [0, n + 2]
+        const float up = u + 2.f, vp = v + 2.f;
+        const int i0 = min(max(__float2int_rd(up), 0), g.nu + 2);
+        const int j0 = min(max(__float2int_rd(vp), 0), g.nv + 2);
         const float au = up - (float)i0, av = vp - (float)j0;
         const float4* p0 = img + (j0 * qu + i0);
         const float4 c00 = __ldg(p0), c10 = __ldg(p0 + 1), c01 = __ldg(p0 + qu), c11 = __ldg(p0 + qu + 1);
@@ -267,7 +269,7 @@ int elementwise_grid(long long n) {
 }  // namespace
 
 cudaError_t launch_detector_prep(const float* d_proj, int n_inst, Geo geo, float4* d_det4, cudaStream_t s) {
-  const long long n = (long long)n_inst * (geo.nu + 2) * (geo.nv + 2);
+  const long long n = (long long)n_inst * (geo.nu + 4) * (geo.nv + 4);
   k_detector_prep<<<elementwise_grid(n), 256, 0, s>>>(d_proj, n_inst, geo, d_det4);
   return cudaGetLastError();
 }

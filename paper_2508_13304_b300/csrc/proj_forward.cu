@@ -47,9 +47,12 @@ struct Ray {
 };
 
 // Ray through the centre of pixel (iu, iv) of instance T, clipped to the
-// open index box (-1, n)^3 (centred: |f~| < (n+1)/2).  Returns false when
-// the ray misses the box.
-__device__ __forceinline__ bool ray_setup(const InstTable& T, const Geo& g, int iu, int iv, Ray& r) {
+// open index box (-m, n - 1 + m)^3 (centred: |f~| < (n - 1)/2 + m) with
+// m = 1 (support of mu~) or m = 2 (support of the interpolated gradient
+// grid); the returned sample origin is in index coordinates shifted by m
+// (the border width of the array marched).  Returns false on a miss.
+template <int M>
+__device__ __forceinline__ bool ray_setup_m(const InstTable& T, const Geo& g, int iu, int iv, Ray& r) {
   const float fu = (float)iu, fv = (float)iv;
   const float dx = fmaf(fv, T.Vo[0], fmaf(fu, T.Uo[0], T.C0[0]));
   const float dy = fmaf(fv, T.Vo[1], fmaf(fu, T.Uo[1], T.C0[1]));
@@ -61,7 +64,7 @@ __device__ __forceinline__ bool ray_setup(const InstTable& T, const Geo& g, int 
   float lo = 0.f, hi = 3.0e8f;
   const float A[3] = {T.A[0], T.A[1], T.A[2]};
   const float D[3] = {r.dx, r.dy, r.dz};
-  const float H[3] = {g.hx, g.hy, g.hz};
+  const float H[3] = {M == 1 ? g.hx : g.gx, M == 1 ? g.hy : g.gy, M == 1 ? g.hz : g.gz};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (fabsf(D[a]) > 1e-20f) {
@@ -76,16 +79,21 @@ __device__ __forceinline__ bool ray_setup(const InstTable& T, const Geo& g, int 
   if (!(hi >= lo)) return false;
   r.k0 = (int)ceilf(lo);
   r.k1 = (int)floorf(hi);
-  r.ax = A[0] + g.cx + 1.0f;
-  r.ay = A[1] + g.cy + 1.0f;
-  r.az = A[2] + g.cz + 1.0f;
+  r.ax = A[0] + g.cx + (float)M;
+  r.ay = A[1] + g.cy + (float)M;
+  r.az = A[2] + g.cz + (float)M;
   return r.k1 >= r.k0;
 }
 
+__device__ __forceinline__ bool ray_setup(const InstTable& T, const Geo& g, int iu, int iv, Ray& r) {
+  return ray_setup_m<1>(T, g, iu, iv, r);
+}
+
 // Cell of padded index point (fx, fy, fz): lower corner clamped to
-// [0, n] so the 8 corners stay inside the (n+2)^3 padded array; fractions
-// are taken from the clamped corner so that a point marginally outside the
-// box (rounding) interpolates towards the zero border.
+// [0, n] (1-voxel border) or [0, n + 2] (2-voxel border) so the 8 corners
+// stay inside the padded array; fractions are taken from the clamped corner
+// so that a point marginally outside the box (rounding) interpolates
+// towards the zero border.
 struct Cell {
   int idx;
   float ax, ay, az;
@@ -103,29 +111,52 @@ __device__ __forceinline__ Cell locate(float fx, float fy, float fz, const Geo& 
   return c;
 }
 
+__device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo& g) {
+  const int ix = min(max(__float2int_rd(fx), 0), g.nx + 2);
+  const int iy = min(max(__float2int_rd(fy), 0), g.ny + 2);
+  const int iz = min(max(__float2int_rd(fz), 0), g.nz + 2);
+  Cell c;
+  c.ax = fx - (float)ix;
+  c.ay = fy - (float)iy;
+  c.az = fz - (float)iz;
+  c.idx = (iz * g.qy + iy) * g.qx + ix;
+  return c;
+}
+
 // ---------------------------------------------------------------- K1
 
+// vol1: mu with a 1-voxel zero border, (n+2)^3.  vol4: (mu, grad mu) with a
+// 2-voxel border, (n+4)^3; grad mu = central differences of the zero-padded
+// volume, non-zero up to one voxel outside the grid and zero on the outer
+// border layer.
 __global__ void k_volume_prep(const float* __restrict__ mu, Geo g, float* __restrict__ vol1,
                               float4* __restrict__ vol4) {
-  const long long n = (long long)g.px * g.py * g.pz;
-  const float sx = 0.5f / g.vx, sy = 0.5f / g.vy, sz = 0.5f / g.vz;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(p % g.px) - 1;
-    const int j = (int)((p / g.px) % g.py) - 1;
-    const int k = (int)(p / ((long long)g.px * g.py)) - 1;
-    auto at = [&](int a, int b, int c) -> float {
-      return (a >= 0 && a < g.nx && b >= 0 && b < g.ny && c >= 0 && c < g.nz)
-                 ? __ldg(mu + ((size_t)c * g.ny + b) * g.nx + a)
-                 : 0.0f;
-    };
-    const float m = at(i, j, k);
-    if (vol1) vol1[p] = m;
-    if (vol4) {
+  auto at = [&](int a, int b, int c) -> float {
+    return (a >= 0 && a < g.nx && b >= 0 && b < g.ny && c >= 0 && c < g.nz)
+               ? __ldg(mu + ((size_t)c * g.ny + b) * g.nx + a)
+               : 0.0f;
+  };
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (vol1) {
+    const long long n = (long long)g.px * g.py * g.pz;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+      const int i = (int)(p % g.px) - 1;
+      const int j = (int)((p / g.px) % g.py) - 1;
+      const int k = (int)(p / ((long long)g.px * g.py)) - 1;
+      vol1[p] = at(i, j, k);
+    }
+  }
+  if (vol4) {
+    const float sx = 0.5f / g.vx, sy = 0.5f / g.vy, sz = 0.5f / g.vz;
+    const long long n = (long long)g.qx * g.qy * g.qz;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+      const int i = (int)(p % g.qx) - 2;
+      const int j = (int)((p / g.qx) % g.qy) - 2;
+      const int k = (int)(p / ((long long)g.qx * g.qy)) - 2;
       const float gx = (at(i + 1, j, k) - at(i - 1, j, k)) * sx;
       const float gy = (at(i, j + 1, k) - at(i, j - 1, k)) * sy;
       const float gz = (at(i, j, k + 1) - at(i, j, k - 1)) * sz;
-      vol4[p] = make_float4(m, gx, gy, gz);
+      vol4[p] = make_float4(at(i, j, k), gx, gy, gz);
     }
   }
 }
@@ -178,7 +209,8 @@ __global__ void k_count(const InstTable* __restrict__ inst, int n_tiles, int til
 //
 // Per ray: a = sum_k mu~, S0 = sum_k g, S1[b][c] = sum_k g_b f~_c with
 // g = interpolated central-difference gradient (per mm) and f~ the centred
-// index coordinate of the sample.  Since r - t = R r' and r' = off + f~ vox,
+// index coordinate of the sample, over the samples in the gradient grid's
+// support (-2, n+1)^3 (mu~ is zero in the outer band, so a is unchanged).  Since r - t = R r' and r' = off + f~ vox,
 // step * (S0, S1) determine the ray's dl/dM exactly (contraction in the
 // reduction kernel).  At the end of the ray the loss residual weights the
 // 12 sums; a warp/block reduction writes one record per tile.
@@ -197,18 +229,18 @@ __global__ void __launch_bounds__(kMarchThreads)
   float s0[3] = {0.f, 0.f, 0.f};
   float s1[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   Ray r;
-  if (on_det && T.valid && ray_setup(T, g, iu, iv, r)) {
-    const int pxy = g.px * g.py;
-    const float ox = g.cx + 1.0f, oy = g.cy + 1.0f, oz = g.cz + 1.0f;
+  if (on_det && T.valid && ray_setup_m<2>(T, g, iu, iv, r)) {
+    const int qxy = g.qx * g.qy;
+    const float ox = g.cx + 2.0f, oy = g.cy + 2.0f, oz = g.cz + 2.0f;
     for (int k = r.k0; k <= r.k1; ++k) {
       const float kf = (float)k;
       const float fx = fmaf(kf, r.dx, r.ax), fy = fmaf(kf, r.dy, r.ay), fz = fmaf(kf, r.dz, r.az);
-      const Cell c = locate(fx, fy, fz, g);
+      const Cell c = locate2(fx, fy, fz, g);
       const float4* p0 = vol + c.idx;
       const float4 v000 = __ldg(p0), v100 = __ldg(p0 + 1);
-      const float4 v010 = __ldg(p0 + g.px), v110 = __ldg(p0 + g.px + 1);
-      const float4 v001 = __ldg(p0 + pxy), v101 = __ldg(p0 + pxy + 1);
-      const float4 v011 = __ldg(p0 + pxy + g.px), v111 = __ldg(p0 + pxy + g.px + 1);
+      const float4 v010 = __ldg(p0 + g.qx), v110 = __ldg(p0 + g.qx + 1);
+      const float4 v001 = __ldg(p0 + qxy), v101 = __ldg(p0 + qxy + 1);
+      const float4 v011 = __ldg(p0 + qxy + g.qx), v111 = __ldg(p0 + qxy + g.qx + 1);
       const float4 c0 = lerp4(lerp4(v000, v100, c.ax), lerp4(v010, v110, c.ax), c.ay);
       const float4 c1 = lerp4(lerp4(v001, v101, c.ax), lerp4(v011, v111, c.ax), c.ay);
       const float4 v = lerp4(c0, c1, c.az);
@@ -430,7 +462,7 @@ int elementwise_grid(long long n) {
 }  // namespace
 
 cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float* d_vol1, float4* d_vol4, cudaStream_t s) {
-  const long long n = (long long)geo.px * geo.py * geo.pz;
+  const long long n = (long long)geo.qx * geo.qy * geo.qz;
   k_volume_prep<<<elementwise_grid(n), 256, 0, s>>>(d_mu, geo, d_vol1, d_vol4);
   return cudaGetLastError();
 }

@@ -47,9 +47,11 @@ static_assert(sizeof(PoseTable) % 8 == 0, "PoseTable layout");
 // Static geometry shared by all kernels of a plan (passed by value).
 struct Geo {
   int nx, ny, nz;       // voxels
-  int px, py, pz;       // padded sizes (n + 2)
+  int px, py, pz;       // sizes with a 1-voxel border (n + 2): the mu copy
+  int qx, qy, qz;       // sizes with a 2-voxel border (n + 4): the (mu, grad mu) volume
   float vx, vy, vz;     // voxel pitch, mm
-  float hx, hy, hz;     // half extent of the open box in centred index units: (n+1)/2
+  float hx, hy, hz;     // half extent of the open box (-1, n) in centred index units: (n+1)/2
+  float gx, gy, gz;     // half extent of the gradient box (-2, n+1): (n+3)/2
   float cx, cy, cz;     // (n-1)/2
   float offx, offy, offz;
   int nu, nv;

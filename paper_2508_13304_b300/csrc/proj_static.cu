@@ -22,7 +22,7 @@ using namespace projk;
 namespace {
 
 // Limits of the static scratch (see include/proj.h).
-constexpr int kMaxPadVoxels = 66 * 66 * 66;  // (nx+2)(ny+2)(nz+2): a 64^3 volume
+constexpr int kMaxPadVoxels = 68 * 68 * 68;  // (nx+4)(ny+4)(nz+4): a 64^3 volume
 constexpr int kMaxInst = 64;
 constexpr int kMaxPose = 64;
 constexpr int kMaxViews = 64;
@@ -103,10 +103,10 @@ int proj_forward_pose_grad_static(const proj_geometry* geom, int n_pose, int n_i
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(G.vol_offset[a])) return fail(PROJ_E_ARG, "volume offset must be finite");
   // Size limits of the static scratch.
-  const long long npad = (long long)(G.nx + 2) * (G.ny + 2) * (G.nz + 2);
+  const long long npad = (long long)(G.nx + 4) * (G.ny + 4) * (G.nz + 4);
   const long long n_tiles = (long long)ceil_div(G.nu, kTileU) * ceil_div(G.nv, kTileV);
   if (npad > kMaxPadVoxels)
-    return fail(PROJ_E_ARG, "volume %d x %d x %d exceeds the static scratch limit ((nx+2)(ny+2)(nz+2) <= 66^3)", G.nx,
+    return fail(PROJ_E_ARG, "volume %d x %d x %d exceeds the static scratch limit ((nx+4)(ny+4)(nz+4) <= 68^3)", G.nx,
                 G.ny, G.nz);
   if (n_inst > kMaxInst || n_pose > kMaxPose || G.n_views > kMaxViews)
     return fail(PROJ_E_ARG, "n_inst %d, n_pose %d, n_views %d exceed the static scratch limit of %d each", n_inst,
@@ -149,12 +149,18 @@ int proj_forward_pose_grad_static(const proj_geometry* geom, int n_pose, int n_i
   g.px = G.nx + 2;
   g.py = G.ny + 2;
   g.pz = G.nz + 2;
+  g.qx = G.nx + 4;
+  g.qy = G.ny + 4;
+  g.qz = G.nz + 4;
   g.vx = (float)G.vx;
   g.vy = (float)G.vy;
   g.vz = (float)G.vz;
   g.hx = 0.5f * (G.nx + 1);
   g.hy = 0.5f * (G.ny + 1);
   g.hz = 0.5f * (G.nz + 1);
+  g.gx = 0.5f * (G.nx + 3);
+  g.gy = 0.5f * (G.ny + 3);
+  g.gz = 0.5f * (G.nz + 3);
   g.cx = 0.5f * (G.nx - 1);
   g.cy = 0.5f * (G.ny - 1);
   g.cz = 0.5f * (G.nz - 1);

@@ -1,0 +1,124 @@
+"""GPU parity at full sizes, in the launch configurations the benchmark times,
+on outputs the FP64 oracle can compute one by one (sampled candidates, views,
+pixels and voxels).  Bars as in test_gpu_parity: images rel-L2 <= 1e-4, pose
+gradients rel <= 1e-3 per pose on each block."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+TOL_IMG = 1e-4
+TOL_GRAD = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_13304_b300 import build
+    build.build()
+
+
+import paper_2508_13304_b300 as pb  # noqa: E402
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def grad_rel(g_gpu, g_ref):
+    worst = 0.0
+    for blk in (slice(0, 3), slice(3, 6)):
+        worst = max(worst, rel(g_gpu[blk], g_ref[blk]))
+    return worst
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32)
+
+
+def test_registration_batch_full_size():
+    """256^3, 2 views of 384^2, 64 candidates in one launch, NCC fused;
+    candidates 0, 31 and 63 checked against the oracle."""
+    w = synth.workload_registration(n_cand=64)
+    g = w["geom"]
+    mu = f32(w["mu"])
+    poses = f32(w["poses"])
+    iv2, ip2 = np.arange(2), np.zeros(2, dtype=np.int32)
+    target = f32(oracle.forward(g, mu.astype(np.float64), f32(w["pose_true"]).astype(np.float64), iv2, ip2))
+    iv = np.tile(np.arange(2, dtype=np.int32), 64)
+    ip = np.repeat(np.arange(64, dtype=np.int32), 2)
+    P = pb.Projector(g, n_pose=64, inst_view=iv, inst_pose=ip, ops=pb.PROJ_OP_FORWARD | pb.PROJ_OP_FORWARD_GRAD)
+    P.set_volume(mu)
+    grad, loss, proj = P.forward_pose_grad(poses, pb.PROJ_LOSS_NCC, target, want_proj=True)
+    grad, loss, proj = grad.cpu().numpy(), loss.cpu().numpy(), proj.cpu().numpy()
+    for c in (0, 31, 63):
+        pose = poses[c].astype(np.float64)
+        pr = oracle.forward(g, mu.astype(np.float64), pose, iv2, ip2)
+        L, wts = oracle.pose_loss_weights("ncc", pr, target, iv2, ip2, 1)
+        gref, _ = oracle.forward_grad(g, mu.astype(np.float64), pose, wts, iv2, ip2)
+        assert rel(proj[2 * c:2 * c + 2], pr) <= TOL_IMG
+        assert grad_rel(grad[c], gref[0]) <= TOL_GRAD, (c, grad[c], gref[0])
+        assert abs(loss[c] - L[0]) <= 1e-4 * abs(L[0])
+
+
+def test_moco_back_projection_full_size():
+    """256^3, 360 views of 512^2 at 0.6 mm, per-view smooth motion, FDK
+    weight: back-projection at 3000 sampled voxels and the pose gradient of
+    6 sampled views, from one full-size launch each."""
+    rng = np.random.default_rng(1003)
+    g = synth.Geometry(256, 256, 256, 0.8, 0.8, 0.8, 512, 512,
+                       synth.circular_views(360, synth.SAD, synth.SDD, 0.6, 0.6), 0.4)
+    motion = f32(synth.smooth_motion(rng, 360, 2.0, 3.0))
+    img = f32(rng.uniform(0.0, 1.0, (360, 512, 512)))
+    wvol = f32(rng.standard_normal((256, 256, 256)))
+    P = pb.Projector(g, n_pose=360, inst_view=np.arange(360), inst_pose=np.arange(360),
+                     ops=pb.PROJ_OP_BACK | pb.PROJ_OP_BACK_GRAD)
+    vol = P.back(img, motion, pb.PROJ_W_FDK).cpu().numpy()
+    grad = P.back_pose_grad(img, motion, wvol, pb.PROJ_W_FDK).cpu().numpy()
+    vox = np.stack([rng.integers(0, 256, 3000), rng.integers(0, 256, 3000), rng.integers(0, 256, 3000)], axis=1)
+    ref = oracle.back_voxels(g, img, motion.astype(np.float64), vox, np.arange(360), np.arange(360),
+                             weight=oracle.W_FDK)
+    assert rel(vol[vox[:, 2], vox[:, 1], vox[:, 0]], ref) <= TOL_IMG
+    views = np.array([0, 77, 151, 200, 299, 359])
+    gref, _ = oracle.back_grad(g, img[views], motion[views].astype(np.float64), wvol.astype(np.float64),
+                               inst_view=views, inst_pose=np.arange(len(views)), weight=oracle.W_FDK)
+    for i, v in enumerate(views):
+        assert grad_rel(grad[v], gref[i]) <= TOL_GRAD, (v, grad[v], gref[i])
+
+
+def test_calibration_forward_full_size():
+    """512^3 at 0.5 mm, 720 views of 768^2 at 0.556 mm, per-view pose
+    noise: forward projection of 2000 sampled pixels and the residual
+    pose gradient of one view, from full-size launches."""
+    rng = np.random.default_rng(1004)
+    base = synth.workload_registration(seed=1004, n_cand=1, nvox=256, ndet=8, vox=1.0)["mu"]
+    mu = f32(np.repeat(np.repeat(np.repeat(base, 2, 0), 2, 1), 2, 2))
+    g = synth.Geometry(512, 512, 512, 0.5, 0.5, 0.5, 768, 768,
+                       synth.circular_views(720, synth.SAD, synth.SDD, 0.556, 0.556), 0.25)
+    poses = np.zeros((720, 6))
+    poses[:, :3] = rng.normal(0.0, 1.0, (720, 3))
+    poses[:, 3:] = np.deg2rad(rng.normal(0.0, 0.5, (720, 3)))
+    poses = f32(poses)
+    P = pb.Projector(g, n_pose=720, inst_view=np.arange(720), inst_pose=np.arange(720),
+                     ops=pb.PROJ_OP_FORWARD | pb.PROJ_OP_FORWARD_GRAD)
+    P.set_volume(mu)
+    proj = P.forward(poses).cpu().numpy()
+    pix = np.stack([rng.integers(0, 720, 2000), rng.integers(0, 768, 2000), rng.integers(0, 768, 2000)], axis=1)
+    ref = oracle.forward_pixels(g, mu.astype(np.float64), poses.astype(np.float64), pix, np.arange(720),
+                                np.arange(720))
+    assert rel(proj[pix[:, 0], pix[:, 2], pix[:, 1]], ref) <= TOL_IMG
+    del proj
+    resid = rng.standard_normal((720, 768, 768), dtype=np.float32)
+    grad, _ = P.forward_pose_grad(poses, pb.PROJ_LOSS_RESIDUAL, resid)
+    grad = grad.cpu().numpy()
+    v = 123
+    gref, _ = oracle.forward_grad(g, mu.astype(np.float64), poses[v].astype(np.float64),
+                                  resid[v:v + 1].astype(np.float64), inst_view=[v], inst_pose=[0])
+    assert grad_rel(grad[v], gref[0]) <= TOL_GRAD, (grad[v], gref[0])

@@ -285,3 +285,19 @@ def test_golden_forward_regression():
     p = oracle.forward(g, data["mu"], data["poses"], inst_view=data["inst_view"],
                        inst_pose=data["inst_pose"])
     np.testing.assert_allclose(p, data["proj"], rtol=1e-12, atol=1e-14)
+
+
+def test_analytic_gradient_is_continuous_across_the_box_face():
+    """The interpolated central-difference volume gradient lives on
+    (-2, n+1)^3: a ray moving across the face of the volume's box changes
+    the analytic forward gradient continuously."""
+    mu = np.ones((3, 3, 3))
+    view = np.array([-800.0, 0.0, 0.0, 400.0, 0.0, 0.0, 0, 1.0, 0, 0, 0, 1.0])
+    g = synth.Geometry(3, 3, 3, 1.0, 1.0, 1.0, 1, 1, view[None, :], 0.5)
+    w = np.ones((1, 1, 1))
+    vals = []
+    for ty in (1.999, 2.001):      # the ray passes at index y = 1 - ty, near the face y = -1
+        gth, _ = oracle.forward_grad(g, mu, np.array([0, ty, 0, 0, 0, 0.0]), w, mode=oracle.GRAD_ANALYTIC)
+        vals.append(gth[0])
+    assert abs(vals[0][1]) > 0.1
+    assert np.linalg.norm(vals[0] - vals[1]) < 1e-2 * np.linalg.norm(vals[0])
