@@ -40,7 +40,7 @@ L2_FLUSH_BYTES = 256 << 20
 # ncu capture of the 8-instance case (profiles/k_forward_grad_ncc_...md,
 # 1.934 GB) scaled by 128/8 instances, since every instance re-streams the
 # volume.  Set to None whenever the kernel changes until it is re-measured.
-TRAFFIC_PER_LAUNCH = 30.9e9
+TRAFFIC_PER_LAUNCH = None
 
 
 def parse():
