@@ -239,9 +239,9 @@ int proj_kernel_time_ms(proj_plan plan, float *ms);
  * neither a plan nor a workspace.  The caller passes only inputs and outputs;
  * the geometry and instance maps are host data as in proj_plan_create.  All
  * scratch (tables, the prepared (mu, grad mu) volume, reduction records) is
- * one static device array of 5.6 MiB inside the library, which every GPU that
+ * one static device array of 6.2 MiB inside the library, which every GPU that
  * loads the library keeps until the process exits.
- *   Limits: (nx+4)(ny+4)(nz+4) <= 68^3 (a 64^3 volume), n_inst, n_pose and
+ *   Limits: pitched (mu, grad mu) volume of at most 74 x 70 x 68 (a 64^3 volume), n_inst, n_pose and
  *   n_views <= 64 each, n_inst x ceil(nu/16) x ceil(nv/16) <= 4096;
  *   larger sizes return PROJ_E_ARG with a message saying which limit.
  *   d_mu   [nz][ny][nx] FP32; d_pose, loss, d_ref, d_grad, d_loss as in

@@ -136,7 +136,9 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   if (G.nx < 1 || G.ny < 1 || G.nz < 1) return fail(PROJ_E_ARG, "volume size %d x %d x %d", G.nx, G.ny, G.nz);
   if (G.nu < 1 || G.nv < 1) return fail(PROJ_E_ARG, "detector size %d x %d", G.nu, G.nv);
   const long long npad = (long long)(G.nx + 2) * (G.ny + 2) * (G.nz + 2);
-  const long long npad2 = (long long)(G.nx + 4) * (G.ny + 4) * (G.nz + 4);
+  int qx, qy, qz;
+  volume_pitches(G.nx, G.ny, G.nz, &qx, &qy, &qz);
+  const long long npad2 = (long long)qx * qy * qz;
   if (npad2 >= (1LL << 31)) return fail(PROJ_E_ARG, "volume too large (padded voxel count %lld >= 2^31)", npad2);
   if ((long long)(G.nu + 4) * (G.nv + 4) >= (1LL << 31)) return fail(PROJ_E_ARG, "detector too large");
   if (!finite_pos(G.vx) || !finite_pos(G.vy) || !finite_pos(G.vz))
@@ -182,9 +184,7 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   g.px = G.nx + 2;
   g.py = G.ny + 2;
   g.pz = G.nz + 2;
-  g.qx = G.nx + 4;
-  g.qy = G.ny + 4;
-  g.qz = G.nz + 4;
+  volume_pitches(G.nx, G.ny, G.nz, &g.qx, &g.qy, &g.qz);
   g.vx = (float)G.vx;
   g.vy = (float)G.vy;
   g.vz = (float)G.vz;

@@ -48,7 +48,7 @@ static_assert(sizeof(PoseTable) % 8 == 0, "PoseTable layout");
 struct Geo {
   int nx, ny, nz;       // voxels
   int px, py, pz;       // sizes with a 1-voxel border (n + 2): the mu copy
-  int qx, qy, qz;       // sizes with a 2-voxel border (n + 4): the (mu, grad mu) volume
+  int qx, qy, qz;       // pitches of the (mu, grad mu) volume (2-voxel border, >= n + 4)
   float vx, vy, vz;     // voxel pitch, mm
   float hx, hy, hz;     // half extent of the open box (-1, n) in centred index units: (n+1)/2
   float gx, gy, gz;     // half extent of the gradient box (-2, n+1): (n+3)/2
@@ -106,6 +106,21 @@ cudaError_t launch_back_grad(const InstTable* d_inst, int n_inst, Geo geo, int w
 cudaError_t launch_back_grad_reduce(const PoseTable* d_ptab, int n_pose, const int* d_pose_ptr,
                                     const int* d_pose_idx, int n_inst, int n_blocks, Geo geo, const float* d_part,
                                     float* d_grad, cudaStream_t s);
+
+// Row and slice pitches (in float4 elements) of the (mu, grad mu) volume:
+// at least n + 4 (2-voxel border), with qx = 2 (mod 8) and qx * qy = 4
+// (mod 8), so the four (y, z) rows of a trilinear cell start 0, 32, 64 and
+// 96 bytes into their 128-byte lines and a warp's corner gathers spread over
+// all L1 data banks.  (Pitches that are whole lines cost up to 1.9x.)
+inline void volume_pitches(int nx, int ny, int nz, int* qx, int* qy, int* qz) {
+  int x = nx + 4;
+  while (x % 8 != 2) ++x;
+  int y = ny + 4;
+  while ((x * y) % 8 != 4) ++y;
+  *qx = x;
+  *qy = y;
+  *qz = nz + 4;
+}
 
 // Sets the calling thread's message returned by proj_last_error().
 void record_error(const char* msg);

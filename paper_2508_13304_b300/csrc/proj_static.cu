@@ -22,7 +22,7 @@ using namespace projk;
 namespace {
 
 // Limits of the static scratch (see include/proj.h).
-constexpr int kMaxPadVoxels = 68 * 68 * 68;  // (nx+4)(ny+4)(nz+4): a 64^3 volume
+constexpr int kMaxPadVoxels = 74 * 70 * 68;  // pitched (mu, grad mu) volume of a 64^3 grid
 constexpr int kMaxInst = 64;
 constexpr int kMaxPose = 64;
 constexpr int kMaxViews = 64;
@@ -40,7 +40,7 @@ constexpr size_t kOffPtab = al(kOffInst + sizeof(InstTable) * kMaxInst);
 constexpr size_t kOffVol4 = al(kOffPtab + sizeof(PoseTable) * kMaxPose);
 constexpr size_t kOffPart = al(kOffVol4 + sizeof(float4) * (size_t)kMaxPadVoxels);
 constexpr size_t kScratchBytes = al(kOffPart + sizeof(float) * kRec * (size_t)kMaxRecords);
-static_assert(kScratchBytes <= (6u << 20), "static scratch is documented as under 6 MiB");
+static_assert(kScratchBytes <= (6.5 * (1 << 20)), "static scratch is documented as 6.2 MiB");
 
 // The scratch itself.  In host code this name is only a host-side stand-in;
 // its device address comes from cudaGetSymbolAddress (per device).
@@ -103,11 +103,13 @@ int proj_forward_pose_grad_static(const proj_geometry* geom, int n_pose, int n_i
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(G.vol_offset[a])) return fail(PROJ_E_ARG, "volume offset must be finite");
   // Size limits of the static scratch.
-  const long long npad = (long long)(G.nx + 4) * (G.ny + 4) * (G.nz + 4);
+  int pqx, pqy, pqz;
+  volume_pitches(G.nx, G.ny, G.nz, &pqx, &pqy, &pqz);
+  const long long npad = (long long)pqx * pqy * pqz;
   const long long n_tiles = (long long)ceil_div(G.nu, kTileU) * ceil_div(G.nv, kTileV);
   if (npad > kMaxPadVoxels)
-    return fail(PROJ_E_ARG, "volume %d x %d x %d exceeds the static scratch limit ((nx+4)(ny+4)(nz+4) <= 68^3)", G.nx,
-                G.ny, G.nz);
+    return fail(PROJ_E_ARG, "volume %d x %d x %d exceeds the static scratch limit (%lld padded voxels > %d)", G.nx,
+                G.ny, G.nz, npad, kMaxPadVoxels);
   if (n_inst > kMaxInst || n_pose > kMaxPose || G.n_views > kMaxViews)
     return fail(PROJ_E_ARG, "n_inst %d, n_pose %d, n_views %d exceed the static scratch limit of %d each", n_inst,
                 n_pose, G.n_views, kMaxInst);
@@ -149,9 +151,7 @@ int proj_forward_pose_grad_static(const proj_geometry* geom, int n_pose, int n_i
   g.px = G.nx + 2;
   g.py = G.ny + 2;
   g.pz = G.nz + 2;
-  g.qx = G.nx + 4;
-  g.qy = G.ny + 4;
-  g.qz = G.nz + 4;
+  volume_pitches(G.nx, G.ny, G.nz, &g.qx, &g.qy, &g.qz);
   g.vx = (float)G.vx;
   g.vy = (float)G.vy;
   g.vz = (float)G.vz;
