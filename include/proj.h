@@ -189,6 +189,16 @@ int proj_forward_pose_grad(proj_plan plan, const float *d_pose, int loss, const 
 int proj_back(proj_plan plan, const float *d_proj, const float *d_pose, int weight, float *d_vol, void *d_ws,
               size_t ws_bytes, proj_stream stream);
 
+/* Exact transpose of proj_back (the projection-side gradient of a
+ * back-projection, for autograd): each voxel value is spread, times W, over
+ * the 4 bilinear corners of its projection in every instance.
+ *   d_vol   [nz][ny][nx] FP32 (dL/dmu).
+ *   weight  PROJ_W_NONE or PROJ_W_FDK (FDK_CONST behaves as FDK).
+ *   d_proj  out [n_inst][nv][nu] FP32 (zeroed, then accumulated with float
+ *           atomics: the last bits depend on the order). */
+int proj_back_adjoint(proj_plan plan, const float *d_vol, const float *d_pose, int weight, float *d_proj, void *d_ws,
+                      size_t ws_bytes, proj_stream stream);
+
 /* Pose gradient of an image-domain loss through the back-projector
  * (Eqs. back_derive, final_back, back_int, dis_back): grad_d l by central
  * differences of each image interpolated at the projected voxel, the

@@ -59,6 +59,7 @@ _SIGS = {
     "proj_forward_pose_grad": [_P, _P, _I, _P, _P, _P, _P, _P, _SZ, _P],
     "proj_back": [_P, _P, _P, _I, _P, _P, _SZ, _P],
     "proj_back_pose_grad": [_P, _P, _P, _I, _P, _P, _P, _SZ, _P],
+    "proj_back_adjoint": [_P, _P, _P, _I, _P, _P, _SZ, _P],
     "proj_forward_adjoint": [_P, _P, _P, _P, _P, _SZ, _P],
     "proj_check": [_P, _P, _SZ, _P, ctypes.POINTER(_I)],
     "proj_count_samples": [_P, _P, _P, _P, _SZ, _P],
@@ -230,6 +231,15 @@ def proj_back(plan: Plan, proj, pose, weight, vol, ws, stream=None):
                            _ptr(vol, torch.float32, plan.vol_numel, "vol"), p, nb, _stream(stream)))
 
 
+def proj_back_adjoint(plan: Plan, vol, pose, weight, proj, ws, stream=None):
+    import torch
+    p, nb = _ws(ws)
+    _check(lib().proj_back_adjoint(plan.handle, _ptr(vol, torch.float32, plan.vol_numel, "vol"),
+                                   _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"), int(weight),
+                                   _ptr(proj, torch.float32, plan.n_inst * plan.img_numel, "proj"), p, nb,
+                                   _stream(stream)))
+
+
 def proj_back_pose_grad(plan: Plan, proj, pose, weight, vol_resid, grad, ws, stream=None):
     import torch
     p, nb = _ws(ws)
@@ -351,6 +361,13 @@ class Projector:
         grad = torch.empty((self.plan.n_pose, 6), device=self.device)
         proj_back_pose_grad(self.plan, self._t(proj), self._t(pose), weight, self._t(vol_resid), grad, self.ws)
         return grad
+
+    def back_adjoint(self, vol, pose, weight=PROJ_W_NONE):
+        import torch
+        g = self.geom
+        out = torch.empty((self.n_inst, g.nv, g.nu), device=self.device)
+        proj_back_adjoint(self.plan, self._t(vol), self._t(pose), weight, out, self.ws)
+        return out
 
     def forward_adjoint(self, y, pose):
         import torch

@@ -373,6 +373,25 @@ int proj_back(proj_plan p, const float* d_proj, const float* d_pose, int weight,
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "back-projection launch");
 }
 
+int proj_back_adjoint(proj_plan p, const float* d_vol, const float* d_pose, int weight, float* d_proj, void* d_ws,
+                      size_t ws_bytes, proj_stream stream) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_vol || !d_pose || !d_proj) return fail(PROJ_E_ARG, "proj_back_adjoint: NULL argument");
+  if (weight != PROJ_W_NONE && weight != PROJ_W_FDK && weight != PROJ_W_FDK_CONST)
+    return fail(PROJ_E_ARG, "unknown weight %d", weight);
+  int rc = need_op(p, PROJ_OP_BACK, "proj_back_adjoint");
+  if (rc) return rc;
+  WsView w;
+  if ((rc = check_ws(p, d_ws, ws_bytes, &w))) return rc;
+  if ((rc = check_device(p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = setup(p, d_pose, w, s))) return rc;
+  mark(p, true, s);
+  cudaError_t e = launch_back_adjoint(w.inst, p->n_inst, p->geo, weight, d_vol, d_proj, s);
+  mark(p, false, s);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "back-projection adjoint launch");
+}
+
 int proj_back_pose_grad(proj_plan p, const float* d_proj, const float* d_pose, int weight, const float* d_vol_resid,
                         float* d_grad, void* d_ws, size_t ws_bytes, proj_stream stream) {
   if (!p) return fail(PROJ_E_ARG, "plan is NULL");

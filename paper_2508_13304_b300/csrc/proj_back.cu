@@ -261,6 +261,56 @@ __global__ void k_back_grad_reduce(const PoseTable* __restrict__ ptab, const int
   }
 }
 
+// ---------------------------------------------------------------- K8
+// Exact transpose of k_back: each voxel spreads W * y_j over the 4 bilinear
+// corners (inside the image) of its projection in every instance.  Output
+// zeroed by the launcher; float atomics (order-dependent in the last bits).
+__global__ void __launch_bounds__(kBpThreads) k_back_adjoint(const InstTable* __restrict__ inst, int n_inst, Geo g,
+                                                             int weight, const float* __restrict__ y,
+                                                             float* __restrict__ proj) {
+  const int ix = blockIdx.x * kBpX + (threadIdx.x & 31);
+  const int iy = blockIdx.y * kBpY + (threadIdx.x >> 5);
+  const int iz0 = blockIdx.z * kZChunk;
+  if (ix >= g.nx || iy >= g.ny) return;
+  const float fx = (float)ix - g.cx, fy = (float)iy - g.cy;
+  float yv[kZChunk];
+#pragma unroll
+  for (int z = 0; z < kZChunk; ++z)
+    yv[z] = (iz0 + z < g.nz) ? __ldg(y + ((size_t)(iz0 + z) * g.ny + iy) * g.nx + ix) : 0.f;
+  const float fu = (float)g.nu, fvv = (float)g.nv;
+  for (int n = 0; n < n_inst; ++n) {
+    const InstTable& T = inst[n];
+    if (!T.valid) continue;
+    const float bu = fmaf(T.Q[3], fy, fmaf(T.Q[0], fx, T.Q[9]));
+    const float bv = fmaf(T.Q[4], fy, fmaf(T.Q[1], fx, T.Q[10]));
+    const float bw = fmaf(T.Q[5], fy, fmaf(T.Q[2], fx, T.Q[11]));
+    float* img = proj + (size_t)n * g.nu * g.nv;
+#pragma unroll
+    for (int z = 0; z < kZChunk; ++z) {
+      if (yv[z] == 0.f) continue;
+      const float fz = (float)(iz0 + z) - g.cz;
+      const float hw = fmaf(T.Q[8], fz, bw);
+      if (!(hw > 0.f)) continue;
+      const float rw = 1.0f / hw;
+      const float u = fmaf(T.Q[6], fz, bu) * rw, v = fmaf(T.Q[7], fz, bv) * rw;
+      if (!(u > -1.f && u < fu && v > -1.f && v < fvv)) continue;
+      const float flu = floorf(u), flv = floorf(v);
+      const int i0 = (int)flu, j0 = (int)flv;
+      const float au = u - flu, av = v - flv;
+      float val = yv[z];
+      if (weight != PROJ_W_NONE) {
+        const float r = T.w0 * rw;
+        val *= r * r;
+      }
+      const int o = j0 * g.nu + i0;
+      if (i0 >= 0 && j0 >= 0) atomicAdd(img + o, val * (1.f - au) * (1.f - av));
+      if (i0 < g.nu - 1 && j0 >= 0) atomicAdd(img + o + 1, val * au * (1.f - av));
+      if (i0 >= 0 && j0 < g.nv - 1) atomicAdd(img + o + g.nu, val * (1.f - au) * av);
+      if (i0 < g.nu - 1 && j0 < g.nv - 1) atomicAdd(img + o + g.nu + 1, val * au * av);
+    }
+  }
+}
+
 int elementwise_grid(long long n) {
   long long b = (n + 255) / 256;
   return (int)(b < 148LL * 64 ? (b < 1 ? 1 : b) : 148LL * 64);
@@ -278,6 +328,15 @@ cudaError_t launch_back(const InstTable* d_inst, int n_inst, Geo geo, int weight
                         float* d_vol, cudaStream_t s) {
   dim3 grid(ceil_div(geo.nx, kBpX), ceil_div(geo.ny, kBpY), ceil_div(geo.nz, kZChunk));
   k_back<<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_proj, d_vol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_back_adjoint(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float* d_y,
+                                float* d_proj, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(d_proj, 0, sizeof(float) * (size_t)n_inst * geo.nu * geo.nv, s);
+  if (e != cudaSuccess) return e;
+  dim3 grid(ceil_div(geo.nx, kBpX), ceil_div(geo.ny, kBpY), ceil_div(geo.nz, kZChunk));
+  k_back_adjoint<<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_y, d_proj);
   return cudaGetLastError();
 }
 

@@ -101,6 +101,8 @@ cudaError_t launch_forward_adjoint(const InstTable* d_inst, int n_inst, Geo geo,
 cudaError_t launch_detector_prep(const float* d_proj, int n_inst, Geo geo, float4* d_det4, cudaStream_t s);
 cudaError_t launch_back(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float* d_proj,
                         float* d_vol, cudaStream_t s);
+cudaError_t launch_back_adjoint(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float* d_y,
+                                float* d_proj, cudaStream_t s);
 cudaError_t launch_back_grad(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float4* d_det4,
                              const float* d_wvol, float* d_part, int n_blocks, cudaStream_t s);
 cudaError_t launch_back_grad_reduce(const PoseTable* d_ptab, int n_pose, const int* d_pose_ptr,

@@ -116,6 +116,7 @@ def test_bad_ops_and_null_arguments(L):
     assert L.proj_forward_pose_grad(None, None, 0, None, None, None, None, None, 0, None) == pb.PROJ_E_ARG
     assert L.proj_back(None, None, None, 0, None, None, 0, None) == pb.PROJ_E_ARG
     assert L.proj_back_pose_grad(None, None, None, 0, None, None, None, 0, None) == pb.PROJ_E_ARG
+    assert L.proj_back_adjoint(None, None, None, 0, None, None, 0, None) == pb.PROJ_E_ARG
     assert L.proj_forward_adjoint(None, None, None, None, None, 0, None) == pb.PROJ_E_ARG
     assert L.proj_set_volume(None, None, None, 0, None) == pb.PROJ_E_ARG
     assert L.proj_check(None, None, 0, None, None) == pb.PROJ_E_ARG

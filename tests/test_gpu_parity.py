@@ -154,6 +154,16 @@ def test_forward_adjoint_ragged(ragged):
     assert abs(np.sum(ax * y) - np.sum(x * got)) <= 1e-4 * np.linalg.norm(ax) * np.linalg.norm(y)
 
 
+@pytest.mark.parametrize("weight", [pb.PROJ_W_NONE, pb.PROJ_W_FDK])
+def test_back_adjoint_ragged(ragged, weight):
+    d = ragged
+    g = d["g"]
+    x = f32(np.random.default_rng(10).standard_normal(g.vol_shape))
+    ref = oracle.back_adjoint(g, x, d["poses"], d["iv"], d["ip"], weight=weight)
+    got = np32(d["P"].back_adjoint(x, d["poses"], weight))
+    assert rel_l2(got, ref) <= TOL_IMG
+
+
 # --------------------------------------------------------------- edge cases
 
 def test_non_finite_pose_sets_status_and_zero_gradient(ragged):
