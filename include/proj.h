@@ -112,7 +112,8 @@ enum {
   PROJ_OP_BACK = 4,
   PROJ_OP_BACK_GRAD = 8,
   PROJ_OP_ADJOINT = 16,
-  PROJ_OP_ALL = 31
+  PROJ_OP_SHARPNESS = 32,
+  PROJ_OP_ALL = 63
 };
 
 /* Device status bits (proj_check). */
@@ -217,6 +218,30 @@ int proj_back_pose_grad(proj_plan plan, const float *d_proj, const float *d_pose
  *   d_vol  out [nz][ny][nx] FP32. */
 int proj_forward_adjoint(proj_plan plan, const float *d_y, const float *d_pose, float *d_vol, void *d_ws,
                          size_t ws_bytes, proj_stream stream);
+
+/* FDK filtering of one image per instance (the "Ramp(l)" of the motion-
+ * compensated reconstruction experiment, Sec. II-D.3): each pixel is
+ * multiplied by the cosine weight SAD / sqrt(SAD^2 + a^2 + b^2) ((a, b): its
+ * offset from the principal point on the isocentre plane, SAD: distance from
+ * the source to that plane), then every row is convolved with the Ram-Lak
+ * ramp kernel (h[0] = 1/4, h[k] = -1/(pi k)^2 for odd k, 0 for even k, in
+ * units of 1/du^2, du the pixel pitch on the isocentre plane) with zero
+ * padding, times du and times scale (e.g. pi / n_views for a full circular
+ * scan, so that proj_back with PROJ_W_FDK then gives the FDK
+ * reconstruction).  Assumes orthogonal pixel axes.
+ *   d_proj  [n_inst][nv][nu] FP32; d_out  out, same shape, must not alias.
+ * Uses no workspace. */
+int proj_fdk_filter(proj_plan plan, const float *d_proj, float scale, float *d_out, proj_stream stream);
+
+/* Image sharpness S = -Var(|grad mu|) over all voxels (|grad mu| from
+ * central differences of the zero-padded volume, per mm; the variance uses
+ * the population mean) and, when d_grad is not NULL, dS/dmu (exact
+ * derivative of that expression; voxels with |grad mu| < 1e-12 contribute
+ * no direction).  Needs PROJ_OP_SHARPNESS.
+ *   d_vol  [nz][ny][nx] FP32; d_loss  out, 1 float; d_grad  out [nz][ny][nx]
+ *          or NULL.  The moments are summed in FP64 in a fixed order. */
+int proj_sharpness(proj_plan plan, const float *d_vol, float *d_loss, float *d_grad, void *d_ws, size_t ws_bytes,
+                   proj_stream stream);
 
 /* Synchronise the stream, read and clear the workspace status word.
  * *status receives the PROJ_STATUS_* bits (may be NULL).  Returns PROJ_OK,

@@ -227,6 +227,90 @@ def back_voxels(geom, proj, poses, vox, inst_view=None, inst_pose=None, weight=W
     return out
 
 
+# ------------------------------------------------------- FDK and sharpness
+
+def ramlak_taps(n):
+    """Ram-Lak ramp kernel h[k], k = -(n-1)..(n-1), in units of 1/du^2:
+    1/4 at 0, -1/(pi k)^2 at odd k, 0 at even k != 0."""
+    k = np.arange(-(n - 1), n)
+    h = np.zeros(k.shape)
+    h[k == 0] = 0.25
+    odd = (k % 2) != 0
+    h[odd] = -1.0 / (np.pi * k[odd]) ** 2
+    return k, h
+
+
+def fdk_constants(view, nu, nv):
+    """SAD (source to the isocentre plane parallel to the detector), pixel
+    pitches on that plane and the principal point in pixel indices."""
+    s, c, U, V = view[0:3], view[3:6], view[6:9], view[9:12]
+    n = np.cross(U, V)
+    n = n / np.linalg.norm(n)
+    if np.dot(c - s, n) < 0:
+        n = -n
+    sdd = np.dot(c - s, n)
+    sad = np.dot(-s, n)
+    P = projection_matrix(view, nu, nv)
+    h = P[:, :3] @ (s + n) + P[:, 3]
+    return sad, np.linalg.norm(U) * sad / sdd, np.linalg.norm(V) * sad / sdd, h[0] / h[2], h[1] / h[2]
+
+
+def fdk_filter(geom, proj, inst_view, scale):
+    """Cosine pre-weight and Ram-Lak filtering along detector rows (the
+    Ramp(l) of Sec. II-D.3's motion-compensated reconstruction): per
+    instance, x = l * SAD / sqrt(SAD^2 + a^2 + b^2), q = scale * du * (x conv h),
+    h in units of 1/du^2 (du the pitch on the isocentre plane)."""
+    proj = np.asarray(proj, dtype=np.float64)
+    out = np.zeros_like(proj)
+    nu, nv = geom.nu, geom.nv
+    _, h = ramlak_taps(nu)
+    idx = np.arange(nu)
+    T = h[(idx[:, None] - idx[None, :]) + (nu - 1)]      # T[u, k] = h[u - k]
+    for n, vi in enumerate(inst_view):
+        sad, du, dv, pu, pv = fdk_constants(geom.views[vi], nu, nv)
+        a = (idx - pu) * du
+        b = (np.arange(nv) - pv) * dv
+        w = sad / np.sqrt(sad ** 2 + a[None, :] ** 2 + b[:, None] ** 2)
+        x = proj[n] * w
+        out[n] = scale * du * (x @ T.T) / du ** 2
+    return out
+
+
+def _central(mu, vox):
+    m = np.pad(np.asarray(mu, dtype=np.float64), 1)
+    gz = (m[2:, 1:-1, 1:-1] - m[:-2, 1:-1, 1:-1]) / (2 * vox[2])
+    gy = (m[1:-1, 2:, 1:-1] - m[1:-1, :-2, 1:-1]) / (2 * vox[1])
+    gx = (m[1:-1, 1:-1, 2:] - m[1:-1, 1:-1, :-2]) / (2 * vox[0])
+    return gx, gy, gz
+
+
+def sharpness(mu, vox):
+    """S = -Var(|grad mu|) with central differences of the zero-padded
+    volume (per mm) and the population variance over all voxels."""
+    gx, gy, gz = _central(mu, vox)
+    m = np.sqrt(gx * gx + gy * gy + gz * gz)
+    return float(-(np.mean(m * m) - np.mean(m) ** 2))
+
+
+def sharpness_grad(mu, vox):
+    """dS/dmu by the chain rule through m_i = |g(i)| and the central
+    differences; voxels with m_i < 1e-12 contribute no direction."""
+    gx, gy, gz = _central(mu, vox)
+    m = np.sqrt(gx * gx + gy * gy + gz * gz)
+    N = m.size
+    safe = np.where(m >= 1e-12, m, 1.0)
+    coef = np.where(m >= 1e-12, (m - m.mean()) / safe, 0.0) * (-2.0 / N)
+    grad = np.zeros(m.shape)
+    for g_a, axis, h in ((gx, 2, vox[0]), (gy, 1, vox[1]), (gz, 0, vox[2])):
+        c = np.pad(coef * g_a / (2 * h), 1)          # dS/dg_a(i) / (2 v_a), zero outside
+        sl_minus = [slice(1, -1)] * 3
+        sl_plus = [slice(1, -1)] * 3
+        sl_minus[axis] = slice(0, -2)                 # neighbour i = j - e_a: g_a(i) has +mu_j
+        sl_plus[axis] = slice(2, None)                # neighbour i = j + e_a: g_a(i) has -mu_j
+        grad += c[tuple(sl_minus)] - c[tuple(sl_plus)]
+    return grad
+
+
 # ------------------------------------------------------------------ losses
 
 def l2_loss(a, b):

@@ -25,7 +25,8 @@ PROJ_OK, PROJ_E_ARG, PROJ_E_CUDA, PROJ_E_WORKSPACE, PROJ_E_UNSUPPORTED, PROJ_E_D
 PROJ_LOSS_RESIDUAL, PROJ_LOSS_L2, PROJ_LOSS_NCC = 0, 1, 2
 PROJ_W_NONE, PROJ_W_FDK, PROJ_W_FDK_CONST = 0, 1, 2
 PROJ_OP_FORWARD, PROJ_OP_FORWARD_GRAD, PROJ_OP_BACK, PROJ_OP_BACK_GRAD, PROJ_OP_ADJOINT = 1, 2, 4, 8, 16
-PROJ_OP_ALL = 31
+PROJ_OP_SHARPNESS = 32
+PROJ_OP_ALL = 63
 PROJ_STATUS_BAD_POSE = 1
 
 
@@ -65,6 +66,8 @@ _SIGS = {
     "proj_count_samples": [_P, _P, _P, _P, _SZ, _P],
     "proj_forward_pose_grad_static": [ctypes.POINTER(proj_geometry), _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                                       _P, _P, _I, _P, _P, _P, _P],
+    "proj_fdk_filter": [_P, _P, ctypes.c_float, _P, _P],
+    "proj_sharpness": [_P, _P, _P, _P, _P, _SZ, _P],
     "proj_enable_kernel_timing": [_P, _I],
     "proj_kernel_time_ms": [_P, ctypes.POINTER(ctypes.c_float)],
     "proj_last_error": [],
@@ -296,6 +299,22 @@ def proj_forward_pose_grad_static(geom, n_pose, inst_view, inst_pose, mu, pose, 
         _ptr(loss_out, torch.float32, int(n_pose), "loss", allow_none=True), _stream(stream)))
 
 
+def proj_fdk_filter(plan: Plan, proj, scale, out, stream=None):
+    import torch
+    n = plan.n_inst * plan.img_numel
+    _check(lib().proj_fdk_filter(plan.handle, _ptr(proj, torch.float32, n, "proj"), float(scale),
+                                 _ptr(out, torch.float32, n, "out"), _stream(stream)))
+
+
+def proj_sharpness(plan: Plan, vol, loss, grad=None, ws=None, stream=None):
+    import torch
+    p, nb = _ws(ws)
+    _check(lib().proj_sharpness(plan.handle, _ptr(vol, torch.float32, plan.vol_numel, "vol"),
+                                _ptr(loss, torch.float32, 1, "loss"),
+                                _ptr(grad, torch.float32, plan.vol_numel, "grad", allow_none=True), p, nb,
+                                _stream(stream)))
+
+
 def proj_enable_kernel_timing(plan: Plan, enable=True):
     _check(lib().proj_enable_kernel_timing(plan.handle, 1 if enable else 0))
 
@@ -375,6 +394,19 @@ class Projector:
         vol = torch.empty((g.nz, g.ny, g.nx), device=self.device)
         proj_forward_adjoint(self.plan, self._t(y), self._t(pose), vol, self.ws)
         return vol
+
+    def fdk_filter(self, proj, scale):
+        import torch
+        out = torch.empty((self.n_inst, self.geom.nv, self.geom.nu), device=self.device)
+        proj_fdk_filter(self.plan, self._t(proj), scale, out)
+        return out
+
+    def sharpness(self, vol, want_grad=True):
+        import torch
+        loss = torch.empty((1,), device=self.device)
+        grad = torch.empty((self.geom.nz, self.geom.ny, self.geom.nx), device=self.device) if want_grad else None
+        proj_sharpness(self.plan, self._t(vol), loss, grad, self.ws)
+        return (loss, grad) if want_grad else loss
 
     def count_samples(self, pose):
         import torch

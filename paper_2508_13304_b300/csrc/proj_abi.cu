@@ -53,12 +53,13 @@ struct proj_plan_s {
   int* d_inst_pose = nullptr;
   int* d_pose_ptr = nullptr;
   int* d_pose_idx = nullptr;
+  FdkView* d_fdk = nullptr;  // per instance
   // optional timing of the main kernel of each call
   bool timing = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // workspace layout (byte offsets; 0 = buffer absent, the status word sits at 0)
   size_t off_status = 0, off_inst = 0, off_ptab = 0, off_vol1 = 0, off_vol4 = 0, off_part_f = 0, off_det4 = 0,
-         off_part_b = 0, off_acc = 0, ws_bytes = 0;
+         off_part_b = 0, off_acc = 0, off_sharp_m = 0, off_sharp_part = 0, ws_bytes = 0;
 };
 
 namespace {
@@ -249,13 +250,58 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   p->off_det4 = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float4) * (size_t)n_inst * (G.nu + 4) * (G.nv + 4)) : 0;
   p->off_part_b = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float) * 12 * (size_t)n_inst * p->bp_blocks) : 0;
   p->off_acc = (ops & PROJ_OP_ADJOINT) ? take(sizeof(float) * npad_sz) : 0;
+  if (ops & PROJ_OP_SHARPNESS) {
+    p->off_sharp_m = take(sizeof(float) * (size_t)G.nx * G.ny * G.nz);
+    p->off_sharp_part = take(sizeof(double) * (2 * (size_t)sharpness_blocks(g) + 2));
+  }
   p->ws_bytes = off;
+
+  // FDK constants per instance (FP64 on the host).
+  std::vector<FdkView> fdk(n_inst);
+  for (int i = 0; i < n_inst; ++i) {
+    const double* w = G.views + 12 * inst_view[i];
+    const double *sv = w, *cv = w + 3, *U = w + 6, *V = w + 9;
+    double nrm[3] = {U[1] * V[2] - U[2] * V[1], U[2] * V[0] - U[0] * V[2], U[0] * V[1] - U[1] * V[0]};
+    const double nl = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+    for (int a = 0; a < 3; ++a) nrm[a] /= nl;
+    double sdd = 0, sad = 0;
+    for (int a = 0; a < 3; ++a) {
+      sdd += (cv[a] - sv[a]) * nrm[a];
+      sad += -sv[a] * nrm[a];
+    }
+    if (sdd < 0) {
+      sdd = -sdd;
+      sad = -sad;
+      for (int a = 0; a < 3; ++a) nrm[a] = -nrm[a];
+    }
+    // principal point: foot of the perpendicular from the source, in pixel
+    // indices (q00 + pu U + pv V, solved in the detector basis)
+    double q00[3], d[3];
+    for (int a = 0; a < 3; ++a) {
+      q00[a] = cv[a] - 0.5 * (G.nu - 1) * U[a] - 0.5 * (G.nv - 1) * V[a];
+      d[a] = sv[a] + sdd * nrm[a] - q00[a];
+    }
+    const double uu = U[0] * U[0] + U[1] * U[1] + U[2] * U[2], vv = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+    const double uvd = U[0] * V[0] + U[1] * V[1] + U[2] * V[2];
+    const double du_ = d[0] * U[0] + d[1] * U[1] + d[2] * U[2], dv_ = d[0] * V[0] + d[1] * V[1] + d[2] * V[2];
+    const double det = uu * vv - uvd * uvd;
+    FdkView f;
+    f.pu = (float)((du_ * vv - dv_ * uvd) / det);
+    f.pv = (float)((dv_ * uu - du_ * uvd) / det);
+    f.sad = (float)sad;
+    f.du = (float)(std::sqrt(uu) * sad / sdd);
+    f.dv = (float)(std::sqrt(vv) * sad / sdd);
+    f.pad[0] = f.pad[1] = f.pad[2] = 0.f;
+    fdk[i] = f;
+  }
 
   e = cudaMalloc(&p->d_views, sizeof(double) * p->views.size());
   if (e == cudaSuccess) e = cudaMalloc(&p->d_inst_view, sizeof(int) * n_inst);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_inst_pose, sizeof(int) * n_inst);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_pose_ptr, sizeof(int) * (n_pose + 1));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_pose_idx, sizeof(int) * n_inst);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_fdk, sizeof(FdkView) * n_inst);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_fdk, fdk.data(), sizeof(FdkView) * n_inst, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(p->d_views, p->views.data(), sizeof(double) * p->views.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_inst_view, inst_view, sizeof(int) * n_inst, cudaMemcpyHostToDevice);
@@ -279,6 +325,7 @@ int proj_plan_destroy(proj_plan p) {
   cudaFree(p->d_inst_pose);
   cudaFree(p->d_pose_ptr);
   cudaFree(p->d_pose_idx);
+  cudaFree(p->d_fdk);
   delete p;
   return PROJ_OK;
 }
@@ -450,6 +497,35 @@ int proj_kernel_time_ms(proj_plan p, float* ms) {
   cudaError_t e = cudaEventSynchronize(p->ev1);
   if (e == cudaSuccess) e = cudaEventElapsedTime(ms, p->ev0, p->ev1);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "kernel timing");
+}
+
+int proj_fdk_filter(proj_plan p, const float* d_proj, float scale, float* d_out, proj_stream stream) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_proj || !d_out) return fail(PROJ_E_ARG, "proj_fdk_filter: NULL argument");
+  if (d_proj == d_out) return fail(PROJ_E_ARG, "proj_fdk_filter: input and output must differ");
+  if (!std::isfinite(scale)) return fail(PROJ_E_ARG, "proj_fdk_filter: scale must be finite");
+  if ((size_t)p->geo.nu * sizeof(float) > 200 * 1024) return fail(PROJ_E_UNSUPPORTED, "detector rows too long");
+  int rc = check_device(p);
+  if (rc) return rc;
+  cudaError_t e = launch_fdk_filter(p->d_fdk, p->n_inst, p->geo, scale, d_proj, d_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "FDK filter launch");
+}
+
+int proj_sharpness(proj_plan p, const float* d_vol, float* d_loss, float* d_grad, void* d_ws, size_t ws_bytes,
+                   proj_stream stream) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_vol || !d_loss) return fail(PROJ_E_ARG, "proj_sharpness: NULL volume or loss");
+  int rc = need_op(p, PROJ_OP_SHARPNESS, "proj_sharpness");
+  if (rc) return rc;
+  WsView w;
+  if ((rc = check_ws(p, d_ws, ws_bytes, &w))) return rc;
+  if ((rc = check_device(p))) return rc;
+  char* b = static_cast<char*>(d_ws);
+  float* m = reinterpret_cast<float*>(b + p->off_sharp_m);
+  double* part = reinterpret_cast<double*>(b + p->off_sharp_part);
+  double* stats = part + 2 * (size_t)sharpness_blocks(p->geo);
+  cudaError_t e = launch_sharpness(d_vol, p->geo, m, part, stats, d_loss, d_grad, (cudaStream_t)stream);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "sharpness launch");
 }
 
 int proj_check(proj_plan p, void* d_ws, size_t ws_bytes, proj_stream stream, int* status) {

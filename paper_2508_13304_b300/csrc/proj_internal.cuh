@@ -58,6 +58,14 @@ struct Geo {
   float step;
 };
 
+// Per-instance constants of FDK filtering: distance from the source to the
+// plane through the isocentre parallel to the detector (sad), pixel pitches
+// on that plane (du, dv) and the principal point in pixel indices (pu, pv).
+struct FdkView {
+  float sad, du, dv, pu, pv;
+  float pad[3];
+};
+
 // Record of one K3 block (ray tile) partial: see kRec* offsets.
 constexpr int kRec = 48;
 constexpr int kRecG = 0;      // 12: sum of w * G   (RESIDUAL, L2)  or sum G (NCC)
@@ -123,6 +131,12 @@ inline void volume_pitches(int nx, int ny, int nz, int* qx, int* qy, int* qz) {
   *qy = y;
   *qz = nz + 4;
 }
+
+cudaError_t launch_fdk_filter(const FdkView* d_fv, int n_inst, Geo geo, float scale, const float* d_proj,
+                              float* d_out, cudaStream_t s);
+int sharpness_blocks(Geo geo);
+cudaError_t launch_sharpness(const float* d_mu, Geo geo, float* d_m, double* d_part, double* d_stats, float* d_loss,
+                             float* d_grad, cudaStream_t s);
 
 // Sets the calling thread's message returned by proj_last_error().
 void record_error(const char* msg);

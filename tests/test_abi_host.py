@@ -107,7 +107,7 @@ def test_instance_indices_are_checked(L, iv, ip, n_pose, msg):
 def test_bad_ops_and_null_arguments(L):
     rc, _ = create(tiny_geom(), ops=0)
     assert rc == pb.PROJ_E_ARG
-    rc, _ = create(tiny_geom(), ops=64)
+    rc, _ = create(tiny_geom(), ops=128)
     assert rc == pb.PROJ_E_ARG
     assert L.proj_plan_create(None, 1, 1, None, None, 1, None) == pb.PROJ_E_ARG
     n = ctypes.c_size_t()
@@ -121,6 +121,8 @@ def test_bad_ops_and_null_arguments(L):
     assert L.proj_set_volume(None, None, None, 0, None) == pb.PROJ_E_ARG
     assert L.proj_check(None, None, 0, None, None) == pb.PROJ_E_ARG
     assert L.proj_count_samples(None, None, None, None, 0, None) == pb.PROJ_E_ARG
+    assert L.proj_fdk_filter(None, None, 1.0, None, None) == pb.PROJ_E_ARG
+    assert L.proj_sharpness(None, None, None, None, None, 0, None) == pb.PROJ_E_ARG
     assert L.proj_enable_kernel_timing(None, 1) == pb.PROJ_E_ARG
     assert L.proj_kernel_time_ms(None, None) == pb.PROJ_E_ARG
     assert L.proj_plan_destroy(None) == pb.PROJ_OK
