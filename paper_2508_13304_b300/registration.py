@@ -47,9 +47,11 @@ def paper_step_sizes():
 
 
 def register(geom, mu, target, init_poses, max_iter=200, lr=None, ncc_stop=0.999, dloss_stop=1e-5,
-             batched=True, device="cuda"):
+             batched=True, device="cuda", true_pose=None, tol=(0.5, 0.5)):
     """Register every start pose in init_poses [n][6] to the target images
-    ([n_views][nv][nu]).  Returns dict(poses, ncc, iters, seconds)."""
+    ([n_views][nv][nu]).  Returns dict(poses, ncc, iters, seconds, and, when
+    true_pose is given, first_hit_s: wall time at which any candidate first
+    came within tol = (mm, deg) of it, or None)."""
     lr = paper_step_sizes() if lr is None else lr
     init = torch.as_tensor(np.asarray(init_poses, dtype=np.float32), device=device)
     n = init.shape[0]
@@ -71,6 +73,9 @@ def register(geom, mu, target, init_poses, max_iter=200, lr=None, ncc_stop=0.999
     grad = torch.empty((n, 6), device=device)
     loss = torch.empty((n,), device=device)
     iters = np.zeros(n, dtype=np.int64)
+    first_hit = None
+    if true_pose is not None:
+        tp = torch.as_tensor(np.asarray(true_pose, dtype=np.float32), device=device).reshape(1, 6)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for it in range(max_iter):
@@ -80,6 +85,11 @@ def register(geom, mu, target, init_poses, max_iter=200, lr=None, ncc_stop=0.999
             g_out = grad[sl]
             l_out = loss[sl]
             proj_forward_pose_grad(P.plan, pg, PROJ_LOSS_NCC, tgt, g_out, l_out, None, P.ws)
+        if true_pose is not None and first_hit is None:
+            d = (pose - tp).abs()
+            hit = (d[:, :3].amax(1) <= tol[0]) & (torch.rad2deg(d[:, 3:]).amax(1) <= tol[1])
+            if bool(hit.any()):
+                first_hit = time.perf_counter() - t0
         done = (-loss >= ncc_stop) | ((last - loss).abs() < dloss_stop)
         active &= ~done
         iters += active.cpu().numpy()
@@ -89,7 +99,8 @@ def register(geom, mu, target, init_poses, max_iter=200, lr=None, ncc_stop=0.999
         last = loss.clone()
     torch.cuda.synchronize()
     seconds = time.perf_counter() - t0
-    return dict(poses=pose.cpu().numpy(), ncc=(-loss).cpu().numpy(), iters=iters, seconds=seconds)
+    return dict(poses=pose.cpu().numpy(), ncc=(-loss).cpu().numpy(), iters=iters, seconds=seconds,
+                first_hit_s=first_hit)
 
 
 def pose_error(a, b):
