@@ -365,13 +365,10 @@ def main():
     clocks.__exit__()
     if dist:
         dist.barrier()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_2508_13304_b300.multigpu import aggregate_rate, max_over_ranks
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.n_cand * args.steps / (total_ms * 1e-3)
+    value = aggregate_rate(world * args.n_cand, args.steps, total_ms)
     k_ms = sum(kern_ms) / len(kern_ms)
     clk = clocks.summary()
     grad_h = grad_d.cpu().numpy().astype(np.float64)
