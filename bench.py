@@ -293,6 +293,95 @@ def secondary(pb, torch, dev, w, mu_d, flush):
         "plain_total_s_all_starts": t_plain,
         "note": "plain = one start per launch, starts run one after another; batched = all starts in one launch "
                 "per iteration"}
+    out["registration_cuda_graph"] = graph_timing(pb, torch, g, mu_h, tgt, starts)
+    out["uneven_batch_small"] = uneven_batch(pb, torch, dev, flush, with_large=False)
+    out["uneven_batch_c4"] = uneven_batch(pb, torch, dev, flush, with_large=True)
+    return out
+
+
+def _event_ms(torch, fn, flush, reps=2):
+    """Median CUDA-event time (ms) of fn() on the current stream, L2 flushed
+    before each repetition, after one warm-up call."""
+    fn()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def uneven_batch(pb, torch, dev, flush, with_large):
+    """Independent L2 pose-gradient problems of uneven size: one persistent
+    batched launch (proj_batch_run) against one proj_forward_pose_grad call
+    per problem on the same stream.  Both include the pose set-ups and the
+    reductions."""
+    probs = synth.workload_uneven(with_large=with_large)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1004)
+    items, keep, samples = [], [], 0
+    for q in probs:
+        g = q["geom"]
+        nvw, npose = g.n_views, len(q["poses"])
+        P = pb.Projector(g, n_pose=npose, inst_view=np.arange(nvw),
+                         inst_pose=np.arange(nvw) if npose == nvw else np.zeros(nvw, np.int32),
+                         ops=pb.PROJ_OP_FORWARD | pb.PROJ_OP_FORWARD_GRAD)
+        P.set_volume(torch.rand((g.nz, g.ny, g.nx), device=dev, generator=gen))
+        pose = torch.from_numpy(q["poses"].astype(np.float32)).to(dev)
+        samples += int(P.count_samples(pose).sum().item())
+        keep.append(P)
+        items.append(dict(plan=P.plan, loss=pb.PROJ_LOSS_L2, pose=pose,
+                          ref=torch.rand((nvw, g.nv, g.nu), device=dev, generator=gen),
+                          grad=torch.zeros((npose, 6), device=dev), loss_out=torch.zeros(npose, device=dev),
+                          ws=P.ws))
+    b = pb.proj_batch_create(items)
+
+    def separate():
+        for it in items:
+            pb.proj_forward_pose_grad(it["plan"], it["pose"], it["loss"], it["ref"], it["grad"], it["loss_out"],
+                                      None, it["ws"])
+
+    ms_sep = _event_ms(torch, separate, flush)
+    g_sep = torch.cat([it["grad"].reshape(-1) for it in items]).clone()
+    ms_bat = _event_ms(torch, lambda: pb.proj_batch_run(b), flush)
+    g_bat = torch.cat([it["grad"].reshape(-1) for it in items])
+    diff = float(((g_bat - g_sep).norm() / g_sep.norm()).item())
+    sizes = [(q["geom"].nx, q["geom"].nu, q["geom"].n_views) for q in probs]
+    del b, items, keep
+    torch.cuda.empty_cache()
+    return {"config": ("512^3 / 720 views of 768^2 (per-view poses) + " if with_large else "")
+            + "%d single-view problems, volumes %d..%d^3, detectors %d..%d^2, L2 loss"
+            % (len(probs) - int(with_large), min(s_[0] for s_ in sizes[int(with_large):]),
+               max(s_[0] for s_ in sizes[int(with_large):]), min(s_[1] for s_ in sizes[int(with_large):]),
+               max(s_[1] for s_ in sizes[int(with_large):])),
+            "problems": len(probs), "ray_samples": samples,
+            "batched_ms": ms_bat, "separate_ms": ms_sep, "speedup": ms_sep / ms_bat,
+            "batched_ray_samples_per_s": samples / (ms_bat * 1e-3),
+            "grad_rel_diff_batched_vs_separate": diff,
+            "what": "batched = set-ups, one persistent work-queue launch over all problems' ray tiles, "
+                    "reductions; separate = proj_forward_pose_grad per problem, back to back"}
+
+
+def graph_timing(pb, torch, g, mu_h, tgt, starts):
+    """Registration iterations eager (one host check per iteration) vs
+    replayed CUDA graphs of 10 iterations; every candidate kept running."""
+    from paper_2508_13304_b300 import registration as reg
+    out = {}
+    for label, st, n_it in (("1_start", starts[:1], 101), ("%d_starts" % len(starts), starts, 31)):
+        res = {}
+        for mode, k in (("eager", 0), ("graph", 10)):
+            reg.register(g, mu_h, tgt, st, max_iter=11, ncc_stop=2.0, dloss_stop=-1.0, graph_steps=k)
+            r = reg.register(g, mu_h, tgt, st, max_iter=n_it, ncc_stop=2.0, dloss_stop=-1.0, graph_steps=k)
+            res[mode + "_ms_per_iteration"] = r["seconds"] * 1e3 / n_it
+        res["speedup"] = res["eager_ms_per_iteration"] / res["graph_ms_per_iteration"]
+        out[label] = res
+    out["what"] = ("wall time per registration iteration (pose-gradient launch, stopping test, Adam step): eager "
+                   "with a host check each iteration vs CUDA graphs of 10 captured iterations")
     return out
 
 

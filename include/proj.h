@@ -212,6 +212,31 @@ int proj_back_pose_grad(proj_plan plan, const float *d_proj, const float *d_pose
                         const float *d_vol_resid, float *d_grad, void *d_ws, size_t ws_bytes,
                         proj_stream stream);
 
+/* Batches: several independent forward pose-gradient problems (each a plan
+ * with its own volume, detector, views, poses and workspace, e.g. registration
+ * problems of uneven size) run by one persistent launch.  Resident blocks
+ * take 16 x 16-pixel ray tiles of any problem from a single atomic work
+ * counter (no waits); problems are ordered by estimated cost per tile,
+ * longest first, so small problems fill the tail of large ones.  Results
+ * are identical to proj_forward_pose_grad on each plan.
+ *
+ * proj_batch_create binds, for problem i: plans[i] (needs
+ * PROJ_OP_FORWARD_GRAD; volume set with proj_set_volume before runs),
+ * loss[i], d_pose[i] [n_pose_i][6], d_ref[i] (as in proj_forward_pose_grad),
+ * d_grad[i] [n_pose_i][6], d_loss[i] (array may be NULL, entries may be
+ * NULL), d_ws[i] / ws_bytes[i] (distinct workspaces).  All arrays are host
+ * arrays of device pointers, read during the call; the device buffers must
+ * outlive the batch.  The batch owns a small device descriptor table.
+ * proj_batch_run launches the pose set-ups, the persistent march and the
+ * per-problem reductions on the stream (no host-device copies).
+ * Errors: PROJ_E_ARG, PROJ_E_UNSUPPORTED, PROJ_E_WORKSPACE, PROJ_E_CUDA. */
+typedef struct proj_batch_s *proj_batch;
+int proj_batch_create(int n, const proj_plan *plans, const int *loss, const float *const *d_pose,
+                      const float *const *d_ref, float *const *d_grad, float *const *d_loss, void *const *d_ws,
+                      const size_t *ws_bytes, proj_batch *out);
+int proj_batch_run(proj_batch batch, proj_stream stream);
+int proj_batch_destroy(proj_batch batch);
+
 /* Exact transpose of proj_forward for the given poses: each sample spreads
  * step * y_i over its 8 trilinear corners.
  *   d_y    [n_inst][nv][nu] FP32.

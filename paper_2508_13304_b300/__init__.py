@@ -68,6 +68,11 @@ _SIGS = {
                                       _P, _P, _I, _P, _P, _P, _P],
     "proj_fdk_filter": [_P, _P, ctypes.c_float, _P, _P],
     "proj_sharpness": [_P, _P, _P, _P, _P, _SZ, _P],
+    "proj_batch_create": [_I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                          ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_SZ),
+                          ctypes.POINTER(_P)],
+    "proj_batch_run": [_P, _P],
+    "proj_batch_destroy": [_P],
     "proj_enable_kernel_timing": [_P, _I],
     "proj_kernel_time_ms": [_P, ctypes.POINTER(ctypes.c_float)],
     "proj_last_error": [],
@@ -313,6 +318,59 @@ def proj_sharpness(plan: Plan, vol, loss, grad=None, ws=None, stream=None):
                                 _ptr(loss, torch.float32, 1, "loss"),
                                 _ptr(grad, torch.float32, plan.vol_numel, "grad", allow_none=True), p, nb,
                                 _stream(stream)))
+
+
+class Batch:
+    """Handle of a proj_batch; keeps the bound plans and tensors alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                lib().proj_batch_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def proj_batch_create(problems) -> Batch:
+    """Bind independent forward pose-gradient problems for one persistent
+    launch.  problems: sequence of dicts with keys plan, loss, pose, ref, grad,
+    ws and optionally loss_out (same meaning as in proj_forward_pose_grad)."""
+    import torch
+    n = len(problems)
+    if n < 1:
+        raise ValueError("need at least one problem")
+    plans = (_P * n)()
+    losses = (_I * n)()
+    poses, refs, grads, louts, wss = (_P * n)(), (_P * n)(), (_P * n)(), (_P * n)(), (_P * n)()
+    nbs = (_SZ * n)()
+    for i, q in enumerate(problems):
+        plan, loss = q["plan"], int(q["loss"])
+        n_ref = (plan.n_inst if loss == PROJ_LOSS_RESIDUAL else plan.geom.n_views) * plan.img_numel
+        plans[i] = plan.handle
+        losses[i] = loss
+        poses[i] = _ptr(q["pose"], torch.float32, 6 * plan.n_pose, "pose")
+        refs[i] = _ptr(q["ref"], torch.float32, n_ref, "ref")
+        grads[i] = _ptr(q["grad"], torch.float32, 6 * plan.n_pose, "grad")
+        louts[i] = _ptr(q.get("loss_out"), torch.float32, plan.n_pose, "loss", allow_none=True)
+        wss[i], nbs[i] = _ws(q["ws"])
+    h = _P()
+    _check(lib().proj_batch_create(n, plans, losses, poses, refs, grads, louts, wss, nbs, ctypes.byref(h)))
+    return Batch(h.value, list(problems))
+
+
+def proj_batch_run(batch: Batch, stream=None):
+    _check(lib().proj_batch_run(batch.handle, _stream(stream)))
+
+
+def proj_batch_destroy(batch: Batch):
+    if batch.handle:
+        _check(lib().proj_batch_destroy(batch.handle))
+        batch.handle = None
 
 
 def proj_enable_kernel_timing(plan: Plan, enable=True):

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -526,6 +527,138 @@ int proj_sharpness(proj_plan p, const float* d_vol, float* d_loss, float* d_grad
   double* stats = part + 2 * (size_t)sharpness_blocks(p->geo);
   cudaError_t e = launch_sharpness(d_vol, p->geo, m, part, stats, d_loss, d_grad, (cudaStream_t)stream);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "sharpness launch");
+}
+
+}  // extern "C"
+
+struct proj_batch_s {
+  int n = 0;
+  int device = -1;
+  long long n_items = 0;
+  int n_blocks = 0;
+  std::vector<proj_plan> plans;
+  std::vector<int> loss;
+  std::vector<const float*> pose;
+  std::vector<float*> grad, loss_out;
+  std::vector<void*> ws;
+  std::vector<size_t> ws_bytes;
+  BatchProblem* d_probs = nullptr;
+  unsigned long long* d_counter = nullptr;
+};
+
+extern "C" {
+
+int proj_batch_create(int n, const proj_plan* plans, const int* loss, const float* const* d_pose,
+                      const float* const* d_ref, float* const* d_grad, float* const* d_loss, void* const* d_ws,
+                      const size_t* ws_bytes, proj_batch* out) {
+  g_last_error.clear();
+  if (!out) return fail(PROJ_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !plans || !loss || !d_pose || !d_ref || !d_grad || !d_ws || !ws_bytes)
+    return fail(PROJ_E_ARG, "proj_batch_create: need n >= 1 and all per-problem arrays");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::vector<BatchProblem> probs(n);
+  std::vector<double> cost(n);
+  for (int i = 0; i < n; ++i) {
+    const proj_plan p = plans[i];
+    if (!p) return fail(PROJ_E_ARG, "problem %d: plan is NULL", i);
+    if (!(p->ops & PROJ_OP_FORWARD_GRAD))
+      return fail(PROJ_E_UNSUPPORTED, "problem %d: plan lacks PROJ_OP_FORWARD_GRAD", i);
+    if (p->device != dev) return fail(PROJ_E_ARG, "problem %d: plan is on device %d, current is %d", i, p->device, dev);
+    if (loss[i] != PROJ_LOSS_RESIDUAL && loss[i] != PROJ_LOSS_L2 && loss[i] != PROJ_LOSS_NCC)
+      return fail(PROJ_E_ARG, "problem %d: unknown loss %d", i, loss[i]);
+    if (!d_pose[i] || !d_ref[i] || !d_grad[i]) return fail(PROJ_E_ARG, "problem %d: NULL pose, reference or grad", i);
+    WsView w;
+    int rc = check_ws(p, d_ws[i], ws_bytes[i], &w);
+    if (rc) return fail(rc, "problem %d: %s", i, g_last_error.c_str());
+    for (int j = 0; j < i; ++j)
+      if (d_ws[j] == d_ws[i]) return fail(PROJ_E_ARG, "problems %d and %d share a workspace", j, i);
+    BatchProblem& B = probs[i];
+    B.geo = p->geo;
+    B.inst = w.inst;
+    B.vol4 = w.vol4;
+    B.ref = d_ref[i];
+    B.part = w.part_f;
+    B.n_tiles = p->n_tiles;
+    B.tiles_u = ceil_div(p->geo.nu, kTileU);
+    B.loss = loss[i];
+    B.pad = 0;
+    // per-tile cost ~ samples per ray ~ volume diagonal / step
+    const double dx = p->geo.nx * (double)p->geo.vx, dy = p->geo.ny * (double)p->geo.vy,
+                 dz = p->geo.nz * (double)p->geo.vz;
+    cost[i] = std::sqrt(dx * dx + dy * dy + dz * dz) / p->geo.step;
+  }
+  // longest tiles first
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  proj_batch_s* b = new proj_batch_s();
+  b->n = n;
+  b->device = dev;
+  std::vector<BatchProblem> sorted(n);
+  long long items = 0;
+  for (int k = 0; k < n; ++k) {
+    const int i = order[k];
+    sorted[k] = probs[i];
+    sorted[k].item_begin = items;
+    items += (long long)plans[i]->n_inst * plans[i]->n_tiles;
+    b->plans.push_back(plans[i]);
+    b->loss.push_back(loss[i]);
+    b->pose.push_back(d_pose[i]);
+    b->grad.push_back(d_grad[i]);
+    b->loss_out.push_back(d_loss ? d_loss[i] : nullptr);
+    b->ws.push_back(d_ws[i]);
+    b->ws_bytes.push_back(ws_bytes[i]);
+  }
+  b->n_items = items;
+  int n_sm = 148;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const long long cap = (long long)n_sm * forward_grad_batch_blocks_per_sm();
+  b->n_blocks = (int)(items < cap ? items : cap);
+  e = cudaMalloc(&b->d_probs, sizeof(BatchProblem) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_probs, sorted.data(), sizeof(BatchProblem) * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    proj_batch_destroy(b);
+    return cuda_fail(e, "batch table allocation");
+  }
+  *out = b;
+  return PROJ_OK;
+}
+
+int proj_batch_destroy(proj_batch b) {
+  if (!b) return PROJ_OK;
+  cudaFree(b->d_probs);
+  cudaFree(b->d_counter);
+  delete b;
+  return PROJ_OK;
+}
+
+int proj_batch_run(proj_batch b, proj_stream stream) {
+  if (!b) return fail(PROJ_E_ARG, "batch is NULL");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != b->device) return fail(PROJ_E_ARG, "current device %d differs from the batch's device %d", dev, b->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<WsView> w(b->n);
+  for (int k = 0; k < b->n; ++k) {
+    int rc = check_ws(b->plans[k], b->ws[k], b->ws_bytes[k], &w[k]);
+    if (rc) return rc;
+    if ((rc = setup(b->plans[k], b->pose[k], w[k], s))) return rc;
+  }
+  e = launch_forward_grad_batch(b->d_probs, b->n, b->n_items, b->d_counter, b->n_blocks, s);
+  if (e != cudaSuccess) return cuda_fail(e, "batched pose-gradient launch");
+  for (int k = 0; k < b->n; ++k) {
+    const proj_plan p = b->plans[k];
+    e = launch_forward_grad_reduce(w[k].inst, w[k].ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx,
+                                   p->n_tiles, p->geo, b->loss[k], w[k].part_f, b->grad[k],
+                                   b->loss_out[k], s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched reduction launch");
+  }
+  return PROJ_OK;
 }
 
 int proj_check(proj_plan p, void* d_ws, size_t ws_bytes, proj_stream stream, int* status) {

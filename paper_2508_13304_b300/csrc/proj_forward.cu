@@ -215,13 +215,14 @@ __global__ void k_count(const InstTable* __restrict__ inst, int n_tiles, int til
 // reduction kernel).  At the end of the ray the loss residual weights the
 // 12 sums; a warp/block reduction writes one record per tile.
 
+// One 16 x 16 ray tile (instance n, tile index) of the fused march, block-
+// wide: writes the tile's record part[(n * n_tiles + tile) * kRec ...].
+// Shared by the per-problem kernel and the persistent multi-problem kernel.
 template <int LOSS>
-__global__ void __launch_bounds__(kMarchThreads)
-    k_forward_grad(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g,
-                   const float4* __restrict__ vol, const float* __restrict__ ref, float* __restrict__ proj,
-                   float* __restrict__ part) {
-  __shared__ float red[kMarchThreads / 32][kRec];
-  const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
+__device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, int n, int tile, int n_tiles,
+                                           int tiles_u, const Geo& g, const float4* __restrict__ vol,
+                                           const float* __restrict__ ref, float* __restrict__ proj,
+                                           float* __restrict__ part, float (*red)[kRec]) {
   int iu, iv;
   const bool on_det = tile_pixel(tile, tiles_u, g, iu, iv);
   const InstTable& T = inst[n];
@@ -320,6 +321,56 @@ __global__ void __launch_bounds__(kMarchThreads)
     if ((int)threadIdx.x < nrec)
       for (int ww = 0; ww < kMarchThreads / 32; ++ww) s += red[ww][threadIdx.x];
     part[((size_t)n * n_tiles + tile) * kRec + threadIdx.x] = s;
+  }
+  __syncthreads();  // red is reused by the next tile of a persistent block
+}
+
+template <int LOSS>
+__global__ void __launch_bounds__(kMarchThreads)
+    k_forward_grad(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g,
+                   const float4* __restrict__ vol, const float* __restrict__ ref, float* __restrict__ proj,
+                   float* __restrict__ part) {
+  __shared__ float red[kMarchThreads / 32][kRec];
+  march_tile<LOSS>(inst, blockIdx.x / n_tiles, blockIdx.x % n_tiles, n_tiles, tiles_u, g, vol, ref, proj, part, red);
+}
+
+// ---------------------------------------------------------------- batch
+//
+// Persistent multi-problem march: a grid of resident blocks takes work items
+// (problem, instance, tile) from one atomic counter until the list is
+// exhausted.  Items are numbered problem by problem in the order the host
+// chose (longest tiles first), so small problems fill the tail of the large
+// ones.  The counter is the only shared state; no block waits for another.
+
+__global__ void __launch_bounds__(kMarchThreads, 4)
+    k_forward_grad_batch(const BatchProblem* __restrict__ probs, int n_probs, long long n_items,
+                         unsigned long long* __restrict__ counter) {
+  __shared__ float red[kMarchThreads / 32][kRec];
+  __shared__ long long item_s;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ULL);
+    __syncthreads();
+    const long long item = item_s;
+    __syncthreads();
+    if (item >= n_items) return;
+    int p = 0;
+    while (p + 1 < n_probs && probs[p + 1].item_begin <= item) ++p;
+    const BatchProblem& B = probs[p];
+    const int local = (int)(item - B.item_begin);
+    const int n = local / B.n_tiles, tile = local % B.n_tiles;
+    switch (B.loss) {
+      case PROJ_LOSS_RESIDUAL:
+        march_tile<PROJ_LOSS_RESIDUAL>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr, B.part,
+                                       red);
+        break;
+      case PROJ_LOSS_L2:
+        march_tile<PROJ_LOSS_L2>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr, B.part, red);
+        break;
+      default:
+        march_tile<PROJ_LOSS_NCC>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr, B.part,
+                                  red);
+        break;
+    }
   }
 }
 
@@ -501,6 +552,20 @@ cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, co
       break;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_forward_grad_batch(const BatchProblem* d_probs, int n_probs, long long n_items,
+                                      unsigned long long* d_counter, int n_blocks, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_forward_grad_batch<<<n_blocks, kMarchThreads, 0, s>>>(d_probs, n_probs, n_items, d_counter);
+  return cudaGetLastError();
+}
+
+int forward_grad_batch_blocks_per_sm() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_grad_batch, kMarchThreads, 0) != cudaSuccess) b = 2;
+  return b < 1 ? 1 : b;
 }
 
 cudaError_t launch_forward_grad_reduce(const InstTable* d_inst, const PoseTable* d_ptab, int n_pose,

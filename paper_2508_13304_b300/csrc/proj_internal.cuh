@@ -66,6 +66,17 @@ struct FdkView {
   float pad[3];
 };
 
+// One problem of a persistent multi-problem fused march (proj_batch_*).
+struct BatchProblem {
+  Geo geo;
+  const InstTable* inst;
+  const float4* vol4;
+  const float* ref;
+  float* part;
+  int n_tiles, tiles_u, loss, pad;
+  long long item_begin;  // first global work item of this problem
+};
+
 // Record of one K3 block (ray tile) partial: see kRec* offsets.
 constexpr int kRec = 48;
 constexpr int kRecG = 0;      // 12: sum of w * G   (RESIDUAL, L2)  or sum G (NCC)
@@ -104,6 +115,9 @@ cudaError_t launch_forward_grad_reduce(const InstTable* d_inst, const PoseTable*
                                        const int* d_pose_ptr, const int* d_pose_idx, int n_tiles, Geo geo,
                                        int loss, const float* d_part, float* d_grad, float* d_loss,
                                        cudaStream_t s);
+cudaError_t launch_forward_grad_batch(const BatchProblem* d_probs, int n_probs, long long n_items,
+                                      unsigned long long* d_counter, int n_blocks, cudaStream_t s);
+int forward_grad_batch_blocks_per_sm();
 cudaError_t launch_forward_adjoint(const InstTable* d_inst, int n_inst, Geo geo, const float* d_y,
                                    float* d_acc, float* d_vol, cudaStream_t s);
 cudaError_t launch_detector_prep(const float* d_proj, int n_inst, Geo geo, float4* d_det4, cudaStream_t s);

@@ -8,7 +8,12 @@ Batched: every start pose (candidate) is a pose of one plan, all candidates
 advance together, one fused launch per iteration; a converged candidate
 keeps its pose (masked update).  Plain: the same loop with one candidate per
 launch.  The Adam update is a few elementwise torch operations on an
-[n, 6] tensor.
+[n, 6] tensor; its step counter lives on the device, so whole iterations
+(pose-gradient launches, stopping test, Adam step) can be captured in a CUDA
+graph and replayed (graph_steps > 0): the host then looks at the stopping
+state once per replay instead of once per iteration.  The trajectories are
+those of the eager loop: after every candidate has stopped, further captured
+iterations leave all poses unchanged.
 """
 from __future__ import annotations
 
@@ -30,15 +35,15 @@ class Adam:
         self.eps = eps
         self.m = torch.zeros((n, 6), device=device)
         self.v = torch.zeros((n, 6), device=device)
-        self.t = 0
+        self.t = torch.zeros((), dtype=torch.float32, device=device)   # step count, on the device
 
     def step(self, pose, grad, active):
-        self.t += 1
+        self.t.add_(1.0)
         a = active.float().reshape(-1, 1)
         self.m.mul_(1 - a * (1 - self.b1)).add_(a * (1 - self.b1) * grad)
         self.v.mul_(1 - a * (1 - self.b2)).add_(a * (1 - self.b2) * grad * grad)
-        mh = self.m / (1 - self.b1 ** self.t)
-        vh = self.v / (1 - self.b2 ** self.t)
+        mh = self.m / (1 - torch.pow(self.b1, self.t))
+        vh = self.v / (1 - torch.pow(self.b2, self.t))
         pose.sub_(a * self.lr * mh / (torch.sqrt(vh) + self.eps))
 
 
@@ -47,11 +52,12 @@ def paper_step_sizes():
 
 
 def register(geom, mu, target, init_poses, max_iter=200, lr=None, ncc_stop=0.999, dloss_stop=1e-5,
-             batched=True, device="cuda", true_pose=None, tol=(0.5, 0.5)):
+             batched=True, device="cuda", true_pose=None, tol=(0.5, 0.5), graph_steps=0):
     """Register every start pose in init_poses [n][6] to the target images
     ([n_views][nv][nu]).  Returns dict(poses, ncc, iters, seconds, and, when
-    true_pose is given, first_hit_s: wall time at which any candidate first
-    came within tol = (mm, deg) of it, or None)."""
+    true_pose is given, first_hit_s: wall time at which any candidate was
+    first seen within tol = (mm, deg) of it, or None).  graph_steps > 0
+    replays CUDA graphs of that many iterations (checked once per replay)."""
     lr = paper_step_sizes() if lr is None else lr
     init = torch.as_tensor(np.asarray(init_poses, dtype=np.float32), device=device)
     n = init.shape[0]
@@ -72,34 +78,50 @@ def register(geom, mu, target, init_poses, max_iter=200, lr=None, ncc_stop=0.999
     last = torch.full((n,), float("inf"), device=device)
     grad = torch.empty((n, 6), device=device)
     loss = torch.empty((n,), device=device)
-    iters = np.zeros(n, dtype=np.int64)
-    first_hit = None
+    iters = torch.zeros(n, dtype=torch.int64, device=device)
+    hit_any = torch.zeros((), dtype=torch.bool, device=device)
+    views = [(pose[grp[0]:grp[-1] + 1], grad[grp[0]:grp[-1] + 1], loss[grp[0]:grp[-1] + 1]) for grp in groups]
     if true_pose is not None:
         tp = torch.as_tensor(np.asarray(true_pose, dtype=np.float32), device=device).reshape(1, 6)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for it in range(max_iter):
-        for grp, P in zip(groups, projs):
-            sl = slice(grp[0], grp[-1] + 1)
-            pg = pose[sl].contiguous()
-            g_out = grad[sl]
-            l_out = loss[sl]
+
+    def iteration():
+        for (pg, g_out, l_out), P in zip(views, projs):
             proj_forward_pose_grad(P.plan, pg, PROJ_LOSS_NCC, tgt, g_out, l_out, None, P.ws)
-        if true_pose is not None and first_hit is None:
+        if true_pose is not None:
             d = (pose - tp).abs()
             hit = (d[:, :3].amax(1) <= tol[0]) & (torch.rad2deg(d[:, 3:]).amax(1) <= tol[1])
-            if bool(hit.any()):
-                first_hit = time.perf_counter() - t0
+            hit_any.logical_or_(hit.any())
         done = (-loss >= ncc_stop) | ((last - loss).abs() < dloss_stop)
-        active &= ~done
-        iters += active.cpu().numpy()
+        active.logical_and_(~done)
+        iters.add_(active)
+        opt.step(pose, grad, active)
+        last.copy_(loss)
+
+    first_hit = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it = 0
+    graph = None
+    while it < max_iter:
+        k = 1
+        if graph_steps > 0 and it > 0 and max_iter - it >= graph_steps:
+            if graph is None:
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph):
+                    for _ in range(graph_steps):
+                        iteration()
+            graph.replay()
+            k = graph_steps
+        else:
+            iteration()
+        it += k
+        if true_pose is not None and first_hit is None and bool(hit_any):
+            first_hit = time.perf_counter() - t0
         if not bool(active.any()):
             break
-        opt.step(pose, grad, active)
-        last = loss.clone()
     torch.cuda.synchronize()
     seconds = time.perf_counter() - t0
-    return dict(poses=pose.cpu().numpy(), ncc=(-loss).cpu().numpy(), iters=iters, seconds=seconds,
+    return dict(poses=pose.cpu().numpy(), ncc=(-loss).cpu().numpy(), iters=iters.cpu().numpy(), seconds=seconds,
                 first_hit_s=first_hit)
 
 

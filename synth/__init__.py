@@ -265,6 +265,40 @@ def workload_moco(seed=1003, n_views=360, nvox=256, ndet=512, vox=0.8,
     return dict(geom=geom, mu=mu, poses=motion, ellipsoids=ell)
 
 
+def workload_uneven(seed=1004, n_extra=24, with_large=True, vox=0.5):
+    """Uneven batch of independent problems (the calibration-style per-view
+    registration scaled up): a 512^3 volume at 0.5 mm seen in 720 views over
+    360 deg on 768^2 detectors at 0.556 mm, each view with its own pose
+    (translations N(0, 1 mm), rotations N(0, 0.5 deg)); plus n_extra
+    problems, each one view (random angle) of its own cubic volume with edge
+    U{128..320} at 0.5 mm on a square detector with edge U{256..512} whose
+    pitch makes the field of view 1.1x the volume diagonal.  Geometry and
+    poses only; the volumes and reference images are drawn by the caller
+    (their values do not change the work)."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    if with_large:
+        g = Geometry(512, 512, 512, vox, vox, vox, 768, 768,
+                     circular_views(720, SAD, SDD, 0.556, 0.556), step=0.5 * vox)
+        pose = np.zeros((720, 6))
+        pose[:, :3] = rng.normal(0.0, 1.0, (720, 3))
+        pose[:, 3:] = np.deg2rad(rng.normal(0.0, 0.5, (720, 3)))
+        probs.append(dict(geom=g, poses=pose))
+    for _ in range(n_extra):
+        n = int(rng.integers(128, 321))
+        nd = int(rng.integers(256, 513))
+        pitch = 1.1 * n * vox * math.sqrt(3.0) * (SDD / SAD) / nd
+        g = Geometry(n, n, n, vox, vox, vox, nd, nd,
+                     circular_views(1, SAD, SDD, pitch, pitch,
+                                    angles=[rng.uniform(0, 2 * np.pi)]),
+                     step=0.5 * vox)
+        pose = np.zeros((1, 6))
+        pose[:, :3] = rng.normal(0.0, 1.0, (1, 3))
+        pose[:, 3:] = np.deg2rad(rng.normal(0.0, 0.5, (1, 3)))
+        probs.append(dict(geom=g, poses=pose))
+    return probs
+
+
 def random_image(rng, shape, lo=0.0, hi=1.0):
     return rng.uniform(lo, hi, shape)
 

@@ -126,6 +126,12 @@ def test_bad_ops_and_null_arguments(L):
     assert L.proj_enable_kernel_timing(None, 1) == pb.PROJ_E_ARG
     assert L.proj_kernel_time_ms(None, None) == pb.PROJ_E_ARG
     assert L.proj_plan_destroy(None) == pb.PROJ_OK
+    out = ctypes.c_void_p()
+    assert L.proj_batch_create(1, None, None, None, None, None, None, None, None, None) == pb.PROJ_E_ARG
+    assert L.proj_batch_create(0, None, None, None, None, None, None, None, None, ctypes.byref(out)) == pb.PROJ_E_ARG
+    assert out.value is None
+    assert L.proj_batch_run(None, None) == pb.PROJ_E_ARG
+    assert L.proj_batch_destroy(None) == pb.PROJ_OK
 
 
 def test_valid_plan_without_a_gpu_reports_a_cuda_error(L):

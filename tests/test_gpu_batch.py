@@ -1,0 +1,177 @@
+"""Uneven batches in one persistent launch (proj_batch_*) and CUDA-graph
+capture of optimisation steps (GPU).
+
+A batch binds independent forward pose-gradient problems of different
+volume sizes, detector sizes, view counts and losses; its results must equal
+those of proj_forward_pose_grad called on each plan (same per-tile arithmetic,
+same fixed-order reductions), and one problem is checked against the oracle
+at the parity bars."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import small_geom, smooth_volume
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_13304_b300 import build
+    build.build()
+
+
+import paper_2508_13304_b300 as pb  # noqa: E402
+from paper_2508_13304_b300 import registration as reg  # noqa: E402
+
+# (volume, detector, pixel, views, poses, loss): sizes are deliberately not
+# multiples of the 16-pixel tile and the problems differ ~40x in work
+SHAPES = [((44, 40, 48), (61, 53), 1.4, 4, 2, pb.PROJ_LOSS_NCC),
+          ((20, 22, 18), (24, 19), 2.0, 1, 1, pb.PROJ_LOSS_L2),
+          ((32, 28, 36), (40, 45), 1.6, 3, 3, pb.PROJ_LOSS_RESIDUAL),
+          ((12, 12, 12), (9, 17), 2.5, 2, 1, pb.PROJ_LOSS_NCC),
+          ((36, 36, 30), (33, 33), 1.8, 2, 2, pb.PROJ_LOSS_L2)]
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def make_problems(seed=11):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k, (n, det, pix, nvw, npose, loss) in enumerate(SHAPES):
+        g = small_geom(n=n, det=det, pix=pix, n_views=nvw, off=tuple(rng.uniform(-1, 1, 3)))
+        mu = smooth_volume(g, rng, n_blobs=6).astype(np.float32)
+        iv = np.tile(np.arange(nvw), npose).astype(np.int32)
+        ip = np.repeat(np.arange(npose), nvw).astype(np.int32)
+        poses = np.concatenate([rng.uniform(-2, 2, (npose, 3)), rng.uniform(-0.1, 0.1, (npose, 3))],
+                               axis=1).astype(np.float32)
+        if loss == pb.PROJ_LOSS_RESIDUAL:
+            ref = rng.standard_normal((iv.size, g.nv, g.nu)).astype(np.float32)
+        else:
+            ref = oracle.forward(g, mu.astype(np.float64), np.zeros(6), np.arange(nvw),
+                                 np.zeros(nvw, dtype=np.int32)).astype(np.float32)
+        P = pb.Projector(g, n_pose=npose, inst_view=iv, inst_pose=ip, ops=pb.PROJ_OP_FORWARD_GRAD)
+        P.set_volume(mu)
+        out.append(dict(P=P, g=g, mu=mu, iv=iv, ip=ip, loss=loss,
+                        pose=torch.tensor(poses, device="cuda"), ref=torch.tensor(ref, device="cuda"),
+                        grad=torch.zeros((npose, 6), device="cuda"), loss_out=torch.zeros(npose, device="cuda")))
+    return out
+
+
+def bind(probs):
+    return pb.proj_batch_create([dict(plan=q["P"].plan, loss=q["loss"], pose=q["pose"], ref=q["ref"],
+                                      grad=q["grad"], loss_out=q["loss_out"], ws=q["P"].ws) for q in probs])
+
+
+def one_by_one(probs):
+    res = []
+    for q in probs:
+        g, L = q["P"].forward_pose_grad(q["pose"], q["loss"], q["ref"])
+        res.append((g.cpu().numpy(), L.cpu().numpy()))
+    return res
+
+
+def test_batch_equals_per_plan_calls():
+    probs = make_problems()
+    b = bind(probs)
+    pb.proj_batch_run(b)
+    torch.cuda.synchronize()
+    got = [(q["grad"].cpu().numpy(), q["loss_out"].cpu().numpy()) for q in probs]
+    want = one_by_one(probs)
+    for k, ((gg, gl), (wg, wl)) in enumerate(zip(got, want)):
+        assert rel(gg, wg) <= 1e-6, (k, gg, wg)
+        if probs[k]["loss"] != pb.PROJ_LOSS_RESIDUAL:
+            np.testing.assert_allclose(gl, wl, rtol=1e-6, atol=1e-7)
+    # a second run restarts the work queue and reads the poses again
+    for q in probs:
+        q["pose"][:, :3] += 0.5
+    pb.proj_batch_run(b)
+    torch.cuda.synchronize()
+    want = one_by_one(probs)
+    for k, q in enumerate(probs):
+        assert rel(q["grad"].cpu().numpy(), want[k][0]) <= 1e-6, k
+
+
+def test_batch_problem_matches_the_oracle():
+    """The NCC problem of the batch at the parity bars (rel <= 1e-3 per
+    pose and block, loss rtol 1e-4)."""
+    probs = make_problems(seed=12)
+    b = bind(probs)
+    pb.proj_batch_run(b)
+    torch.cuda.synchronize()
+    q = probs[0]
+    g = q["g"]
+    poses = q["pose"].cpu().numpy().astype(np.float64)
+    target = q["ref"].cpu().numpy().astype(np.float64)
+    proj = oracle.forward(g, q["mu"].astype(np.float64), poses, q["iv"], q["ip"])
+    L_ref, w = oracle.pose_loss_weights("ncc", proj, target, q["iv"], q["ip"], poses.shape[0])
+    gth, _ = oracle.forward_grad(g, q["mu"].astype(np.float64), poses, w, q["iv"], q["ip"],
+                                 mode=oracle.GRAD_ANALYTIC)
+    got = q["grad"].cpu().numpy()
+    for p in range(poses.shape[0]):
+        for blk in (slice(0, 3), slice(3, 6)):
+            assert rel(got[p, blk], gth[p, blk]) <= 1e-3
+    np.testing.assert_allclose(q["loss_out"].cpu().numpy(), L_ref, rtol=1e-4)
+
+
+def test_batch_rejects_bad_bindings():
+    probs = make_problems()[:2]
+    spec = [dict(plan=q["P"].plan, loss=q["loss"], pose=q["pose"], ref=q["ref"], grad=q["grad"], ws=q["P"].ws)
+            for q in probs]
+    shared = [dict(spec[0]), dict(spec[1], ws=spec[0]["ws"])]
+    with pytest.raises(pb.ProjError) as e:
+        pb.proj_batch_create(shared)
+    assert e.value.code in (pb.PROJ_E_ARG, pb.PROJ_E_WORKSPACE)
+    small = [dict(spec[0], ws=spec[0]["ws"][:256])]
+    with pytest.raises(pb.ProjError) as e:
+        pb.proj_batch_create(small)
+    assert e.value.code == pb.PROJ_E_WORKSPACE
+    g = probs[0]["g"]
+    P = pb.Projector(g, n_pose=2, inst_view=probs[0]["iv"], inst_pose=probs[0]["ip"], ops=pb.PROJ_OP_FORWARD)
+    with pytest.raises(pb.ProjError) as e:
+        pb.proj_batch_create([dict(spec[0], plan=P.plan, ws=P.ws)])
+    assert e.value.code == pb.PROJ_E_UNSUPPORTED
+
+
+def test_batch_run_replays_from_a_cuda_graph():
+    probs = make_problems(seed=13)
+    b = bind(probs)
+    pb.proj_batch_run(b)
+    torch.cuda.synchronize()
+    want = [q["grad"].clone() for q in probs]
+    for q in probs:
+        q["grad"].zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        pb.proj_batch_run(b)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    for q, w in zip(probs, want):
+        assert torch.equal(q["grad"], w)
+
+
+def test_graph_captured_registration_follows_the_eager_trajectory():
+    rng = np.random.default_rng(5)
+    views = synth.circular_views(3, 300.0, 450.0, 1.2, 1.2, angles=[0.0, 1.2, 2.4])
+    g = synth.Geometry(40, 40, 40, 1.0, 1.0, 1.0, 48, 48, views, 0.5)
+    ell = synth.random_ellipsoids(rng, 8, 8.0, (3.0, 8.0), (0.01, 0.03))
+    mu = synth.voxelise(g, ell, supersample=2).astype(np.float32)
+    true = np.array([1.5, -1.0, 0.5, 0.03, -0.02, 0.04], dtype=np.float32)
+    target = oracle.forward(g, mu.astype(np.float64), true.astype(np.float64), np.arange(3),
+                            np.zeros(3, dtype=np.int32))
+    starts = true + np.concatenate([rng.uniform(-3, 3, (4, 3)), np.deg2rad(rng.uniform(-3, 3, (4, 3)))], axis=1)
+    kw = dict(max_iter=57, lr=[0.5] * 3 + [np.deg2rad(0.5)] * 3, ncc_stop=1.0, dloss_stop=1e-8)
+    eager = reg.register(g, mu, target, starts, **kw)
+    graph = reg.register(g, mu, target, starts, graph_steps=10, **kw)
+    np.testing.assert_array_equal(graph["iters"], eager["iters"])
+    np.testing.assert_allclose(graph["poses"], eager["poses"], atol=1e-6)
+    np.testing.assert_allclose(graph["ncc"], eager["ncc"], atol=1e-6)
