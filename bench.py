@@ -293,6 +293,15 @@ def secondary(pb, torch, dev, w, mu_d, flush):
         "plain_total_s_all_starts": t_plain,
         "note": "plain = one start per launch, starts run one after another; batched = all starts in one launch "
                 "per iteration"}
+    # ray-tile shape autotuner on the benchmark's own launch (64 candidates x 2 views)
+    Pa = pb.Projector(g, n_pose=nc, inst_view=iv, inst_pose=ip, ops=pb.PROJ_OP_FORWARD_GRAD)
+    Pa.set_volume(mu_d)
+    tg = torch.from_numpy(np.ascontiguousarray(tgt, dtype=np.float32)).to(dev)
+    width, times = pb.proj_autotune_forward_grad(Pa.plan, pose, pb.PROJ_LOSS_NCC, tg, Pa.ws, reps=2)
+    out["warp_shape_autotune"] = {"config": "256^3, 128 view instances of 384^2, NCC",
+                                  "ms_per_launch": {"%dx%d" % (k, 32 // k): v for k, v in times.items()},
+                                  "chosen": "%dx%d" % (width, 32 // width)}
+    del Pa
     out["registration_cuda_graph"] = graph_timing(pb, torch, g, mu_h, tgt, starts)
     out["uneven_batch_small"] = uneven_batch(pb, torch, dev, flush, with_large=False)
     out["uneven_batch_c4"] = uneven_batch(pb, torch, dev, flush, with_large=True)

@@ -212,13 +212,33 @@ int proj_back_pose_grad(proj_plan plan, const float *d_proj, const float *d_pose
                         const float *d_vol_resid, float *d_grad, void *d_ws, size_t ws_bytes,
                         proj_stream stream);
 
+/* Ray-tile shape of the fused pose-gradient march.  Each CTA marches a
+ * 16 x 16-pixel tile with 8 warps; warp_width is the number of pixels along
+ * u covered by one warp (warp_width x 32/warp_width rays: 2 x 16, 4 x 8,
+ * 8 x 4 or 16 x 2).  Which shape gathers (mu, grad mu) with the fewest L1
+ * wavefronts depends on how the rays cross the volume, so it is a tuning
+ * parameter of the plan (default 4).  Results of different shapes agree to
+ * FP32 rounding (the per-tile sums are taken in a different order).
+ * proj_set_warp_shape: PROJ_E_ARG unless warp_width is 2, 4, 8 or 16.
+ * proj_autotune_forward_grad: sets up the poses, then times `reps` launches
+ * of the march per shape on the caller's data (plan volume set, d_pose,
+ * loss, d_ref as in proj_forward_pose_grad), stores the fastest shape in
+ * the plan and returns it in *warp_width (may be NULL) with the mean
+ * per-launch times in times_ms[4] (order 2, 4, 8, 16; may be NULL).
+ * Writes only the workspace; synchronises the stream (not for capture). */
+int proj_set_warp_shape(proj_plan plan, int warp_width);
+int proj_get_warp_shape(proj_plan plan, int *warp_width);
+int proj_autotune_forward_grad(proj_plan plan, const float *d_pose, int loss, const float *d_ref, void *d_ws,
+                               size_t ws_bytes, proj_stream stream, int reps, float *times_ms, int *warp_width);
+
 /* Batches: several independent forward pose-gradient problems (each a plan
  * with its own volume, detector, views, poses and workspace, e.g. registration
  * problems of uneven size) run by one persistent launch.  Resident blocks
  * take 16 x 16-pixel ray tiles of any problem from a single atomic work
  * counter (no waits); problems are ordered by estimated cost per tile,
  * longest first, so small problems fill the tail of large ones.  Results
- * are identical to proj_forward_pose_grad on each plan.
+ * are identical to proj_forward_pose_grad on each plan at the default warp
+ * shape (the batched march always uses 4 x 8-pixel warps).
  *
  * proj_batch_create binds, for problem i: plans[i] (needs
  * PROJ_OP_FORWARD_GRAD; volume set with proj_set_volume before runs),

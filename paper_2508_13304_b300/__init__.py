@@ -68,6 +68,10 @@ _SIGS = {
                                       _P, _P, _I, _P, _P, _P, _P],
     "proj_fdk_filter": [_P, _P, ctypes.c_float, _P, _P],
     "proj_sharpness": [_P, _P, _P, _P, _P, _SZ, _P],
+    "proj_set_warp_shape": [_P, _I],
+    "proj_get_warp_shape": [_P, ctypes.POINTER(_I)],
+    "proj_autotune_forward_grad": [_P, _P, _I, _P, _P, _SZ, _P, _I, ctypes.POINTER(ctypes.c_float),
+                                   ctypes.POINTER(_I)],
     "proj_batch_create": [_I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P),
                           ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_SZ),
                           ctypes.POINTER(_P)],
@@ -320,6 +324,33 @@ def proj_sharpness(plan: Plan, vol, loss, grad=None, ws=None, stream=None):
                                 _stream(stream)))
 
 
+WARP_WIDTHS = (2, 4, 8, 16)
+
+
+def proj_set_warp_shape(plan: Plan, warp_width: int):
+    _check(lib().proj_set_warp_shape(plan.handle, int(warp_width)))
+
+
+def proj_get_warp_shape(plan: Plan) -> int:
+    w = ctypes.c_int()
+    _check(lib().proj_get_warp_shape(plan.handle, ctypes.byref(w)))
+    return int(w.value)
+
+
+def proj_autotune_forward_grad(plan: Plan, pose, loss, ref, ws, reps=3, stream=None):
+    """Time the fused march per warp shape on this data, keep the fastest in
+    the plan; returns (warp_width, {width: ms per launch})."""
+    import torch
+    p, nb = _ws(ws)
+    n_ref = (plan.n_inst if loss == PROJ_LOSS_RESIDUAL else plan.geom.n_views) * plan.img_numel
+    times = (ctypes.c_float * 4)()
+    w = ctypes.c_int()
+    _check(lib().proj_autotune_forward_grad(plan.handle, _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"),
+                                            int(loss), _ptr(ref, torch.float32, n_ref, "ref"), p, nb,
+                                            _stream(stream), int(reps), times, ctypes.byref(w)))
+    return int(w.value), dict(zip(WARP_WIDTHS, [float(t) for t in times]))
+
+
 class Batch:
     """Handle of a proj_batch; keeps the bound plans and tensors alive."""
 
@@ -425,6 +456,9 @@ class Projector:
         proj = torch.empty((self.n_inst, g.nv, g.nu), device=self.device) if want_proj else None
         proj_forward_pose_grad(self.plan, self._t(pose), loss, self._t(ref), grad, lossv, proj, self.ws)
         return (grad, lossv, proj) if want_proj else (grad, lossv)
+
+    def autotune(self, pose, loss, ref, reps=3):
+        return proj_autotune_forward_grad(self.plan, self._t(pose), loss, self._t(ref), self.ws, reps)
 
     def back(self, proj, pose, weight=PROJ_W_NONE):
         import torch

@@ -55,6 +55,8 @@ struct proj_plan_s {
   int* d_pose_ptr = nullptr;
   int* d_pose_idx = nullptr;
   FdkView* d_fdk = nullptr;  // per instance
+  // rays per warp row in the fused pose-gradient march (2, 4, 8 or 16)
+  int warp_width = 4;
   // optional timing of the main kernel of each call
   bool timing = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -394,7 +396,8 @@ int proj_forward_pose_grad(proj_plan p, const float* d_pose, int loss, const flo
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = setup(p, d_pose, w, s))) return rc;
   mark(p, true, s);
-  cudaError_t e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, loss, d_ref, d_proj, w.part_f, s);
+  cudaError_t e =
+      launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, loss, d_ref, d_proj, w.part_f, s, p->warp_width);
   mark(p, false, s);
   if (e != cudaSuccess) return cuda_fail(e, "forward pose-gradient launch");
   e = launch_forward_grad_reduce(w.inst, w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_tiles, p->geo, loss,
@@ -479,6 +482,64 @@ int proj_forward_adjoint(proj_plan p, const float* d_y, const float* d_pose, flo
   cudaError_t e = launch_forward_adjoint(w.inst, p->n_inst, p->geo, d_y, w.acc, d_vol, s);
   mark(p, false, s);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "forward adjoint launch");
+}
+
+int proj_set_warp_shape(proj_plan p, int warp_width) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (warp_width != 2 && warp_width != 4 && warp_width != 8 && warp_width != 16)
+    return fail(PROJ_E_ARG, "warp width %d is not one of 2, 4, 8, 16", warp_width);
+  p->warp_width = warp_width;
+  return PROJ_OK;
+}
+
+int proj_get_warp_shape(proj_plan p, int* warp_width) {
+  if (!p || !warp_width) return fail(PROJ_E_ARG, "plan or warp_width is NULL");
+  *warp_width = p->warp_width;
+  return PROJ_OK;
+}
+
+int proj_autotune_forward_grad(proj_plan p, const float* d_pose, int loss, const float* d_ref, void* d_ws,
+                               size_t ws_bytes, proj_stream stream, int reps, float* times_ms, int* warp_width) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_pose || !d_ref) return fail(PROJ_E_ARG, "proj_autotune_forward_grad: NULL pose or reference");
+  if (loss != PROJ_LOSS_RESIDUAL && loss != PROJ_LOSS_L2 && loss != PROJ_LOSS_NCC)
+    return fail(PROJ_E_ARG, "unknown loss mode %d", loss);
+  if (reps < 1 || reps > 1000) return fail(PROJ_E_ARG, "reps must be in 1..1000");
+  int rc = need_op(p, PROJ_OP_FORWARD_GRAD, "proj_autotune_forward_grad");
+  if (rc) return rc;
+  WsView w;
+  if ((rc = check_ws(p, d_ws, ws_bytes, &w))) return rc;
+  if ((rc = check_device(p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = setup(p, d_pose, w, s))) return rc;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  const int widths[4] = {2, 4, 8, 16};
+  float best = 0.f;
+  int pick = p->warp_width;
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+    e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, loss, d_ref, nullptr, w.part_f, s, widths[i]);
+    if (e == cudaSuccess) e = cudaEventRecord(a, s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r)
+      e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, loss, d_ref, nullptr, w.part_f, s, widths[i]);
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    ms /= (float)reps;
+    if (times_ms) times_ms[i] = ms;
+    if (e == cudaSuccess && (i == 0 || ms < best)) {
+      best = ms;
+      pick = widths[i];
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune launches");
+  p->warp_width = pick;
+  if (warp_width) *warp_width = pick;
+  return PROJ_OK;
 }
 
 int proj_enable_kernel_timing(proj_plan p, int enable) {

@@ -32,11 +32,16 @@ __device__ __forceinline__ float warp_sum(float v) {
 // detector (ragged tiles).  Each warp takes a 4 x 8 pixel sub-tile, so each
 // quarter-warp (the 8 lanes served together by the L1 data pipe for 16-byte
 // loads) is a compact 4 x 2 patch of rays whose gathers share cache lines.
+// WU is the warp's width in pixels (WU x 32/WU rays); 4 is the default, the
+// other widths (2, 8, 16) serve the fused march's shape autotuner.
+template <int WU = 4>
 __device__ __forceinline__ bool tile_pixel(int tile, int tiles_u, const Geo& g, int& iu, int& iv) {
+  static_assert(WU == 2 || WU == 4 || WU == 8 || WU == 16, "warp width");
+  constexpr int WV = 32 / WU, kPerRow = kTileU / WU;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int tu = tile % tiles_u, tv = tile / tiles_u;
-  iu = tu * kTileU + (w & 3) * 4 + (lane & 3);
-  iv = tv * kTileV + (w >> 2) * 8 + (lane >> 2);
+  iu = tu * kTileU + (w % kPerRow) * WU + (lane % WU);
+  iv = tv * kTileV + (w / kPerRow) * WV + (lane / WU);
   return iu < g.nu && iv < g.nv;
 }
 
@@ -218,13 +223,13 @@ __global__ void k_count(const InstTable* __restrict__ inst, int n_tiles, int til
 // One 16 x 16 ray tile (instance n, tile index) of the fused march, block-
 // wide: writes the tile's record part[(n * n_tiles + tile) * kRec ...].
 // Shared by the per-problem kernel and the persistent multi-problem kernel.
-template <int LOSS>
+template <int LOSS, int WU = 4>
 __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, int n, int tile, int n_tiles,
                                            int tiles_u, const Geo& g, const float4* __restrict__ vol,
                                            const float* __restrict__ ref, float* __restrict__ proj,
                                            float* __restrict__ part, float (*red)[kRec]) {
   int iu, iv;
-  const bool on_det = tile_pixel(tile, tiles_u, g, iu, iv);
+  const bool on_det = tile_pixel<WU>(tile, tiles_u, g, iu, iv);
   const InstTable& T = inst[n];
   float a = 0.f;
   float s0[3] = {0.f, 0.f, 0.f};
@@ -325,13 +330,14 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
   __syncthreads();  // red is reused by the next tile of a persistent block
 }
 
-template <int LOSS>
+template <int LOSS, int WU>
 __global__ void __launch_bounds__(kMarchThreads)
     k_forward_grad(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g,
                    const float4* __restrict__ vol, const float* __restrict__ ref, float* __restrict__ proj,
                    float* __restrict__ part) {
   __shared__ float red[kMarchThreads / 32][kRec];
-  march_tile<LOSS>(inst, blockIdx.x / n_tiles, blockIdx.x % n_tiles, n_tiles, tiles_u, g, vol, ref, proj, part, red);
+  march_tile<LOSS, WU>(inst, blockIdx.x / n_tiles, blockIdx.x % n_tiles, n_tiles, tiles_u, g, vol, ref, proj, part,
+                       red);
 }
 
 // ---------------------------------------------------------------- batch
@@ -534,22 +540,36 @@ cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long
   return cudaGetLastError();
 }
 
-cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4, int loss,
-                                const float* d_ref, float* d_proj, float* d_part, cudaStream_t s) {
-  const int nt = tiles_of(geo), tu = tiles_u_of(geo);
-  const int grid = n_inst * nt;
+namespace {
+template <int WU>
+void launch_forward_grad_w(const InstTable* d_inst, int grid, int nt, int tu, const Geo& geo, const float4* d_vol4,
+                           int loss, const float* d_ref, float* d_proj, float* d_part, cudaStream_t s) {
   switch (loss) {
     case PROJ_LOSS_RESIDUAL:
-      k_forward_grad<PROJ_LOSS_RESIDUAL><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_ref, d_proj,
-                                                                        d_part);
+      k_forward_grad<PROJ_LOSS_RESIDUAL, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_ref,
+                                                                            d_proj, d_part);
       break;
     case PROJ_LOSS_L2:
-      k_forward_grad<PROJ_LOSS_L2><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_ref, d_proj, d_part);
+      k_forward_grad<PROJ_LOSS_L2, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_ref, d_proj,
+                                                                      d_part);
       break;
     default:
-      k_forward_grad<PROJ_LOSS_NCC><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_ref, d_proj,
-                                                                   d_part);
+      k_forward_grad<PROJ_LOSS_NCC, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_ref, d_proj,
+                                                                       d_part);
       break;
+  }
+}
+}  // namespace
+
+cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4, int loss,
+                                const float* d_ref, float* d_proj, float* d_part, cudaStream_t s, int warp_width) {
+  const int nt = tiles_of(geo), tu = tiles_u_of(geo);
+  const int grid = n_inst * nt;
+  switch (warp_width) {
+    case 2: launch_forward_grad_w<2>(d_inst, grid, nt, tu, geo, d_vol4, loss, d_ref, d_proj, d_part, s); break;
+    case 8: launch_forward_grad_w<8>(d_inst, grid, nt, tu, geo, d_vol4, loss, d_ref, d_proj, d_part, s); break;
+    case 16: launch_forward_grad_w<16>(d_inst, grid, nt, tu, geo, d_vol4, loss, d_ref, d_proj, d_part, s); break;
+    default: launch_forward_grad_w<4>(d_inst, grid, nt, tu, geo, d_vol4, loss, d_ref, d_proj, d_part, s); break;
   }
   return cudaGetLastError();
 }

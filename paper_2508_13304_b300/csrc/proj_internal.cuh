@@ -109,8 +109,10 @@ cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float* d_vol1, float4
 cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const float* d_vol1, float* d_proj,
                            cudaStream_t s);
 cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long* d_count, cudaStream_t s);
+// warp_width: rays per warp row of the 16x16 tile (2, 4, 8 or 16; other values use 4)
 cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4, int loss,
-                                const float* d_ref, float* d_proj, float* d_part, cudaStream_t s);
+                                const float* d_ref, float* d_proj, float* d_part, cudaStream_t s,
+                                int warp_width = 4);
 cudaError_t launch_forward_grad_reduce(const InstTable* d_inst, const PoseTable* d_ptab, int n_pose,
                                        const int* d_pose_ptr, const int* d_pose_idx, int n_tiles, Geo geo,
                                        int loss, const float* d_part, float* d_grad, float* d_loss,

@@ -107,6 +107,45 @@ def test_forward_pose_grad_ragged(ragged, loss):
         np.testing.assert_allclose(np32(L), L_ref, rtol=1e-4)
 
 
+@pytest.mark.parametrize("width", [2, 8, 16])
+def test_forward_pose_grad_warp_shapes(ragged, width):
+    """Every ray-tile shape of the fused march meets the parity bars and
+    agrees with the default shape to FP32 rounding of the tile sums."""
+    d = ragged
+    g, mu, poses, iv, ip = d["g"], d["mu"], d["poses"], d["iv"], d["ip"]
+    target = f32(oracle.forward(g, mu, f32([[1.0, -1.0, 0.5, 0.05, -0.02, 0.03]]), inst_view=[0, 1, 2],
+                                inst_pose=[0, 0, 0]))
+    proj_ref = oracle.forward(g, mu, poses, iv, ip)
+    L_ref, w = oracle.pose_loss_weights("ncc", proj_ref, target, iv, ip, 2)
+    gth, _ = oracle.forward_grad(g, mu, poses, w, iv, ip, mode=oracle.GRAD_ANALYTIC)
+    P = d["P"]
+    base, _ = P.forward_pose_grad(poses, pb.PROJ_LOSS_NCC, target)
+    pb.proj_set_warp_shape(P.plan, width)
+    try:
+        assert pb.proj_get_warp_shape(P.plan) == width
+        grad, L = P.forward_pose_grad(poses, pb.PROJ_LOSS_NCC, target)
+    finally:
+        pb.proj_set_warp_shape(P.plan, 4)
+    assert grad_rel(np32(grad), gth) <= TOL_GRAD
+    assert grad_rel(np32(grad), np32(base)) <= 1e-5
+    np.testing.assert_allclose(np32(L), L_ref, rtol=1e-4)
+    with pytest.raises(pb.ProjError):
+        pb.proj_set_warp_shape(P.plan, 3)
+
+
+def test_autotune_picks_a_shape_and_keeps_results(ragged):
+    d = ragged
+    P = pb.Projector(d["g"], n_pose=2, inst_view=d["iv"], inst_pose=d["ip"], ops=pb.PROJ_OP_FORWARD_GRAD)
+    P.set_volume(d["mu"])
+    target = f32(oracle.forward(d["g"], d["mu"], np.zeros(6), inst_view=[0, 1, 2], inst_pose=[0, 0, 0]))
+    base, _ = P.forward_pose_grad(d["poses"], pb.PROJ_LOSS_L2, target)
+    width, times = P.autotune(d["poses"], pb.PROJ_LOSS_L2, target, reps=2)
+    assert width in pb.WARP_WIDTHS and pb.proj_get_warp_shape(P.plan) == width
+    assert all(t > 0 for t in times.values()) and times[width] == min(times.values())
+    grad, _ = P.forward_pose_grad(d["poses"], pb.PROJ_LOSS_L2, target)
+    assert grad_rel(np32(grad), np32(base)) <= 1e-5
+
+
 def test_forward_pose_grad_is_deterministic(ragged):
     d = ragged
     w = f32(np.random.default_rng(3).standard_normal((5, d["g"].nv, d["g"].nu)))
