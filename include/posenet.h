@@ -1,0 +1,105 @@
+/* C ABI of the pose-proposal network kernels of libproj.so (sm_103a).
+ *
+ * The paper closes with learned, coarse-to-fine pose initialisation as
+ * future work (Sec. V); this library provides the building blocks of a
+ * small convolutional pose regressor trained on digitally reconstructed
+ * radiographs from proj_forward: a BF16 GEMM on the 5th-generation tensor
+ * cores (tcgen05.mma with the accumulator in tensor memory, operands staged
+ * by TMA) and the data-movement kernels that map 3x3 stride-2 convolutions
+ * and their gradients onto it.  The paper has no counterpart of these calls.
+ *
+ * Conventions.  BF16 arrays are passed as void* (IEEE bfloat16, 2 bytes).
+ * Matrices are row-major with an explicit leading dimension in elements.
+ * Images and activations are NHWC: [batch][height][width][channels].
+ * Every pointer is a device pointer on the current device unless stated;
+ * every call only enqueues work on `stream` (no synchronisation, no
+ * allocation) except pn_status.  Return codes are those of proj.h
+ * (PROJ_OK, PROJ_E_ARG, PROJ_E_CUDA); the message of the last failure is
+ * in proj_last_error().  Device-side wait timeouts set bits of a per-device
+ * status word, read with pn_status. */
+#ifndef PAPER_2508_13304_POSENET_H
+#define PAPER_2508_13304_POSENET_H
+
+#include <stddef.h>
+
+#include "proj.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* D = epilogue(A . B^T): A [M][K] (leading dimension lda), B [N][K] (ldb),
+ * both BF16, FP32 accumulation.  Epilogue per element, in this order: + bias[n]
+ * (bias may be NULL), max(0, .) if relu, times (mask[m][n] > 0) if mask
+ * (BF16 [M][ldm]) is not NULL.  Output to D32 (FP32) and/or D16 (BF16),
+ * both [M][ldd]; at least one.  Requirements: M, N, K >= 1; lda, ldb
+ * multiples of 8 and >= K; A and B 16-byte aligned (TMA); ldd >= N.
+ * split_k >= 1 divides the K loop over that many CTAs per tile; with
+ * split_k > 1, part must hold split_k * M * N floats (raw partial sums,
+ * added in a fixed order by a second kernel, so results are deterministic).
+ * Elements of A and B past M, N or K are read as zero. */
+int pn_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
+                 const void *mask, int ldm, int relu, float *D32, void *D16, int ldd, int split_k, float *part,
+                 proj_stream stream);
+
+/* The split_k that pn_gemm_bf16 would use well for this shape (about two
+ * waves of CTAs on the device's SMs, at least 4 K blocks of 64 per CTA). */
+int pn_gemm_split_hint(int M, int N, int K);
+
+/* im2col of a 3x3, stride-2, padding-1 convolution: x NHWC BF16
+ * [B][H][W][C] -> col BF16 [B*Ho*Wo][kp] with Ho = (H+1)/2, Wo = (W+1)/2,
+ * col[(b,ho,wo)][(kh*3+kw)*C + c] = x[b][2ho-1+kh][2wo-1+kw][c] (zero outside
+ * the image) and zero for columns >= 9C.  kp: multiple of 8, >= 9C.  With C
+ * a multiple of 8, x must be 16-byte aligned. */
+int pn_im2col_3x3s2(const void *x, int B, int H, int W, int C, int kp, void *col, proj_stream stream);
+
+/* Adjoint of pn_im2col_3x3s2 (input gradient of the convolution): dx[b][hi][wi][c]
+ * = sum of dcol over the (output pixel, tap) pairs that read (hi, wi, c),
+ * dcol FP32 [B*Ho*Wo][kp].  If mask (BF16 NHWC like dx) is not NULL the sum
+ * is zeroed where mask <= 0 (ReLU backward of the layer that produced x).
+ * Output BF16 (dx16) and/or FP32 (dx32). */
+int pn_col2im_3x3s2(const float *dcol, int B, int H, int W, int C, int kp, const void *mask, void *dx16,
+                    float *dx32, proj_stream stream);
+
+/* dst [cols][ld_dst] = src [rows][cols]^T, BF16; columns rows..ld_dst-1 of
+ * dst are written with zeros (so a GEMM operand can have a leading
+ * dimension that is a multiple of 8).  ld_dst >= rows. */
+int pn_transpose_bf16(const void *src, int rows, int cols, void *dst, int ld_dst, proj_stream stream);
+
+/* out[n] = sum over m of y[m][n] (y BF16 [M][ld]) with FP32 partial sums per
+ * row block and an FP64 fixed-order final sum (bias gradients).  scratch:
+ * at least pn_colsum_scratch_floats(M, N) floats. */
+size_t pn_colsum_scratch_floats(int M, int N);
+int pn_colsum_bf16(const void *y, int M, int N, int ld, float *out, float *scratch, proj_stream stream);
+
+/* Network input from DRRs: proj FP32 [n_img][n_views][nv][nu] (the views of
+ * an image consecutive, as proj_forward writes instances) -> out BF16 NHWC
+ * [n_img][nv/factor][nu/factor][n_views]: box average over factor x factor
+ * pixels, then per (image, view) zero mean and unit variance (a constant
+ * image maps to zeros).  nu and nv multiples of factor; (nu/factor)*(nv/factor)
+ * floats must fit in 200 KB of shared memory. */
+int pn_prepare_images(const float *proj, int n_img, int n_views, int nu, int nv, int factor, void *out,
+                      proj_stream stream);
+
+/* Mean squared error of y (FP32 [B][ldy], first n_out columns) against
+ * target (FP32 [B][n_out]): *loss = mean (y - t)^2 over B*n_out (loss may be
+ * NULL); dy (BF16 [B][lddy], may be NULL) = 2 (y - t) / (B n_out), zero in
+ * columns n_out..lddy-1.  B * lddy <= 2^24. */
+int pn_mse_loss(const float *y, int B, int n_out, int ldy, const float *target, float *loss, void *dy, int lddy,
+                proj_stream stream);
+
+/* dst = BF16(src), round to nearest even, n elements. */
+int pn_to_bf16(const float *src, long long n, void *dst, proj_stream stream);
+
+/* Synchronise the stream, return and clear the status word of the current
+ * device: 0 = clean; bit 1: a TMA stage never filled, bit 2: an
+ * accumulator never completed, bit 4: a stage was never released (each
+ * after a 2 s bound on the wait; the CTA then released its tensor memory
+ * and returned, and the output of that launch is undefined). */
+int pn_status(proj_stream stream, int *status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -77,6 +77,17 @@ _SIGS = {
                           ctypes.POINTER(_P)],
     "proj_batch_run": [_P, _P],
     "proj_batch_destroy": [_P],
+    "pn_gemm_bf16": [_I, _I, _I, _P, _I, _P, _I, _P, _P, _I, _I, _P, _P, _I, _I, _P, _P],
+    "pn_gemm_split_hint": [_I, _I, _I],
+    "pn_im2col_3x3s2": [_P, _I, _I, _I, _I, _I, _P, _P],
+    "pn_col2im_3x3s2": [_P, _I, _I, _I, _I, _I, _P, _P, _P, _P],
+    "pn_transpose_bf16": [_P, _I, _I, _P, _I, _P],
+    "pn_colsum_scratch_floats": [_I, _I],
+    "pn_colsum_bf16": [_P, _I, _I, _I, _P, _P, _P],
+    "pn_prepare_images": [_P, _I, _I, _I, _I, _I, _P, _P],
+    "pn_mse_loss": [_P, _I, _I, _I, _P, _P, _P, _I, _P],
+    "pn_to_bf16": [_P, ctypes.c_longlong, _P, _P],
+    "pn_status": [_P, ctypes.POINTER(_I)],
     "proj_enable_kernel_timing": [_P, _I],
     "proj_kernel_time_ms": [_P, ctypes.POINTER(ctypes.c_float)],
     "proj_last_error": [],
@@ -96,7 +107,8 @@ def lib():
         for name, args in _SIGS.items():
             f = getattr(L, name)
             f.argtypes = args
-            f.restype = ctypes.c_char_p if name in ("proj_last_error", "proj_version") else ctypes.c_int
+            f.restype = (ctypes.c_char_p if name in ("proj_last_error", "proj_version") else
+                         ctypes.c_size_t if name == "pn_colsum_scratch_floats" else ctypes.c_int)
         _lib = L
     return _lib
 
@@ -412,6 +424,96 @@ def proj_kernel_time_ms(plan: Plan) -> float:
     ms = ctypes.c_float()
     _check(lib().proj_kernel_time_ms(plan.handle, ctypes.byref(ms)))
     return float(ms.value)
+
+
+# ------------------------------------------------------- network kernels (posenet.h)
+
+def _bf(t, numel=None, name="tensor", allow_none=False):
+    import torch
+    return _ptr(t, torch.bfloat16, numel, name, allow_none)
+
+
+def _f32(t, numel=None, name="tensor", allow_none=False):
+    import torch
+    return _ptr(t, torch.float32, numel, name, allow_none)
+
+
+def pn_gemm_bf16(M, N, K, A, lda, B, ldb, bias=None, mask=None, ldm=0, relu=False, D32=None, D16=None, ldd=None,
+                 split_k=1, part=None, stream=None):
+    """D = epilogue(A . B^T) on the tensor cores (see include/posenet.h)."""
+    ldd = N if ldd is None else ldd
+    if A is None or B is None or A.numel() < (M - 1) * lda + K or B.numel() < (N - 1) * ldb + K:
+        raise ValueError("A or B smaller than the stated shape")
+    for t, nm in ((D32, "D32"), (D16, "D16")):
+        if t is not None and t.numel() < (M - 1) * ldd + N:
+            raise ValueError("%s smaller than the stated shape" % nm)
+    if mask is not None and mask.numel() < (M - 1) * ldm + N:
+        raise ValueError("mask smaller than the stated shape")
+    if split_k > 1 and (part is None or part.numel() < split_k * M * N):
+        raise ValueError("part must hold split_k * M * N floats")
+    _check(lib().pn_gemm_bf16(int(M), int(N), int(K), _bf(A, name="A"), int(lda), _bf(B, name="B"), int(ldb),
+                              _f32(bias, N, "bias", allow_none=True), _bf(mask, name="mask", allow_none=True),
+                              int(ldm), 1 if relu else 0, _f32(D32, name="D32", allow_none=True),
+                              _bf(D16, name="D16", allow_none=True), int(ldd), int(split_k),
+                              _f32(part, name="part", allow_none=True), _stream(stream)))
+
+
+def pn_gemm_split_hint(M, N, K) -> int:
+    return int(lib().pn_gemm_split_hint(int(M), int(N), int(K)))
+
+
+def pn_im2col_3x3s2(x, B, H, W, C, kp, col, stream=None):
+    Ho, Wo = (H + 1) // 2, (W + 1) // 2
+    _check(lib().pn_im2col_3x3s2(_bf(x, B * H * W * C, "x"), B, H, W, C, kp, _bf(col, B * Ho * Wo * kp, "col"),
+                                 _stream(stream)))
+
+
+def pn_col2im_3x3s2(dcol, B, H, W, C, kp, mask=None, dx16=None, dx32=None, stream=None):
+    Ho, Wo = (H + 1) // 2, (W + 1) // 2
+    n = B * H * W * C
+    _check(lib().pn_col2im_3x3s2(_f32(dcol, B * Ho * Wo * kp, "dcol"), B, H, W, C, kp,
+                                 _bf(mask, n, "mask", allow_none=True), _bf(dx16, n, "dx16", allow_none=True),
+                                 _f32(dx32, n, "dx32", allow_none=True), _stream(stream)))
+
+
+def pn_transpose_bf16(src, rows, cols, dst, ld_dst=None, stream=None):
+    ld_dst = rows if ld_dst is None else ld_dst
+    _check(lib().pn_transpose_bf16(_bf(src, rows * cols, "src"), rows, cols, _bf(dst, cols * ld_dst, "dst"),
+                                   int(ld_dst), _stream(stream)))
+
+
+def pn_colsum_scratch_floats(M, N) -> int:
+    return int(lib().pn_colsum_scratch_floats(int(M), int(N)))
+
+
+def pn_colsum_bf16(y, M, N, ld, out, scratch, stream=None):
+    if y.numel() < (M - 1) * ld + N or scratch.numel() < pn_colsum_scratch_floats(M, N):
+        raise ValueError("y or scratch smaller than the stated shape")
+    _check(lib().pn_colsum_bf16(_bf(y, name="y"), M, N, ld, _f32(out, N, "out"), _f32(scratch, name="scratch"),
+                                _stream(stream)))
+
+
+def pn_prepare_images(proj, n_img, n_views, nu, nv, factor, out, stream=None):
+    _check(lib().pn_prepare_images(_f32(proj, n_img * n_views * nu * nv, "proj"), n_img, n_views, nu, nv, factor,
+                                   _bf(out, n_img * n_views * (nu // factor) * (nv // factor), "out"),
+                                   _stream(stream)))
+
+
+def pn_mse_loss(y, B, n_out, ldy, target, loss=None, dy=None, lddy=None, stream=None):
+    lddy = n_out if lddy is None else lddy
+    _check(lib().pn_mse_loss(_f32(y, B * ldy, "y"), B, n_out, ldy, _f32(target, B * n_out, "target"),
+                             _f32(loss, 1, "loss", allow_none=True), _bf(dy, B * lddy, "dy", allow_none=True),
+                             int(lddy), _stream(stream)))
+
+
+def pn_to_bf16(src, dst, stream=None):
+    _check(lib().pn_to_bf16(_f32(src, name="src"), src.numel(), _bf(dst, src.numel(), "dst"), _stream(stream)))
+
+
+def pn_status(stream=None) -> int:
+    st = ctypes.c_int(0)
+    _check(lib().pn_status(_stream(stream), ctypes.byref(st)))
+    return int(st.value)
 
 
 class Projector:

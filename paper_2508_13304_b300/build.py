@@ -31,7 +31,7 @@ def sources():
 
 def deps():
     return sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + \
-        [os.path.join(ROOT, "include", "proj.h"), os.path.abspath(__file__)]
+        sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))) + [os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:

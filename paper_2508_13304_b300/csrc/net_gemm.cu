@@ -1,0 +1,316 @@
+// BF16 GEMM on the 5th-generation tensor cores (sm_103a):
+//   D[M][N] = epilogue( A[M][K] . B[N][K]^T ),  FP32 accumulation in TMEM.
+//
+// One CTA computes a 128 x BN tile of D.  Warp 0 (one lane) streams 128 x 64
+// tiles of A and BN x 64 tiles of B into a kStages-deep shared-memory ring
+// with TMA (128-byte swizzle, zero fill past the matrix edges); warp 1 (one
+// lane) issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128,
+// K = 16 per instruction) into the TMEM accumulator and releases each stage
+// with tcgen05.commit; then all four warps read their 32 TMEM lanes
+// (tcgen05.ld 32x32b) and apply bias, ReLU and a ReLU mask before storing
+// FP32 and/or BF16.  With split-K the CTA writes raw FP32 partial sums that
+// a second kernel adds in a fixed order.  Every wait on an mbarrier is
+// bounded by the global timer; a timeout sets a status bit and the CTA
+// releases its TMEM and returns.
+#include <cstdio>
+
+#include "net_internal.cuh"
+
+namespace pnk {
+
+namespace {
+
+constexpr unsigned long long kWaitNs = 2000000000ULL;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the completion of the phase with the given parity, at most kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand tile stored as rows
+// of 128 bytes (64 BF16 of K) with the 128-byte swizzle, 8-row groups 1024
+// bytes apart: start address, leading offset (unused by swizzled K-major
+// layouts), stride offset 1024 B, descriptor version 1, layout SWIZZLE_128B.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = bn, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int bn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(bn >> 3) << 17) |
+         (static_cast<uint32_t>(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN>
+__host__ __device__ constexpr int tmem_cols() {
+  return BN < 32 ? 32 : BN;
+}
+
+__device__ __forceinline__ float epi_value(float acc, int row, int col, const GemmEpi& e) {
+  float v = acc;
+  if (e.bias) v += __ldg(e.bias + col);
+  if (e.relu) v = fmaxf(v, 0.f);
+  if (e.mask && !(__bfloat162float(e.mask[(size_t)row * e.ldm + col]) > 0.f)) v = 0.f;
+  return v;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N, int K,
+                int kb_per_split, GemmEpi epi, int* status) {
+  constexpr uint32_t kBytesA = kBM * kBK * 2, kBytesB = BN * kBK * 2;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
+  uint8_t* const gbase = smem_raw + (base - raw);
+  const uint32_t sA = base, sB = base + kStages * kBytesA;
+  const uint32_t bars = sB + kStages * kBytesB;  // full[kStages], empty[kStages], done
+  uint64_t* const bar_ptr = reinterpret_cast<uint64_t*>(gbase + (bars - base));
+  uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bar_ptr + 2 * kStages + 1);
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (kStages + s); };
+  const uint32_t done = bars + 8u * (2 * kStages);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  const int nkb_all = (K + kBK - 1) / kBK;
+  const int kb0 = blockIdx.z * kb_per_split;
+  const int nkb = min(nkb_all, kb0 + kb_per_split) - kb0;  // >= 1 by construction on the host
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(tmem_cols<BN>())
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_d = *tmem_slot;
+  int fail = 0;
+
+  if (warp == 0 && lane == 0) {
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % kStages;
+      if (i >= kStages && !mbar_wait(empty(s), ((i / kStages) - 1) & 1)) {
+        fail = kStatusTimeoutFree;
+        break;
+      }
+      mbar_expect_tx(full(s), kBytesA + kBytesB);
+      tma_load_2d(sA + s * kBytesA, &ta, full(s), (kb0 + i) * kBK, m0);
+      tma_load_2d(sB + s * kBytesB, &tb, full(s), (kb0 + i) * kBK, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(BN);
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % kStages;
+      if (!mbar_wait(full(s), (i / kStages) & 1)) {
+        fail = kStatusTimeoutTma;
+        break;
+      }
+      tc_fence_after();
+      const uint64_t da = sw128_desc(sA + s * kBytesA), db = sw128_desc(sB + s * kBytesB);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk)  // +32 bytes of K per instruction
+        umma_bf16(tmem_d, da + 2 * kk, db + 2 * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+      umma_commit(empty(s));
+    }
+    umma_commit(done);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(done, 0);
+  if (!ok && threadIdx.x == 0) fail |= kStatusTimeoutMma;
+  if (fail) atomicOr(status, fail);
+  tc_fence_after();
+
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t lane_base = tmem_d + (static_cast<uint32_t>(warp * 32) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      __syncwarp();  // tcgen05.ld is warp-collective
+      tmem_ld16(lane_base + c0, v);
+      const int col0 = n0 + c0;
+      if (row >= M || col0 >= N) continue;
+      const int nval = min(16, N - col0);
+      if (epi.part) {
+        float* dst = epi.part + ((size_t)blockIdx.z * M + row) * N + col0;
+        for (int j = 0; j < nval; ++j) dst[j] = v[j];
+        continue;
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (j < nval) v[j] = epi_value(v[j], row, col0 + j, epi);
+      if (epi.d32) {
+        float* dst = epi.d32 + (size_t)row * epi.ldd + col0;
+        if (nval == 16 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        } else {
+          for (int j = 0; j < nval; ++j) dst[j] = v[j];
+        }
+      }
+      if (epi.d16) {
+        __nv_bfloat16* dst = epi.d16 + (size_t)row * epi.ldd + col0;
+        if (nval == 16 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+          __nv_bfloat162 h[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+          reinterpret_cast<uint4*>(dst)[0] = *reinterpret_cast<uint4*>(&h[0]);
+          reinterpret_cast<uint4*>(dst)[1] = *reinterpret_cast<uint4*>(&h[4]);
+        } else {
+          for (int j = 0; j < nval; ++j) dst[j] = __float2bfloat16_rn(v[j]);
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(tmem_cols<BN>())
+                 : "memory");
+  }
+}
+
+// Fixed-order sum of the split-K partials, then the epilogue.
+__global__ void k_split_reduce(const float* __restrict__ part, int split, int M, int N, GemmEpi epi) {
+  const long long total = (long long)M * N;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < split; ++z) s += part[(size_t)z * total + i];
+    const int row = (int)(i / N), col = (int)(i % N);
+    const float v = epi_value(s, row, col, epi);
+    if (epi.d32) epi.d32[(size_t)row * epi.ldd + col] = v;
+    if (epi.d16) epi.d16[(size_t)row * epi.ldd + col] = __float2bfloat16_rn(v);
+  }
+}
+
+template <int BN>
+cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int split, int kbs,
+                      const GemmEpi& epi, int* status, cudaStream_t s) {
+  const size_t smem = gemm_smem_bytes(BN);
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN, split);
+  k_gemm_bf16<BN><<<grid, kGemmThreads, smem, s>>>(ta, tb, M, N, K, kbs, epi, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t gemm_smem_bytes(int bn) {
+  return 1024 + (size_t)kStages * (kBM * kBK * 2 + (size_t)bn * kBK * 2) + 8 * (2 * kStages + 1) + 16;
+}
+
+cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int bn, int split,
+                        int kb_per_split, const GemmEpi& epi, int* status, cudaStream_t s) {
+  switch (bn) {
+    case 32: return launch_bn<32>(ta, tb, M, N, K, split, kb_per_split, epi, status, s);
+    case 64: return launch_bn<64>(ta, tb, M, N, K, split, kb_per_split, epi, status, s);
+    case 128: return launch_bn<128>(ta, tb, M, N, K, split, kb_per_split, epi, status, s);
+    case 256: return launch_bn<256>(ta, tb, M, N, K, split, kb_per_split, epi, status, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_split_reduce(const float* part, int split, int M, int N, const GemmEpi& epi, cudaStream_t s) {
+  const long long total = (long long)M * N;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 148LL * 16) blocks = 148LL * 16;
+  k_split_reduce<<<(int)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(part, split, M, N, epi);
+  return cudaGetLastError();
+}
+
+}  // namespace pnk

@@ -1,5 +1,5 @@
 """Host-side checks of the C ABI that need no GPU: the library loads, exports
-every entry point include/proj.h declares, and rejects invalid arguments on
+every entry point include/*.h declares, and rejects invalid arguments on
 the host (before any CUDA call) with the documented error codes."""
 import ctypes
 import os
@@ -13,7 +13,8 @@ import paper_2508_13304_b300 as pb
 import synth
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "proj.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -24,17 +25,19 @@ def L():
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(proj_[a-z_]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b((?:proj|pn)_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(L):
     names = declared_functions()
-    assert len(names) >= 12
+    assert len(names) >= 30 and any(n.startswith("pn_") for n in names)
     out = subprocess.run(["nm", "-D", "--defined-only", pb.LIB_PATH], capture_output=True, text=True,
                          check=True).stdout
-    exported = set(re.findall(r"\bT (proj_\w+)", out))
+    exported = set(re.findall(r"\bT ((?:proj|pn)_\w+)", out))
     missing = [n for n in names if n not in exported]
     assert not missing, missing
     for n in names:

@@ -1,0 +1,203 @@
+"""GPU parity of the pose-proposal network kernels (tensor-core BF16 GEMM,
+im2col / col2im, transposes, column sums, input preparation, loss) against
+the FP64 oracle on the same BF16-rounded inputs.
+
+Bars.  FP32 outputs of the GEMM: the only difference from FP64 is FP32
+accumulation of K exact BF16 x BF16 products, rel-L2 <= 1e-5 up to K = 8192.
+BF16 outputs: one final rounding (relative 2^-9), rel-L2 <= 4e-3.  Layer
+gradients that pass through a BF16 intermediate: rel-L2 <= 1e-2."""
+import numpy as np
+import pytest
+
+from oracle import posenet as on
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_13304_b300 import build
+    build.build()
+
+
+import paper_2508_13304_b300 as pb  # noqa: E402
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def bf16(rng, shape, scale=1.0):
+    return (scale * torch.from_numpy(rng.standard_normal(shape).astype(np.float32))).to("cuda").bfloat16()
+
+
+def f64(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("M,N,K,lda,ldb", [(128, 128, 64, 64, 64), (300, 48, 200, 200, 208), (1000, 256, 576, 576, 576),
+                                           (64, 6, 256, 256, 256), (517, 1152, 128, 136, 128), (256, 96, 24, 24, 24)])
+def test_gemm_fp32_output(M, N, K, lda, ldb):
+    rng = np.random.default_rng(M + N + K)
+    A, B = bf16(rng, (M, lda)), bf16(rng, (N, ldb))
+    D = torch.full((M, N), float("nan"), device="cuda")
+    pb.pn_gemm_bf16(M, N, K, A, lda, B, ldb, D32=D)
+    torch.cuda.synchronize()
+    assert pb.pn_status() == 0
+    ref = f64(A)[:, :K] @ f64(B)[:, :K].T
+    assert rel(D.cpu().numpy(), ref) <= 1e-5
+
+
+def test_gemm_split_k_is_deterministic_and_exact():
+    rng = np.random.default_rng(9)
+    M, N, K = 96, 160, 8192
+    A, B = bf16(rng, (M, K)), bf16(rng, (N, K))
+    split = 8
+    part = torch.empty(split * M * N, device="cuda")
+    D1 = torch.empty((M, N), device="cuda")
+    D2 = torch.empty((M, N), device="cuda")
+    pb.pn_gemm_bf16(M, N, K, A, K, B, K, D32=D1, split_k=split, part=part)
+    pb.pn_gemm_bf16(M, N, K, A, K, B, K, D32=D2, split_k=split, part=part)
+    torch.cuda.synchronize()
+    assert pb.pn_status() == 0
+    assert torch.equal(D1, D2)
+    assert rel(D1.cpu().numpy(), f64(A) @ f64(B).T) <= 1e-5
+    assert 1 <= pb.pn_gemm_split_hint(M, N, K) <= 64
+
+
+def test_gemm_epilogue_bias_relu_mask_bf16():
+    rng = np.random.default_rng(10)
+    M, N, K = 700, 64, 288
+    A, B = bf16(rng, (M, K)), bf16(rng, (N, K))
+    bias = torch.from_numpy(rng.standard_normal(N).astype(np.float32)).cuda()
+    mask = bf16(rng, (M, N))
+    D16 = torch.empty((M, N), device="cuda", dtype=torch.bfloat16)
+    D32 = torch.empty((M, N), device="cuda")
+    pb.pn_gemm_bf16(M, N, K, A, K, B, K, bias=bias, mask=mask, ldm=N, relu=True, D32=D32, D16=D16)
+    torch.cuda.synchronize()
+    ref = np.maximum(f64(A) @ f64(B).T + bias.cpu().numpy(), 0.0) * (f64(mask) > 0)
+    assert rel(D32.cpu().numpy(), ref) <= 1e-5
+    assert rel(f64(D16), ref) <= 4e-3
+    assert np.all(f64(D16)[f64(mask) <= 0] == 0)
+
+
+def test_gemm_rejects_bad_arguments():
+    A = torch.zeros((8, 24), device="cuda", dtype=torch.bfloat16)
+    D = torch.zeros((8, 8), device="cuda")
+    L = pb.lib()
+    # lda not a multiple of 8
+    assert L.pn_gemm_bf16(8, 8, 20, A.data_ptr(), 20, A.data_ptr(), 24, None, None, 0, 0, D.data_ptr(), None, 8, 1,
+                          None, None) == pb.PROJ_E_ARG
+    # split-K without a partial-sum buffer
+    assert L.pn_gemm_bf16(8, 8, 16, A.data_ptr(), 24, A.data_ptr(), 24, None, None, 0, 0, D.data_ptr(), None, 8, 2,
+                          None, None) == pb.PROJ_E_ARG
+    # misaligned operand
+    assert L.pn_gemm_bf16(8, 8, 16, A.data_ptr() + 2, 24, A.data_ptr(), 24, None, None, 0, 0, D.data_ptr(), None, 8,
+                          1, None, None) == pb.PROJ_E_ARG
+    assert "16-byte" in pb.proj_last_error()
+
+
+# ------------------------------------------------------------ conv layer pieces
+
+def conv_case(rng, B, H, W, Ci, Co):
+    x = torch.relu(bf16(rng, (B, H, W, Ci)))
+    w = bf16(rng, (Co, 3, 3, Ci), scale=(2.0 / (9 * Ci)) ** 0.5)
+    return x, w
+
+
+def kpad(Ci):
+    return (9 * Ci + 7) // 8 * 8
+
+
+def weight_matrix(w, kp):
+    Co = w.shape[0]
+    Wm = torch.zeros((Co, kp), device="cuda", dtype=torch.bfloat16)
+    Wm[:, :w[0].numel()] = w.reshape(Co, -1)
+    return Wm
+
+
+@pytest.mark.parametrize("B,H,W,Ci,Co", [(3, 16, 16, 2, 32), (2, 18, 14, 32, 64), (1, 9, 7, 64, 128)])
+def test_conv_forward_im2col_gemm(B, H, W, Ci, Co):
+    rng = np.random.default_rng(B * H + Ci)
+    x, w = conv_case(rng, B, H, W, Ci, Co)
+    b = torch.from_numpy(0.1 * rng.standard_normal(Co).astype(np.float32)).cuda()
+    kp = kpad(Ci)
+    Ho, Wo = (H + 1) // 2, (W + 1) // 2
+    M = B * Ho * Wo
+    col = torch.empty((M, kp), device="cuda", dtype=torch.bfloat16)
+    pb.pn_im2col_3x3s2(x, B, H, W, Ci, kp, col)
+    Wm = weight_matrix(w, kp)
+    y = torch.empty((M, Co), device="cuda")
+    pb.pn_gemm_bf16(M, Co, kp, col, kp, Wm, kp, bias=b, D32=y)
+    torch.cuda.synchronize()
+    ref = on.conv3x3s2(f64(x), f64(w), b.cpu().numpy())
+    assert rel(y.cpu().numpy().reshape(ref.shape), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("B,H,W,Ci,Co", [(3, 16, 16, 2, 32), (2, 18, 14, 32, 64), (2, 8, 8, 128, 128)])
+def test_conv_backward_pieces(B, H, W, Ci, Co):
+    """dx = col2im(dy . W) with the ReLU mask of x; dW = dy^T . col via
+    transposes and split-K; db = column sums of dy."""
+    rng = np.random.default_rng(B * W + Co)
+    x, w = conv_case(rng, B, H, W, Ci, Co)
+    kp = kpad(Ci)
+    Ho, Wo = (H + 1) // 2, (W + 1) // 2
+    M = B * Ho * Wo
+    dy = bf16(rng, (M, Co))
+    Wm = weight_matrix(w, kp)
+    WmT = torch.empty((kp, Co), device="cuda", dtype=torch.bfloat16)
+    pb.pn_transpose_bf16(Wm, Co, kp, WmT, Co)
+    dcol = torch.empty((M, kp), device="cuda")
+    pb.pn_gemm_bf16(M, kp, Co, dy, Co, WmT, Co, D32=dcol)
+    dx = torch.empty((B, H, W, Ci), device="cuda")
+    pb.pn_col2im_3x3s2(dcol, B, H, W, Ci, kp, mask=x, dx32=dx)
+    col = torch.empty((M, kp), device="cuda", dtype=torch.bfloat16)
+    pb.pn_im2col_3x3s2(x, B, H, W, Ci, kp, col)
+    Mp = (M + 7) // 8 * 8   # TMA needs 16-byte row strides
+    dyT = torch.full((Co, Mp), 7.0, device="cuda", dtype=torch.bfloat16)
+    colT = torch.full((kp, Mp), 7.0, device="cuda", dtype=torch.bfloat16)
+    pb.pn_transpose_bf16(dy, M, Co, dyT, Mp)
+    pb.pn_transpose_bf16(col, M, kp, colT, Mp)
+    split = pb.pn_gemm_split_hint(Co, kp, Mp)
+    part = torch.empty(max(1, split) * Co * kp, device="cuda")
+    dW = torch.empty((Co, kp), device="cuda")
+    pb.pn_gemm_bf16(Co, kp, Mp, dyT, Mp, colT, Mp, D32=dW, split_k=split, part=part)
+    db = torch.empty(Co, device="cuda")
+    scratch = torch.empty(pb.pn_colsum_scratch_floats(M, Co), device="cuda")
+    pb.pn_colsum_bf16(dy, M, Co, Co, db, scratch)
+    torch.cuda.synchronize()
+    assert pb.pn_status() == 0
+    dx_ref, dw_ref, db_ref = on.conv3x3s2_grad(f64(x), f64(w), f64(dy).reshape(B, Ho, Wo, Co))
+    dx_ref = dx_ref * (f64(x) > 0)
+    assert rel(dx.cpu().numpy(), dx_ref) <= 1e-5
+    assert rel(dW.cpu().numpy()[:, :9 * Ci].reshape(dw_ref.shape), dw_ref) <= 1e-5
+    assert np.all(dW.cpu().numpy()[:, 9 * Ci:] == 0)
+    assert rel(db.cpu().numpy(), db_ref) <= 1e-6
+
+
+def test_prepare_and_mse():
+    rng = np.random.default_rng(12)
+    n_img, n_views, nu, nv, f = 5, 2, 96, 72, 3
+    proj = torch.from_numpy(rng.uniform(0, 4, (n_img * n_views, nv, nu)).astype(np.float32)).cuda()
+    proj[3] = 2.0   # a constant image
+    out = torch.empty((n_img, nv // f, nu // f, n_views), device="cuda", dtype=torch.bfloat16)
+    pb.pn_prepare_images(proj, n_img, n_views, nu, nv, f, out)
+    ref = on.prepare(proj.cpu().numpy(), n_views, f)
+    torch.cuda.synchronize()
+    assert rel(f64(out), ref) <= 4e-3
+    assert np.all(f64(out)[1, :, :, 1] == 0)
+    B, n_out, ld = 37, 6, 8
+    y = torch.from_numpy(rng.standard_normal((B, ld)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.standard_normal((B, n_out)).astype(np.float32)).cuda()
+    loss = torch.empty(1, device="cuda")
+    dy = torch.empty((B, ld), device="cuda", dtype=torch.bfloat16)
+    pb.pn_mse_loss(y, B, n_out, ld, t, loss, dy, ld)
+    L_ref, g_ref = on.mse(y.cpu().numpy()[:, :n_out], t.cpu().numpy())
+    assert loss.item() == pytest.approx(L_ref, rel=1e-6)
+    assert rel(f64(dy)[:, :n_out], g_ref) <= 4e-3
+    assert np.all(f64(dy)[:, n_out:] == 0)
