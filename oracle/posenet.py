@@ -17,6 +17,14 @@ serve.  Everything is the textbook definition written out:
 * ReLU, fully connected layers y = x W^T + b, mean squared error;
 * the input preparation: box average of each DRR over factor x factor
   pixels, then zero mean and unit variance per image.
+
+The network stores its activations and back-propagated gradients in BF16.
+``net_forward`` / ``net_backward`` take ``bf16=True`` to round to BF16
+(round to nearest even, after rounding to FP32) at exactly those points,
+so the same network can be checked tightly (same rounding points) and
+loosely (pure FP64); ``bf16_round`` follows the IEEE definition of the
+format (8 exponent bits, 7 stored mantissa bits) and is pinned against
+torch's own conversion.
 """
 from __future__ import annotations
 
@@ -62,41 +70,60 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
-def net_forward(params, x):
+def bf16_round(a):
+    """Round to FP32, then to BF16 with round-to-nearest-even on the 16
+    dropped bits (finite values)."""
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _keep(x):
+    return x
+
+
+def net_forward(params, x, bf16=False):
     """params: dict(conv=[(w, b), ...], fc=[(W, b), ...]); ReLU after every
-    layer but the last fully connected one.  x NHWC.  Returns (out, cache)."""
+    layer but the last fully connected one.  x NHWC.  Returns (out, cache).
+    bf16: round every stored activation (not the output) to BF16."""
+    rd = bf16_round if bf16 else _keep
     acts = [np.asarray(x, dtype=np.float64)]
     h = acts[0]
     for w, b in params["conv"]:
-        h = relu(conv3x3s2(h, w, b))
+        h = rd(relu(conv3x3s2(h, w, b)))
         acts.append(h)
     f = h.reshape(h.shape[0], -1)
     fcs = [f]
     for j, (W, b) in enumerate(params["fc"]):
         f = f @ np.asarray(W, dtype=np.float64).T + np.asarray(b, dtype=np.float64)
         if j + 1 < len(params["fc"]):
-            f = relu(f)
+            f = rd(relu(f))
         fcs.append(f)
     return f, dict(acts=acts, fcs=fcs)
 
 
-def net_backward(params, cache, dout):
+def net_backward(params, cache, dout, bf16=False):
     """Gradients of sum(out * dout) for every parameter, same structure as
-    params, plus the input gradient."""
+    params, plus the input gradient.  bf16: round every back-propagated
+    activation gradient (after its ReLU mask) to BF16; dout is used as
+    given."""
+    rd = bf16_round if bf16 else _keep
     acts, fcs = cache["acts"], cache["fcs"]
     g = np.asarray(dout, dtype=np.float64)
     fc_grads = []
-    for j in reversed(range(len(params["fc"]))):
+    n_fc = len(params["fc"])
+    for j in reversed(range(n_fc)):
         W = np.asarray(params["fc"][j][0], dtype=np.float64)
-        if j + 1 < len(params["fc"]):
-            g = g * (fcs[j + 1] > 0)
+        if j + 1 < n_fc:
+            g = rd(g * (fcs[j + 1] > 0))
         fc_grads.append((g.T @ fcs[j], g.sum(axis=0)))
         g = g @ W
     fc_grads.reverse()
     g = g.reshape(acts[-1].shape)
     conv_grads = []
     for l in reversed(range(len(params["conv"]))):
-        g = g * (acts[l + 1] > 0)
+        g = rd(g * (acts[l + 1] > 0))
         dx, dw, db = conv3x3s2_grad(acts[l], params["conv"][l][0], g)
         conv_grads.append((dw, db))
         g = dx

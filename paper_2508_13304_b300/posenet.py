@@ -1,0 +1,291 @@
+"""Learned pose proposal: a small convolutional regressor from two DRR views
+to the six rigid-pose parameters, trained on digitally reconstructed
+radiographs rendered on the fly by the forward projector, and used to start
+the gradient-based registration near the answer.
+
+The paper leaves learned, coarse-to-fine pose initialisation to future work
+(Sec. V); this module builds it on the library's tensor-core kernels
+(include/posenet.h).  Architecture: n_conv layers of 3x3, stride-2,
+padding-1 convolutions with ReLU (default 2 -> 32 -> 64 -> 128 -> 128 ->
+128 -> 128 channels on a 128 x 128 input, ending at 2 x 2), then a fully
+connected layer of 256 with ReLU and a linear output of 6 (normalised pose:
+translations / t_range, rotations / r_range).  Loss: mean squared error.
+
+Every forward and backward step runs in the library's kernels: im2col +
+GEMM (bias and ReLU fused) forward; GEMM + col2im (ReLU mask fused) for the
+input gradients; transposes + split-K GEMM for the weight gradients; column
+sums for the bias gradients.  Parameters are FP32 masters updated by Adam
+(a few torch elementwise operations, as in the registration loop) and
+converted to BF16 (and transposed) for the GEMMs after every update.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import (PROJ_OP_FORWARD, Projector, pn_col2im_3x3s2, pn_colsum_bf16, pn_colsum_scratch_floats,
+               pn_gemm_bf16, pn_gemm_split_hint, pn_im2col_3x3s2, pn_mse_loss, pn_prepare_images, pn_to_bf16,
+               pn_transpose_bf16, proj_forward)
+
+BF = torch.bfloat16
+
+
+def _r8(n):
+    return (n + 7) // 8 * 8
+
+
+class PoseNet:
+    """The network with its parameters, BF16 copies and activation buffers
+    for a fixed batch size.  forward() then backward() compute the loss
+    gradients of one batch into .grads (FP32, same shapes as .params)."""
+
+    def __init__(self, batch, in_hw=128, n_views=2, channels=(32, 64, 128, 128, 128, 128), hidden=256, n_out=6,
+                 device="cuda", seed=0):
+        self.B, self.hw, self.n_views, self.n_out = batch, in_hw, n_views, n_out
+        self.dev = torch.device(device)
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        self.layers = []
+        cin, hw = n_views, in_hw
+        for cout in channels:
+            kp = _r8(9 * cin)
+            w = torch.zeros((cout, kp))
+            w[:, :9 * cin] = torch.randn((cout, 9 * cin), generator=g) * math.sqrt(2.0 / (9 * cin))
+            self.layers.append(dict(cin=cin, cout=cout, H=hw, kp=kp, Ho=(hw + 1) // 2, w=w.to(self.dev),
+                                    b=torch.zeros(cout, device=self.dev)))
+            hw, cin = (hw + 1) // 2, cout
+        self.out_hw = hw
+        self.flat = hw * hw * cin
+        self.n_pad = _r8(n_out)
+        w1 = torch.randn((hidden, self.flat), generator=g) * math.sqrt(2.0 / self.flat)
+        w2 = torch.zeros((self.n_pad, hidden))
+        w2[:n_out] = torch.randn((n_out, hidden), generator=g) * math.sqrt(1.0 / hidden)
+        self.fc = [dict(w=w1.to(self.dev), b=torch.zeros(hidden, device=self.dev), n_in=self.flat, n=hidden),
+                   dict(w=w2.to(self.dev), b=torch.zeros(self.n_pad, device=self.dev), n_in=hidden, n=self.n_pad)]
+        self.hidden = hidden
+        self._alloc()
+        self.refresh()
+
+    # ---------------------------------------------------------------- buffers
+    def _alloc(self):
+        B, d = self.B, self.dev
+        self.x = torch.zeros((B, self.hw, self.hw, self.n_views), device=d, dtype=BF)
+        biggest_t, biggest_dcol, biggest_part = 0, 0, 0
+        for L in self.layers:
+            M = B * L["Ho"] * L["Ho"]
+            L["M"], L["Mp"] = M, _r8(M)
+            L["col"] = torch.empty((M, L["kp"]), device=d, dtype=BF)
+            L["a"] = torch.empty((M, L["cout"]), device=d, dtype=BF)       # post-ReLU output, NHWC
+            L["d"] = torch.empty((M, L["cout"]), device=d, dtype=BF)       # gradient w.r.t. pre-activation
+            L["wb"] = torch.empty((L["cout"], L["kp"]), device=d, dtype=BF)
+            L["wbT"] = torch.empty((L["kp"], L["cout"]), device=d, dtype=BF)
+            L["gw"] = torch.zeros_like(L["w"])
+            L["gb"] = torch.zeros_like(L["b"])
+            L["split"] = pn_gemm_split_hint(L["cout"], L["kp"], L["Mp"])
+            biggest_t = max(biggest_t, L["kp"] * L["Mp"], L["cout"] * L["Mp"])
+            biggest_dcol = max(biggest_dcol, M * L["kp"])
+            biggest_part = max(biggest_part, L["split"] * L["cout"] * L["kp"])
+        Bp = _r8(B)
+        self.Bp = Bp
+        for F in self.fc:
+            F["wb"] = torch.empty((F["n"], F["n_in"]), device=d, dtype=BF)
+            F["wbT"] = torch.empty((F["n_in"], F["n"]), device=d, dtype=BF)
+            F["gw"] = torch.zeros_like(F["w"])
+            F["gb"] = torch.zeros_like(F["b"])
+            F["split"] = pn_gemm_split_hint(F["n"], F["n_in"], Bp)
+            biggest_t = max(biggest_t, F["n"] * Bp, F["n_in"] * Bp)
+            biggest_part = max(biggest_part, F["split"] * F["n"] * F["n_in"])
+        self.h = torch.empty((B, self.hidden), device=d, dtype=BF)
+        self.dh = torch.empty((B, self.hidden), device=d, dtype=BF)
+        self.out = torch.empty((B, self.n_pad), device=d)
+        self.dout = torch.empty((B, self.n_pad), device=d, dtype=BF)
+        self.loss = torch.zeros(1, device=d)
+        self.tA = torch.empty(biggest_t, device=d, dtype=BF)
+        self.tB = torch.empty(biggest_t, device=d, dtype=BF)
+        self.dcol = torch.empty(biggest_dcol, device=d)
+        self.part = torch.empty(max(1, biggest_part), device=d)
+        cs = max(pn_colsum_scratch_floats(L["M"], L["cout"]) for L in self.layers)
+        cs = max(cs, pn_colsum_scratch_floats(B, self.hidden), pn_colsum_scratch_floats(B, self.n_pad))
+        self.cs = torch.empty(cs, device=d)
+
+    @property
+    def params(self):
+        return [t for L in self.layers for t in (L["w"], L["b"])] + [t for F in self.fc for t in (F["w"], F["b"])]
+
+    @property
+    def grads(self):
+        return [t for L in self.layers for t in (L["gw"], L["gb"])] + [t for F in self.fc for t in (F["gw"], F["gb"])]
+
+    def refresh(self):
+        """BF16 copies (and transposes) of the FP32 weights for the GEMMs."""
+        for P in self.layers + self.fc:
+            pn_to_bf16(P["w"], P["wb"])
+            rows, cols = P["wb"].shape
+            pn_transpose_bf16(P["wb"], rows, cols, P["wbT"], rows)
+
+    # ---------------------------------------------------------------- passes
+    def forward(self, x=None):
+        """Outputs [B][n_pad] FP32 (columns n_out.. are zero) for the input
+        in self.x (or x, BF16 NHWC [B][hw][hw][n_views])."""
+        if x is not None:
+            self.x.copy_(x)
+        B = self.B
+        a, cin = self.x, self.n_views
+        for L in self.layers:
+            pn_im2col_3x3s2(a, B, L["H"], L["H"], cin, L["kp"], L["col"])
+            pn_gemm_bf16(L["M"], L["cout"], L["kp"], L["col"], L["kp"], L["wb"], L["kp"], bias=L["b"], relu=True,
+                         D16=L["a"])
+            a, cin = L["a"], L["cout"]
+        F1, F2 = self.fc
+        pn_gemm_bf16(B, F1["n"], F1["n_in"], a, F1["n_in"], F1["wb"], F1["n_in"], bias=F1["b"], relu=True,
+                     D16=self.h)
+        pn_gemm_bf16(B, F2["n"], F2["n_in"], self.h, F2["n_in"], F2["wb"], F2["n_in"], bias=F2["b"], D32=self.out)
+        return self.out
+
+    def loss_grad(self, target):
+        """MSE of the first n_out outputs against target [B][n_out] (FP32);
+        writes self.loss and the output gradient."""
+        pn_mse_loss(self.out, self.B, self.n_out, self.n_pad, target, self.loss, self.dout, self.n_pad)
+        return self.loss
+
+    def _wgrad(self, dy, M, N_out, inp, K_in, gw, split):
+        """gw [N_out][K_in] = dy^T . inp over M rows (dy [M][N_out], inp [M][K_in])."""
+        Mp = _r8(M)
+        dyT = self.tA[:N_out * Mp]
+        inT = self.tB[:K_in * Mp]
+        pn_transpose_bf16(dy, M, N_out, dyT, Mp)
+        pn_transpose_bf16(inp, M, K_in, inT, Mp)
+        pn_gemm_bf16(N_out, K_in, Mp, dyT, Mp, inT, Mp, D32=gw, split_k=split, part=self.part)
+
+    def backward(self):
+        """Gradients of the loss (after loss_grad) into .grads."""
+        B = self.B
+        F1, F2 = self.fc
+        last = self.layers[-1]
+        # output layer
+        self._wgrad(self.dout, B, F2["n"], self.h, F2["n_in"], F2["gw"], F2["split"])
+        pn_colsum_bf16(self.dout, B, F2["n"], F2["n"], F2["gb"], self.cs)
+        pn_gemm_bf16(B, F2["n_in"], F2["n"], self.dout, F2["n"], F2["wbT"], F2["n"], mask=self.h, ldm=F2["n_in"],
+                     D16=self.dh)
+        # hidden layer
+        self._wgrad(self.dh, B, F1["n"], last["a"], F1["n_in"], F1["gw"], F1["split"])
+        pn_colsum_bf16(self.dh, B, F1["n"], F1["n"], F1["gb"], self.cs)
+        pn_gemm_bf16(B, F1["n_in"], F1["n"], self.dh, F1["n"], F1["wbT"], F1["n"], mask=last["a"],
+                     ldm=F1["n_in"], D16=last["d"])
+        # convolutions, last to first
+        for i in reversed(range(len(self.layers))):
+            L = self.layers[i]
+            self._wgrad(L["d"], L["M"], L["cout"], L["col"], L["kp"], L["gw"], L["split"])
+            pn_colsum_bf16(L["d"], L["M"], L["cout"], L["cout"], L["gb"], self.cs)
+            if i > 0:
+                P = self.layers[i - 1]
+                dcol = self.dcol[:L["M"] * L["kp"]]
+                pn_gemm_bf16(L["M"], L["kp"], L["cout"], L["d"], L["cout"], L["wbT"], L["cout"], D32=dcol)
+                pn_col2im_3x3s2(dcol, B, L["H"], L["H"], L["cin"], L["kp"], mask=P["a"], dx16=P["d"])
+
+    # ---------------------------------------------------------------- oracle view
+    def as_oracle_params(self):
+        """The BF16-rounded weights in the layout of oracle.posenet (numpy FP64):
+        conv [Co][3][3][Ci], fc [n][n_in] (output rows n_out.. dropped)."""
+        conv = []
+        for L in self.layers:
+            w = L["w"].bfloat16().float().cpu().numpy().astype(np.float64)[:, :9 * L["cin"]]
+            conv.append((w.reshape(L["cout"], 3, 3, L["cin"]), L["b"].cpu().numpy().astype(np.float64)))
+        F1, F2 = self.fc
+        fc = [(F1["w"].bfloat16().float().cpu().numpy().astype(np.float64), F1["b"].cpu().numpy().astype(np.float64)),
+              (F2["w"].bfloat16().float().cpu().numpy().astype(np.float64)[:self.n_out],
+               F2["b"].cpu().numpy().astype(np.float64)[:self.n_out])]
+        return dict(conv=conv, fc=fc)
+
+
+class AdamW:
+    """Adam on a list of FP32 tensors (decoupled weight decay optional)."""
+
+    def __init__(self, params, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, wd=0.0):
+        self.p = params
+        self.m = [torch.zeros_like(t) for t in params]
+        self.v = [torch.zeros_like(t) for t in params]
+        self.lr, self.b1, self.b2, self.eps, self.wd = lr, betas[0], betas[1], eps, wd
+        self.t = 0
+
+    def step(self, grads, lr=None):
+        self.t += 1
+        lr = self.lr if lr is None else lr
+        c1 = 1 - self.b1 ** self.t
+        c2 = 1 - self.b2 ** self.t
+        for p, g, m, v in zip(self.p, grads, self.m, self.v):
+            m.mul_(self.b1).add_(g, alpha=1 - self.b1)
+            v.mul_(self.b2).addcmul_(g, g, value=1 - self.b2)
+            if self.wd:
+                p.mul_(1 - lr * self.wd)
+            p.addcdiv_(m, v.sqrt().add_(self.eps), value=-lr * math.sqrt(c2) / c1)
+
+
+class DrrSource:
+    """Batches of (network input, normalised pose) rendered on the fly:
+    uniform random poses (translations within +-t_range mm, rotations within
+    +-r_range deg), proj_forward of every view, then box downsampling and
+    standardisation (pn_prepare_images)."""
+
+    def __init__(self, geom, mu, batch, factor, t_range=40.0, r_range=30.0, device="cuda", seed=0):
+        self.geom, self.B, self.factor = geom, batch, factor
+        self.nvw = geom.views.shape[0]
+        self.scale = torch.tensor([t_range] * 3 + [math.radians(r_range)] * 3, device=device)
+        self.P = Projector(geom, n_pose=batch, inst_view=np.tile(np.arange(self.nvw), batch),
+                           inst_pose=np.repeat(np.arange(batch), self.nvw), ops=PROJ_OP_FORWARD, device=device)
+        self.P.set_volume(mu)
+        self.proj = torch.empty((batch * self.nvw, geom.nv, geom.nu), device=device)
+        self.gen = torch.Generator(device=device).manual_seed(seed)
+        self.dev = device
+
+    def render(self, pose, out):
+        """Network input for the given poses [B][6] (FP32, physical units)."""
+        proj_forward(self.P.plan, pose, self.proj, self.P.ws)
+        pn_prepare_images(self.proj, self.B, self.nvw, self.geom.nu, self.geom.nv, self.factor, out)
+
+    def batch(self, out, target):
+        """Fill out (BF16 NHWC) and target ([B][6] normalised) with a fresh batch."""
+        u = torch.rand((self.B, 6), device=self.dev, generator=self.gen) * 2 - 1
+        target.copy_(u)
+        self.render((u * self.scale).contiguous(), out)
+
+    def images_for(self, proj_views, out):
+        """Network input for given projections [n][n_views][nv][nu] (e.g. the
+        target images of a registration)."""
+        n = proj_views.shape[0]
+        pn_prepare_images(proj_views.reshape(-1).contiguous(), n, self.nvw, self.geom.nu, self.geom.nv, self.factor,
+                          out)
+
+
+def train(net, source, n_samples, lr=1e-3, lr_final=1e-5, log_every=0, log=print):
+    """Adam with cosine decay over n_samples DRRs; returns the loss history."""
+    opt = AdamW(net.params, lr=lr)
+    target = torch.empty((net.B, 6), device=net.dev)
+    steps = max(1, n_samples // net.B)
+    hist = []
+    t0 = time.perf_counter()
+    for s in range(steps):
+        source.batch(net.x, target)
+        net.forward()
+        net.loss_grad(target)
+        net.backward()
+        k = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * s / steps))
+        opt.step(net.grads, lr=k)
+        net.refresh()
+        hist.append(net.loss.clone())
+        if log_every and (s + 1) % log_every == 0:
+            log("step %d/%d loss %.5f (%.1f s)" % (s + 1, steps, float(torch.stack(hist[-log_every:]).mean()),
+                                                   time.perf_counter() - t0))
+    return torch.cat(hist).cpu().numpy()
+
+
+def propose(net, source, images):
+    """Poses [n][6] (physical units) proposed for network inputs [n][hw][hw][views]
+    (n <= batch)."""
+    n = images.shape[0]
+    net.x.zero_()
+    net.x[:n].copy_(images)
+    out = net.forward()
+    return (out[:n, :6] * source.scale).contiguous()

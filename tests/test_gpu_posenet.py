@@ -201,3 +201,59 @@ def test_prepare_and_mse():
     assert loss.item() == pytest.approx(L_ref, rel=1e-6)
     assert rel(f64(dy)[:, :n_out], g_ref) <= 4e-3
     assert np.all(f64(dy)[:, n_out:] == 0)
+
+
+# ------------------------------------------------------------ whole network
+
+def test_network_step_matches_oracle():
+    """One forward / loss / backward step of a small network.
+
+    Tight: against the oracle network rounding to BF16 at the same points
+    as the GPU (every stored activation and back-propagated gradient), on
+    the same BF16 weights and input.  What remains is FP32 vs FP64
+    accumulation, which moves a stored value to the neighbouring BF16 value
+    for a small fraction of elements: rel-L2 <= 3e-3.
+
+    Loose: against the plain FP64 network.  BF16 storage alone moves the
+    early layers' weight gradients by 1-5 % (measured by emulating the
+    rounding in FP64 on random networks of this shape), the outputs by
+    < 0.6 %: bars 1e-1 and 2e-2."""
+    from paper_2508_13304_b300 import posenet as pn
+    rng = np.random.default_rng(21)
+    B = 12
+    net = pn.PoseNet(B, in_hw=32, n_views=2, channels=(8, 16, 16, 16), hidden=32, seed=3)
+    for L in net.layers:
+        L["b"].copy_(torch.from_numpy(0.05 * rng.standard_normal(L["cout"]).astype(np.float32)))
+    net.fc[0]["b"].copy_(torch.from_numpy(0.05 * rng.standard_normal(32).astype(np.float32)))
+    net.fc[1]["b"][:6] = torch.from_numpy(0.05 * rng.standard_normal(6).astype(np.float32))
+    net.refresh()
+    x = bf16(rng, (B, 32, 32, 2))
+    t = torch.from_numpy(rng.uniform(-1, 1, (B, 6)).astype(np.float32)).cuda()
+    out = net.forward(x)
+    loss = net.loss_grad(t)
+    net.backward()
+    torch.cuda.synchronize()
+    assert pb.pn_status() == 0
+    P = net.as_oracle_params()
+    got_out = out.cpu().numpy()
+    assert np.all(got_out[:, 6:] == 0)
+    got = [(L["gw"].cpu().numpy(), L["gb"].cpu().numpy(), L["cin"]) for L in net.layers]
+    for L in net.layers:
+        assert np.all(L["gw"].cpu().numpy()[:, 9 * L["cin"]:] == 0)
+    assert np.all(net.fc[1]["gw"].cpu().numpy()[6:] == 0)
+    fc_got = [(net.fc[0]["gw"].cpu().numpy(), net.fc[0]["gb"].cpu().numpy()),
+              (net.fc[1]["gw"].cpu().numpy()[:6], net.fc[1]["gb"].cpu().numpy()[:6])]
+    for mode, tol_out, tol_g in ((True, 3e-3, 3e-3), (False, 2e-2, 1e-1)):
+        out_ref, cache = on.net_forward(P, f64(x), bf16=mode)
+        L_ref, dout_ref = on.mse(out_ref, t.cpu().numpy())
+        if mode:
+            dout_ref = on.bf16_round(dout_ref)
+        G = on.net_backward(P, cache, dout_ref, bf16=mode)
+        assert rel(got_out[:, :6], out_ref) <= tol_out, mode
+        assert loss.item() == pytest.approx(L_ref, rel=tol_out)
+        for (gw, gb, cin), (dw, db) in zip(got, G["conv"]):
+            assert rel(gw[:, :9 * cin].reshape(dw.shape), dw) <= tol_g, mode
+            assert rel(gb, db) <= tol_g, mode
+        for (gw, gb), (dw, db) in zip(fc_got, G["fc"]):
+            assert rel(gw, dw) <= tol_g, mode
+            assert rel(gb, db) <= tol_g, mode

@@ -112,3 +112,32 @@ def test_prepare_closed_forms():
     expect = (k - (n - 1) / 2) / np.sqrt((n * n - 1) / 12.0)
     for c in range(2):
         np.testing.assert_allclose(z[1, :, :, c], np.tile(expect, (4, 1)), rtol=1e-12)
+
+
+def test_bf16_round_matches_torch_conversion():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    vals = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-20, 20, 20000),
+                           # exact ties: bit patterns with the dropped half exactly 0x8000
+                           (np.arange(1, 2001, dtype=np.uint32) << 16 | 0x8000).view(np.float32).astype(np.float64),
+                           [0.0, -0.0, 1.0, -1.5, 3.0e38]])
+    ref = torch.from_numpy(vals.astype(np.float32)).bfloat16().float().numpy().astype(np.float64)
+    np.testing.assert_array_equal(on.bf16_round(vals), ref)
+
+
+def test_bf16_network_rounds_only_stored_values():
+    """With bf16=True every stored activation is a BF16 value; without it
+    the result equals the plain network; the two differ by BF16-sized
+    amounts."""
+    rng = np.random.default_rng(5)
+    P = tiny_params(rng)
+    x = on.bf16_round(rng.standard_normal((2, 8, 8, 2)))
+    out_f, cache_f = on.net_forward(P, x)
+    out_b, cache_b = on.net_forward(P, x, bf16=True)
+    for a in cache_b["acts"][1:] + cache_b["fcs"][1:-1]:
+        np.testing.assert_array_equal(a, on.bf16_round(a))
+    assert 0 < np.linalg.norm(out_b - out_f) <= 2e-2 * np.linalg.norm(out_f)
+    g_b = on.net_backward(P, cache_b, np.ones_like(out_b), bf16=True)
+    g_f = on.net_backward(P, cache_f, np.ones_like(out_f))
+    for (a, _), (b, _) in zip(g_b["conv"], g_f["conv"]):
+        assert np.linalg.norm(a - b) <= 0.1 * np.linalg.norm(b)
