@@ -16,6 +16,7 @@ from __future__ import annotations
 import argparse
 import csv
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -43,6 +44,14 @@ L2_FLUSH_BYTES = 256 << 20
 TRAFFIC_PER_LAUNCH = 30.4e9
 
 
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -54,6 +63,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other kernels' measurements")
+    ap.add_argument("--section", default=None, choices=["gemm"],
+                    help="run only one secondary measurement (gemm: the tensor-core GEMM shapes) and print it")
+    ap.add_argument("--posenet-eval", action="store_true",
+                    help="also train the pose-proposal network on 200k DRRs and compare proposal + registration "
+                         "with 16-start registration (about 3 minutes)")
     return ap.parse_args()
 
 
@@ -303,6 +317,7 @@ def secondary(pb, torch, dev, w, mu_d, flush):
                                   "chosen": "%dx%d" % (width, 32 // width)}
     del Pa
     out["registration_cuda_graph"] = graph_timing(pb, torch, g, mu_h, tgt, starts)
+    out["posenet"] = posenet_measure(pb, torch, dev, flush, g, mu_d, load_peaks())
     out["uneven_batch_small"] = uneven_batch(pb, torch, dev, flush, with_large=False)
     out["uneven_batch_c4"] = uneven_batch(pb, torch, dev, flush, with_large=True)
     return out
@@ -394,6 +409,77 @@ def graph_timing(pb, torch, g, mu_h, tgt, starts):
     return out
 
 
+GEMM_SHAPES = ((8192, 8192, 8192), (262144, 64, 288), (65536, 128, 576), (16384, 128, 1152), (16384, 1152, 128))
+
+
+def gemm_throughput(pb, torch, dev, flush, bf16_peak, shapes=GEMM_SHAPES):
+    """Tensor-core GEMM (pn_gemm_bf16, BF16 in, FP32 accumulate, BF16 out)
+    on a square shape and on the convolution shapes of the pose network."""
+    out = []
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    for M, N, K in shapes:
+        A = torch.randn((M, K), device=dev, generator=gen).bfloat16()
+        B = torch.randn((N, K), device=dev, generator=gen).bfloat16()
+        D = torch.empty((M, N), device=dev, dtype=torch.bfloat16)
+        ms = _event_ms(torch, lambda: pb.pn_gemm_bf16(M, N, K, A, K, B, K, D16=D), flush, reps=5)
+        tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+        byts = 2.0 * (M * K + N * K + M * N)
+        out.append({"M": M, "N": N, "K": K, "ms": ms, "tflops": tf, "frac_of_bf16_peak": tf / bf16_peak,
+                    "hbm_gbs_min_traffic": byts / (ms * 1e-3) / 1e9})
+        del A, B, D
+    return out
+
+
+def posenet_measure(pb, torch, dev, flush, g, mu_d, peaks):
+    """Pose-proposal network: GEMM roofline, DRR batch generation, network
+    training step (batch 256, 2 views of 128^2 from 384^2 DRRs)."""
+    from paper_2508_13304_b300 import posenet as pn
+    bf16_peak = float(peaks.get("bf16_tflops", 1800.0))
+    gem = gemm_throughput(pb, torch, dev, flush, bf16_peak)
+    top = gem[0]
+    B = 256
+    net = pn.PoseNet(B, in_hw=128, n_views=2)
+    src = pn.DrrSource(g, mu_d, B, factor=3, seed=1)
+    tgt = torch.empty((B, 6), device=dev)
+    ms_drr = _event_ms(torch, lambda: src.batch(net.x, tgt), flush, reps=3)
+
+    def step():
+        net.forward()
+        net.loss_grad(tgt)
+        net.backward()
+
+    ms_net = _event_ms(torch, step, flush, reps=5)
+    ms_fwd = _event_ms(torch, net.forward, flush, reps=5)
+    status = pb.pn_status()
+    return {"gemm": gem,
+            "roofline": {"bound": "tensor", "kernel": "k_gemm_bf16 (tcgen05.mma kind::f16, TMEM accumulator, TMA)",
+                         "achieved": top["tflops"], "peak": bf16_peak, "unit": "TFLOP/s",
+                         "frac": top["tflops"] / bf16_peak,
+                         "shape": "%dx%dx%d" % (top["M"], top["N"], top["K"]),
+                         "peak_from": "MEASURED_PEAKS.json bf16_tflops (cuBLAS 8192^3 burst)"},
+            "drr_batch_ms": ms_drr, "drr_batch": "256 poses x 2 views of 384^2 (K2), box-downsampled to 128^2",
+            "net_train_step_ms": ms_net, "net_forward_ms": ms_fwd,
+            "training_drrs_per_s": B / ((ms_drr + ms_net) * 1e-3),
+            "device_status": status}
+
+
+def posenet_eval(pb, torch, dev, g, mu_d):
+    from paper_2508_13304_b300 import posenet as pn
+    net = pn.PoseNet(256, in_hw=128, n_views=2)
+    src = pn.DrrSource(g, mu_d, 256, factor=3, seed=1)
+    t0 = time.perf_counter()
+    hist = pn.train(net, src, 200000, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    res = pn.proposal_vs_multistart(net, src, mu_d, n_targets=8, n_starts=16,
+                                    lr_refine=[0.5] * 3 + [math.radians(0.2)] * 3)
+    res.update({"train_s": train_s, "train_drrs": 200000, "final_loss": float(hist[-50:].mean()),
+                "config": "256^3 / 2 x 384^2 (registration phantom), poses +-40 mm / +-30 deg, 8 targets, "
+                          "16 random starts, Adam 10 mm / 2 deg, stops off, tolerance 0.5 mm / 0.5 deg"})
+    return res
+
+
 # ------------------------------------------------------------------ main arm
 
 def main():
@@ -409,6 +495,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.section == "gemm":
+        dev0 = torch.device("cuda", local)
+        fl = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev0)
+        print(json.dumps({"section": "gemm", "gemm": gemm_throughput(
+            pb, torch, dev0, fl, float(load_peaks().get("bf16_tflops", 1800.0)))}), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -542,12 +634,7 @@ def main():
             dist.destroy_process_group()
         return
 
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
+    peaks = load_peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
@@ -585,6 +672,8 @@ def main():
     }
     if not args.no_secondary:
         line["secondary"] = secondary(pb, torch, dev, w, mu_d, flush)
+    if args.posenet_eval:
+        line["posenet_eval"] = posenet_eval(pb, torch, dev, g, mu_d)
     if not args.no_cpu_baseline and world == 1:
         cands = list(range(min(args.cpu_sample, args.n_cand)))
         og, dt, threads, _ = cpu_oracle_eval(w, cands)

@@ -289,3 +289,74 @@ def propose(net, source, images):
     net.x[:n].copy_(images)
     out = net.forward()
     return (out[:n, :6] * source.scale).contiguous()
+
+
+def proposal_vs_multistart(net, source, mu, n_targets=8, n_starts=16, tol=(0.5, 0.5), max_iter=150, seed=5,
+                           lr=None, ncc_stop=2.0, dloss_stop=-1.0, lr_refine=None, log=None):
+    """Time to a pose within tol = (mm, deg) of the truth (first iteration
+    inside the tolerance box), per target pose drawn uniformly from the
+    training range, with the same registration settings in both arms (Adam
+    with steps lr, default the paper's 10 mm / 2 deg; the loss-based stops
+    ncc_stop / dloss_stop, default off):
+
+    * proposal: the network's pose from the target images (input
+      preparation + one forward pass), then the NCC registration from that
+      single start; with lr_refine also from the same start with those steps;
+    * multi-start: n_starts uniform random starts from the same range, each
+      registered in turn, until one reaches the tolerance.
+
+    Returns a dict of per-target times (None where no start succeeded) and
+    the proposals' errors (max over axes: mm, deg)."""
+    from .registration import paper_step_sizes, register
+    lr = list(paper_step_sizes() if lr is None else lr)
+    geom, dev = source.geom, source.dev
+    nvw = source.nvw
+    rng = np.random.default_rng(seed)
+    scale = source.scale.cpu().numpy().astype(np.float64)
+    targets = rng.uniform(-1, 1, (n_targets, 6)) * scale
+    mu_h = mu.detach().float().cpu().numpy() if torch.is_tensor(mu) else np.asarray(mu, dtype=np.float32)
+    Pt = Projector(geom, n_pose=1, inst_view=np.arange(nvw), inst_pose=np.zeros(nvw, np.int32), ops=PROJ_OP_FORWARD,
+                   device=dev)
+    Pt.set_volume(torch.as_tensor(mu_h, device=dev))
+    x = torch.zeros_like(net.x)
+    kw = dict(max_iter=max_iter, ncc_stop=ncc_stop, dloss_stop=dloss_stop, tol=tol, device=dev)
+    # one untimed call first: the first use of some library kernels in a process pays one-off set-up costs
+    warm = Pt.forward(torch.zeros((1, 6), device=dev)).cpu().numpy()
+    register(geom, mu_h, warm, np.zeros((1, 6), np.float32), lr=lr, true_pose=np.zeros(6, np.float32),
+             **dict(kw, max_iter=3))
+    source.images_for(torch.from_numpy(warm).to(dev).reshape(1, nvw, geom.nv, geom.nu), x[:1])
+    propose(net, source, x[:1])
+    res = dict(proposal_s=[], proposal_err=[], proposal_small_steps_s=[], multistart_s=[], multistart_starts=[])
+    for k in range(n_targets):
+        true = targets[k].astype(np.float32)
+        img = Pt.forward(torch.from_numpy(true[None]).to(dev)).contiguous()
+        img_h = img.cpu().numpy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        source.images_for(img.reshape(1, nvw, geom.nv, geom.nu), x[:1])
+        prop = propose(net, source, x[:1]).cpu().numpy()
+        t_prop = time.perf_counter() - t0
+        d = np.abs(prop[0] - true)
+        res["proposal_err"].append((float(d[:3].max()), float(np.degrees(d[3:].max()))))
+        r = register(geom, mu_h, img_h, prop, lr=lr, true_pose=true, **kw)
+        res["proposal_s"].append(None if r["first_hit_s"] is None else t_prop + r["first_hit_s"])
+        if lr_refine is not None:
+            r = register(geom, mu_h, img_h, prop, lr=list(lr_refine), true_pose=true, **kw)
+            res["proposal_small_steps_s"].append(None if r["first_hit_s"] is None else t_prop + r["first_hit_s"])
+        starts = (rng.uniform(-1, 1, (n_starts, 6)) * scale).astype(np.float32)
+        spent, hit = 0.0, None
+        for c in range(n_starts):
+            r = register(geom, mu_h, img_h, starts[c:c + 1], lr=lr, true_pose=true, **kw)
+            if r["first_hit_s"] is not None:
+                hit = (spent + r["first_hit_s"], c + 1)
+                break
+            spent += r["seconds"]
+        res["multistart_s"].append(hit[0] if hit else None)
+        res["multistart_starts"].append(hit[1] if hit else None)
+        if log:
+            log("target %d: proposal %s s, multistart %s s" % (k, res["proposal_s"][-1], res["multistart_s"][-1]))
+    for key in ("proposal_s", "proposal_small_steps_s", "multistart_s"):
+        v = [t for t in res[key] if t is not None]
+        res[key + "_found"] = len(v)
+        res[key + "_median"] = float(np.median(v)) if v else None
+    return res
