@@ -418,15 +418,19 @@ def gemm_throughput(pb, torch, dev, flush, bf16_peak, shapes=GEMM_SHAPES):
     out = []
     gen = torch.Generator(device=dev)
     gen.manual_seed(7)
-    for M, N, K in shapes:
+    for i, (M, N, K) in enumerate(shapes):
         A = torch.randn((M, K), device=dev, generator=gen).bfloat16()
         B = torch.randn((N, K), device=dev, generator=gen).bfloat16()
         D = torch.empty((M, N), device=dev, dtype=torch.bfloat16)
-        ms = _event_ms(torch, lambda: pb.pn_gemm_bf16(M, N, K, A, K, B, K, D16=D), flush, reps=5)
-        tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
-        byts = 2.0 * (M * K + N * K + M * N)
-        out.append({"M": M, "N": N, "K": K, "ms": ms, "tflops": tf, "frac_of_bf16_peak": tf / bf16_peak,
-                    "hbm_gbs_min_traffic": byts / (ms * 1e-3) / 1e9})
+        for pair in ((True, False) if i == 0 else (True,)):
+            pb.pn_gemm_use_pair_tiles(pair)
+            ms = _event_ms(torch, lambda: pb.pn_gemm_bf16(M, N, K, A, K, B, K, D16=D), flush, reps=5)
+            tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+            byts = 2.0 * (M * K + N * K + M * N)
+            out.append({"M": M, "N": N, "K": K, "tiles": "2-SM 256x256" if pair and N > 128 and M > 128 else "1-SM",
+                        "ms": ms, "tflops": tf, "frac_of_bf16_peak": tf / bf16_peak,
+                        "hbm_gbs_min_traffic": byts / (ms * 1e-3) / 1e9})
+        pb.pn_gemm_use_pair_tiles(True)
         del A, B, D
     return out
 

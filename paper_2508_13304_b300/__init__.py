@@ -79,6 +79,7 @@ _SIGS = {
     "proj_batch_destroy": [_P],
     "pn_gemm_bf16": [_I, _I, _I, _P, _I, _P, _I, _P, _P, _I, _I, _P, _P, _I, _I, _P, _P],
     "pn_gemm_split_hint": [_I, _I, _I],
+    "pn_gemm_use_pair_tiles": [_I],
     "pn_im2col_3x3s2": [_P, _I, _I, _I, _I, _I, _P, _P],
     "pn_col2im_3x3s2": [_P, _I, _I, _I, _I, _I, _P, _P, _P, _P],
     "pn_transpose_bf16": [_P, _I, _I, _P, _I, _P],
@@ -456,6 +457,11 @@ def pn_gemm_bf16(M, N, K, A, lda, B, ldb, bias=None, mask=None, ldm=0, relu=Fals
                               int(ldm), 1 if relu else 0, _f32(D32, name="D32", allow_none=True),
                               _bf(D16, name="D16", allow_none=True), int(ldd), int(split_k),
                               _f32(part, name="part", allow_none=True), _stream(stream)))
+
+
+def pn_gemm_use_pair_tiles(enable=True) -> bool:
+    """Use 2-SM 256 x 256 tiles for wide GEMMs (default); returns the previous setting."""
+    return bool(lib().pn_gemm_use_pair_tiles(1 if enable else 0))
 
 
 def pn_gemm_split_hint(M, N, K) -> int:

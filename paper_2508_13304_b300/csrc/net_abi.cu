@@ -38,6 +38,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 std::mutex g_mu;
 EncodeTiledFn g_encode = nullptr;
+int g_use_pair = 1;
 int* g_status_addr[64] = {};
 int g_n_sm[64] = {};
 
@@ -113,6 +114,12 @@ using namespace pnk;
 
 extern "C" {
 
+int pn_gemm_use_pair_tiles(int enable) {
+  const int old = g_use_pair;
+  g_use_pair = enable ? 1 : 0;
+  return old;
+}
+
 int pn_gemm_split_hint(int M, int N, int K) {
   if (M < 1 || N < 1 || K < 1) return 1;
   const int bn = bn_for(N);
@@ -140,10 +147,11 @@ int pn_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int
   int* status = status_word();
   if (!status) return fail(PROJ_E_CUDA, "pn_gemm_bf16: no device status word");
   const int bn = bn_for(N);
+  const bool pair = g_use_pair && bn == 256 && M > kBM;
   CUtensorMap ta, tb;
   int rc = make_map(&ta, A, M, K, lda, kBM);
   if (rc) return rc;
-  if ((rc = make_map(&tb, B, N, K, ldb, bn))) return rc;
+  if ((rc = make_map(&tb, B, N, K, ldb, pair ? 128 : bn))) return rc;
   const int nkb = (K + kBK - 1) / kBK;
   const int kbs = (nkb + split_k - 1) / split_k;
   const int split = (nkb + kbs - 1) / kbs;  // every CTA gets at least one K block
@@ -157,7 +165,7 @@ int pn_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int
   epi.ldd = ldd;
   epi.part = split > 1 ? part : nullptr;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = launch_gemm(ta, tb, M, N, K, bn, split, kbs, epi, status, s);
+  cudaError_t e = launch_gemm(ta, tb, M, N, K, bn, pair, split, kbs, epi, status, s);
   if (e != cudaSuccess) return cuda_fail(e, "GEMM launch");
   if (split > 1) {
     epi.part = nullptr;

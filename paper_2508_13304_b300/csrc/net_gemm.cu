@@ -134,6 +134,54 @@ __device__ __forceinline__ float epi_value(float acc, int row, int col, const Ge
   return v;
 }
 
+// Epilogue of one CTA: its 128 TMEM lanes are rows m0..m0+127 of D, its BN
+// columns are n0..; each warp reads its 32 lanes 16 columns at a time.
+template <int BN>
+__device__ __forceinline__ void epilogue(uint32_t tmem_d, int m0, int n0, int M, int N, int z, const GemmEpi& epi) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = m0 + warp * 32 + lane;
+  const uint32_t lane_base = tmem_d + (static_cast<uint32_t>(warp * 32) << 16);
+#pragma unroll 1
+  for (int c0 = 0; c0 < BN; c0 += 16) {
+    float v[16];
+    __syncwarp();  // tcgen05.ld is warp-collective
+    tmem_ld16(lane_base + c0, v);
+    const int col0 = n0 + c0;
+    if (row >= M || col0 >= N) continue;
+    const int nval = min(16, N - col0);
+    if (epi.part) {
+      float* dst = epi.part + ((size_t)z * M + row) * N + col0;
+      for (int j = 0; j < nval; ++j) dst[j] = v[j];
+      continue;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < nval) v[j] = epi_value(v[j], row, col0 + j, epi);
+    if (epi.d32) {
+      float* dst = epi.d32 + (size_t)row * epi.ldd + col0;
+      if (nval == 16 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      } else {
+        for (int j = 0; j < nval; ++j) dst[j] = v[j];
+      }
+    }
+    if (epi.d16) {
+      __nv_bfloat16* dst = epi.d16 + (size_t)row * epi.ldd + col0;
+      if (nval == 16 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        __nv_bfloat162 h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        reinterpret_cast<uint4*>(dst)[0] = *reinterpret_cast<uint4*>(&h[0]);
+        reinterpret_cast<uint4*>(dst)[1] = *reinterpret_cast<uint4*>(&h[4]);
+      } else {
+        for (int j = 0; j < nval; ++j) dst[j] = __float2bfloat16_rn(v[j]);
+      }
+    }
+  }
+}
+
 template <int BN>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N, int K,
@@ -211,48 +259,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   if (fail) atomicOr(status, fail);
   tc_fence_after();
 
-  if (ok) {
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t lane_base = tmem_d + (static_cast<uint32_t>(warp * 32) << 16);
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      float v[16];
-      __syncwarp();  // tcgen05.ld is warp-collective
-      tmem_ld16(lane_base + c0, v);
-      const int col0 = n0 + c0;
-      if (row >= M || col0 >= N) continue;
-      const int nval = min(16, N - col0);
-      if (epi.part) {
-        float* dst = epi.part + ((size_t)blockIdx.z * M + row) * N + col0;
-        for (int j = 0; j < nval; ++j) dst[j] = v[j];
-        continue;
-      }
-#pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (j < nval) v[j] = epi_value(v[j], row, col0 + j, epi);
-      if (epi.d32) {
-        float* dst = epi.d32 + (size_t)row * epi.ldd + col0;
-        if (nval == 16 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-#pragma unroll
-          for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-        } else {
-          for (int j = 0; j < nval; ++j) dst[j] = v[j];
-        }
-      }
-      if (epi.d16) {
-        __nv_bfloat16* dst = epi.d16 + (size_t)row * epi.ldd + col0;
-        if (nval == 16 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-          __nv_bfloat162 h[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-          reinterpret_cast<uint4*>(dst)[0] = *reinterpret_cast<uint4*>(&h[0]);
-          reinterpret_cast<uint4*>(dst)[1] = *reinterpret_cast<uint4*>(&h[4]);
-        } else {
-          for (int j = 0; j < nval; ++j) dst[j] = __float2bfloat16_rn(v[j]);
-        }
-      }
-    }
-  }
+  if (ok) epilogue<BN>(tmem_d, m0, n0, M, N, blockIdx.z, epi);
 
   tc_fence_before();
   __syncthreads();
@@ -260,6 +267,157 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(tmem_cols<BN>())
                  : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- 2-SM tile
+//
+// A cluster of two CTAs on two SMs computes a 256 x 256 tile with
+// tcgen05.mma.cta_group::2 (M = 256): CTA r of the pair stages rows
+// [128 r, 128 r + 128) of the A tile and rows [128 r, 128 r + 128) of the B
+// tile, so each SM moves half the B bytes of a 1-SM 128 x 256 tile and the
+// ring can be 6 stages deep.  Both CTAs' TMA loads signal the even CTA's
+// "full" barrier (which expects the bytes of both); the even CTA issues the
+// MMAs and multicasts each commit to both CTAs' "empty" / "done" barriers.
+// Each CTA's TMEM holds its 128 rows of the accumulator.
+
+constexpr int kStagesPair = 6;
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t addr, uint32_t rank) {
+  uint32_t o;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(o) : "r"(addr), "r"(rank));
+  return o;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, uint32_t bar_cluster, int x,
+                                                 int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16_pair(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                               uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
+  const uint16_t both = 3;
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(both)
+      : "memory");
+}
+
+__host__ __device__ constexpr uint32_t idesc_bf16_pair() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(256 >> 3) << 17) |
+         (static_cast<uint32_t>(256 >> 4) << 24);
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
+    k_gemm_bf16_pair(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N,
+                     int K, int kb_per_split, GemmEpi epi, int* status) {
+  constexpr uint32_t kBytesA = kBM * kBK * 2, kBytesB = 128 * kBK * 2;
+  constexpr uint32_t kCols = 256;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* const gbase = smem_raw + (base - raw);
+  const uint32_t sA = base, sB = base + kStagesPair * kBytesA;
+  const uint32_t bars = sB + kStagesPair * kBytesB;
+  uint64_t* const bar_ptr = reinterpret_cast<uint64_t*>(gbase + (bars - base));
+  uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bar_ptr + 2 * kStagesPair + 1);
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (kStagesPair + s); };
+  const uint32_t done = bars + 8u * (2 * kStagesPair);
+
+  const uint32_t rank = cluster_rank();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = (blockIdx.x >> 1) * 256 + (int)rank * 128;  // this CTA's rows of A and D
+  const int n0 = blockIdx.y * 256;                           // the pair's columns of D
+  const int nb = n0 + (int)rank * 128;                       // this CTA's rows of B
+  const int nkb_all = (K + kBK - 1) / kBK;
+  const int kb0 = blockIdx.z * kb_per_split;
+  const int nkb = min(nkb_all, kb0 + kb_per_split) - kb0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStagesPair; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  cluster_sync();  // both CTAs' barriers initialised and TMEM allocated
+  tc_fence_after();
+  const uint32_t tmem_d = *tmem_slot;
+  int fail = 0;
+
+  if (warp == 0 && lane == 0) {
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % kStagesPair;
+      if (i >= kStagesPair && !mbar_wait(empty(s), ((i / kStagesPair) - 1) & 1)) {
+        fail = kStatusTimeoutFree;
+        break;
+      }
+      if (rank == 0) mbar_expect_tx(full(s), 2 * (kBytesA + kBytesB));
+      const uint32_t leader_full = map_to_rank(full(s), 0);
+      tma_load_2d_pair(sA + s * kBytesA, &ta, leader_full, (kb0 + i) * kBK, m0);
+      tma_load_2d_pair(sB + s * kBytesB, &tb, leader_full, (kb0 + i) * kBK, nb);
+    }
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    constexpr uint32_t idesc = idesc_bf16_pair();
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % kStagesPair;
+      if (!mbar_wait(full(s), (i / kStagesPair) & 1)) {
+        fail = kStatusTimeoutTma;
+        break;
+      }
+      tc_fence_after();
+      const uint64_t da = sw128_desc(sA + s * kBytesA), db = sw128_desc(sB + s * kBytesB);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk)
+        umma_bf16_pair(tmem_d, da + 2 * kk, db + 2 * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+      umma_commit_pair(empty(s));
+    }
+    umma_commit_pair(done);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(done, 0);
+  if (!ok && threadIdx.x == 0) fail |= kStatusTimeoutMma;
+  if (fail) atomicOr(status, fail);
+  tc_fence_after();
+  if (ok) epilogue<256>(tmem_d, m0, n0, M, N, blockIdx.z, epi);
+
+  tc_fence_before();
+  cluster_sync();  // neither CTA frees TMEM or exits while its peer may still touch the pair's state
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(kCols) : "memory");
   }
 }
 
@@ -288,14 +446,25 @@ cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N
   return cudaGetLastError();
 }
 
+cudaError_t launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int split, int kbs,
+                        const GemmEpi& epi, int* status, cudaStream_t s) {
+  const size_t smem = 1024 + (size_t)kStagesPair * (kBM * kBK * 2 + 128 * kBK * 2) + 8 * (2 * kStagesPair + 1) + 16;
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(2 * ((M + 255) / 256), (N + 255) / 256, split);
+  k_gemm_bf16_pair<<<grid, kGemmThreads, smem, s>>>(ta, tb, M, N, K, kbs, epi, status);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t gemm_smem_bytes(int bn) {
   return 1024 + (size_t)kStages * (kBM * kBK * 2 + (size_t)bn * kBK * 2) + 8 * (2 * kStages + 1) + 16;
 }
 
-cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int bn, int split,
-                        int kb_per_split, const GemmEpi& epi, int* status, cudaStream_t s) {
+cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int bn, bool pair,
+                        int split, int kb_per_split, const GemmEpi& epi, int* status, cudaStream_t s) {
+  if (pair) return launch_pair(ta, tb, M, N, K, split, kb_per_split, epi, status, s);  // 2-SM 256 x 256 tiles
   switch (bn) {
     case 32: return launch_bn<32>(ta, tb, M, N, K, split, kb_per_split, epi, status, s);
     case 64: return launch_bn<64>(ta, tb, M, N, K, split, kb_per_split, epi, status, s);

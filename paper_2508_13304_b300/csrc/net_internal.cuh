@@ -34,8 +34,9 @@ struct GemmEpi {
 };
 
 size_t gemm_smem_bytes(int bn);
-cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int bn, int split,
-                        int kb_per_split, const GemmEpi& epi, int* status, cudaStream_t s);
+// pair: 2-SM 256 x 256 tiles (bn must be 256, the B tensor map's box 128 rows)
+cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int bn, bool pair,
+                        int split, int kb_per_split, const GemmEpi& epi, int* status, cudaStream_t s);
 cudaError_t launch_split_reduce(const float* part, int split, int M, int N, const GemmEpi& epi, cudaStream_t s);
 
 cudaError_t launch_im2col(const __nv_bfloat16* x, int B, int H, int W, int C, int kp, __nv_bfloat16* col,

@@ -53,9 +53,30 @@ def test_gemm_fp32_output(M, N, K, lda, ldb):
     assert rel(D.cpu().numpy(), ref) <= 1e-5
 
 
+@pytest.mark.parametrize("M,N,K", [(512, 512, 256), (300, 512, 1000), (517, 1152, 136)])
+def test_gemm_pair_tiles_match_single_sm_tiles(M, N, K):
+    """The 2-SM 256 x 256 tiles (cta_group::2) and the 1-SM 128 x 256 tiles
+    give the same products (same K order per element) and match FP64."""
+    rng = np.random.default_rng(M * 7 + N)
+    A, B = bf16(rng, (M, K)), bf16(rng, (N, K))
+    D2 = torch.empty((M, N), device="cuda")
+    D1 = torch.empty((M, N), device="cuda")
+    pb.pn_gemm_bf16(M, N, K, A, K, B, K, D32=D2)
+    old = pb.pn_gemm_use_pair_tiles(False)
+    try:
+        pb.pn_gemm_bf16(M, N, K, A, K, B, K, D32=D1)
+    finally:
+        pb.pn_gemm_use_pair_tiles(old)
+    torch.cuda.synchronize()
+    assert pb.pn_status() == 0
+    ref = f64(A) @ f64(B).T
+    assert rel(D2.cpu().numpy(), ref) <= 1e-5
+    assert rel(D2.cpu().numpy(), D1.cpu().numpy()) <= 1e-6
+
+
 def test_gemm_split_k_is_deterministic_and_exact():
     rng = np.random.default_rng(9)
-    M, N, K = 96, 160, 8192
+    M, N, K = 300, 520, 8192   # 2-SM tiles with a ragged pair and split-K
     A, B = bf16(rng, (M, K)), bf16(rng, (N, K))
     split = 8
     part = torch.empty(split * M * N, device="cuda")
