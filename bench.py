@@ -422,15 +422,17 @@ def gemm_throughput(pb, torch, dev, flush, bf16_peak, shapes=GEMM_SHAPES):
         A = torch.randn((M, K), device=dev, generator=gen).bfloat16()
         B = torch.randn((N, K), device=dev, generator=gen).bfloat16()
         D = torch.empty((M, N), device=dev, dtype=torch.bfloat16)
-        for pair in ((True, False) if i == 0 else (True,)):
-            pb.pn_gemm_use_pair_tiles(pair)
+        names = {2: "2-SM 256x256 persistent", 1: "2-SM 256x256 per tile", 0: "1-SM 128x256"}
+        for mode in ((2, 1, 0) if i == 0 else (2,)):
+            pb.pn_gemm_use_pair_tiles(mode)
             ms = _event_ms(torch, lambda: pb.pn_gemm_bf16(M, N, K, A, K, B, K, D16=D), flush, reps=5)
             tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
             byts = 2.0 * (M * K + N * K + M * N)
-            out.append({"M": M, "N": N, "K": K, "tiles": "2-SM 256x256" if pair and N > 128 and M > 128 else "1-SM",
+            wide = N > 128 and M > 128
+            out.append({"M": M, "N": N, "K": K, "tiles": names[mode] if wide else "1-SM",
                         "ms": ms, "tflops": tf, "frac_of_bf16_peak": tf / bf16_peak,
                         "hbm_gbs_min_traffic": byts / (ms * 1e-3) / 1e9})
-        pb.pn_gemm_use_pair_tiles(True)
+        pb.pn_gemm_use_pair_tiles(2)
         del A, B, D
     return out
 

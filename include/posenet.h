@@ -43,12 +43,14 @@ int pn_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B, int
                  proj_stream stream);
 
 /* Tile choice of pn_gemm_bf16 for wide outputs (N tiles of 256, M > 128):
- * enable != 0 (the default) uses 256 x 256 tiles on pairs of SMs (a
- * cluster of two CTAs, tcgen05.mma.cta_group::2, each SM staging half of
- * the B tile); 0 uses 128 x 256 tiles on single SMs.  Results are
- * identical up to FP32 summation order within a tile (both accumulate K in
- * the same order).  Process-wide; returns the previous setting. */
-int pn_gemm_use_pair_tiles(int enable);
+ * mode 2 (the default): 256 x 256 tiles on pairs of SMs (a cluster of two
+ * CTAs, tcgen05.mma.cta_group::2, each SM staging half of the B tile), one
+ * cluster per pair of SMs looping over tiles with two TMEM accumulators so
+ * that one tile's epilogue overlaps the next tile's MMAs; mode 1: the same
+ * tiles, one cluster per tile; mode 0: 128 x 256 tiles on single SMs.
+ * Results are identical across modes (each element accumulates K in the
+ * same order).  Process-wide; returns the previous mode. */
+int pn_gemm_use_pair_tiles(int mode);
 
 /* The split_k that pn_gemm_bf16 would use well for this shape (about two
  * waves of CTAs on the device's SMs, at least 4 K blocks of 64 per CTA). */

@@ -459,9 +459,10 @@ def pn_gemm_bf16(M, N, K, A, lda, B, ldb, bias=None, mask=None, ldm=0, relu=Fals
                               _f32(part, name="part", allow_none=True), _stream(stream)))
 
 
-def pn_gemm_use_pair_tiles(enable=True) -> bool:
-    """Use 2-SM 256 x 256 tiles for wide GEMMs (default); returns the previous setting."""
-    return bool(lib().pn_gemm_use_pair_tiles(1 if enable else 0))
+def pn_gemm_use_pair_tiles(mode=2) -> int:
+    """Tiles of wide GEMMs: 2 persistent 2-SM (default), 1 2-SM per tile, 0 1-SM;
+    returns the previous mode."""
+    return int(lib().pn_gemm_use_pair_tiles(int(mode)))
 
 
 def pn_gemm_split_hint(M, N, K) -> int:

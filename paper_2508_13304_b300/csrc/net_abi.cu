@@ -38,7 +38,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 std::mutex g_mu;
 EncodeTiledFn g_encode = nullptr;
-int g_use_pair = 1;
+int g_use_pair = 2;
 int* g_status_addr[64] = {};
 int g_n_sm[64] = {};
 
@@ -114,9 +114,9 @@ using namespace pnk;
 
 extern "C" {
 
-int pn_gemm_use_pair_tiles(int enable) {
+int pn_gemm_use_pair_tiles(int mode) {
   const int old = g_use_pair;
-  g_use_pair = enable ? 1 : 0;
+  g_use_pair = mode < 0 ? 0 : (mode > 2 ? 2 : mode);
   return old;
 }
 
@@ -147,7 +147,7 @@ int pn_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int
   int* status = status_word();
   if (!status) return fail(PROJ_E_CUDA, "pn_gemm_bf16: no device status word");
   const int bn = bn_for(N);
-  const bool pair = g_use_pair && bn == 256 && M > kBM;
+  const int pair = (bn == 256 && M > kBM) ? g_use_pair : 0;
   CUtensorMap ta, tb;
   int rc = make_map(&ta, A, M, K, lda, kBM);
   if (rc) return rc;

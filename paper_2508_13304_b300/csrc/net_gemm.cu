@@ -12,6 +12,7 @@
 // a second kernel adds in a fixed order.  Every wait on an mbarrier is
 // bounded by the global timer; a timeout sets a status bit and the CTA
 // releases its TMEM and returns.
+#include <algorithm>
 #include <cstdio>
 
 #include "net_internal.cuh"
@@ -137,10 +138,11 @@ __device__ __forceinline__ float epi_value(float acc, int row, int col, const Ge
 // Epilogue of one CTA: its 128 TMEM lanes are rows m0..m0+127 of D, its BN
 // columns are n0..; each warp reads its 32 lanes 16 columns at a time.
 template <int BN>
-__device__ __forceinline__ void epilogue(uint32_t tmem_d, int m0, int n0, int M, int N, int z, const GemmEpi& epi) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = m0 + warp * 32 + lane;
-  const uint32_t lane_base = tmem_d + (static_cast<uint32_t>(warp * 32) << 16);
+__device__ __forceinline__ void epilogue(uint32_t tmem_d, int m0, int n0, int M, int N, int z, const GemmEpi& epi,
+                                         int quarter) {
+  const int lane = threadIdx.x & 31;
+  const int row = m0 + quarter * 32 + lane;  // a warp reads TMEM lanes 32 * (warp id mod 4) ...
+  const uint32_t lane_base = tmem_d + (static_cast<uint32_t>(quarter * 32) << 16);
 #pragma unroll 1
   for (int c0 = 0; c0 < BN; c0 += 16) {
     float v[16];
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   if (fail) atomicOr(status, fail);
   tc_fence_after();
 
-  if (ok) epilogue<BN>(tmem_d, m0, n0, M, N, blockIdx.z, epi);
+  if (ok) epilogue<BN>(tmem_d, m0, n0, M, N, blockIdx.z, epi, warp);
 
   tc_fence_before();
   __syncthreads();
@@ -365,6 +367,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  __syncwarp();
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kCols)
@@ -411,10 +414,175 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
   if (!ok && threadIdx.x == 0) fail |= kStatusTimeoutMma;
   if (fail) atomicOr(status, fail);
   tc_fence_after();
-  if (ok) epilogue<256>(tmem_d, m0, n0, M, N, blockIdx.z, epi);
+  if (ok) epilogue<256>(tmem_d, m0, n0, M, N, blockIdx.z, epi, warp);
 
   tc_fence_before();
   cluster_sync();  // neither CTA frees TMEM or exits while its peer may still touch the pair's state
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(kCols) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- persistent 2-SM
+//
+// The same 256 x 256 pair tiles, with one cluster per pair of SMs looping
+// over tiles and two TMEM accumulators (2 x 256 columns): warp 0 streams
+// K blocks without pausing between tiles, warp 1 of the even CTA issues the
+// MMAs of tile j into accumulator j % 2 once the epilogue has drained it,
+// and warps 2..5 of both CTAs drain the other accumulator meanwhile (warp w
+// reads TMEM lanes 32 (w mod 4) ...).  An epilogue releases an accumulator
+// by arriving, once per CTA, on the even CTA's "tmem_empty" barrier.
+
+constexpr int kPersistThreads = 192;
+
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPersistThreads, 1)
+    k_gemm_bf16_pair_persistent(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                                int M, int N, int K, int kb_per_split, int m_pairs, int n_tiles, int n_work,
+                                GemmEpi epi, int* status) {
+  constexpr uint32_t kBytesA = kBM * kBK * 2, kBytesB = 128 * kBK * 2;
+  constexpr uint32_t kCols = 512;  // two accumulators of 256 columns
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* const gbase = smem_raw + (base - raw);
+  const uint32_t sA = base, sB = base + kStagesPair * kBytesA;
+  const uint32_t bars = sB + kStagesPair * kBytesB;
+  // full[S], empty[S], tmem_full[2], tmem_empty[2]
+  uint64_t* const bar_ptr = reinterpret_cast<uint64_t*>(gbase + (bars - base));
+  uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bar_ptr + 2 * kStagesPair + 4);
+  volatile int* const epi_abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (kStagesPair + s); };
+  auto tmem_full = [&](int b) { return bars + 8u * (2 * kStagesPair + b); };
+  auto tmem_empty = [&](int b) { return bars + 8u * (2 * kStagesPair + 2 + b); };
+
+  const uint32_t rank = cluster_rank();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cluster = blockIdx.x >> 1, n_clusters = gridDim.x >> 1;
+  const int nkb_all = (K + kBK - 1) / kBK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStagesPair; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tmem_full(b), 1);
+      mbar_init(tmem_empty(b), 2);  // one arrival per CTA of the pair (used in the even CTA)
+    }
+    *epi_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  cluster_sync();
+  tc_fence_after();
+  const uint32_t tmem_d = *tmem_slot;
+  int fail = 0;
+
+  // work item w -> (split z, N tile, M pair), M pairs fastest
+  auto decode = [&](int w, int& mp, int& nt, int& z) {
+    mp = w % m_pairs;
+    nt = (w / m_pairs) % n_tiles;
+    z = w / (m_pairs * n_tiles);
+  };
+  auto kb_range = [&](int z, int& kb0, int& nkb) {
+    kb0 = z * kb_per_split;
+    nkb = min(nkb_all, kb0 + kb_per_split) - kb0;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      long long g = 0;  // K blocks issued so far (ring position)
+      for (int w = cluster; w < n_work && !fail; w += n_clusters) {
+        int mp, nt, z, kb0, nkb;
+        decode(w, mp, nt, z);
+        kb_range(z, kb0, nkb);
+        const int m0 = mp * 256 + (int)rank * 128, nb = nt * 256 + (int)rank * 128;
+        for (int i = 0; i < nkb; ++i, ++g) {
+          const int s = (int)(g % kStagesPair);
+          const long long u = g / kStagesPair;
+          if (u > 0 && !mbar_wait(empty(s), (uint32_t)((u - 1) & 1))) {
+            fail = kStatusTimeoutFree;
+            break;
+          }
+          if (rank == 0) mbar_expect_tx(full(s), 2 * (kBytesA + kBytesB));
+          const uint32_t leader_full = map_to_rank(full(s), 0);
+          tma_load_2d_pair(sA + s * kBytesA, &ta, leader_full, (kb0 + i) * kBK, m0);
+          tma_load_2d_pair(sB + s * kBytesB, &tb, leader_full, (kb0 + i) * kBK, nb);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      constexpr uint32_t idesc = idesc_bf16_pair();
+      long long g = 0;
+      int j = 0;  // tiles of this cluster so far
+      for (int w = cluster; w < n_work && !fail; w += n_clusters, ++j) {
+        int mp, nt, z, kb0, nkb;
+        decode(w, mp, nt, z);
+        kb_range(z, kb0, nkb);
+        const int b = j & 1, ub = j >> 1;
+        if (ub > 0 && !mbar_wait(tmem_empty(b), (uint32_t)((ub - 1) & 1))) {
+          fail = kStatusTimeoutMma;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc = tmem_d + (uint32_t)(b * 256);
+        for (int i = 0; i < nkb; ++i, ++g) {
+          const int s = (int)(g % kStagesPair);
+          if (!mbar_wait(full(s), (uint32_t)((g / kStagesPair) & 1))) {
+            fail = kStatusTimeoutTma;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t da = sw128_desc(sA + s * kBytesA), db = sw128_desc(sB + s * kBytesB);
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk)
+            umma_bf16_pair(acc, da + 2 * kk, db + 2 * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+          umma_commit_pair(empty(s));
+        }
+        umma_commit_pair(tmem_full(b));
+      }
+    }
+  } else {
+    const int quarter = warp & 3;
+    int j = 0;
+    for (int w = cluster; w < n_work; w += n_clusters, ++j) {
+      int mp, nt, z;
+      decode(w, mp, nt, z);
+      const int b = j & 1;
+      const bool ok = mbar_wait(tmem_full(b), (uint32_t)((j >> 1) & 1));
+      if (!ok) {
+        fail = kStatusTimeoutMma;
+        *epi_abort = 1;
+      } else {
+        tc_fence_after();
+        epilogue<256>(tmem_d + (uint32_t)(b * 256), mp * 256 + (int)rank * 128, nt * 256, M, N, z, epi, quarter);
+      }
+      tc_fence_before();
+      asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps of this CTA are done with b
+      const bool stop = *epi_abort != 0;              // same value in all four warps (read after the barrier)
+      if (stop) break;
+      if (warp == 2 && lane == 0) mbar_arrive_remote(map_to_rank(tmem_empty(b), 0));
+    }
+  }
+  __syncwarp();
+  if (fail) atomicOr(status, fail);
+
+  tc_fence_before();
+  cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(kCols) : "memory");
@@ -456,14 +624,42 @@ cudaError_t launch_pair(const CUtensorMap& ta, const CUtensorMap& tb, int M, int
   return cudaGetLastError();
 }
 
+cudaError_t launch_pair_persistent(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int split,
+                                   int kbs, const GemmEpi& epi, int* status, cudaStream_t s) {
+  const size_t smem = 1024 + (size_t)kStagesPair * (kBM * kBK * 2 + 128 * kBK * 2) + 8 * (2 * kStagesPair + 4) + 16;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_gemm_bf16_pair_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, n_sm = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const int m_pairs = (M + 255) / 256, n_tiles = (N + 255) / 256;
+  const long long work = (long long)m_pairs * n_tiles * split;
+  if (work > (1LL << 30)) return cudaErrorInvalidValue;
+  // as many clusters as can be resident at once (not every SM need find a partner in its GPC)
+  int resident = 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n_sm - n_sm % 2, 1, 1);
+  cfg.blockDim = dim3(kPersistThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  if (cudaOccupancyMaxActiveClusters(&resident, k_gemm_bf16_pair_persistent, &cfg) != cudaSuccess || resident < 1) {
+    cudaGetLastError();
+    resident = std::max(1, n_sm / 2);
+  }
+  const int clusters = (int)std::min<long long>(work, resident);
+  k_gemm_bf16_pair_persistent<<<2 * clusters, kPersistThreads, smem, s>>>(ta, tb, M, N, K, kbs, m_pairs, n_tiles,
+                                                                          (int)work, epi, status);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t gemm_smem_bytes(int bn) {
   return 1024 + (size_t)kStages * (kBM * kBK * 2 + (size_t)bn * kBK * 2) + 8 * (2 * kStages + 1) + 16;
 }
 
-cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int bn, bool pair,
+cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int bn, int pair,
                         int split, int kb_per_split, const GemmEpi& epi, int* status, cudaStream_t s) {
+  if (pair == 2) return launch_pair_persistent(ta, tb, M, N, K, split, kb_per_split, epi, status, s);
   if (pair) return launch_pair(ta, tb, M, N, K, split, kb_per_split, epi, status, s);  // 2-SM 256 x 256 tiles
   switch (bn) {
     case 32: return launch_bn<32>(ta, tb, M, N, K, split, kb_per_split, epi, status, s);

@@ -34,8 +34,9 @@ struct GemmEpi {
 };
 
 size_t gemm_smem_bytes(int bn);
-// pair: 2-SM 256 x 256 tiles (bn must be 256, the B tensor map's box 128 rows)
-cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int bn, bool pair,
+// pair: 0 = 1-SM 128 x bn tiles; 1 = 2-SM 256 x 256 tiles, one per cluster; 2 = the same
+// tiles on a persistent grid with two TMEM accumulators (pair != 0: bn 256, B box 128 rows)
+cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int bn, int pair,
                         int split, int kb_per_split, const GemmEpi& epi, int* status, cudaStream_t s);
 cudaError_t launch_split_reduce(const float* part, int split, int M, int N, const GemmEpi& epi, cudaStream_t s);
 

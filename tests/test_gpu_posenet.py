@@ -55,23 +55,26 @@ def test_gemm_fp32_output(M, N, K, lda, ldb):
 
 @pytest.mark.parametrize("M,N,K", [(512, 512, 256), (300, 512, 1000), (517, 1152, 136)])
 def test_gemm_pair_tiles_match_single_sm_tiles(M, N, K):
-    """The 2-SM 256 x 256 tiles (cta_group::2) and the 1-SM 128 x 256 tiles
-    give the same products (same K order per element) and match FP64."""
+    """The persistent and per-tile 2-SM 256 x 256 tiles (cta_group::2) and
+    the 1-SM 128 x 256 tiles give the same products (same K order per
+    element) and match FP64."""
     rng = np.random.default_rng(M * 7 + N)
     A, B = bf16(rng, (M, K)), bf16(rng, (N, K))
-    D2 = torch.empty((M, N), device="cuda")
-    D1 = torch.empty((M, N), device="cuda")
-    pb.pn_gemm_bf16(M, N, K, A, K, B, K, D32=D2)
-    old = pb.pn_gemm_use_pair_tiles(False)
+    outs = {}
+    old = pb.pn_gemm_use_pair_tiles(2)
     try:
-        pb.pn_gemm_bf16(M, N, K, A, K, B, K, D32=D1)
+        for mode in (2, 1, 0):   # persistent 2-SM, 2-SM per tile, 1-SM
+            pb.pn_gemm_use_pair_tiles(mode)
+            outs[mode] = torch.empty((M, N), device="cuda")
+            pb.pn_gemm_bf16(M, N, K, A, K, B, K, D32=outs[mode])
     finally:
         pb.pn_gemm_use_pair_tiles(old)
     torch.cuda.synchronize()
     assert pb.pn_status() == 0
     ref = f64(A) @ f64(B).T
-    assert rel(D2.cpu().numpy(), ref) <= 1e-5
-    assert rel(D2.cpu().numpy(), D1.cpu().numpy()) <= 1e-6
+    assert rel(outs[2].cpu().numpy(), ref) <= 1e-5
+    assert rel(outs[2].cpu().numpy(), outs[1].cpu().numpy()) <= 1e-6
+    assert rel(outs[2].cpu().numpy(), outs[0].cpu().numpy()) <= 1e-6
 
 
 def test_gemm_split_k_is_deterministic_and_exact():
