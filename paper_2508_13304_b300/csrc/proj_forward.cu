@@ -482,19 +482,68 @@ __global__ void __launch_bounds__(kMarchThreads) k_forward_adjoint(const InstTab
   Ray r;
   if (yi == 0.f || !T.valid || !ray_setup(T, g, iu, iv, r)) return;
   const int pxy = g.px * g.py;
+  // Samples 0.5 voxel apart often fall in the same cell, or in a cell that
+  // shares a face with the previous one.  The 8 corner weights (corner q =
+  // offsets (q & 1, (q >> 1) & 1, q >> 2)) are summed in registers while the
+  // cell is unchanged; on a step to a face neighbour the 4 shared corners
+  // carry over and only the 4 left behind are added to the volume; any
+  // other step adds all 8.
+  int cur = -1;
+  float w[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int off[8] = {0, 1, g.px, g.px + 1, pxy, pxy + 1, pxy + g.px, pxy + g.px + 1};
+  auto put = [&](int idx, int q) {
+    atomicAdd(acc + idx + off[q], yi * w[q]);
+    w[q] = 0.f;
+  };
+  // move along one axis: corners with bit `bit` == from go to the volume,
+  // corners with bit == 1 - from shift into their place
+  auto step_axis = [&](int bit, int from) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (((q >> bit) & 1) == from) {
+        const int o = q ^ (1 << bit);
+        put(cur, q);
+        w[q] = w[o];
+        w[o] = 0.f;
+      }
+  };
   for (int k = r.k0; k <= r.k1; ++k) {
     const float kf = (float)k;
     const Cell c = locate(fmaf(kf, r.dx, r.ax), fmaf(kf, r.dy, r.ay), fmaf(kf, r.dz, r.az), g);
-    float* p0 = acc + c.idx;
+    if (c.idx != cur) {
+      const int d = c.idx - cur;
+      if (cur < 0) {
+      } else if (d == 1) {
+        step_axis(0, 0);
+      } else if (d == -1) {
+        step_axis(0, 1);
+      } else if (d == g.px) {
+        step_axis(1, 0);
+      } else if (d == -g.px) {
+        step_axis(1, 1);
+      } else if (d == pxy) {
+        step_axis(2, 0);
+      } else if (d == -pxy) {
+        step_axis(2, 1);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) put(cur, q);
+      }
+      cur = c.idx;
+    }
     const float bx = 1.f - c.ax, by = 1.f - c.ay, bz = 1.f - c.az;
-    atomicAdd(p0, yi * bx * by * bz);
-    atomicAdd(p0 + 1, yi * c.ax * by * bz);
-    atomicAdd(p0 + g.px, yi * bx * c.ay * bz);
-    atomicAdd(p0 + g.px + 1, yi * c.ax * c.ay * bz);
-    atomicAdd(p0 + pxy, yi * bx * by * c.az);
-    atomicAdd(p0 + pxy + 1, yi * c.ax * by * c.az);
-    atomicAdd(p0 + pxy + g.px, yi * bx * c.ay * c.az);
-    atomicAdd(p0 + pxy + g.px + 1, yi * c.ax * c.ay * c.az);
+    w[0] += bx * by * bz;
+    w[1] += c.ax * by * bz;
+    w[2] += bx * c.ay * bz;
+    w[3] += c.ax * c.ay * bz;
+    w[4] += bx * by * c.az;
+    w[5] += c.ax * by * c.az;
+    w[6] += bx * c.ay * c.az;
+    w[7] += c.ax * c.ay * c.az;
+  }
+  if (cur >= 0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) put(cur, q);
   }
 }
 
