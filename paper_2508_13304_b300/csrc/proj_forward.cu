@@ -179,16 +179,47 @@ __global__ void __launch_bounds__(kMarchThreads) k_forward(const InstTable* __re
   Ray r;
   if (T.valid && ray_setup(T, g, iu, iv, r)) {
     const int pxy = g.px * g.py;
+    // The 8 corners (corner q = offsets (q & 1, (q >> 1) & 1, q >> 2)) stay in
+    // registers while the ray is in one cell; a step to a face neighbour
+    // keeps the 4 shared corners and loads the other 4.
+    float v[8];
+    int cur = -1;
     for (int k = r.k0; k <= r.k1; ++k) {
       const float kf = (float)k;
       const Cell c = locate(fmaf(kf, r.dx, r.ax), fmaf(kf, r.dy, r.ay), fmaf(kf, r.dz, r.az), g);
-      const float* p0 = vol + c.idx;
-      const float v000 = __ldg(p0), v100 = __ldg(p0 + 1);
-      const float v010 = __ldg(p0 + g.px), v110 = __ldg(p0 + g.px + 1);
-      const float v001 = __ldg(p0 + pxy), v101 = __ldg(p0 + pxy + 1);
-      const float v011 = __ldg(p0 + pxy + g.px), v111 = __ldg(p0 + pxy + g.px + 1);
-      const float c0 = lerp(lerp(v000, v100, c.ax), lerp(v010, v110, c.ax), c.ay);
-      const float c1 = lerp(lerp(v001, v101, c.ax), lerp(v011, v111, c.ax), c.ay);
+      if (c.idx != cur) {
+        const float* p0 = vol + c.idx;
+        const int d = c.idx - cur;
+        if (cur >= 0 && d == 1) {
+          v[0] = v[1]; v[2] = v[3]; v[4] = v[5]; v[6] = v[7];
+          v[1] = __ldg(p0 + 1); v[3] = __ldg(p0 + g.px + 1); v[5] = __ldg(p0 + pxy + 1);
+          v[7] = __ldg(p0 + pxy + g.px + 1);
+        } else if (cur >= 0 && d == -1) {
+          v[1] = v[0]; v[3] = v[2]; v[5] = v[4]; v[7] = v[6];
+          v[0] = __ldg(p0); v[2] = __ldg(p0 + g.px); v[4] = __ldg(p0 + pxy); v[6] = __ldg(p0 + pxy + g.px);
+        } else if (cur >= 0 && d == g.px) {
+          v[0] = v[2]; v[1] = v[3]; v[4] = v[6]; v[5] = v[7];
+          v[2] = __ldg(p0 + g.px); v[3] = __ldg(p0 + g.px + 1); v[6] = __ldg(p0 + pxy + g.px);
+          v[7] = __ldg(p0 + pxy + g.px + 1);
+        } else if (cur >= 0 && d == -g.px) {
+          v[2] = v[0]; v[3] = v[1]; v[6] = v[4]; v[7] = v[5];
+          v[0] = __ldg(p0); v[1] = __ldg(p0 + 1); v[4] = __ldg(p0 + pxy); v[5] = __ldg(p0 + pxy + 1);
+        } else if (cur >= 0 && d == pxy) {
+          v[0] = v[4]; v[1] = v[5]; v[2] = v[6]; v[3] = v[7];
+          v[4] = __ldg(p0 + pxy); v[5] = __ldg(p0 + pxy + 1); v[6] = __ldg(p0 + pxy + g.px);
+          v[7] = __ldg(p0 + pxy + g.px + 1);
+        } else if (cur >= 0 && d == -pxy) {
+          v[4] = v[0]; v[5] = v[1]; v[6] = v[2]; v[7] = v[3];
+          v[0] = __ldg(p0); v[1] = __ldg(p0 + 1); v[2] = __ldg(p0 + g.px); v[3] = __ldg(p0 + g.px + 1);
+        } else {
+          v[0] = __ldg(p0); v[1] = __ldg(p0 + 1); v[2] = __ldg(p0 + g.px); v[3] = __ldg(p0 + g.px + 1);
+          v[4] = __ldg(p0 + pxy); v[5] = __ldg(p0 + pxy + 1); v[6] = __ldg(p0 + pxy + g.px);
+          v[7] = __ldg(p0 + pxy + g.px + 1);
+        }
+        cur = c.idx;
+      }
+      const float c0 = lerp(lerp(v[0], v[1], c.ax), lerp(v[2], v[3], c.ax), c.ay);
+      const float c1 = lerp(lerp(v[4], v[5], c.ax), lerp(v[6], v[7], c.ax), c.ay);
       acc += lerp(c0, c1, c.az);
     }
   }
