@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
       const float fz = (float)(iz0 + z) - g.cz;
       const float hw = fmaf(qz2, fz, bw);
       if (!(hw > 0.f)) continue;
-      const float rw = 1.0f / hw;
+      const float rw = __fdividef(1.0f, hw);  // fast reciprocal (about 2 ulp), the same in k_back and k_back_adjoint
       const float u = fmaf(qz0, fz, bu) * rw, v = fmaf(qz1, fz, bv) * rw;
       if (!(u > -1.f && u < fu && v > -1.f && v < fvv)) continue;
       // u in (-1, nu) and v in (-1, nv): the lower corner is in [-1, n-1],
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kBpThreads) k_back_adjoint(const InstTable* __
       const float fz = (float)(iz0 + z) - g.cz;
       const float hw = fmaf(T.Q[8], fz, bw);
       if (!(hw > 0.f)) continue;
-      const float rw = 1.0f / hw;
+      const float rw = __fdividef(1.0f, hw);  // fast reciprocal (about 2 ulp), the same in k_back and k_back_adjoint
       const float u = fmaf(T.Q[6], fz, bu) * rw, v = fmaf(T.Q[7], fz, bv) * rw;
       if (!(u > -1.f && u < fu && v > -1.f && v < fvv)) continue;
       const float flu = floorf(u), flv = floorf(v);
