@@ -61,7 +61,8 @@ struct proj_plan_s {
   bool timing = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // workspace layout (byte offsets; 0 = buffer absent, the status word sits at 0)
-  size_t off_status = 0, off_inst = 0, off_ptab = 0, off_vol1 = 0, off_vol4 = 0, off_part_f = 0, off_det4 = 0,
+  size_t off_status = 0, off_inst = 0, off_ptab = 0, off_vol1 = 0, off_vol4 = 0, off_vol4y = 0, off_part_f = 0,
+         off_det4 = 0,
          off_part_b = 0, off_acc = 0, off_sharp_m = 0, off_sharp_part = 0, ws_bytes = 0;
 };
 
@@ -75,6 +76,7 @@ struct WsView {
   PoseTable* ptab = nullptr;
   float* vol1 = nullptr;
   float4* vol4 = nullptr;
+  float4* vol4y = nullptr;
   float* part_f = nullptr;
   float4* det4 = nullptr;
   float* part_b = nullptr;
@@ -92,6 +94,7 @@ int check_ws(const proj_plan_s* p, void* d_ws, size_t ws_bytes, WsView* w) {
   w->ptab = reinterpret_cast<PoseTable*>(b + p->off_ptab);
   w->vol1 = p->off_vol1 ? reinterpret_cast<float*>(b + p->off_vol1) : nullptr;
   w->vol4 = p->off_vol4 ? reinterpret_cast<float4*>(b + p->off_vol4) : nullptr;
+  w->vol4y = p->off_vol4y ? reinterpret_cast<float4*>(b + p->off_vol4y) : nullptr;
   w->part_f = p->off_part_f ? reinterpret_cast<float*>(b + p->off_part_f) : nullptr;
   w->det4 = p->off_det4 ? reinterpret_cast<float4*>(b + p->off_det4) : nullptr;
   w->part_b = p->off_part_b ? reinterpret_cast<float*>(b + p->off_part_b) : nullptr;
@@ -144,6 +147,10 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   volume_pitches(G.nx, G.ny, G.nz, &qx, &qy, &qz);
   const long long npad2 = (long long)qx * qy * qz;
   if (npad2 >= (1LL << 31)) return fail(PROJ_E_ARG, "volume too large (padded voxel count %lld >= 2^31)", npad2);
+  int rqx, rqy;
+  volume_pitches_yfast(G.nx, G.ny, &rqx, &rqy);
+  const long long npad2y = (long long)rqx * rqy * qz;
+  if (npad2y >= (1LL << 31)) return fail(PROJ_E_ARG, "volume too large (padded voxel count %lld >= 2^31)", npad2y);
   if ((long long)(G.nu + 4) * (G.nv + 4) >= (1LL << 31)) return fail(PROJ_E_ARG, "detector too large");
   if (!finite_pos(G.vx) || !finite_pos(G.vy) || !finite_pos(G.vz))
     return fail(PROJ_E_ARG, "voxel pitch must be finite and > 0");
@@ -189,6 +196,7 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   g.py = G.ny + 2;
   g.pz = G.nz + 2;
   volume_pitches(G.nx, G.ny, G.nz, &g.qx, &g.qy, &g.qz);
+  volume_pitches_yfast(G.nx, G.ny, &g.rqx, &g.rqy);
   g.vx = (float)G.vx;
   g.vy = (float)G.vy;
   g.vz = (float)G.vz;
@@ -249,6 +257,7 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   const size_t npad_sz = (size_t)npad;
   p->off_vol1 = (ops & PROJ_OP_FORWARD) ? take(sizeof(float) * npad_sz) : 0;
   p->off_vol4 = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float4) * (size_t)npad2) : 0;
+  p->off_vol4y = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float4) * (size_t)npad2y) : 0;
   p->off_part_f = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float) * kRec * (size_t)n_inst * p->n_tiles) : 0;
   p->off_det4 = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float4) * (size_t)n_inst * (G.nu + 4) * (G.nv + 4)) : 0;
   p->off_part_b = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float) * 12 * (size_t)n_inst * p->bp_blocks) : 0;
@@ -349,6 +358,7 @@ int proj_set_volume(proj_plan p, const float* d_mu, void* d_ws, size_t ws_bytes,
   if (rc) return rc;
   if ((rc = check_device(p))) return rc;
   cudaError_t e = launch_volume_prep(d_mu, p->geo, w.vol1, w.vol4, (cudaStream_t)stream);
+  if (e == cudaSuccess && w.vol4y) e = launch_volume_yfast(w.vol4, p->geo, w.vol4y, (cudaStream_t)stream);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "volume preparation launch");
 }
 
@@ -397,7 +407,7 @@ int proj_forward_pose_grad(proj_plan p, const float* d_pose, int loss, const flo
   if ((rc = setup(p, d_pose, w, s))) return rc;
   mark(p, true, s);
   cudaError_t e =
-      launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, loss, d_ref, d_proj, w.part_f, s, p->warp_width);
+      launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, d_proj, w.part_f, s, p->warp_width);
   mark(p, false, s);
   if (e != cudaSuccess) return cuda_fail(e, "forward pose-gradient launch");
   e = launch_forward_grad_reduce(w.inst, w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_tiles, p->geo, loss,
@@ -519,10 +529,12 @@ int proj_autotune_forward_grad(proj_plan p, const float* d_pose, int loss, const
   float best = 0.f;
   int pick = p->warp_width;
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
-    e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, loss, d_ref, nullptr, w.part_f, s, widths[i]);
+    e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, nullptr, w.part_f, s,
+                            widths[i]);
     if (e == cudaSuccess) e = cudaEventRecord(a, s);
     for (int r = 0; r < reps && e == cudaSuccess; ++r)
-      e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, loss, d_ref, nullptr, w.part_f, s, widths[i]);
+      e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, nullptr, w.part_f, s,
+                            widths[i]);
     if (e == cudaSuccess) e = cudaEventRecord(b, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(b);
     float ms = 0.f;
@@ -640,6 +652,7 @@ int proj_batch_create(int n, const proj_plan* plans, const int* loss, const floa
     B.geo = p->geo;
     B.inst = w.inst;
     B.vol4 = w.vol4;
+    B.vol4y = w.vol4y;
     B.ref = d_ref[i];
     B.part = w.part_f;
     B.n_tiles = p->n_tiles;

@@ -116,6 +116,9 @@ __device__ __forceinline__ Cell locate(float fx, float fy, float fz, const Geo& 
   return c;
 }
 
+// YF = 0: the pitched (mu, grad mu) volume with x fastest; YF = 1: its copy
+// with y fastest.
+template <int YF = 0>
 __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo& g) {
   const int ix = min(max(__float2int_rd(fx), 0), g.nx + 2);
   const int iy = min(max(__float2int_rd(fy), 0), g.ny + 2);
@@ -124,7 +127,7 @@ __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo&
   c.ax = fx - (float)ix;
   c.ay = fy - (float)iy;
   c.az = fz - (float)iz;
-  c.idx = (iz * g.qy + iy) * g.qx + ix;
+  c.idx = YF ? (iz * g.rqx + ix) * g.rqy + iy : (iz * g.qy + iy) * g.qx + ix;
   return c;
 }
 
@@ -254,7 +257,7 @@ __global__ void k_count(const InstTable* __restrict__ inst, int n_tiles, int til
 // One 16 x 16 ray tile (instance n, tile index) of the fused march, block-
 // wide: writes the tile's record part[(n * n_tiles + tile) * kRec ...].
 // Shared by the per-problem kernel and the persistent multi-problem kernel.
-template <int LOSS, int WU = 4>
+template <int LOSS, int WU = 4, int YF = 0>
 __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, int n, int tile, int n_tiles,
                                            int tiles_u, const Geo& g, const float4* __restrict__ vol,
                                            const float* __restrict__ ref, float* __restrict__ proj,
@@ -267,17 +270,18 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
   float s1[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   Ray r;
   if (on_det && T.valid && ray_setup_m<2>(T, g, iu, iv, r)) {
-    const int qxy = g.qx * g.qy;
+    // element strides of +1 voxel along x, y, z in the marched copy
+    const int sx = YF ? g.rqy : 1, sy = YF ? 1 : g.qx, sz = YF ? g.rqx * g.rqy : g.qx * g.qy;
     const float ox = g.cx + 2.0f, oy = g.cy + 2.0f, oz = g.cz + 2.0f;
     for (int k = r.k0; k <= r.k1; ++k) {
       const float kf = (float)k;
       const float fx = fmaf(kf, r.dx, r.ax), fy = fmaf(kf, r.dy, r.ay), fz = fmaf(kf, r.dz, r.az);
-      const Cell c = locate2(fx, fy, fz, g);
+      const Cell c = locate2<YF>(fx, fy, fz, g);
       const float4* p0 = vol + c.idx;
-      const float4 v000 = __ldg(p0), v100 = __ldg(p0 + 1);
-      const float4 v010 = __ldg(p0 + g.qx), v110 = __ldg(p0 + g.qx + 1);
-      const float4 v001 = __ldg(p0 + qxy), v101 = __ldg(p0 + qxy + 1);
-      const float4 v011 = __ldg(p0 + qxy + g.qx), v111 = __ldg(p0 + qxy + g.qx + 1);
+      const float4 v000 = __ldg(p0), v100 = __ldg(p0 + sx);
+      const float4 v010 = __ldg(p0 + sy), v110 = __ldg(p0 + sy + sx);
+      const float4 v001 = __ldg(p0 + sz), v101 = __ldg(p0 + sz + sx);
+      const float4 v011 = __ldg(p0 + sz + sy), v111 = __ldg(p0 + sz + sy + sx);
       const float4 c0 = lerp4(lerp4(v000, v100, c.ax), lerp4(v010, v110, c.ax), c.ay);
       const float4 c1 = lerp4(lerp4(v001, v101, c.ax), lerp4(v011, v111, c.ax), c.ay);
       const float4 v = lerp4(c0, c1, c.az);
@@ -362,13 +366,16 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
 }
 
 template <int LOSS, int WU>
-__global__ void __launch_bounds__(kMarchThreads)
+__global__ void __launch_bounds__(kMarchThreads, 4)
     k_forward_grad(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g,
-                   const float4* __restrict__ vol, const float* __restrict__ ref, float* __restrict__ proj,
-                   float* __restrict__ part) {
+                   const float4* __restrict__ vol, const float4* __restrict__ voly, const float* __restrict__ ref,
+                   float* __restrict__ proj, float* __restrict__ part) {
   __shared__ float red[kMarchThreads / 32][kRec];
-  march_tile<LOSS, WU>(inst, blockIdx.x / n_tiles, blockIdx.x % n_tiles, n_tiles, tiles_u, g, vol, ref, proj, part,
-                       red);
+  const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
+  if (voly && inst[n].yfast)  // uniform per block
+    march_tile<LOSS, WU, 1>(inst, n, tile, n_tiles, tiles_u, g, voly, ref, proj, part, red);
+  else
+    march_tile<LOSS, WU, 0>(inst, n, tile, n_tiles, tiles_u, g, vol, ref, proj, part, red);
 }
 
 // ---------------------------------------------------------------- batch
@@ -395,17 +402,31 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
     const BatchProblem& B = probs[p];
     const int local = (int)(item - B.item_begin);
     const int n = local / B.n_tiles, tile = local % B.n_tiles;
-    switch (B.loss) {
-      case PROJ_LOSS_RESIDUAL:
-        march_tile<PROJ_LOSS_RESIDUAL>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr, B.part,
+    const bool yf = B.vol4y && B.inst[n].yfast;
+    switch (B.loss * 2 + (yf ? 1 : 0)) {
+      case PROJ_LOSS_RESIDUAL * 2:
+        march_tile<PROJ_LOSS_RESIDUAL, 4, 0>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr,
+                                             B.part, red);
+        break;
+      case PROJ_LOSS_RESIDUAL * 2 + 1:
+        march_tile<PROJ_LOSS_RESIDUAL, 4, 1>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4y, B.ref, nullptr,
+                                             B.part, red);
+        break;
+      case PROJ_LOSS_L2 * 2:
+        march_tile<PROJ_LOSS_L2, 4, 0>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr, B.part,
                                        red);
         break;
-      case PROJ_LOSS_L2:
-        march_tile<PROJ_LOSS_L2>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr, B.part, red);
+      case PROJ_LOSS_L2 * 2 + 1:
+        march_tile<PROJ_LOSS_L2, 4, 1>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4y, B.ref, nullptr, B.part,
+                                       red);
+        break;
+      case PROJ_LOSS_NCC * 2 + 1:
+        march_tile<PROJ_LOSS_NCC, 4, 1>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4y, B.ref, nullptr,
+                                        B.part, red);
         break;
       default:
-        march_tile<PROJ_LOSS_NCC>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr, B.part,
-                                  red);
+        march_tile<PROJ_LOSS_NCC, 4, 0>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr,
+                                        B.part, red);
         break;
     }
   }
@@ -623,34 +644,64 @@ cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long
 namespace {
 template <int WU>
 void launch_forward_grad_w(const InstTable* d_inst, int grid, int nt, int tu, const Geo& geo, const float4* d_vol4,
-                           int loss, const float* d_ref, float* d_proj, float* d_part, cudaStream_t s) {
+                           const float4* d_vol4y, int loss, const float* d_ref, float* d_proj, float* d_part,
+                           cudaStream_t s) {
   switch (loss) {
     case PROJ_LOSS_RESIDUAL:
-      k_forward_grad<PROJ_LOSS_RESIDUAL, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_ref,
-                                                                            d_proj, d_part);
+      k_forward_grad<PROJ_LOSS_RESIDUAL, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_vol4y,
+                                                                            d_ref, d_proj, d_part);
       break;
     case PROJ_LOSS_L2:
-      k_forward_grad<PROJ_LOSS_L2, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_ref, d_proj,
-                                                                      d_part);
+      k_forward_grad<PROJ_LOSS_L2, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_vol4y, d_ref,
+                                                                      d_proj, d_part);
       break;
     default:
-      k_forward_grad<PROJ_LOSS_NCC, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_ref, d_proj,
-                                                                       d_part);
+      k_forward_grad<PROJ_LOSS_NCC, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_vol4y, d_ref,
+                                                                       d_proj, d_part);
       break;
   }
 }
 }  // namespace
 
-cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4, int loss,
-                                const float* d_ref, float* d_proj, float* d_part, cudaStream_t s, int warp_width) {
+cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
+                                const float4* d_vol4y, int loss, const float* d_ref, float* d_proj, float* d_part,
+                                cudaStream_t s, int warp_width) {
   const int nt = tiles_of(geo), tu = tiles_u_of(geo);
   const int grid = n_inst * nt;
   switch (warp_width) {
-    case 2: launch_forward_grad_w<2>(d_inst, grid, nt, tu, geo, d_vol4, loss, d_ref, d_proj, d_part, s); break;
-    case 8: launch_forward_grad_w<8>(d_inst, grid, nt, tu, geo, d_vol4, loss, d_ref, d_proj, d_part, s); break;
-    case 16: launch_forward_grad_w<16>(d_inst, grid, nt, tu, geo, d_vol4, loss, d_ref, d_proj, d_part, s); break;
-    default: launch_forward_grad_w<4>(d_inst, grid, nt, tu, geo, d_vol4, loss, d_ref, d_proj, d_part, s); break;
+    case 2: launch_forward_grad_w<2>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, s); break;
+    case 8: launch_forward_grad_w<8>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, s); break;
+    case 16:
+      launch_forward_grad_w<16>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, s);
+      break;
+    default: launch_forward_grad_w<4>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, s); break;
   }
+  return cudaGetLastError();
+}
+
+namespace {
+constexpr int kTr = 32;
+
+// One z slice tile of 32 x 32 (x, y): read rows along x, write rows along y.
+__global__ void k_volume_yfast(const float4* __restrict__ v, Geo g, float4* __restrict__ vy) {
+  __shared__ float4 t[kTr][kTr + 1];
+  const int X = g.nx + 4, Y = g.ny + 4;
+  const int x0 = blockIdx.x * kTr, y0 = blockIdx.y * kTr, z = blockIdx.z;
+  for (int j = threadIdx.y; j < kTr; j += blockDim.y) {
+    const int x = x0 + threadIdx.x, y = y0 + j;
+    t[j][threadIdx.x] = (x < X && y < Y) ? v[((size_t)z * g.qy + y) * g.qx + x] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < kTr; j += blockDim.y) {
+    const int y = y0 + threadIdx.x, x = x0 + j;
+    if (x < g.rqx && y < g.rqy) vy[((size_t)z * g.rqx + x) * g.rqy + y] = t[threadIdx.x][j];
+  }
+}
+}  // namespace
+
+cudaError_t launch_volume_yfast(const float4* d_vol4, Geo geo, float4* d_vol4y, cudaStream_t s) {
+  dim3 grid(ceil_div(geo.rqx, kTr), ceil_div(geo.rqy, kTr), geo.qz), block(kTr, 8);
+  k_volume_yfast<<<grid, block, 0, s>>>(d_vol4, geo, d_vol4y);
   return cudaGetLastError();
 }
 

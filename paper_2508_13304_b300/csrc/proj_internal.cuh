@@ -30,7 +30,8 @@ struct InstTable {
   int view;
   int pose;
   int valid;
-  int pad[3];
+  int yfast;  // march the copy of the (mu, grad mu) volume whose rows run along y (detector u closer to y than x)
+  int pad[2];
 };
 static_assert(sizeof(InstTable) == 40 * 4, "InstTable layout");
 
@@ -48,7 +49,8 @@ static_assert(sizeof(PoseTable) % 8 == 0, "PoseTable layout");
 struct Geo {
   int nx, ny, nz;       // voxels
   int px, py, pz;       // sizes with a 1-voxel border (n + 2): the mu copy
-  int qx, qy, qz;       // pitches of the (mu, grad mu) volume (2-voxel border, >= n + 4)
+  int qx, qy, qz;       // pitches of the (mu, grad mu) volume (2-voxel border, >= n + 4), x fastest
+  int rqx, rqy;         // pitches of its copy with y fastest: element (x, y, z) at (z * rqx + x) * rqy + y
   float vx, vy, vz;     // voxel pitch, mm
   float hx, hy, hz;     // half extent of the open box (-1, n) in centred index units: (n+1)/2
   float gx, gy, gz;     // half extent of the gradient box (-2, n+1): (n+3)/2
@@ -71,6 +73,7 @@ struct BatchProblem {
   Geo geo;
   const InstTable* inst;
   const float4* vol4;
+  const float4* vol4y;  // y-fast copy, or null
   const float* ref;
   float* part;
   int n_tiles, tiles_u, loss, pad;
@@ -110,9 +113,12 @@ cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const f
                            cudaStream_t s);
 cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long* d_count, cudaStream_t s);
 // warp_width: rays per warp row of the 16x16 tile (2, 4, 8 or 16; other values use 4)
-cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4, int loss,
-                                const float* d_ref, float* d_proj, float* d_part, cudaStream_t s,
-                                int warp_width = 4);
+// d_vol4y: the y-fast copy (instances with yfast set march it), or null (all march d_vol4)
+cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
+                                const float4* d_vol4y, int loss, const float* d_ref, float* d_proj, float* d_part,
+                                cudaStream_t s, int warp_width = 4);
+// y-fast copy of the pitched (mu, grad mu) volume (tiled transpose of every z slice)
+cudaError_t launch_volume_yfast(const float4* d_vol4, Geo geo, float4* d_vol4y, cudaStream_t s);
 cudaError_t launch_forward_grad_reduce(const InstTable* d_inst, const PoseTable* d_ptab, int n_pose,
                                        const int* d_pose_ptr, const int* d_pose_idx, int n_tiles, Geo geo,
                                        int loss, const float* d_part, float* d_grad, float* d_loss,
@@ -146,6 +152,17 @@ inline void volume_pitches(int nx, int ny, int nz, int* qx, int* qy, int* qz) {
   *qx = x;
   *qy = y;
   *qz = nz + 4;
+}
+
+// The same rule for the copy whose rows run along y: row pitch (y) = 2 mod 8,
+// slice pitch = 4 mod 8 (float4 units).
+inline void volume_pitches_yfast(int nx, int ny, int* rqx, int* rqy) {
+  int y = ny + 4;
+  while (y % 8 != 2) ++y;
+  int x = nx + 4;
+  while ((x * y) % 8 != 4) ++x;
+  *rqx = x;
+  *rqy = y;
 }
 
 cudaError_t launch_fdk_filter(const FdkView* d_fv, int n_inst, Geo geo, float scale, const float* d_proj,

@@ -123,7 +123,10 @@ __global__ void k_setup(const float* __restrict__ pose, int n_pose, const double
   T.view = v;
   T.pose = p;
   T.valid = valid ? 1 : 0;
-  T.pad[0] = T.pad[1] = T.pad[2] = 0;
+  // neighbouring pixels along u are neighbouring rays: march the copy of the
+  // volume whose rows run along the index axis (x or y) closest to u
+  T.yfast = fabs(T.Uo[1] / vox[1]) > fabs(T.Uo[0] / vox[0]) ? 1 : 0;
+  T.pad[0] = T.pad[1] = 0;
   inst[i] = T;
 }
 

@@ -152,6 +152,7 @@ int proj_forward_pose_grad_static(const proj_geometry* geom, int n_pose, int n_i
   g.py = G.ny + 2;
   g.pz = G.nz + 2;
   volume_pitches(G.nx, G.ny, G.nz, &g.qx, &g.qy, &g.qz);
+  volume_pitches_yfast(G.nx, G.ny, &g.rqx, &g.rqy);  // no y-fast copy here: every instance marches vol4
   g.vx = (float)G.vx;
   g.vy = (float)G.vy;
   g.vz = (float)G.vz;
@@ -198,7 +199,7 @@ int proj_forward_pose_grad_static(const proj_geometry* geom, int n_pose, int n_i
   if (e != cudaSuccess) return fail(PROJ_E_CUDA, "table upload: %s", cudaGetErrorString(e));
   e = launch_volume_prep(d_mu, g, nullptr, vol4, s);
   if (e == cudaSuccess) e = launch_setup(d_pose, n_pose, views, d_iv, d_ip, n_inst, g, inst, ptab, status, s);
-  if (e == cudaSuccess) e = launch_forward_grad(inst, n_inst, g, vol4, loss, d_ref, nullptr, part, s);
+  if (e == cudaSuccess) e = launch_forward_grad(inst, n_inst, g, vol4, nullptr, loss, d_ref, nullptr, part, s);
   if (e == cudaSuccess)
     e = launch_forward_grad_reduce(inst, ptab, n_pose, d_ptr, d_idx, (int)n_tiles, g, loss, part, d_grad, d_loss, s);
   if (e != cudaSuccess) return fail(PROJ_E_CUDA, "launch: %s", cudaGetErrorString(e));
