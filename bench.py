@@ -289,6 +289,8 @@ def secondary(pb, torch, dev, w, mu_d, flush):
     Pt.set_volume(mu_d)
     tgt = Pt.forward(torch.from_numpy(w["pose_true"]).to(dev)).cpu().numpy()
     mu_h = mu_d.cpu().numpy()
+    # one untimed call first: the first registration in a process pays one-off set-up costs
+    reg.register(g, mu_h, tgt, starts[:2], max_iter=3, batched=True, true_pose=true)
     rb = reg.register(g, mu_h, tgt, starts, max_iter=150, batched=True, true_pose=true)
     t_plain, found, tried = 0.0, None, 0
     for c in range(len(starts)):
