@@ -63,8 +63,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other kernels' measurements")
-    ap.add_argument("--section", default=None, choices=["gemm"],
-                    help="run only one secondary measurement (gemm: the tensor-core GEMM shapes) and print it")
+    ap.add_argument("--section", default=None, choices=["gemm", "forward"],
+                    help="run only one secondary measurement and print it (gemm: the tensor-core GEMM shapes; "
+                         "forward: forward projection of the 128 registration instances)")
     ap.add_argument("--posenet-eval", action="store_true",
                     help="also train the pose-proposal network on 200k DRRs and compare proposal + registration "
                          "with 16-start registration (about 3 minutes)")
@@ -503,6 +504,21 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.section == "forward":
+        dev0 = torch.device("cuda", local)
+        fl = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev0)
+        w0 = workload(64)
+        g0 = w0["geom"]
+        iv0, ip0 = instance_maps(64, g0.n_views)
+        P0 = pb.Projector(g0, n_pose=64, inst_view=iv0, inst_pose=ip0, ops=pb.PROJ_OP_FORWARD)
+        pb.proj_enable_kernel_timing(P0.plan)
+        P0.set_volume(torch.from_numpy(w0["mu"]).to(dev0))
+        pose0 = torch.from_numpy(w0["poses"]).to(dev0)
+        out0 = torch.empty((P0.n_inst, g0.nv, g0.nu), device=dev0)
+        ms0 = _timed(lambda: pb.proj_forward(P0.plan, pose0, out0, P0.ws), P0.plan, pb, fl)
+        print(json.dumps({"section": "forward", "kernel": "k_forward", "kernel_ms": ms0,
+                          "config": "256^3, 128 view instances of 384^2"}), flush=True)
+        return
     if args.section == "gemm":
         dev0 = torch.device("cuda", local)
         fl = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev0)
