@@ -25,7 +25,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-GRAD_ANALYTIC, GRAD_EXACT = 0, 1
+GRAD_ANALYTIC, GRAD_EXACT, GRAD_VOXEL_CENTRE = 0, 1, 2
 W_NONE, W_FDK, W_FDK_CONST = 0, 1, 2
 
 

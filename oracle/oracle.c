@@ -21,7 +21,10 @@
  *    G_f evaluated at every integration point; grad mu = trilinear
  *    interpolation of the central-difference grid of the zero-padded volume,
  *    defined on the extended index grid [-1, n]^3 (mode OR_GRAD_ANALYTIC),
- *    or the exact derivative of mu~ (mode OR_GRAD_EXACT).  Each channel of
+ *    or the exact derivative of mu~ (mode OR_GRAD_EXACT); mode
+ *    OR_GRAD_VOXEL_CENTRE reads the paper's three-step recipe literally and
+ *    interpolates G = grad mu (x) (r - t) formed at voxel centres (reported,
+ *    not graded: it differs from the graded reading at second order).  Each channel of
  *    G_f is projected by the same ray march over the support of its own
  *    interpolant: the open box (-2, n+1)^3 for the analytic gradient grid
  *    (mu~ itself is zero outside (-1, n)^3), which keeps the gradient
@@ -56,7 +59,7 @@ typedef struct {
   double step;
 } or_geom;
 
-enum { OR_GRAD_ANALYTIC = 0, OR_GRAD_EXACT = 1 };
+enum { OR_GRAD_ANALYTIC = 0, OR_GRAD_EXACT = 1, OR_GRAD_VOXEL_CENTRE = 2 };
 enum { OR_W_NONE = 0, OR_W_FDK = 1, OR_W_FDK_CONST = 2 };
 
 void or_set_threads(int n) {
@@ -354,13 +357,34 @@ void or_forward_grad(const or_geom *g, const double *mu, const double *poses, in
       double s[3], e[3];
       pixel_ray(g, view, iu, iv, s, e);
       long klo, khi;
-      const int m = (mode == OR_GRAD_ANALYTIC) ? 2 : 1;
+      const int m = (mode == OR_GRAD_EXACT) ? 1 : 2;
       if (wn[p] != 0.0 && sample_range_m(g, R, t, s, e, m, &klo, &khi)) {
         for (long k = klo; k <= khi; ++k) {
           double r[3], f[3], gr[3];
           for (int a = 0; a < 3; ++a) r[a] = s[a] + (double)k * g->step * e[a];
           world_to_index(g, R, t, r, f);
           if (!inside_box_m(g, f, m)) continue;
+          if (mode == OR_GRAD_VOXEL_CENTRE) {
+            /* the paper's recipe read literally: G = grad mu (x) (r - t) formed at the
+             * voxel centres of the gradient grid, then interpolated like mu */
+            int i0 = (int)floor(f[0]), j0 = (int)floor(f[1]), k0 = (int)floor(f[2]);
+            double ax = f[0] - i0, ay = f[1] - j0, az = f[2] - k0;
+            for (int c = 0; c < 8; ++c) {
+              int di = c & 1, dj = (c >> 1) & 1, dk = (c >> 2) & 1;
+              double wgt = (di ? ax : 1.0 - ax) * (dj ? ay : 1.0 - ay) * (dk ? az : 1.0 - az);
+              double gg[3], rp[3], rc[3];
+              grad_grid(mu, g, i0 + di, j0 + dj, k0 + dk, gg);
+              rp[0] = g->off[0] + (i0 + di - 0.5 * (g->nx - 1)) * g->vx;
+              rp[1] = g->off[1] + (j0 + dj - 0.5 * (g->ny - 1)) * g->vy;
+              rp[2] = g->off[2] + (k0 + dk - 0.5 * (g->nz - 1)) * g->vz;
+              for (int a = 0; a < 3; ++a) rc[a] = R[3 * a + 0] * rp[0] + R[3 * a + 1] * rp[1] + R[3 * a + 2] * rp[2];
+              for (int a = 0; a < 3; ++a) {
+                for (int b = 0; b < 3; ++b) acc[4 * a + b] += wgt * gg[b] * rc[a];
+                acc[4 * a + 3] -= wgt * (R[3 * a + 0] * gg[0] + R[3 * a + 1] * gg[1] + R[3 * a + 2] * gg[2]);
+              }
+            }
+            continue;
+          }
           gradient_at(mu, g, f, mode, gr);
           for (int a = 0; a < 3; ++a) {
             for (int b = 0; b < 3; ++b) acc[4 * a + b] += gr[b] * (r[a] - t[a]);
