@@ -156,3 +156,19 @@ def test_binding_rejects_host_tensors():
     torch = pytest.importorskip("torch")
     with pytest.raises(TypeError):
         pb._ptr(torch.zeros(3), name="x")
+
+
+def test_c_program_uses_the_abi_without_python(tmp_path, L):
+    """The headers compile as C, a C program links libproj.so and gets the
+    documented host-side errors (gcc; no GPU, no Python binding)."""
+    import shutil
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    exe = str(tmp_path / "abi_host")
+    libdir = os.path.dirname(pb.LIB_PATH)
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c", "abi_host.c"), "-L", libdir, "-lproj",
+                    "-Wl,-rpath," + libdir, "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stdout + out.stderr
