@@ -63,9 +63,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other kernels' measurements")
-    ap.add_argument("--section", default=None, choices=["gemm", "forward"],
+    ap.add_argument("--section", default=None, choices=["gemm", "forward", "back"],
                     help="run only one secondary measurement and print it (gemm: the tensor-core GEMM shapes; "
-                         "forward: forward projection of the 128 registration instances)")
+                         "forward: forward projection of the 128 registration instances; back: FDK "
+                         "back-projection and its pose gradient, 360 views of 512^2 on 256^3)")
     ap.add_argument("--posenet-eval", action="store_true",
                     help="also train the pose-proposal network on 200k DRRs and compare proposal + registration "
                          "with 16-start registration (about 3 minutes)")
@@ -519,6 +520,28 @@ def main():
         print(json.dumps({"section": "forward", "kernel": "k_forward", "kernel_ms": ms0,
                           "config": "256^3, 128 view instances of 384^2"}), flush=True)
         return
+    if args.section == "back":
+        dev0 = torch.device("cuda", local)
+        fl = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev0)
+        gm = synth.Geometry(256, 256, 256, 0.8, 0.8, 0.8, 512, 512,
+                            synth.circular_views(360, synth.SAD, synth.SDD, 0.6, 0.6), 0.4)
+        rng0 = np.random.default_rng(1003)
+        motion = torch.from_numpy(synth.smooth_motion(rng0, 360, 2.0, 3.0).astype(np.float32)).to(dev0)
+        Pb = pb.Projector(gm, n_pose=360, inst_view=np.arange(360), inst_pose=np.arange(360),
+                          ops=pb.PROJ_OP_BACK | pb.PROJ_OP_BACK_GRAD)
+        pb.proj_enable_kernel_timing(Pb.plan)
+        gen = torch.Generator(device=dev0)
+        gen.manual_seed(1003)
+        img = torch.rand((360, 512, 512), device=dev0, generator=gen)
+        wvol = torch.randn((256, 256, 256), device=dev0, generator=gen)
+        volb = torch.empty((256, 256, 256), device=dev0)
+        gradb = torch.empty((360, 6), device=dev0)
+        ms_b = _timed(lambda: pb.proj_back(Pb.plan, img, motion, pb.PROJ_W_FDK, volb, Pb.ws), Pb.plan, pb, fl)
+        ms_g = _timed(lambda: pb.proj_back_pose_grad(Pb.plan, img, motion, pb.PROJ_W_FDK, wvol, gradb, Pb.ws),
+                      Pb.plan, pb, fl)
+        print(json.dumps({"section": "back", "k_back_ms": ms_b, "k_back_grad_ms": ms_g,
+                          "config": "256^3, 360 views of 512^2, FDK weight"}), flush=True)
+        return
     if args.section == "gemm":
         dev0 = torch.device("cuda", local)
         fl = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev0)
@@ -709,7 +732,7 @@ def main():
                         "losses copied out every step; step k+1's copies overlap step k's compute; no L2 flush "
                         "between steps (the two 285 MB (mu, grad mu) copies exceed L2)",
                 "serial_value": args.n_cand / (em_serial * 1e-3), "serial_ms_per_step": em_serial},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 5 * args.steps,   # per step: k_volume_prep, k_volume_yfast, k_setup, k_forward_grad, reduce
         "clocks": clk,
         "wall_s_timed_region": wall,
     }
