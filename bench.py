@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-cand", type=int, default=64)
-    ap.add_argument("--cpu-sample", type=int, default=2, help="candidates timed on the CPU oracle")
+    ap.add_argument("--cpu-sample", type=int, default=8,
+                    help="candidates timed on the CPU oracle (about 1.5 s of 16-core FP64 work each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other kernels' measurements")
