@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other kernels' measurements")
-    ap.add_argument("--section", default=None, choices=["gemm", "forward", "back"],
+    ap.add_argument("--section", default=None, choices=["gemm", "forward", "back", "accuracy"],
                     help="run only one secondary measurement and print it (gemm: the tensor-core GEMM shapes; "
                          "forward: forward projection of the 128 registration instances; back: FDK "
                          "back-projection and its pose gradient, 360 views of 512^2 on 256^3)")
@@ -321,6 +321,7 @@ def secondary(pb, torch, dev, w, mu_d, flush):
                                   "ms_per_launch": {"%dx%d" % (k, 32 // k): v for k, v in times.items()},
                                   "chosen": "%dx%d" % (width, 32 // width)}
     del Pa
+    out["gradient_accuracy"] = gradient_accuracy(pb, torch, dev, mu_d)
     out["registration_cuda_graph"] = graph_timing(pb, torch, g, mu_h, tgt, starts)
     out["posenet"] = posenet_measure(pb, torch, dev, flush, g, mu_d, load_peaks())
     out["uneven_batch_small"] = uneven_batch(pb, torch, dev, flush, with_large=False)
@@ -394,6 +395,93 @@ def uneven_batch(pb, torch, dev, flush, with_large):
             "grad_rel_diff_batched_vs_separate": diff,
             "what": "batched = set-ups, one persistent work-queue launch over all problems' ray tiles, "
                     "reductions; separate = proj_forward_pose_grad per problem, back to back"}
+
+
+def gradient_accuracy(pb, torch, dev, mu_d, n_motion=128, n_views=8):
+    """The paper's accuracy protocol (Sec. II-D.1 / III-A) on the GPU: 8 views
+    over 0-90 deg, 128 random motions per view (translations N(0, 20 mm),
+    rotations N(0, 10 deg)), L2 loss against the projection at zero motion;
+    cosine similarity per motion between the fused analytic pose gradient and
+    a central finite difference of the same loss (projections by the forward
+    projector, loss summed in FP64)."""
+    import math
+    g0 = workload(1)["geom"]
+    views = synth.circular_views(n_views, synth.SAD, synth.SDD, 0.8, 0.8,
+                                 angles=np.linspace(0.0, math.pi / 2, n_views))
+    g = synth.Geometry(g0.nx, g0.ny, g0.nz, g0.vx, g0.vy, g0.vz, g0.nu, g0.nv, views, g0.step)
+    rng = np.random.default_rng(1009)
+    n = n_motion * n_views
+    pose = np.zeros((n, 6), np.float32)
+    pose[:, :3] = rng.normal(0.0, 20.0, (n, 3))
+    pose[:, 3:] = np.deg2rad(rng.normal(0.0, 10.0, (n, 3)))
+    iv = np.repeat(np.arange(n_views), n_motion).astype(np.int32)
+    ip = np.arange(n, dtype=np.int32)
+    P = pb.Projector(g, n_pose=n, inst_view=iv, inst_pose=ip, ops=pb.PROJ_OP_FORWARD | pb.PROJ_OP_FORWARD_GRAD)
+    P.set_volume(mu_d)
+    P0 = pb.Projector(g, n_pose=1, inst_view=np.arange(n_views), inst_pose=np.zeros(n_views, np.int32),
+                      ops=pb.PROJ_OP_FORWARD)
+    P0.set_volume(mu_d)
+    target = P0.forward(torch.zeros((1, 6), device=dev)).contiguous()          # [views][nv][nu]
+    tgt_inst = target[torch.from_numpy(iv).long().to(dev)]
+    pose_d = torch.from_numpy(pose).to(dev)
+    grad, _ = P.forward_pose_grad(pose_d, pb.PROJ_LOSS_L2, target)
+
+    def losses(pz):
+        d = (P.forward(pz) - tgt_inst).double()
+        return (d * d).sum(dim=(1, 2))
+
+    steps = [0.05] * 3 + [5e-4] * 3
+    fd = torch.zeros((n, 6), dtype=torch.float64, device=dev)
+    for j in range(6):
+        e = torch.zeros((1, 6), device=dev)
+        e[0, j] = steps[j]
+        fd[:, j] = (losses((pose_d + e).contiguous()) - losses((pose_d - e).contiguous())) / (2 * steps[j])
+    ga = grad.double()
+    cos = (ga * fd).sum(1) / (ga.norm(dim=1) * fd.norm(dim=1)).clamp_min(1e-300)
+    valid = fd.norm(dim=1) > 0
+    c = cos[valid].cpu().numpy()
+    return {"config": "256^3 registration phantom, %d views over 0-90 deg of 384^2, %d motions (t N(0, 20 mm), "
+                      "rot N(0, 10 deg)), L2 loss vs zero motion; FD steps 0.05 mm / 5e-4 rad" % (n_views, n),
+            "motions": int(valid.sum().item()), "mean_cosine": float(c.mean()), "p5_cosine": float(np.percentile(c, 5)),
+            "min_cosine": float(c.min()), "paper_rd_mean": 0.9952,
+            "back": back_gradient_accuracy(pb, torch, dev, mu_d, g, target, n_motion=n_motion // 4)}
+
+
+def back_gradient_accuracy(pb, torch, dev, mu_d, g, target, n_motion=32):
+    """The back-projection half of the accuracy protocol: per (view, motion)
+    the L2 loss between the voxel-driven back-projection of that view's
+    zero-motion projection at the moved pose and the volume, its analytic pose
+    gradient (back-projection pose gradient with dL/dmu = 2 (b - mu)) and a
+    central finite difference (losses summed in FP64)."""
+    n_views = g.n_views
+    rng = np.random.default_rng(1010)
+    mu64 = mu_d.double()
+    steps = [0.05] * 3 + [5e-4] * 3
+    cos = []
+    for v in range(n_views):
+        P = pb.Projector(g, n_pose=1, inst_view=np.array([v], np.int32), inst_pose=np.zeros(1, np.int32),
+                         ops=pb.PROJ_OP_BACK | pb.PROJ_OP_BACK_GRAD)
+        img = target[v:v + 1].contiguous()
+        for _ in range(n_motion):
+            th = np.zeros((1, 6), np.float32)
+            th[0, :3] = rng.normal(0.0, 20.0, 3)
+            th[0, 3:] = np.deg2rad(rng.normal(0.0, 10.0, 3))
+            pose = torch.from_numpy(th).to(dev)
+            b = P.back(img, pose)
+            ga = P.back_pose_grad(img, pose, (2.0 * (b.double() - mu64)).float())[0].double()
+            fd = torch.zeros(6, dtype=torch.float64, device=dev)
+            for j in range(6):
+                e = torch.zeros((1, 6), device=dev)
+                e[0, j] = steps[j]
+                lp = ((P.back(img, (pose + e).contiguous()).double() - mu64) ** 2).sum()
+                lm = ((P.back(img, (pose - e).contiguous()).double() - mu64) ** 2).sum()
+                fd[j] = (lp - lm) / (2 * steps[j])
+            cos.append(float((ga @ fd) / (ga.norm() * fd.norm())))
+    c = np.array(cos)
+    return {"config": "%d views over 0-90 deg, %d motions, plain back-projection, L2 loss vs the volume" %
+                      (n_views, len(c)),
+            "mean_cosine": float(c.mean()), "p5_cosine": float(np.percentile(c, 5)), "min_cosine": float(c.min()),
+            "paper_vd_mean": 0.9984, "paper_vd_p95": 0.9938}
 
 
 def graph_timing(pb, torch, g, mu_h, tgt, starts):
@@ -520,6 +608,11 @@ def main():
         ms0 = _timed(lambda: pb.proj_forward(P0.plan, pose0, out0, P0.ws), P0.plan, pb, fl)
         print(json.dumps({"section": "forward", "kernel": "k_forward", "kernel_ms": ms0,
                           "config": "256^3, 128 view instances of 384^2"}), flush=True)
+        return
+    if args.section == "accuracy":
+        dev0 = torch.device("cuda", local)
+        mu0 = torch.from_numpy(workload(1)["mu"]).to(dev0)
+        print(json.dumps({"section": "accuracy", **gradient_accuracy(pb, torch, dev0, mu0)}), flush=True)
         return
     if args.section == "back":
         dev0 = torch.device("cuda", local)
