@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other kernels' measurements")
-    ap.add_argument("--section", default=None, choices=["gemm", "forward", "back", "accuracy"],
+    ap.add_argument("--section", default=None, choices=["gemm", "forward", "back", "accuracy", "tables"],
                     help="run only one secondary measurement and print it (gemm: the tensor-core GEMM shapes; "
                          "forward: forward projection of the 128 registration instances; back: FDK "
                          "back-projection and its pose gradient, 360 views of 512^2 on 256^3)")
@@ -322,6 +322,7 @@ def secondary(pb, torch, dev, w, mu_d, flush):
                                   "chosen": "%dx%d" % (width, 32 // width)}
     del Pa
     out["gradient_accuracy"] = gradient_accuracy(pb, torch, dev, mu_d)
+    out["paper_tables"] = paper_tables(pb, torch, dev, flush)
     out["registration_cuda_graph"] = graph_timing(pb, torch, g, mu_h, tgt, starts)
     out["posenet"] = posenet_measure(pb, torch, dev, flush, g, mu_d, load_peaks())
     out["uneven_batch_small"] = uneven_batch(pb, torch, dev, flush, with_large=False)
@@ -484,6 +485,75 @@ def back_gradient_accuracy(pb, torch, dev, mu_d, g, target, n_motion=32):
             "paper_vd_mean": 0.9984, "paper_vd_p95": 0.9938}
 
 
+PAPER_TABLES = (  # volume, detector, paper Table III (RD, 100 iterations) s, Table IV (VD, 256 views, 1 iteration) s
+    (128, 192, 1.25, 0.17), (256, 384, 2.44, 1.21), (384, 576, 6.24, 3.99), (512, 768, 12.70, 9.50))
+
+
+def paper_tables(pb, torch, dev, flush):
+    """The paper's timing tables at their sizes, each time covering the whole
+    step as the paper's do (loss, pose gradient, one gradient-descent update):
+    Table III = 100 iterations of the L2 pose gradient of one view's
+    projection; Table IV = one iteration of the L2 image loss of the
+    back-projection of 256 views and its per-view pose gradient.  Volumes
+    span 204.8 mm, the detector covers them (SAD 800 / SDD 1200 mm); the
+    volume values are uniform noise (they do not change the work)."""
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1011)
+    rows = []
+    for n, d, t3_paper, t4_paper in PAPER_TABLES:
+        vox = 204.8 / n
+        pix = 1.1 * 204.8 * math.sqrt(2.0) * (synth.SDD / synth.SAD) / d
+        mu = torch.rand((n, n, n), device=dev, generator=gen)
+        # Table III: one view, 100 iterations of loss + pose gradient + update
+        g1 = synth.Geometry(n, n, n, vox, vox, vox, d, d, synth.circular_views(1, synth.SAD, synth.SDD, pix, pix),
+                            0.5 * vox)
+        P1 = pb.Projector(g1, n_pose=1, inst_view=np.zeros(1, np.int32), inst_pose=np.zeros(1, np.int32),
+                          ops=pb.PROJ_OP_FORWARD | pb.PROJ_OP_FORWARD_GRAD)
+        P1.set_volume(mu)
+        target = P1.forward(torch.zeros((1, 6), device=dev)).contiguous()
+        pose = torch.tensor([[2.0, -1.0, 1.5, 0.02, -0.03, 0.01]], device=dev)
+        gbuf = torch.empty((1, 6), device=dev)
+        lbuf = torch.empty(1, device=dev)
+        lr = torch.tensor([[0.1, 0.1, 0.1, 1e-3, 1e-3, 1e-3]], device=dev)
+
+        def t3():
+            for _ in range(100):
+                pb.proj_forward_pose_grad(P1.plan, pose, pb.PROJ_LOSS_L2, target, gbuf, lbuf, None, P1.ws)
+                pose.sub_(lr * gbuf.sign())
+
+        ms3 = _event_ms(torch, t3, flush, reps=2)
+        ws3 = pb.proj_workspace_size(P1.plan)
+        del P1
+        # Table IV: 256 views, one iteration of back-projection, image loss, pose gradient, update
+        g4 = synth.Geometry(n, n, n, vox, vox, vox, d, d, synth.circular_views(256, synth.SAD, synth.SDD, pix, pix),
+                            0.5 * vox)
+        P4 = pb.Projector(g4, n_pose=256, inst_view=np.arange(256), inst_pose=np.arange(256),
+                          ops=pb.PROJ_OP_BACK | pb.PROJ_OP_BACK_GRAD)
+        img = torch.rand((256, d, d), device=dev, generator=gen)
+        pose4 = torch.zeros((256, 6), device=dev)
+        vol = torch.empty((n, n, n), device=dev)
+        g4buf = torch.empty((256, 6), device=dev)
+
+        def t4():
+            pb.proj_back(P4.plan, img, pose4, pb.PROJ_W_NONE, vol, P4.ws)
+            resid = 2.0 * (vol - mu)                 # d/dvol of the L2 image loss
+            pb.proj_back_pose_grad(P4.plan, img, pose4, pb.PROJ_W_NONE, resid, g4buf, P4.ws)
+            pose4.sub_(1e-6 * g4buf)
+
+        ms4 = _event_ms(torch, t4, flush, reps=2)
+        ws4 = pb.proj_workspace_size(P4.plan)
+        del P4, img, vol, mu
+        torch.cuda.empty_cache()
+        rows.append({"volume": n, "detector": d,
+                     "table3_100_iter_s": ms3 * 1e-3, "table3_paper_s": t3_paper, "table3_ratio": t3_paper / (ms3 * 1e-3),
+                     "table3_workspace_gb": ws3 / 1e9,
+                     "table4_iter_s": ms4 * 1e-3, "table4_paper_s": t4_paper, "table4_ratio": t4_paper / (ms4 * 1e-3),
+                     "table4_workspace_gb": ws4 / 1e9})
+    return {"rows": rows, "note": "paper: RTX 4090, whole autograd steps in PyTorch with the authors' kernels and "
+                                  "the exact path-length projector; ratios are context, not a like-for-like "
+                                  "comparison"}
+
+
 def graph_timing(pb, torch, g, mu_h, tgt, starts):
     """Registration iterations eager (one host check per iteration) vs
     replayed CUDA graphs of 10 iterations; every candidate kept running."""
@@ -608,6 +678,11 @@ def main():
         ms0 = _timed(lambda: pb.proj_forward(P0.plan, pose0, out0, P0.ws), P0.plan, pb, fl)
         print(json.dumps({"section": "forward", "kernel": "k_forward", "kernel_ms": ms0,
                           "config": "256^3, 128 view instances of 384^2"}), flush=True)
+        return
+    if args.section == "tables":
+        dev0 = torch.device("cuda", local)
+        fl = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev0)
+        print(json.dumps({"section": "tables", **paper_tables(pb, torch, dev0, fl)}), flush=True)
         return
     if args.section == "accuracy":
         dev0 = torch.device("cuda", local)
