@@ -52,24 +52,32 @@ def paper_step_sizes():
 
 
 def register(geom, mu, target, init_poses, max_iter=200, lr=None, ncc_stop=0.999, dloss_stop=1e-5,
-             batched=True, device="cuda", true_pose=None, tol=(0.5, 0.5), graph_steps=0):
+             batched=True, device="cuda", true_pose=None, tol=(0.5, 0.5), graph_steps=0, inst_view=None):
     """Register every start pose in init_poses [n][6] to the target images
-    ([n_views][nv][nu]).  Returns dict(poses, ncc, iters, seconds, and, when
-    true_pose is given, first_hit_s: wall time at which any candidate was
-    first seen within tol = (mm, deg) of it, or None).  graph_steps > 0
-    replays CUDA graphs of that many iterations (checked once per replay)."""
+    ([n_views][nv][nu]).  By default every pose sees every view; with
+    inst_view ([n] view indices) pose i sees only view inst_view[i], i.e. n
+    independent single-view registrations advancing together (batched).
+    Returns dict(poses, ncc, iters, seconds, and, when true_pose is given,
+    first_hit_s: wall time at which any candidate was first seen within
+    tol = (mm, deg) of it, or None; true_pose may be [6] or [n][6]).
+    graph_steps > 0 replays CUDA graphs of that many iterations (checked
+    once per replay)."""
     lr = paper_step_sizes() if lr is None else lr
     init = torch.as_tensor(np.asarray(init_poses, dtype=np.float32), device=device)
     n = init.shape[0]
     nv = geom.views.shape[0]
     mu_d = torch.as_tensor(np.asarray(mu, dtype=np.float32), device=device).contiguous()
     tgt = torch.as_tensor(np.asarray(target, dtype=np.float32), device=device).contiguous()
-    groups = [list(range(n))] if batched else [[c] for c in range(n)]
+    groups = [list(range(n))] if (batched or inst_view is not None) else [[c] for c in range(n)]
     projs = []
     for grp in groups:
         k = len(grp)
-        P = Projector(geom, n_pose=k, inst_view=np.tile(np.arange(nv), k),
-                      inst_pose=np.repeat(np.arange(k), nv), ops=PROJ_OP_FORWARD_GRAD, device=device)
+        if inst_view is not None:
+            P = Projector(geom, n_pose=k, inst_view=np.asarray(inst_view, dtype=np.int32),
+                          inst_pose=np.arange(k, dtype=np.int32), ops=PROJ_OP_FORWARD_GRAD, device=device)
+        else:
+            P = Projector(geom, n_pose=k, inst_view=np.tile(np.arange(nv), k),
+                          inst_pose=np.repeat(np.arange(k), nv), ops=PROJ_OP_FORWARD_GRAD, device=device)
         proj_set_volume(P.plan, mu_d, P.ws)
         projs.append(P)
     pose = init.clone()
@@ -82,7 +90,7 @@ def register(geom, mu, target, init_poses, max_iter=200, lr=None, ncc_stop=0.999
     hit_any = torch.zeros((), dtype=torch.bool, device=device)
     views = [(pose[grp[0]:grp[-1] + 1], grad[grp[0]:grp[-1] + 1], loss[grp[0]:grp[-1] + 1]) for grp in groups]
     if true_pose is not None:
-        tp = torch.as_tensor(np.asarray(true_pose, dtype=np.float32), device=device).reshape(1, 6)
+        tp = torch.as_tensor(np.asarray(true_pose, dtype=np.float32), device=device).reshape(-1, 6)
 
     def iteration():
         for (pg, g_out, l_out), P in zip(views, projs):
