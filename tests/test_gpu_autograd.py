@@ -128,3 +128,24 @@ def test_batched_registration_converges():
     assert np.all(out_b["ncc"] > 0.99), out_b["ncc"]
     assert np.median(te) < 0.5 and np.median(re) < 0.5, (te, re, out_b["ncc"])
     np.testing.assert_allclose(out_p["poses"], out_b["poses"][:2], atol=1e-4)
+
+
+def test_independent_single_view_registrations_match_separate_runs():
+    """register(inst_view=...) advances independent single-view problems
+    (pose i against view i) in one launch; each follows the trajectory it
+    has when registered alone."""
+    rng = np.random.default_rng(6)
+    views = synth.circular_views(3, 300.0, 450.0, 1.2, 1.2, angles=[0.2, 1.3, 2.5])
+    g = synth.Geometry(40, 40, 40, 1.0, 1.0, 1.0, 48, 48, views, 0.5)
+    ell = synth.random_ellipsoids(rng, 8, 8.0, (3.0, 8.0), (0.01, 0.03))
+    mu = synth.voxelise(g, ell, supersample=2).astype(np.float32)
+    target = oracle.forward(g, mu.astype(np.float64), np.zeros(6), np.arange(3), np.zeros(3, dtype=np.int32))
+    starts = np.concatenate([rng.uniform(-2, 2, (3, 3)), np.deg2rad(rng.uniform(-2, 2, (3, 3)))],
+                            axis=1).astype(np.float32)
+    kw = dict(max_iter=40, lr=[0.5] * 3 + [np.deg2rad(0.5)] * 3, ncc_stop=1.0, dloss_stop=-1.0)
+    together = reg.register(g, mu, target, starts, inst_view=[0, 1, 2], **kw)
+    for i in range(3):
+        alone = reg.register(g, mu, target, starts[i:i + 1], inst_view=[i], **kw)
+        np.testing.assert_array_equal(together["poses"][i], alone["poses"][0])
+        assert together["ncc"][i] == alone["ncc"][0]
+    assert np.all(together["ncc"] > 0.9)
