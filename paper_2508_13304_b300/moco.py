@@ -9,6 +9,13 @@ dS/dmu (proj_sharpness), the per-view pose gradient (proj_back_pose_grad
 with the FDK weight derivative), and an Adam step on the [n_views, 6] poses.
 The paper uses gradient entropy as the sharpness criterion; this build uses
 the negative variance of the gradient magnitude.
+
+With spline_nodes = K the per-view poses are not free: the motion is a
+clamped cubic B-spline over the view index with K coefficients per
+parameter (the paper's comparison optimiser uses a 24-node spline), minus
+its mean over the views (a global rigid offset does not change sharpness),
+so theta = A c with A = (I - 11^T / n) B and dS/dc = A^T dS/dtheta, one
+small matrix product on top of the library's per-view pose gradients.
 """
 from __future__ import annotations
 
@@ -22,18 +29,39 @@ from . import PROJ_OP_BACK, PROJ_OP_BACK_GRAD, PROJ_OP_SHARPNESS, PROJ_W_FDK, Pr
 from .registration import Adam
 
 
+def spline_basis(n_views, n_nodes):
+    """[n_views][n_nodes] design matrix of a clamped cubic B-spline with
+    n_nodes coefficients on [0, 1], evaluated at the views (k / (n - 1))."""
+    from scipy.interpolate import BSpline
+    deg = 3
+    inner = np.linspace(0.0, 1.0, n_nodes - deg + 1)
+    knots = np.concatenate([[0.0] * deg, inner, [1.0] * deg])
+    x = np.linspace(0.0, 1.0, n_views)
+    return BSpline.design_matrix(x, knots, deg).toarray()
+
+
 def moco_fdk(geom, proj, n_iter=80, lr=(0.5, 0.5, 0.5, math.radians(0.5), math.radians(0.5), math.radians(0.5)),
-             init=None, device="cuda"):
+             init=None, device="cuda", spline_nodes=None):
     """Returns dict(poses [n_views][6], sharpness history, seconds, fdk0 (the
-    uncompensated reconstruction), fdk (the final one))."""
+    uncompensated reconstruction), fdk (the final one)).  spline_nodes: if
+    given, optimise that many centred cubic B-spline coefficients per pose
+    parameter instead of free per-view poses (init is then ignored)."""
     n = geom.views.shape[0]
     P = Projector(geom, n_pose=n, inst_view=np.arange(n), inst_pose=np.arange(n),
                   ops=PROJ_OP_BACK | PROJ_OP_BACK_GRAD | PROJ_OP_SHARPNESS, device=device)
     q = P.fdk_filter(torch.as_tensor(np.asarray(proj, dtype=np.float32), device=device), math.pi / n)
-    pose = torch.zeros((n, 6), device=device) if init is None else \
-        torch.as_tensor(np.asarray(init, dtype=np.float32), device=device).clone()
-    opt = Adam(n, lr, device=device)
-    active = torch.ones(n, dtype=torch.bool, device=device)
+    if spline_nodes:
+        B = spline_basis(n, int(spline_nodes))
+        A = torch.as_tensor(B - B.mean(axis=0, keepdims=True), dtype=torch.float32, device=device)  # centred
+        coef = torch.zeros((A.shape[1], 6), device=device)
+        opt = Adam(A.shape[1], lr, device=device)
+        active = torch.ones(A.shape[1], dtype=torch.bool, device=device)
+        pose = (A @ coef).contiguous()
+    else:
+        pose = torch.zeros((n, 6), device=device) if init is None else \
+            torch.as_tensor(np.asarray(init, dtype=np.float32), device=device).clone()
+        opt = Adam(n, lr, device=device)
+        active = torch.ones(n, dtype=torch.bool, device=device)
     hist = []
     fdk0 = None
     torch.cuda.synchronize()
@@ -45,7 +73,11 @@ def moco_fdk(geom, proj, n_iter=80, lr=(0.5, 0.5, 0.5, math.radians(0.5), math.r
         loss, dvol = P.sharpness(vol)
         grad = P.back_pose_grad(q, pose, dvol, PROJ_W_FDK)
         hist.append(loss)
-        opt.step(pose, grad, active)
+        if spline_nodes:
+            opt.step(coef, (A.t() @ grad).contiguous(), active)
+            pose = (A @ coef).contiguous()
+        else:
+            opt.step(pose, grad, active)
     vol = P.back(q, pose, PROJ_W_FDK)
     loss = P.sharpness(vol, want_grad=False)
     hist.append(loss)

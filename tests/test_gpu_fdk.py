@@ -83,3 +83,31 @@ def test_motion_compensated_fdk_loop():
                         lr=[0.02] * 3 + [math.radians(0.02)] * 3)
     s = out["sharpness"]
     assert s[-1] < s[0], s
+
+
+def test_spline_motion_recovers_the_reconstruction():
+    """Motion-compensated FDK with the motion as a centred 24-node cubic
+    B-spline over the views (translations only): on the 60-view phantom of
+    the test above, the reconstruction's distance to the motion-free one
+    falls by more than half (to the level that the true motion gives), and
+    the translation error drops."""
+    rng = np.random.default_rng(63)
+    n_views = 60
+    views = synth.circular_views(n_views, 300.0, 450.0, 1.6, 1.6)
+    g = synth.Geometry(48, 48, 48, 1.5, 1.5, 1.5, 80, 80, views, 0.75)
+    ell = synth.random_ellipsoids(rng, 10, 12.0, (3.0, 10.0), (0.01, 0.03))
+    mu = synth.voxelise(g, ell, supersample=2).astype(np.float32)
+    motion = synth.smooth_motion(rng, n_views, 2.0, 3.0).astype(np.float32)
+    motion -= motion.mean(axis=0)
+    F = pb.Projector(g, n_pose=n_views, inst_view=np.arange(n_views), inst_pose=np.arange(n_views),
+                     ops=pb.PROJ_OP_FORWARD | pb.PROJ_OP_BACK)
+    F.set_volume(mu)
+    proj = F.forward(motion)
+    zero = np.zeros((n_views, 6), np.float32)
+    ref = F.back(F.fdk_filter(F.forward(zero), math.pi / n_views), zero, pb.PROJ_W_FDK).cpu().numpy()
+    out = moco.moco_fdk(g, proj.cpu().numpy(), n_iter=80, lr=[0.05] * 3 + [0.0] * 3, spline_nodes=24)
+    e0, e1 = rel(out["fdk0"], ref), rel(out["fdk"], ref)
+    assert e1 < 0.5 * e0, (e0, e1)
+    d = out["poses"] - motion
+    assert np.sqrt((d[:, :3] ** 2).mean()) < np.sqrt((motion[:, :3] ** 2).mean())
+    assert out["sharpness"][-1] < out["sharpness"][0]
