@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other kernels' measurements")
     ap.add_argument("--section", default=None,
-                    choices=["gemm", "forward", "back", "accuracy", "tables", "registration500"],
+                    choices=["gemm", "forward", "back", "accuracy", "tables", "registration500", "moco"],
                     help="run only one secondary measurement and print it (gemm: the tensor-core GEMM shapes; "
                          "forward: forward projection of the 128 registration instances; back: FDK "
                          "back-projection and its pose gradient, 360 views of 512^2 on 256^3)")
@@ -322,6 +322,7 @@ def secondary(pb, torch, dev, w, mu_d, flush):
                                   "ms_per_launch": {"%dx%d" % (k, 32 // k): v for k, v in times.items()},
                                   "chosen": "%dx%d" % (width, 32 // width)}
     del Pa
+    out["moco_quality"] = moco_quality(pb, torch, dev)
     out["gradient_accuracy"] = gradient_accuracy(pb, torch, dev, mu_d)
     out["paper_tables"] = paper_tables(pb, torch, dev, flush)
     out["registration_cuda_graph"] = graph_timing(pb, torch, g, mu_h, tgt, starts)
@@ -600,6 +601,43 @@ def registration_500(pb, torch, dev, n_prob=500, max_iter=200):
             "paper": "RTX 4090, CQ500 head: 18.45 min for 500 views (2.21 s each), 343 successes"}
 
 
+def moco_quality(pb, torch, dev):
+    """Motion-compensated FDK on the 360-view workload (256^3 at 0.8 mm,
+    512^2 at 0.6 mm, smooth per-view motion rot <= 2 deg, trans <= 3 mm):
+    projections rendered at the moving poses, then 80 iterations of the
+    sharpness loss with a centred 24-node spline motion model
+    (translations).  Errors are relative L2 distances to the FDK of
+    motion-free projections."""
+    from paper_2508_13304_b300 import moco
+    w = synth.workload_moco()
+    g = w["geom"]
+    n = g.n_views
+    motion = w["poses"].astype(np.float32)
+    motion -= motion.mean(axis=0)
+    F = pb.Projector(g, n_pose=n, inst_view=np.arange(n), inst_pose=np.arange(n),
+                     ops=pb.PROJ_OP_FORWARD | pb.PROJ_OP_BACK)
+    F.set_volume(torch.from_numpy(w["mu"].astype(np.float32)).to(dev))
+    proj = F.forward(motion)
+    zero = np.zeros((n, 6), np.float32)
+    ref = F.back(F.fdk_filter(F.forward(zero), math.pi / n), zero, pb.PROJ_W_FDK)
+    best = F.back(F.fdk_filter(proj, math.pi / n), motion, pb.PROJ_W_FDK)
+
+    def rel(a):
+        return float((a - ref).norm() / ref.norm())
+
+    out = moco.moco_fdk(g, proj.cpu().numpy(), n_iter=80, lr=[0.05] * 3 + [0.0] * 3, spline_nodes=24,
+                        device=dev)
+    d = out["poses"] - motion
+    return {"config": "256^3, 360 views of 512^2, 24-node spline (translations), 80 iterations",
+            "recon_err_uncompensated": rel(torch.from_numpy(out["fdk0"]).to(dev)),
+            "recon_err_compensated": rel(torch.from_numpy(out["fdk"]).to(dev)),
+            "recon_err_true_motion": rel(best),
+            "trans_rms_mm_before_after": [float(np.sqrt((motion[:, :3] ** 2).mean())),
+                                          float(np.sqrt((d[:, :3] ** 2).mean()))],
+            "sharpness_before_after": [float(out["sharpness"][0]), float(out["sharpness"][-1])],
+            "seconds": out["seconds"]}
+
+
 def graph_timing(pb, torch, g, mu_h, tgt, starts):
     """Registration iterations eager (one host check per iteration) vs
     replayed CUDA graphs of 10 iterations; every candidate kept running."""
@@ -724,6 +762,9 @@ def main():
         ms0 = _timed(lambda: pb.proj_forward(P0.plan, pose0, out0, P0.ws), P0.plan, pb, fl)
         print(json.dumps({"section": "forward", "kernel": "k_forward", "kernel_ms": ms0,
                           "config": "256^3, 128 view instances of 384^2"}), flush=True)
+        return
+    if args.section == "moco":
+        print(json.dumps({"section": "moco", **moco_quality(pb, torch, torch.device("cuda", local))}), flush=True)
         return
     if args.section == "registration500":
         print(json.dumps({"section": "registration500", **registration_500(pb, torch, torch.device("cuda", local))}),
