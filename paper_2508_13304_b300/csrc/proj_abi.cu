@@ -617,6 +617,7 @@ struct proj_batch_s {
   std::vector<size_t> ws_bytes;
   BatchProblem* d_probs = nullptr;
   unsigned long long* d_counter = nullptr;
+  int loss_all = -1;  // the loss every problem shares, or -1
 };
 
 extern "C" {
@@ -687,9 +688,12 @@ int proj_batch_create(int n, const proj_plan* plans, const int* loss, const floa
     b->ws_bytes.push_back(ws_bytes[i]);
   }
   b->n_items = items;
+  b->loss_all = loss[0];
+  for (int i = 1; i < n; ++i)
+    if (loss[i] != loss[0]) b->loss_all = -1;
   int n_sm = 148;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  const long long cap = (long long)n_sm * forward_grad_batch_blocks_per_sm();
+  const long long cap = (long long)n_sm * forward_grad_batch_blocks_per_sm(b->loss_all);
   b->n_blocks = (int)(items < cap ? items : cap);
   e = cudaMalloc(&b->d_probs, sizeof(BatchProblem) * n);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
@@ -723,7 +727,7 @@ int proj_batch_run(proj_batch b, proj_stream stream) {
     if (rc) return rc;
     if ((rc = setup(b->plans[k], b->pose[k], w[k], s))) return rc;
   }
-  e = launch_forward_grad_batch(b->d_probs, b->n, b->n_items, b->d_counter, b->n_blocks, s);
+  e = launch_forward_grad_batch(b->d_probs, b->n, b->n_items, b->d_counter, b->n_blocks, b->loss_all, s);
   if (e != cudaSuccess) return cuda_fail(e, "batched pose-gradient launch");
   for (int k = 0; k < b->n; ++k) {
     const proj_plan p = b->plans[k];

@@ -386,6 +386,9 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
 // chose (longest tiles first), so small problems fill the tail of the large
 // ones.  The counter is the only shared state; no block waits for another.
 
+// LOSS >= 0: every problem of the batch has that loss (2 march variants, the two
+// volume copies); LOSS < 0: each problem's own loss (6 variants, more registers).
+template <int LOSS>
 __global__ void __launch_bounds__(kMarchThreads, 4)
     k_forward_grad_batch(const BatchProblem* __restrict__ probs, int n_probs, long long n_items,
                          unsigned long long* __restrict__ counter) {
@@ -403,6 +406,13 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
     const int local = (int)(item - B.item_begin);
     const int n = local / B.n_tiles, tile = local % B.n_tiles;
     const bool yf = B.vol4y && B.inst[n].yfast;
+    if constexpr (LOSS >= 0) {
+      if (yf)
+        march_tile<LOSS, 4, 1>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4y, B.ref, nullptr, B.part, red);
+      else
+        march_tile<LOSS, 4, 0>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr, B.part, red);
+      continue;
+    }
     switch (B.loss * 2 + (yf ? 1 : 0)) {
       case PROJ_LOSS_RESIDUAL * 2:
         march_tile<PROJ_LOSS_RESIDUAL, 4, 0>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr,
@@ -706,16 +716,44 @@ cudaError_t launch_volume_yfast(const float4* d_vol4, Geo geo, float4* d_vol4y, 
 }
 
 cudaError_t launch_forward_grad_batch(const BatchProblem* d_probs, int n_probs, long long n_items,
-                                      unsigned long long* d_counter, int n_blocks, cudaStream_t s) {
+                                      unsigned long long* d_counter, int n_blocks, int loss_all, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_forward_grad_batch<<<n_blocks, kMarchThreads, 0, s>>>(d_probs, n_probs, n_items, d_counter);
+  switch (loss_all) {
+    case PROJ_LOSS_RESIDUAL:
+      k_forward_grad_batch<PROJ_LOSS_RESIDUAL><<<n_blocks, kMarchThreads, 0, s>>>(d_probs, n_probs, n_items, d_counter);
+      break;
+    case PROJ_LOSS_L2:
+      k_forward_grad_batch<PROJ_LOSS_L2><<<n_blocks, kMarchThreads, 0, s>>>(d_probs, n_probs, n_items, d_counter);
+      break;
+    case PROJ_LOSS_NCC:
+      k_forward_grad_batch<PROJ_LOSS_NCC><<<n_blocks, kMarchThreads, 0, s>>>(d_probs, n_probs, n_items, d_counter);
+      break;
+    default:
+      k_forward_grad_batch<-1><<<n_blocks, kMarchThreads, 0, s>>>(d_probs, n_probs, n_items, d_counter);
+      break;
+  }
   return cudaGetLastError();
 }
 
-int forward_grad_batch_blocks_per_sm() {
+int forward_grad_batch_blocks_per_sm(int loss_all) {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_grad_batch, kMarchThreads, 0) != cudaSuccess) b = 2;
+  cudaError_t e;
+  switch (loss_all) {
+    case PROJ_LOSS_RESIDUAL:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_grad_batch<PROJ_LOSS_RESIDUAL>, kMarchThreads, 0);
+      break;
+    case PROJ_LOSS_L2:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_grad_batch<PROJ_LOSS_L2>, kMarchThreads, 0);
+      break;
+    case PROJ_LOSS_NCC:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_grad_batch<PROJ_LOSS_NCC>, kMarchThreads, 0);
+      break;
+    default:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_forward_grad_batch<-1>, kMarchThreads, 0);
+      break;
+  }
+  if (e != cudaSuccess) b = 2;
   return b < 1 ? 1 : b;
 }
 

@@ -123,9 +123,10 @@ cudaError_t launch_forward_grad_reduce(const InstTable* d_inst, const PoseTable*
                                        const int* d_pose_ptr, const int* d_pose_idx, int n_tiles, Geo geo,
                                        int loss, const float* d_part, float* d_grad, float* d_loss,
                                        cudaStream_t s);
+// loss_all: the loss shared by every problem, or -1 for a batch of mixed losses
 cudaError_t launch_forward_grad_batch(const BatchProblem* d_probs, int n_probs, long long n_items,
-                                      unsigned long long* d_counter, int n_blocks, cudaStream_t s);
-int forward_grad_batch_blocks_per_sm();
+                                      unsigned long long* d_counter, int n_blocks, int loss_all, cudaStream_t s);
+int forward_grad_batch_blocks_per_sm(int loss_all);
 cudaError_t launch_forward_adjoint(const InstTable* d_inst, int n_inst, Geo geo, const float* d_y,
                                    float* d_acc, float* d_vol, cudaStream_t s);
 cudaError_t launch_detector_prep(const float* d_proj, int n_inst, Geo geo, float4* d_det4, cudaStream_t s);
