@@ -161,6 +161,11 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   if (n_pose < 1) return fail(PROJ_E_ARG, "n_pose must be >= 1");
   if (n_inst < 1 || !inst_view || !inst_pose) return fail(PROJ_E_ARG, "need n_inst >= 1 and instance maps");
   if (ops <= 0 || (ops & ~PROJ_OP_ALL)) return fail(PROJ_E_ARG, "ops must be a non-empty OR of PROJ_OP_*");
+  // launch grids put volume rows / slices, detector rows and (for the detector stack) instances in
+  // the y and z grid dimensions
+  if (G.ny > 65000 || G.nz > 65000 || G.nv > 65000) return fail(PROJ_E_ARG, "ny, nz and nv must be <= 65000");
+  if ((ops & PROJ_OP_BACK_GRAD) && n_inst > 65535)
+    return fail(PROJ_E_ARG, "PROJ_OP_BACK_GRAD supports at most 65535 instances per plan");
   for (int v = 0; v < G.n_views; ++v) {
     const double* w = G.views + 12 * v;
     for (int a = 0; a < 12; ++a)

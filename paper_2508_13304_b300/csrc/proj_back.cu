@@ -24,20 +24,18 @@ __device__ __forceinline__ float pix(const float* __restrict__ img, int nu, int 
 // (l, d_u l, d_v l, 0) with a 2-pixel border, [n_inst][nv+4][nu+4]: the
 // central differences of the zero-padded image are non-zero up to one pixel
 // outside the image and zero on the outer border.
+// One thread per element of a row of the bordered float4 stack (x along u,
+// row y = blockIdx.y, instance blockIdx.z; no integer division).
 __global__ void k_detector_prep(const float* __restrict__ proj, int n_inst, Geo g, float4* __restrict__ det4) {
   const int qu = g.nu + 4, qv = g.nv + 4;
-  const long long n = (long long)n_inst * qu * qv;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
-    const int iu = (int)(p % qu) - 2;
-    const int iv = (int)((p / qu) % qv) - 2;
-    const int in = (int)(p / ((long long)qu * qv));
-    const float* img = proj + (size_t)in * g.nu * g.nv;
-    const float l = pix(img, g.nu, g.nv, iu, iv);
-    const float du = 0.5f * (pix(img, g.nu, g.nv, iu + 1, iv) - pix(img, g.nu, g.nv, iu - 1, iv));
-    const float dv = 0.5f * (pix(img, g.nu, g.nv, iu, iv + 1) - pix(img, g.nu, g.nv, iu, iv - 1));
-    det4[p] = make_float4(l, du, dv, 0.f);
-  }
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, in = blockIdx.z;
+  if (x >= qu) return;
+  const int iu = x - 2, iv = y - 2;
+  const float* img = proj + (size_t)in * g.nu * g.nv;
+  const float l = pix(img, g.nu, g.nv, iu, iv);
+  const float du = 0.5f * (pix(img, g.nu, g.nv, iu + 1, iv) - pix(img, g.nu, g.nv, iu - 1, iv));
+  const float dv = 0.5f * (pix(img, g.nu, g.nv, iu, iv + 1) - pix(img, g.nu, g.nv, iu, iv - 1));
+  det4[((size_t)in * qv + y) * qu + x] = make_float4(l, du, dv, 0.f);
 }
 
 // ---------------------------------------------------------------- K5
@@ -311,16 +309,12 @@ __global__ void __launch_bounds__(kBpThreads) k_back_adjoint(const InstTable* __
   }
 }
 
-int elementwise_grid(long long n) {
-  long long b = (n + 255) / 256;
-  return (int)(b < 148LL * 64 ? (b < 1 ? 1 : b) : 148LL * 64);
-}
 
 }  // namespace
 
 cudaError_t launch_detector_prep(const float* d_proj, int n_inst, Geo geo, float4* d_det4, cudaStream_t s) {
-  const long long n = (long long)n_inst * (geo.nu + 4) * (geo.nv + 4);
-  k_detector_prep<<<elementwise_grid(n), 256, 0, s>>>(d_proj, n_inst, geo, d_det4);
+  dim3 grid(ceil_div(geo.nu + 4, 128), geo.nv + 4, n_inst);
+  k_detector_prep<<<grid, 128, 0, s>>>(d_proj, n_inst, geo, d_det4);
   return cudaGetLastError();
 }
 

@@ -137,6 +137,10 @@ __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo&
 // 2-voxel border, (n+4)^3; grad mu = central differences of the zero-padded
 // volume, non-zero up to one voxel outside the grid and zero on the outer
 // border layer.
+// One thread per element of a row of the pitched (mu, grad mu) volume (x =
+// threadIdx + blockIdx.x * blockDim.x, row y = blockIdx.y, slice z =
+// blockIdx.z; no integer division); the same thread writes the 1-padded mu
+// copy where its element falls inside that copy's extent.
 __global__ void k_volume_prep(const float* __restrict__ mu, Geo g, float* __restrict__ vol1,
                               float4* __restrict__ vol4) {
   auto at = [&](int a, int b, int c) -> float {
@@ -144,29 +148,18 @@ __global__ void k_volume_prep(const float* __restrict__ mu, Geo g, float* __rest
                ? __ldg(mu + ((size_t)c * g.ny + b) * g.nx + a)
                : 0.0f;
   };
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  if (vol1) {
-    const long long n = (long long)g.px * g.py * g.pz;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-      const int i = (int)(p % g.px) - 1;
-      const int j = (int)((p / g.px) % g.py) - 1;
-      const int k = (int)(p / ((long long)g.px * g.py)) - 1;
-      vol1[p] = at(i, j, k);
-    }
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+  const int i = x - 2, j = y - 2, k = z - 2;  // voxel index of this element
+  const float m = at(i, j, k);
+  if (vol4 && x < g.qx) {
+    const float gx = (at(i + 1, j, k) - at(i - 1, j, k)) * (0.5f / g.vx);
+    const float gy = (at(i, j + 1, k) - at(i, j - 1, k)) * (0.5f / g.vy);
+    const float gz = (at(i, j, k + 1) - at(i, j, k - 1)) * (0.5f / g.vz);
+    vol4[((size_t)z * g.qy + y) * g.qx + x] = make_float4(m, gx, gy, gz);
   }
-  if (vol4) {
-    const float sx = 0.5f / g.vx, sy = 0.5f / g.vy, sz = 0.5f / g.vz;
-    const long long n = (long long)g.qx * g.qy * g.qz;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-      const int i = (int)(p % g.qx) - 2;
-      const int j = (int)((p / g.qx) % g.qy) - 2;
-      const int k = (int)(p / ((long long)g.qx * g.qy)) - 2;
-      const float gx = (at(i + 1, j, k) - at(i - 1, j, k)) * sx;
-      const float gy = (at(i, j + 1, k) - at(i, j - 1, k)) * sy;
-      const float gz = (at(i, j, k + 1) - at(i, j, k - 1)) * sz;
-      vol4[p] = make_float4(at(i, j, k), gx, gy, gz);
-    }
-  }
+  const int x1 = x - 1, y1 = y - 1, z1 = z - 1;  // position in the 1-padded copy
+  if (vol1 && x1 >= 0 && x1 < g.px && y1 >= 0 && y1 < g.py && z1 >= 0 && z1 < g.pz)
+    vol1[((size_t)z1 * g.py + y1) * g.px + x1] = m;
 }
 
 // ---------------------------------------------------------------- K2
@@ -630,8 +623,9 @@ int elementwise_grid(long long n) {
 }  // namespace
 
 cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float* d_vol1, float4* d_vol4, cudaStream_t s) {
-  const long long n = (long long)geo.qx * geo.qy * geo.qz;
-  k_volume_prep<<<elementwise_grid(n), 256, 0, s>>>(d_mu, geo, d_vol1, d_vol4);
+  // the pitched extents (qx, qy, qz) exceed the 1-padded ones (n + 2) in every axis
+  dim3 grid(ceil_div(geo.qx, 128), geo.qy, geo.qz);
+  k_volume_prep<<<grid, 128, 0, s>>>(d_mu, geo, d_vol1, d_vol4);
   return cudaGetLastError();
 }
 
