@@ -860,6 +860,13 @@ def main():
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
     clocks.__exit__()
+    # the same launch's gathers without the arithmetic: the empirical gather ceiling
+    probe_ms = []
+    for _ in range(3):
+        flush.zero_()
+        pb.proj_gather_probe(P.plan, pose_d, P.ws)
+        probe_ms.append(pb.proj_kernel_time_ms(P.plan))
+    probe_ms = float(np.median(probe_ms))
     if dist:
         dist.barrier()
     from paper_2508_13304_b300.multigpu import aggregate_rate, max_over_ranks
@@ -983,6 +990,11 @@ def main():
                              "%d B/clk x %.0f MHz" % (L1_BYTES_PER_SAMPLE, n_sm, L1_BYTES_PER_CLK_SM, sm_max),
                      "alu": {"achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
                              "frac": alu_achieved / alu_peak, "flop_per_sample": FLOP_PER_SAMPLE},
+                     "empirical_gather_ceiling": {
+                         "kernel_ms": probe_ms, "ray_samples_per_s": samples / (probe_ms * 1e-3),
+                         "frac": probe_ms / k_ms,
+                         "what": "proj_gather_probe: the same launch's rays, samples, volume copies and eight "
+                                 "16-byte corner loads per sample without the interpolation and accumulation"},
                      "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                              "frac": hbm_achieved / hbm_peak, "compulsory_bytes": hbm_bytes,
                              "peak_from": "MEASURED_PEAKS.json hbm_gbs"}},

@@ -215,6 +215,15 @@ int proj_back_pose_grad(proj_plan plan, const float *d_proj, const float *d_pose
                         const float *d_vol_resid, float *d_grad, void *d_ws, size_t ws_bytes,
                         proj_stream stream);
 
+/* Measurement aid, no counterpart in the paper: runs the pose set-up and a
+ * kernel with the memory access pattern of the fused pose-gradient march
+ * (same grid, rays, samples, volume copies and eight 16-byte corner loads
+ * per sample) but none of its arithmetic, so its duration (with kernel
+ * timing enabled, proj_kernel_time_ms) is the empirical ceiling of that
+ * gather on this device.  The volume must be set.  Writes only the
+ * workspace.  Errors as proj_forward_pose_grad. */
+int proj_gather_probe(proj_plan plan, const float *d_pose, void *d_ws, size_t ws_bytes, proj_stream stream);
+
 /* Ray-tile shape of the fused pose-gradient march.  Each CTA marches a
  * 16 x 16-pixel tile with 8 warps; warp_width is the number of pixels along
  * u covered by one warp (warp_width x 32/warp_width rays: 2 x 16, 4 x 8,

@@ -68,6 +68,7 @@ _SIGS = {
                                       _P, _P, _I, _P, _P, _P, _P],
     "proj_fdk_filter": [_P, _P, ctypes.c_float, _P, _P],
     "proj_sharpness": [_P, _P, _P, _P, _P, _SZ, _P],
+    "proj_gather_probe": [_P, _P, _P, _SZ, _P],
     "proj_set_warp_shape": [_P, _I],
     "proj_get_warp_shape": [_P, ctypes.POINTER(_I)],
     "proj_autotune_forward_grad": [_P, _P, _I, _P, _P, _SZ, _P, _I, ctypes.POINTER(ctypes.c_float),
@@ -338,6 +339,14 @@ def proj_sharpness(plan: Plan, vol, loss, grad=None, ws=None, stream=None):
 
 
 WARP_WIDTHS = (2, 4, 8, 16)
+
+
+def proj_gather_probe(plan: Plan, pose, ws, stream=None):
+    """The fused march's gathers without its arithmetic (empirical ceiling)."""
+    import torch
+    p, nb = _ws(ws)
+    _check(lib().proj_gather_probe(plan.handle, _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"), p, nb,
+                                   _stream(stream)))
 
 
 def proj_set_warp_shape(plan: Plan, warp_width: int):

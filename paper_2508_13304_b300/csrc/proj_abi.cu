@@ -499,6 +499,22 @@ int proj_forward_adjoint(proj_plan p, const float* d_y, const float* d_pose, flo
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "forward adjoint launch");
 }
 
+int proj_gather_probe(proj_plan p, const float* d_pose, void* d_ws, size_t ws_bytes, proj_stream stream) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_pose) return fail(PROJ_E_ARG, "proj_gather_probe: NULL pose");
+  int rc = need_op(p, PROJ_OP_FORWARD_GRAD, "proj_gather_probe");
+  if (rc) return rc;
+  WsView w;
+  if ((rc = check_ws(p, d_ws, ws_bytes, &w))) return rc;
+  if ((rc = check_device(p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = setup(p, d_pose, w, s))) return rc;
+  mark(p, true, s);
+  cudaError_t e = launch_gather_probe(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, w.part_f, s);
+  mark(p, false, s);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "gather probe launch");
+}
+
 int proj_set_warp_shape(proj_plan p, int warp_width) {
   if (!p) return fail(PROJ_E_ARG, "plan is NULL");
   if (warp_width != 2 && warp_width != 4 && warp_width != 8 && warp_width != 16)

@@ -371,6 +371,49 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
     march_tile<LOSS, WU, 0>(inst, n, tile, n_tiles, tiles_u, g, vol, ref, proj, part, red);
 }
 
+// ---------------------------------------------------------------- gather probe
+//
+// The fused march's memory access pattern without its arithmetic: the same
+// grid, pixel mapping, ray set-up, stepping, volume copy and the same eight
+// 16-byte corner loads per sample (as volatile 128-bit loads, so none is
+// dropped or narrowed), but only one add per load instead of the
+// interpolation and accumulation.  Its duration is the empirical ceiling of
+// the gather the fused march performs.
+
+__device__ __forceinline__ float ld_probe(const float4* p) {
+  float v[4];
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(p));
+  return v[0];
+}
+
+template <int YF>
+__device__ __forceinline__ float probe_ray(const InstTable& T, const Geo& g, int iu, int iv, const float4* vol) {
+  Ray r;
+  float acc = 0.f;
+  if (!(T.valid && ray_setup_m<2>(T, g, iu, iv, r))) return acc;
+  const int sx = YF ? g.rqy : 1, sy = YF ? 1 : g.qx, sz = YF ? g.rqx * g.rqy : g.qx * g.qy;
+  for (int k = r.k0; k <= r.k1; ++k) {
+    const float kf = (float)k;
+    const Cell c = locate2<YF>(fmaf(kf, r.dx, r.ax), fmaf(kf, r.dy, r.ay), fmaf(kf, r.dz, r.az), g);
+    const float4* p0 = vol + c.idx;
+    acc += ld_probe(p0) + ld_probe(p0 + sx) + ld_probe(p0 + sy) + ld_probe(p0 + sy + sx) + ld_probe(p0 + sz) +
+           ld_probe(p0 + sz + sx) + ld_probe(p0 + sz + sy) + ld_probe(p0 + sz + sy + sx);
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(kMarchThreads, 4)
+    k_gather_probe(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g, const float4* __restrict__ vol,
+                   const float4* __restrict__ voly, float* __restrict__ sink) {
+  const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
+  int iu, iv;
+  const bool on = tile_pixel<4>(tile, tiles_u, g, iu, iv);
+  float acc = 0.f;
+  if (on) acc = (voly && inst[n].yfast) ? probe_ray<1>(inst[n], g, iu, iv, voly) : probe_ray<0>(inst[n], g, iu, iv, vol);
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0 && acc == 1.2345e-30f) sink[0] = acc;  // keeps the loads live; never taken in practice
+}
+
 // ---------------------------------------------------------------- batch
 //
 // Persistent multi-problem march: a grid of resident blocks takes work items
@@ -680,6 +723,13 @@ cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, co
       break;
     default: launch_forward_grad_w<4>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, s); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_probe(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
+                                const float4* d_vol4y, float* d_sink, cudaStream_t s) {
+  const int nt = tiles_of(geo);
+  k_gather_probe<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo, d_vol4, d_vol4y, d_sink);
   return cudaGetLastError();
 }
 

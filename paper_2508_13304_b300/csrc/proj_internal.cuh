@@ -117,6 +117,9 @@ cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long
 cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
                                 const float4* d_vol4y, int loss, const float* d_ref, float* d_proj, float* d_part,
                                 cudaStream_t s, int warp_width = 4);
+// the fused march's gathers without its arithmetic (empirical gather ceiling)
+cudaError_t launch_gather_probe(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
+                                const float4* d_vol4y, float* d_sink, cudaStream_t s);
 // y-fast copy of the pitched (mu, grad mu) volume (tiled transpose of every z slice)
 cudaError_t launch_volume_yfast(const float4* d_vol4, Geo geo, float4* d_vol4y, cudaStream_t s);
 cudaError_t launch_forward_grad_reduce(const InstTable* d_inst, const PoseTable* d_ptab, int n_pose,

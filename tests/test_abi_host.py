@@ -136,6 +136,7 @@ def test_bad_ops_and_null_arguments(L):
     assert L.proj_batch_run(None, None) == pb.PROJ_E_ARG
     assert L.proj_batch_destroy(None) == pb.PROJ_OK
     assert L.proj_set_warp_shape(None, 4) == pb.PROJ_E_ARG
+    assert L.proj_gather_probe(None, None, None, 0, None) == pb.PROJ_E_ARG
     assert L.proj_get_warp_shape(None, None) == pb.PROJ_E_ARG
     assert L.proj_autotune_forward_grad(None, None, 0, None, None, 0, None, 1, None, None) == pb.PROJ_E_ARG
 
