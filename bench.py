@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other kernels' measurements")
     ap.add_argument("--section", default=None,
-                    choices=["gemm", "forward", "back", "accuracy", "tables", "registration500", "moco"],
+                    choices=["gemm", "forward", "back", "accuracy", "tables", "registration500", "moco", "c1"],
                     help="run only one secondary measurement and print it (gemm: the tensor-core GEMM shapes; "
                          "forward: forward projection of the 128 registration instances; back: FDK "
                          "back-projection and its pose gradient, 360 views of 512^2 on 256^3)")
@@ -322,6 +322,7 @@ def secondary(pb, torch, dev, w, mu_d, flush):
                                   "ms_per_launch": {"%dx%d" % (k, 32 // k): v for k, v in times.items()},
                                   "chosen": "%dx%d" % (width, 32 // width)}
     del Pa
+    out["c1_small"] = c1_small(pb, torch, dev, flush)
     out["moco_quality"] = moco_quality(pb, torch, dev)
     out["gradient_accuracy"] = gradient_accuracy(pb, torch, dev, mu_d)
     out["paper_tables"] = paper_tables(pb, torch, dev, flush)
@@ -638,6 +639,56 @@ def moco_quality(pb, torch, dev):
             "seconds": out["seconds"]}
 
 
+def c1_small(pb, torch, dev, flush):
+    """The small configuration (64^3 at 1 mm, 8 views of 128^2 at 1.5 mm, one
+    pose, L2 target at a second pose): the four hot-path calls on the GPU, and
+    the FP64 oracle's forward pose gradient on the same work with one thread
+    and with all host threads (ray-samples/s)."""
+    import oracle
+    w = synth.workload_tiny()
+    g = w["geom"]
+    P = pb.Projector(g, n_pose=1, inst_view=np.arange(g.n_views), inst_pose=np.zeros(g.n_views, np.int32))
+    pb.proj_enable_kernel_timing(P.plan)
+    mu = torch.from_numpy(w["mu"].astype(np.float32)).to(dev)
+    P.set_volume(mu)
+    pose = torch.from_numpy(w["pose"].astype(np.float32)).to(dev)
+    target = P.forward(torch.from_numpy(w["pose_true"].astype(np.float32)).to(dev)).contiguous()
+    det = torch.from_numpy(w["det_image"].astype(np.float32)).to(dev)
+    samples = int(P.count_samples(pose).sum().item())
+    proj = torch.empty_like(target)
+    vol = torch.empty_like(mu)
+    grad = torch.empty((1, 6), device=dev)
+    loss = torch.empty(1, device=dev)
+    wv = torch.randn(mu.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(1001))
+    out = {"config": "64^3 at 1 mm, 8 views of 128^2 at 1.5 mm, one pose", "ray_samples": samples}
+    out["forward_ms"] = _timed(lambda: pb.proj_forward(P.plan, pose, proj, P.ws), P.plan, pb, flush)
+    out["forward_pose_grad_ms"] = _timed(
+        lambda: pb.proj_forward_pose_grad(P.plan, pose, pb.PROJ_LOSS_L2, target, grad, loss, None, P.ws), P.plan, pb,
+        flush)
+    out["back_ms"] = _timed(lambda: pb.proj_back(P.plan, det, pose, pb.PROJ_W_NONE, vol, P.ws), P.plan, pb, flush)
+    out["back_pose_grad_ms"] = _timed(
+        lambda: pb.proj_back_pose_grad(P.plan, det, pose, pb.PROJ_W_NONE, wv, grad, P.ws), P.plan, pb, flush)
+    # oracle: forward pose gradient of the same L2 loss, 1 thread and all threads
+    mu64 = w["mu"].astype(np.float64)
+    pose64 = w["pose"].astype(np.float64)
+    tgt64 = target.double().cpu().numpy()
+    iv = np.arange(g.n_views)
+    ip = np.zeros(g.n_views, dtype=np.int32)
+    rates = {}
+    n_all = oracle.max_threads()
+    for n_thr in (1, n_all):
+        oracle.set_threads(n_thr)
+        t0 = time.perf_counter()
+        p64 = oracle.forward(g, mu64, pose64, iv, ip)
+        _, wts = oracle.pose_loss_weights("l2", p64, tgt64, iv, ip, 1)
+        oracle.forward_grad(g, mu64, pose64, wts, iv, ip)
+        rates[n_thr] = samples / (time.perf_counter() - t0)
+    oracle.set_threads(n_all)
+    out["oracle_forward_pose_grad_samples_per_s"] = {"1_thread": rates[1], "%d_threads" % n_all: rates[n_all]}
+    out["gpu_forward_pose_grad_samples_per_s"] = samples / (out["forward_pose_grad_ms"] * 1e-3)
+    return out
+
+
 def graph_timing(pb, torch, g, mu_h, tgt, starts):
     """Registration iterations eager (one host check per iteration) vs
     replayed CUDA graphs of 10 iterations; every candidate kept running."""
@@ -762,6 +813,11 @@ def main():
         ms0 = _timed(lambda: pb.proj_forward(P0.plan, pose0, out0, P0.ws), P0.plan, pb, fl)
         print(json.dumps({"section": "forward", "kernel": "k_forward", "kernel_ms": ms0,
                           "config": "256^3, 128 view instances of 384^2"}), flush=True)
+        return
+    if args.section == "c1":
+        dev0 = torch.device("cuda", local)
+        fl = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev0)
+        print(json.dumps({"section": "c1", **c1_small(pb, torch, dev0, fl)}), flush=True)
         return
     if args.section == "moco":
         print(json.dumps({"section": "moco", **moco_quality(pb, torch, torch.device("cuda", local))}), flush=True)
