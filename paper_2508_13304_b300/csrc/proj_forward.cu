@@ -117,7 +117,11 @@ __device__ __forceinline__ Cell locate(float fx, float fy, float fz, const Geo& 
 }
 
 // YF = 0: the pitched (mu, grad mu) volume with x fastest; YF = 1: its copy
-// with y fastest.
+// with y fastest.  In both, the two slices of a z pair are interleaved element
+// by element, so the two detector rows of a quarter-warp's 4 x 2 ray patch
+// (v runs along z in a circular orbit) gather from neighbouring 16-byte slots;
+// the +z corner is the neighbouring slot for an even slice and the next pair's
+// slot for an odd one.
 template <int YF = 0>
 __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo& g) {
   const int ix = min(max(__float2int_rd(fx), 0), g.nx + 2);
@@ -127,7 +131,8 @@ __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo&
   c.ax = fx - (float)ix;
   c.ay = fy - (float)iy;
   c.az = fz - (float)iz;
-  c.idx = YF ? (iz * g.rqx + ix) * g.rqy + iy : (iz * g.qy + iy) * g.qx + ix;
+  c.idx = YF ? ((((iz >> 1) * g.rqx + ix) * g.rqy + iy) << 1) + (iz & 1)
+             : ((((iz >> 1) * g.qy + iy) * g.qx + ix) << 1) + (iz & 1);
   return c;
 }
 
@@ -155,7 +160,7 @@ __global__ void k_volume_prep(const float* __restrict__ mu, Geo g, float* __rest
     const float gx = (at(i + 1, j, k) - at(i - 1, j, k)) * (0.5f / g.vx);
     const float gy = (at(i, j + 1, k) - at(i, j - 1, k)) * (0.5f / g.vy);
     const float gz = (at(i, j, k + 1) - at(i, j, k - 1)) * (0.5f / g.vz);
-    vol4[((size_t)z * g.qy + y) * g.qx + x] = make_float4(m, gx, gy, gz);
+    vol4[((((size_t)(z >> 1) * g.qy + y) * g.qx + x) << 1) + (z & 1)] = make_float4(m, gx, gy, gz);
   }
   const int x1 = x - 1, y1 = y - 1, z1 = z - 1;  // position in the 1-padded copy
   if (vol1 && x1 >= 0 && x1 < g.px && y1 >= 0 && y1 < g.py && z1 >= 0 && z1 < g.pz)
@@ -264,13 +269,14 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
   Ray r;
   if (on_det && T.valid && ray_setup_m<2>(T, g, iu, iv, r)) {
     // element strides of +1 voxel along x, y, z in the marched copy
-    const int sx = YF ? g.rqy : 1, sy = YF ? 1 : g.qx, sz = YF ? g.rqx * g.rqy : g.qx * g.qy;
+    const int sx = YF ? 2 * g.rqy : 2, sy = YF ? 2 : 2 * g.qx, szp = YF ? 2 * g.rqx * g.rqy : 2 * g.qx * g.qy;
     const float ox = g.cx + 2.0f, oy = g.cy + 2.0f, oz = g.cz + 2.0f;
     for (int k = r.k0; k <= r.k1; ++k) {
       const float kf = (float)k;
       const float fx = fmaf(kf, r.dx, r.ax), fy = fmaf(kf, r.dy, r.ay), fz = fmaf(kf, r.dz, r.az);
       const Cell c = locate2<YF>(fx, fy, fz, g);
       const float4* p0 = vol + c.idx;
+      const int sz = (c.idx & 1) ? szp - 1 : 1;
       const float4 v000 = __ldg(p0), v100 = __ldg(p0 + sx);
       const float4 v010 = __ldg(p0 + sy), v110 = __ldg(p0 + sy + sx);
       const float4 v001 = __ldg(p0 + sz), v101 = __ldg(p0 + sz + sx);
@@ -391,11 +397,12 @@ __device__ __forceinline__ float probe_ray(const InstTable& T, const Geo& g, int
   Ray r;
   float acc = 0.f;
   if (!(T.valid && ray_setup_m<2>(T, g, iu, iv, r))) return acc;
-  const int sx = YF ? g.rqy : 1, sy = YF ? 1 : g.qx, sz = YF ? g.rqx * g.rqy : g.qx * g.qy;
+  const int sx = YF ? 2 * g.rqy : 2, sy = YF ? 2 : 2 * g.qx, szp = YF ? 2 * g.rqx * g.rqy : 2 * g.qx * g.qy;
   for (int k = r.k0; k <= r.k1; ++k) {
     const float kf = (float)k;
     const Cell c = locate2<YF>(fmaf(kf, r.dx, r.ax), fmaf(kf, r.dy, r.ay), fmaf(kf, r.dz, r.az), g);
     const float4* p0 = vol + c.idx;
+    const int sz = (c.idx & 1) ? szp - 1 : 1;
     acc += ld_probe(p0) + ld_probe(p0 + sx) + ld_probe(p0 + sy) + ld_probe(p0 + sy + sx) + ld_probe(p0 + sz) +
            ld_probe(p0 + sz + sx) + ld_probe(p0 + sz + sy) + ld_probe(p0 + sz + sy + sx);
   }
@@ -743,12 +750,13 @@ __global__ void k_volume_yfast(const float4* __restrict__ v, Geo g, float4* __re
   const int x0 = blockIdx.x * kTr, y0 = blockIdx.y * kTr, z = blockIdx.z;
   for (int j = threadIdx.y; j < kTr; j += blockDim.y) {
     const int x = x0 + threadIdx.x, y = y0 + j;
-    t[j][threadIdx.x] = (x < X && y < Y) ? v[((size_t)z * g.qy + y) * g.qx + x] : make_float4(0.f, 0.f, 0.f, 0.f);
+    t[j][threadIdx.x] = (x < X && y < Y) ? v[((((size_t)(z >> 1) * g.qy + y) * g.qx + x) << 1) + (z & 1)]
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
   for (int j = threadIdx.y; j < kTr; j += blockDim.y) {
     const int y = y0 + threadIdx.x, x = x0 + j;
-    if (x < g.rqx && y < g.rqy) vy[((size_t)z * g.rqx + x) * g.rqy + y] = t[threadIdx.x][j];
+    if (x < g.rqx && y < g.rqy) vy[((((size_t)(z >> 1) * g.rqx + x) * g.rqy + y) << 1) + (z & 1)] = t[threadIdx.x][j];
   }
 }
 }  // namespace

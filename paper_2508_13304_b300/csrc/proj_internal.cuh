@@ -49,8 +49,10 @@ static_assert(sizeof(PoseTable) % 8 == 0, "PoseTable layout");
 struct Geo {
   int nx, ny, nz;       // voxels
   int px, py, pz;       // sizes with a 1-voxel border (n + 2): the mu copy
-  int qx, qy, qz;       // pitches of the (mu, grad mu) volume (2-voxel border, >= n + 4), x fastest
-  int rqx, rqy;         // pitches of its copy with y fastest: element (x, y, z) at (z * rqx + x) * rqy + y
+  int qx, qy, qz;       // pitches of the (mu, grad mu) volume (2-voxel border, >= n + 4; qz even): element
+                        // (x, y, z) at (((z >> 1) * qy + y) * qx + x) * 2 + (z & 1), i.e. x fastest with
+                        // the two slices of a z pair interleaved element by element
+  int rqx, rqy;         // pitches of its copy with y fastest: (((z >> 1) * rqx + x) * rqy + y) * 2 + (z & 1)
   float vx, vy, vz;     // voxel pitch, mm
   float hx, hy, hz;     // half extent of the open box (-1, n) in centred index units: (n+1)/2
   float gx, gy, gz;     // half extent of the gradient box (-2, n+1): (n+3)/2
@@ -155,7 +157,7 @@ inline void volume_pitches(int nx, int ny, int nz, int* qx, int* qy, int* qz) {
   while ((x * y) % 8 != 4) ++y;
   *qx = x;
   *qy = y;
-  *qz = nz + 4;
+  *qz = (nz + 5) & ~1;  // even: z slices are stored in interleaved pairs
 }
 
 // The same rule for the copy whose rows run along y: row pitch (y) = 2 mod 8,
