@@ -142,29 +142,43 @@ __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo&
 // 2-voxel border, (n+4)^3; grad mu = central differences of the zero-padded
 // volume, non-zero up to one voxel outside the grid and zero on the outer
 // border layer.
-// One thread per element of a row of the pitched (mu, grad mu) volume (x =
-// threadIdx + blockIdx.x * blockDim.x, row y = blockIdx.y, slice z =
-// blockIdx.z; no integer division); the same thread writes the 1-padded mu
-// copy where its element falls inside that copy's extent.
-__global__ void k_volume_prep(const float* __restrict__ mu, Geo g, float* __restrict__ vol1,
-                              float4* __restrict__ vol4) {
+// A block owns a 32 x 8 tile of (x, y) columns of the pitched (mu, grad mu)
+// volume and walks a chunk of z slices, carrying mu at z - 1, z and z + 1 in
+// registers: every voxel of mu is read once from DRAM (the x and y
+// neighbours come from the slice the block just loaded, through L1).  The
+// same thread writes the 1-padded mu copy where its element falls inside
+// that copy's extent.
+constexpr int kPrepZChunk = 32;
+
+__global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ mu, Geo g, float* __restrict__ vol1,
+                                                     float4* __restrict__ vol4) {
   auto at = [&](int a, int b, int c) -> float {
     return (a >= 0 && a < g.nx && b >= 0 && b < g.ny && c >= 0 && c < g.nz)
                ? __ldg(mu + ((size_t)c * g.ny + b) * g.nx + a)
                : 0.0f;
   };
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-  const int i = x - 2, j = y - 2, k = z - 2;  // voxel index of this element
-  const float m = at(i, j, k);
-  if (vol4 && x < g.qx) {
-    const float gx = (at(i + 1, j, k) - at(i - 1, j, k)) * (0.5f / g.vx);
-    const float gy = (at(i, j + 1, k) - at(i, j - 1, k)) * (0.5f / g.vy);
-    const float gz = (at(i, j, k + 1) - at(i, j, k - 1)) * (0.5f / g.vz);
-    vol4[((((size_t)(z >> 1) * g.qy + y) * g.qx + x) << 1) + (z & 1)] = make_float4(m, gx, gy, gz);
+  const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+  const int z0 = blockIdx.z * kPrepZChunk, z1 = min(g.qz, z0 + kPrepZChunk);
+  const int i = x - 2, j = y - 2;  // voxel column of this element
+  const bool in4 = vol4 && x < g.qx && y < g.qy;
+  const int x1 = x - 1, y1 = y - 1;
+  const bool in1xy = vol1 && x1 >= 0 && x1 < g.px && y1 >= 0 && y1 < g.py;
+  float m_prev = at(i, j, z0 - 3), m = at(i, j, z0 - 2);
+  const float sx = 0.5f / g.vx, sy = 0.5f / g.vy, sz = 0.5f / g.vz;
+  for (int z = z0; z < z1; ++z) {
+    const int k = z - 2;
+    const float m_next = at(i, j, k + 1);
+    if (in4) {
+      const float gx = (at(i + 1, j, k) - at(i - 1, j, k)) * sx;
+      const float gy = (at(i, j + 1, k) - at(i, j - 1, k)) * sy;
+      vol4[((((size_t)(z >> 1) * g.qy + y) * g.qx + x) << 1) + (z & 1)] =
+          make_float4(m, gx, gy, (m_next - m_prev) * sz);
+    }
+    const int zz1 = z - 1;
+    if (in1xy && zz1 >= 0 && zz1 < g.pz) vol1[((size_t)zz1 * g.py + y1) * g.px + x1] = m;
+    m_prev = m;
+    m = m_next;
   }
-  const int x1 = x - 1, y1 = y - 1, z1 = z - 1;  // position in the 1-padded copy
-  if (vol1 && x1 >= 0 && x1 < g.px && y1 >= 0 && y1 < g.py && z1 >= 0 && z1 < g.pz)
-    vol1[((size_t)z1 * g.py + y1) * g.px + x1] = m;
 }
 
 // ---------------------------------------------------------------- K2
@@ -674,8 +688,8 @@ int elementwise_grid(long long n) {
 
 cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float* d_vol1, float4* d_vol4, cudaStream_t s) {
   // the pitched extents (qx, qy, qz) exceed the 1-padded ones (n + 2) in every axis
-  dim3 grid(ceil_div(geo.qx, 128), geo.qy, geo.qz);
-  k_volume_prep<<<grid, 128, 0, s>>>(d_mu, geo, d_vol1, d_vol4);
+  dim3 grid(ceil_div(geo.qx, 32), ceil_div(geo.qy, 8), ceil_div(geo.qz, kPrepZChunk));
+  k_volume_prep<<<grid, 256, 0, s>>>(d_mu, geo, d_vol1, d_vol4);
   return cudaGetLastError();
 }
 
