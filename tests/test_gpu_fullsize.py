@@ -122,3 +122,36 @@ def test_calibration_forward_full_size():
     gref, _ = oracle.forward_grad(g, mu.astype(np.float64), poses[v].astype(np.float64),
                                   resid[v:v + 1].astype(np.float64), inst_view=[v], inst_pose=[0])
     assert grad_rel(grad[v], gref[0]) <= TOL_GRAD, (grad[v], gref[0])
+
+
+def test_pose_proposal_drr_batch_full_size():
+    """The network's training batch in the benchmark's configuration: 256
+    poses (rot +-30 deg, trans +-40 mm) x 2 views of 384^2 from 256^3 at
+    0.8 mm, down-sampled 3x to 128^2 BF16 inputs.  2000 sampled DRR pixels
+    against the FP64 march, and the prepared inputs of three poses against
+    the oracle's box average and standardisation of the same projections
+    (BF16 storage: <= 4e-3 rel-L2)."""
+    from oracle import posenet as on
+    from paper_2508_13304_b300 import posenet as pn
+    w = synth.workload_registration(seed=1002, n_cand=1)
+    g = w["geom"]
+    mu = torch.from_numpy(w["mu"]).cuda()
+    B = 256
+    src = pn.DrrSource(g, mu, B, factor=3, seed=7)
+    x = torch.empty((B, 128, 128, 2), device="cuda", dtype=torch.bfloat16)
+    t = torch.empty((B, 6), device="cuda")
+    src.batch(x, t)
+    torch.cuda.synchronize()
+    assert float(t.abs().max()) <= 1.0
+    pose = (t * src.scale).cpu().numpy()      # the poses the batch was rendered at
+    proj = src.proj.cpu().numpy()
+    rng = np.random.default_rng(55)
+    inst = rng.integers(0, 2 * B, 2000)
+    pix = np.stack([inst, rng.integers(0, 384, 2000), rng.integers(0, 384, 2000)], axis=1)
+    ref = oracle.forward_pixels(g, w["mu"].astype(np.float64), pose.astype(np.float64), pix,
+                                np.tile([0, 1], B), np.repeat(np.arange(B), 2))
+    assert rel(proj[pix[:, 0], pix[:, 2], pix[:, 1]], ref) <= TOL_IMG
+    xs = x.float().cpu().numpy()
+    for b in (0, 101, 255):
+        prep = on.prepare(proj[2 * b:2 * b + 2], 2, 3)[0]
+        assert rel(xs[b], prep) <= 4e-3, b
