@@ -155,3 +155,42 @@ def test_pose_proposal_drr_batch_full_size():
     for b in (0, 101, 255):
         prep = on.prepare(proj[2 * b:2 * b + 2], 2, 3)[0]
         assert rel(xs[b], prep) <= 4e-3, b
+
+
+def test_uneven_batch_full_size():
+    """The uneven calibration batch in one persistent launch: 512^3 with 720
+    per-view poses on 768^2 detectors plus 24 single-view problems (volumes
+    128..320^3, detectors 256..512^2), L2 loss.  Every problem's gradients
+    and losses equal those of its own proj_forward_pose_grad call; two views
+    of the large problem and three of the small ones against the oracle."""
+    rng = np.random.default_rng(1004)
+    gen = torch.Generator(device="cuda").manual_seed(1004)
+    items, host = [], []
+    for q in synth.workload_uneven(with_large=True):
+        g = q["geom"]
+        nvw = g.n_views
+        mu = rng.random((g.nz, g.ny, g.nx), dtype=np.float32)
+        P = pb.Projector(g, n_pose=nvw, inst_view=np.arange(nvw), inst_pose=np.arange(nvw),
+                         ops=pb.PROJ_OP_FORWARD_GRAD)
+        P.set_volume(mu)
+        items.append(dict(plan=P.plan, loss=pb.PROJ_LOSS_L2, pose=torch.from_numpy(f32(q["poses"])).cuda(),
+                          ref=torch.rand((nvw, g.nv, g.nu), device="cuda", generator=gen), grad=torch.zeros((nvw, 6), device="cuda"),
+                          loss_out=torch.zeros(nvw, device="cuda"), ws=P.ws))
+        host.append((g, mu, f32(q["poses"]), P))
+    b = pb.proj_batch_create(items)
+    pb.proj_batch_run(b)
+    torch.cuda.synchronize()
+    got = [(it["grad"].cpu().numpy(), it["loss_out"].cpu().numpy()) for it in items]
+    for k, (it, (g, mu, pose, P)) in enumerate(zip(items, host)):
+        gs, ls = P.forward_pose_grad(it["pose"], pb.PROJ_LOSS_L2, it["ref"])
+        assert rel(got[k][0], gs.cpu().numpy()) <= 1e-6, k
+        np.testing.assert_allclose(got[k][1], ls.cpu().numpy(), rtol=1e-6)
+    order = np.argsort([h[0].nx * h[0].nu ** 2 for h in host[1:]]) + 1
+    for k, v in [(0, 0), (0, 437)] + [(int(k), 0) for k in (order[0], order[12], order[-1])]:
+        g, mu, pose, _ = host[k]
+        ref = items[k]["ref"][v:v + 1].cpu().numpy().astype(np.float64)
+        pr = oracle.forward(g, mu.astype(np.float64), pose[v].astype(np.float64), [v], [0])
+        L, w = oracle.pose_loss_weights("l2", pr, ref, [0], [0], 1)
+        gref, _ = oracle.forward_grad(g, mu.astype(np.float64), pose[v].astype(np.float64), w, [v], [0])
+        assert grad_rel(got[k][0][v], gref[0]) <= TOL_GRAD, (k, v, got[k][0][v], gref[0])
+        assert abs(got[k][1][v] - L[0]) <= 1e-4 * abs(L[0]), (k, v)
