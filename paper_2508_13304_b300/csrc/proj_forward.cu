@@ -138,7 +138,10 @@ __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo&
 
 // ---------------------------------------------------------------- K1
 
-// vol1: mu with a 1-voxel zero border, (n+2)^3.  vol4: (mu, grad mu) with a
+// volq: mu with a 1-voxel zero border, (n+2)^3 cells, each cell holding the
+// 2 x 2 corners of its xy face, (mu(x, y), mu(x+1, y), mu(x, y+1),
+// mu(x+1, y+1)) at its own z: a trilinear sample reads its 8 corners as two
+// 16-byte loads (this cell and the one above).  vol4: (mu, grad mu) with a
 // 2-voxel border, (n+4)^3; grad mu = central differences of the zero-padded
 // volume, non-zero up to one voxel outside the grid and zero on the outer
 // border layer.
@@ -146,11 +149,11 @@ __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo&
 // volume and walks a chunk of z slices, carrying mu at z - 1, z and z + 1 in
 // registers: every voxel of mu is read once from DRAM (the x and y
 // neighbours come from the slice the block just loaded, through L1).  The
-// same thread writes the 1-padded mu copy where its element falls inside
-// that copy's extent.
+// same thread writes the volq cell whose base corner is its element, where
+// that falls inside volq's extent.
 constexpr int kPrepZChunk = 32;
 
-__global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ mu, Geo g, float* __restrict__ vol1,
+__global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ mu, Geo g, float4* __restrict__ volq,
                                                      float4* __restrict__ vol4) {
   auto at = [&](int a, int b, int c) -> float {
     return (a >= 0 && a < g.nx && b >= 0 && b < g.ny && c >= 0 && c < g.nz)
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ m
   const int i = x - 2, j = y - 2;  // voxel column of this element
   const bool in4 = vol4 && x < g.qx && y < g.qy;
   const int x1 = x - 1, y1 = y - 1;
-  const bool in1xy = vol1 && x1 >= 0 && x1 < g.px && y1 >= 0 && y1 < g.py;
+  const bool in1xy = volq && x1 >= 0 && x1 < g.px && y1 >= 0 && y1 < g.py;
   float m_prev = at(i, j, z0 - 3), m = at(i, j, z0 - 2);
   const float sx = 0.5f / g.vx, sy = 0.5f / g.vy, sz = 0.5f / g.vz;
   for (int z = z0; z < z1; ++z) {
@@ -175,7 +178,8 @@ __global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ m
           make_float4(m, gx, gy, (m_next - m_prev) * sz);
     }
     const int zz1 = z - 1;
-    if (in1xy && zz1 >= 0 && zz1 < g.pz) vol1[((size_t)zz1 * g.py + y1) * g.px + x1] = m;
+    if (in1xy && zz1 >= 0 && zz1 < g.pz)
+      volq[((size_t)zz1 * g.py + y1) * g.px + x1] = make_float4(m, at(i + 1, j, k), at(i, j + 1, k), at(i + 1, j + 1, k));
     m_prev = m;
     m = m_next;
   }
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ m
 // ---------------------------------------------------------------- K2
 
 __global__ void __launch_bounds__(kMarchThreads) k_forward(const InstTable* __restrict__ inst, int n_tiles,
-                                                           int tiles_u, Geo g, const float* __restrict__ vol,
+                                                           int tiles_u, Geo g, const float4* __restrict__ volq,
                                                            float* __restrict__ proj) {
   const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
   int iu, iv;
@@ -194,47 +198,14 @@ __global__ void __launch_bounds__(kMarchThreads) k_forward(const InstTable* __re
   Ray r;
   if (T.valid && ray_setup(T, g, iu, iv, r)) {
     const int pxy = g.px * g.py;
-    // The 8 corners (corner q = offsets (q & 1, (q >> 1) & 1, q >> 2)) stay in
-    // registers while the ray is in one cell; a step to a face neighbour
-    // keeps the 4 shared corners and loads the other 4.
-    float v[8];
-    int cur = -1;
+    // corners of the sample's cell: the xy face at z in one 16-byte cell
+    // record, the face at z + 1 in the record one slice up
     for (int k = r.k0; k <= r.k1; ++k) {
       const float kf = (float)k;
       const Cell c = locate(fmaf(kf, r.dx, r.ax), fmaf(kf, r.dy, r.ay), fmaf(kf, r.dz, r.az), g);
-      if (c.idx != cur) {
-        const float* p0 = vol + c.idx;
-        const int d = c.idx - cur;
-        if (cur >= 0 && d == 1) {
-          v[0] = v[1]; v[2] = v[3]; v[4] = v[5]; v[6] = v[7];
-          v[1] = __ldg(p0 + 1); v[3] = __ldg(p0 + g.px + 1); v[5] = __ldg(p0 + pxy + 1);
-          v[7] = __ldg(p0 + pxy + g.px + 1);
-        } else if (cur >= 0 && d == -1) {
-          v[1] = v[0]; v[3] = v[2]; v[5] = v[4]; v[7] = v[6];
-          v[0] = __ldg(p0); v[2] = __ldg(p0 + g.px); v[4] = __ldg(p0 + pxy); v[6] = __ldg(p0 + pxy + g.px);
-        } else if (cur >= 0 && d == g.px) {
-          v[0] = v[2]; v[1] = v[3]; v[4] = v[6]; v[5] = v[7];
-          v[2] = __ldg(p0 + g.px); v[3] = __ldg(p0 + g.px + 1); v[6] = __ldg(p0 + pxy + g.px);
-          v[7] = __ldg(p0 + pxy + g.px + 1);
-        } else if (cur >= 0 && d == -g.px) {
-          v[2] = v[0]; v[3] = v[1]; v[6] = v[4]; v[7] = v[5];
-          v[0] = __ldg(p0); v[1] = __ldg(p0 + 1); v[4] = __ldg(p0 + pxy); v[5] = __ldg(p0 + pxy + 1);
-        } else if (cur >= 0 && d == pxy) {
-          v[0] = v[4]; v[1] = v[5]; v[2] = v[6]; v[3] = v[7];
-          v[4] = __ldg(p0 + pxy); v[5] = __ldg(p0 + pxy + 1); v[6] = __ldg(p0 + pxy + g.px);
-          v[7] = __ldg(p0 + pxy + g.px + 1);
-        } else if (cur >= 0 && d == -pxy) {
-          v[4] = v[0]; v[5] = v[1]; v[6] = v[2]; v[7] = v[3];
-          v[0] = __ldg(p0); v[1] = __ldg(p0 + 1); v[2] = __ldg(p0 + g.px); v[3] = __ldg(p0 + g.px + 1);
-        } else {
-          v[0] = __ldg(p0); v[1] = __ldg(p0 + 1); v[2] = __ldg(p0 + g.px); v[3] = __ldg(p0 + g.px + 1);
-          v[4] = __ldg(p0 + pxy); v[5] = __ldg(p0 + pxy + 1); v[6] = __ldg(p0 + pxy + g.px);
-          v[7] = __ldg(p0 + pxy + g.px + 1);
-        }
-        cur = c.idx;
-      }
-      const float c0 = lerp(lerp(v[0], v[1], c.ax), lerp(v[2], v[3], c.ax), c.ay);
-      const float c1 = lerp(lerp(v[4], v[5], c.ax), lerp(v[6], v[7], c.ax), c.ay);
+      const float4 f0 = __ldg(volq + c.idx), f1 = __ldg(volq + c.idx + pxy);
+      const float c0 = lerp(lerp(f0.x, f0.y, c.ax), lerp(f0.z, f0.w, c.ax), c.ay);
+      const float c1 = lerp(lerp(f1.x, f1.y, c.ax), lerp(f1.z, f1.w, c.ax), c.ay);
       acc += lerp(c0, c1, c.az);
     }
   }
@@ -686,17 +657,17 @@ int elementwise_grid(long long n) {
 
 }  // namespace
 
-cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float* d_vol1, float4* d_vol4, cudaStream_t s) {
+cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float4* d_vol4, cudaStream_t s) {
   // the pitched extents (qx, qy, qz) exceed the 1-padded ones (n + 2) in every axis
   dim3 grid(ceil_div(geo.qx, 32), ceil_div(geo.qy, 8), ceil_div(geo.qz, kPrepZChunk));
-  k_volume_prep<<<grid, 256, 0, s>>>(d_mu, geo, d_vol1, d_vol4);
+  k_volume_prep<<<grid, 256, 0, s>>>(d_mu, geo, d_volq, d_vol4);
   return cudaGetLastError();
 }
 
-cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const float* d_vol1, float* d_proj,
+cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_volq, float* d_proj,
                            cudaStream_t s) {
   const int nt = tiles_of(geo);
-  k_forward<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo, d_vol1, d_proj);
+  k_forward<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo, d_volq, d_proj);
   return cudaGetLastError();
 }
 

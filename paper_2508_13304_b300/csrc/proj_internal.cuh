@@ -110,8 +110,8 @@ constexpr int kGbViews = 8;
 cudaError_t launch_setup(const float* d_pose, int n_pose, const double* d_views, const int* d_inst_view,
                          const int* d_inst_pose, int n_inst, Geo geo, InstTable* d_inst, PoseTable* d_ptab,
                          int* d_status, cudaStream_t s);
-cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float* d_vol1, float4* d_vol4, cudaStream_t s);
-cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const float* d_vol1, float* d_proj,
+cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float4* d_vol4, cudaStream_t s);
+cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_volq, float* d_proj,
                            cudaStream_t s);
 cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long* d_count, cudaStream_t s);
 // warp_width: rays per warp row of the 16x16 tile (2, 4, 8 or 16; other values use 4)
