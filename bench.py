@@ -873,8 +873,7 @@ def main():
     w = workload(args.n_cand)
     g = w["geom"]
     iv, ip = instance_maps(args.n_cand, g.n_views)
-    P = pb.Projector(g, n_pose=args.n_cand, inst_view=iv, inst_pose=ip,
-                     ops=pb.PROJ_OP_FORWARD | pb.PROJ_OP_FORWARD_GRAD)
+    P = pb.Projector(g, n_pose=args.n_cand, inst_view=iv, inst_pose=ip, ops=pb.PROJ_OP_FORWARD_GRAD)
     mu_d = torch.from_numpy(w["mu"]).to(dev)
     pose_d = torch.from_numpy(w["poses"]).to(dev)
     # target projections at the true pose, rendered once by the forward projector (input data only)

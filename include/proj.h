@@ -157,10 +157,12 @@ int proj_plan_destroy(proj_plan plan);
 int proj_workspace_size(proj_plan plan, size_t *bytes);
 
 /* Prepare the volume for the ray-driven calls (Sec. II-C.1: grad mu by
- * central differences of the zero-padded volume): writes a zero-bordered
- * copy of mu and, when PROJ_OP_FORWARD_GRAD is enabled, a float4
+ * central differences of the zero-padded volume): writes into the workspace,
+ * when PROJ_OP_FORWARD is enabled, zero-bordered cell records of mu (the
+ * four corners of each cell's xy face, two copies with rows along x and y)
+ * and, when PROJ_OP_FORWARD_GRAD is enabled, a float4
  * (mu, d mu/dx', d mu/dy', d mu/dz') volume (per mm, object frame) on the
- * index grid [-1, n]^3 into the workspace.
+ * index grid [-1, n]^3 and its copy with rows along y.
  *   d_mu  [nz][ny][nx] FP32.
  * Must run before proj_forward / proj_forward_pose_grad; stays valid until
  * the workspace is reused for another volume. */

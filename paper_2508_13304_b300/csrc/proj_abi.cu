@@ -61,7 +61,7 @@ struct proj_plan_s {
   bool timing = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // workspace layout (byte offsets; 0 = buffer absent, the status word sits at 0)
-  size_t off_status = 0, off_inst = 0, off_ptab = 0, off_volq = 0, off_vol4 = 0, off_vol4y = 0, off_part_f = 0,
+  size_t off_status = 0, off_inst = 0, off_ptab = 0, off_volq = 0, off_volqy = 0, off_vol4 = 0, off_vol4y = 0, off_part_f = 0,
          off_det4 = 0,
          off_part_b = 0, off_acc = 0, off_sharp_m = 0, off_sharp_part = 0, ws_bytes = 0;
 };
@@ -75,6 +75,7 @@ struct WsView {
   InstTable* inst = nullptr;
   PoseTable* ptab = nullptr;
   float4* volq = nullptr;
+  float4* volqy = nullptr;
   float4* vol4 = nullptr;
   float4* vol4y = nullptr;
   float* part_f = nullptr;
@@ -93,6 +94,7 @@ int check_ws(const proj_plan_s* p, void* d_ws, size_t ws_bytes, WsView* w) {
   w->inst = reinterpret_cast<InstTable*>(b + p->off_inst);
   w->ptab = reinterpret_cast<PoseTable*>(b + p->off_ptab);
   w->volq = p->off_volq ? reinterpret_cast<float4*>(b + p->off_volq) : nullptr;
+  w->volqy = p->off_volqy ? reinterpret_cast<float4*>(b + p->off_volqy) : nullptr;
   w->vol4 = p->off_vol4 ? reinterpret_cast<float4*>(b + p->off_vol4) : nullptr;
   w->vol4y = p->off_vol4y ? reinterpret_cast<float4*>(b + p->off_vol4y) : nullptr;
   w->part_f = p->off_part_f ? reinterpret_cast<float*>(b + p->off_part_f) : nullptr;
@@ -260,7 +262,9 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   p->off_inst = take(sizeof(InstTable) * (size_t)n_inst);
   p->off_ptab = take(sizeof(PoseTable) * (size_t)n_pose);
   const size_t npad_sz = (size_t)npad;
-  p->off_volq = (ops & PROJ_OP_FORWARD) ? take(sizeof(float4) * npad_sz) : 0;
+  const size_t nrec = (size_t)(G.nx + 2) * (G.ny + 2) * record_slices(G.nz);
+  p->off_volq = (ops & PROJ_OP_FORWARD) ? take(sizeof(float4) * nrec) : 0;
+  p->off_volqy = (ops & PROJ_OP_FORWARD) ? take(sizeof(float4) * nrec) : 0;
   p->off_vol4 = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float4) * (size_t)npad2) : 0;
   p->off_vol4y = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float4) * (size_t)npad2y) : 0;
   p->off_part_f = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float) * kRec * (size_t)n_inst * p->n_tiles) : 0;
@@ -364,6 +368,7 @@ int proj_set_volume(proj_plan p, const float* d_mu, void* d_ws, size_t ws_bytes,
   if ((rc = check_device(p))) return rc;
   cudaError_t e = launch_volume_prep(d_mu, p->geo, w.volq, w.vol4, (cudaStream_t)stream);
   if (e == cudaSuccess && w.vol4y) e = launch_volume_yfast(w.vol4, p->geo, w.vol4y, (cudaStream_t)stream);
+  if (e == cudaSuccess && w.volqy) e = launch_records_yfast(w.volq, p->geo, w.volqy, (cudaStream_t)stream);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "volume preparation launch");
 }
 
@@ -378,7 +383,7 @@ int proj_forward(proj_plan p, const float* d_pose, float* d_proj, void* d_ws, si
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = setup(p, d_pose, w, s))) return rc;
   mark(p, true, s);
-  cudaError_t e = launch_forward(w.inst, p->n_inst, p->geo, w.volq, d_proj, s);
+  cudaError_t e = launch_forward(w.inst, p->n_inst, p->geo, w.volq, w.volqy, d_proj, s);
   mark(p, false, s);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "forward launch");
 }

@@ -116,6 +116,22 @@ __device__ __forceinline__ Cell locate(float fx, float fy, float fz, const Geo& 
   return c;
 }
 
+// Cell records of the DRR march (YF = 0: rows along x; 1: the copy with rows
+// along y), z slices interleaved in pairs as in the (mu, grad mu) volumes.
+template <int YF>
+__device__ __forceinline__ Cell locate_q(float fx, float fy, float fz, const Geo& g) {
+  const int ix = min(max(__float2int_rd(fx), 0), g.nx);
+  const int iy = min(max(__float2int_rd(fy), 0), g.ny);
+  const int iz = min(max(__float2int_rd(fz), 0), g.nz);
+  Cell c;
+  c.ax = fx - (float)ix;
+  c.ay = fy - (float)iy;
+  c.az = fz - (float)iz;
+  c.idx = YF ? ((((iz >> 1) * g.px + ix) * g.py + iy) << 1) + (iz & 1)
+             : ((((iz >> 1) * g.py + iy) * g.px + ix) << 1) + (iz & 1);
+  return c;
+}
+
 // YF = 0: the pitched (mu, grad mu) volume with x fastest; YF = 1: its copy
 // with y fastest.  In both, the two slices of a z pair are interleaved element
 // by element, so the two detector rows of a quarter-warp's 4 x 2 ray patch
@@ -179,7 +195,8 @@ __global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ m
     }
     const int zz1 = z - 1;
     if (in1xy && zz1 >= 0 && zz1 < g.pz)
-      volq[((size_t)zz1 * g.py + y1) * g.px + x1] = make_float4(m, at(i + 1, j, k), at(i, j + 1, k), at(i + 1, j + 1, k));
+      volq[((((size_t)(zz1 >> 1) * g.py + y1) * g.px + x1) << 1) + (zz1 & 1)] =
+          make_float4(m, at(i + 1, j, k), at(i, j + 1, k), at(i + 1, j + 1, k));
     m_prev = m;
     m = m_next;
   }
@@ -187,28 +204,36 @@ __global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ m
 
 // ---------------------------------------------------------------- K2
 
+// Corners of a sample's cell: the xy face at z in one 16-byte cell record,
+// the face at z + 1 in the record of the slice above (the neighbouring slot
+// for an even slice, the next pair's slot for an odd one).
+template <int YF>
+__device__ __forceinline__ float drr_ray(const InstTable& T, const Geo& g, int iu, int iv,
+                                         const float4* __restrict__ volq) {
+  float acc = 0.f;
+  Ray r;
+  if (!ray_setup(T, g, iu, iv, r)) return acc;
+  const int szp = 2 * g.px * g.py;
+  for (int k = r.k0; k <= r.k1; ++k) {
+    const float kf = (float)k;
+    const Cell c = locate_q<YF>(fmaf(kf, r.dx, r.ax), fmaf(kf, r.dy, r.ay), fmaf(kf, r.dz, r.az), g);
+    const float4 f0 = __ldg(volq + c.idx), f1 = __ldg(volq + c.idx + ((c.idx & 1) ? szp - 1 : 1));
+    const float c0 = lerp(lerp(f0.x, f0.y, c.ax), lerp(f0.z, f0.w, c.ax), c.ay);
+    const float c1 = lerp(lerp(f1.x, f1.y, c.ax), lerp(f1.z, f1.w, c.ax), c.ay);
+    acc += lerp(c0, c1, c.az);
+  }
+  return acc;
+}
+
 __global__ void __launch_bounds__(kMarchThreads) k_forward(const InstTable* __restrict__ inst, int n_tiles,
                                                            int tiles_u, Geo g, const float4* __restrict__ volq,
-                                                           float* __restrict__ proj) {
+                                                           const float4* __restrict__ volqy, float* __restrict__ proj) {
   const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
   int iu, iv;
   if (!tile_pixel(tile, tiles_u, g, iu, iv)) return;
   const InstTable& T = inst[n];
   float acc = 0.f;
-  Ray r;
-  if (T.valid && ray_setup(T, g, iu, iv, r)) {
-    const int pxy = g.px * g.py;
-    // corners of the sample's cell: the xy face at z in one 16-byte cell
-    // record, the face at z + 1 in the record one slice up
-    for (int k = r.k0; k <= r.k1; ++k) {
-      const float kf = (float)k;
-      const Cell c = locate(fmaf(kf, r.dx, r.ax), fmaf(kf, r.dy, r.ay), fmaf(kf, r.dz, r.az), g);
-      const float4 f0 = __ldg(volq + c.idx), f1 = __ldg(volq + c.idx + pxy);
-      const float c0 = lerp(lerp(f0.x, f0.y, c.ax), lerp(f0.z, f0.w, c.ax), c.ay);
-      const float c1 = lerp(lerp(f1.x, f1.y, c.ax), lerp(f1.z, f1.w, c.ax), c.ay);
-      acc += lerp(c0, c1, c.az);
-    }
-  }
+  if (T.valid) acc = (volqy && T.yfast) ? drr_ray<1>(T, g, iu, iv, volqy) : drr_ray<0>(T, g, iu, iv, volq);
   proj[((size_t)n * g.nv + iv) * g.nu + iu] = g.step * acc;
 }
 
@@ -664,10 +689,10 @@ cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float
   return cudaGetLastError();
 }
 
-cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_volq, float* d_proj,
-                           cudaStream_t s) {
+cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_volq, const float4* d_volqy,
+                           float* d_proj, cudaStream_t s) {
   const int nt = tiles_of(geo);
-  k_forward<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo, d_volq, d_proj);
+  k_forward<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo, d_volq, d_volqy, d_proj);
   return cudaGetLastError();
 }
 
@@ -728,27 +753,37 @@ cudaError_t launch_gather_probe(const InstTable* d_inst, int n_inst, Geo geo, co
 namespace {
 constexpr int kTr = 32;
 
-// One z slice tile of 32 x 32 (x, y): read rows along x, write rows along y.
-__global__ void k_volume_yfast(const float4* __restrict__ v, Geo g, float4* __restrict__ vy) {
+// One z slice tile of 32 x 32 (x, y) of a volume stored in interleaved z
+// pairs: reads element (x, y, z) at (((z >> 1) * sqy + y) * sqx + x) * 2 + (z & 1)
+// for x < X, y < Y (zero beyond), writes it at
+// (((z >> 1) * dqx + x) * dqy + y) * 2 + (z & 1) for x < dqx, y < dqy: rows
+// along x in, rows along y out.
+__global__ void k_transpose_xy(const float4* __restrict__ v, int X, int Y, int sqx, int sqy, float4* __restrict__ vy,
+                               int dqx, int dqy) {
   __shared__ float4 t[kTr][kTr + 1];
-  const int X = g.nx + 4, Y = g.ny + 4;
   const int x0 = blockIdx.x * kTr, y0 = blockIdx.y * kTr, z = blockIdx.z;
   for (int j = threadIdx.y; j < kTr; j += blockDim.y) {
     const int x = x0 + threadIdx.x, y = y0 + j;
-    t[j][threadIdx.x] = (x < X && y < Y) ? v[((((size_t)(z >> 1) * g.qy + y) * g.qx + x) << 1) + (z & 1)]
+    t[j][threadIdx.x] = (x < X && y < Y) ? v[((((size_t)(z >> 1) * sqy + y) * sqx + x) << 1) + (z & 1)]
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
   for (int j = threadIdx.y; j < kTr; j += blockDim.y) {
     const int y = y0 + threadIdx.x, x = x0 + j;
-    if (x < g.rqx && y < g.rqy) vy[((((size_t)(z >> 1) * g.rqx + x) * g.rqy + y) << 1) + (z & 1)] = t[threadIdx.x][j];
+    if (x < dqx && y < dqy) vy[((((size_t)(z >> 1) * dqx + x) * dqy + y) << 1) + (z & 1)] = t[threadIdx.x][j];
   }
 }
 }  // namespace
 
 cudaError_t launch_volume_yfast(const float4* d_vol4, Geo geo, float4* d_vol4y, cudaStream_t s) {
   dim3 grid(ceil_div(geo.rqx, kTr), ceil_div(geo.rqy, kTr), geo.qz), block(kTr, 8);
-  k_volume_yfast<<<grid, block, 0, s>>>(d_vol4, geo, d_vol4y);
+  k_transpose_xy<<<grid, block, 0, s>>>(d_vol4, geo.nx + 4, geo.ny + 4, geo.qx, geo.qy, d_vol4y, geo.rqx, geo.rqy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_records_yfast(const float4* d_volq, Geo geo, float4* d_volqy, cudaStream_t s) {
+  dim3 grid(ceil_div(geo.px, kTr), ceil_div(geo.py, kTr), record_slices(geo.nz)), block(kTr, 8);
+  k_transpose_xy<<<grid, block, 0, s>>>(d_volq, geo.px, geo.py, geo.px, geo.py, d_volqy, geo.px, geo.py);
   return cudaGetLastError();
 }
 

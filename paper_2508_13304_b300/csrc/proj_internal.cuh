@@ -111,8 +111,10 @@ cudaError_t launch_setup(const float* d_pose, int n_pose, const double* d_views,
                          const int* d_inst_pose, int n_inst, Geo geo, InstTable* d_inst, PoseTable* d_ptab,
                          int* d_status, cudaStream_t s);
 cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float4* d_vol4, cudaStream_t s);
-cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_volq, float* d_proj,
-                           cudaStream_t s);
+// d_volqy: the copy of the cell records with rows along y (instances with yfast
+// set march it), or null (all march d_volq)
+cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_volq, const float4* d_volqy,
+                           float* d_proj, cudaStream_t s);
 cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long* d_count, cudaStream_t s);
 // warp_width: rays per warp row of the 16x16 tile (2, 4, 8 or 16; other values use 4)
 // d_vol4y: the y-fast copy (instances with yfast set march it), or null (all march d_vol4)
@@ -124,6 +126,7 @@ cudaError_t launch_gather_probe(const InstTable* d_inst, int n_inst, Geo geo, co
                                 const float4* d_vol4y, float* d_sink, cudaStream_t s);
 // y-fast copy of the pitched (mu, grad mu) volume (tiled transpose of every z slice)
 cudaError_t launch_volume_yfast(const float4* d_vol4, Geo geo, float4* d_vol4y, cudaStream_t s);
+cudaError_t launch_records_yfast(const float4* d_volq, Geo geo, float4* d_volqy, cudaStream_t s);
 cudaError_t launch_forward_grad_reduce(const InstTable* d_inst, const PoseTable* d_ptab, int n_pose,
                                        const int* d_pose_ptr, const int* d_pose_idx, int n_tiles, Geo geo,
                                        int loss, const float* d_part, float* d_grad, float* d_loss,
@@ -159,6 +162,9 @@ inline void volume_pitches(int nx, int ny, int nz, int* qx, int* qy, int* qz) {
   *qy = y;
   *qz = (nz + 5) & ~1;  // even: z slices are stored in interleaved pairs
 }
+
+// z slices of the DRR march's cell records: n + 2, rounded up to even (pairs).
+__host__ __device__ constexpr int record_slices(int nz) { return (nz + 3) & ~1; }
 
 // The same rule for the copy whose rows run along y: row pitch (y) = 2 mod 8,
 // slice pitch = 4 mod 8 (float4 units).
