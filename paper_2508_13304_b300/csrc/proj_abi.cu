@@ -81,7 +81,7 @@ struct WsView {
   float* part_f = nullptr;
   float4* det4 = nullptr;
   float* part_b = nullptr;
-  float* acc = nullptr;
+  float4* acc = nullptr;
 };
 
 int check_ws(const proj_plan_s* p, void* d_ws, size_t ws_bytes, WsView* w) {
@@ -100,7 +100,7 @@ int check_ws(const proj_plan_s* p, void* d_ws, size_t ws_bytes, WsView* w) {
   w->part_f = p->off_part_f ? reinterpret_cast<float*>(b + p->off_part_f) : nullptr;
   w->det4 = p->off_det4 ? reinterpret_cast<float4*>(b + p->off_det4) : nullptr;
   w->part_b = p->off_part_b ? reinterpret_cast<float*>(b + p->off_part_b) : nullptr;
-  w->acc = p->off_acc ? reinterpret_cast<float*>(b + p->off_acc) : nullptr;
+  w->acc = p->off_acc ? reinterpret_cast<float4*>(b + p->off_acc) : nullptr;
   return PROJ_OK;
 }
 
@@ -270,7 +270,7 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   p->off_part_f = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float) * kRec * (size_t)n_inst * p->n_tiles) : 0;
   p->off_det4 = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float4) * (size_t)n_inst * (G.nu + 4) * (G.nv + 4)) : 0;
   p->off_part_b = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float) * 12 * (size_t)n_inst * p->bp_blocks) : 0;
-  p->off_acc = (ops & PROJ_OP_ADJOINT) ? take(sizeof(float) * npad_sz) : 0;
+  p->off_acc = (ops & PROJ_OP_ADJOINT) ? take(sizeof(float4) * npad_sz) : 0;
   if (ops & PROJ_OP_SHARPNESS) {
     p->off_sharp_m = take(sizeof(float) * (size_t)G.nx * G.ny * G.nz);
     p->off_sharp_part = take(sizeof(double) * (2 * (size_t)sharpness_blocks(g) + 2));

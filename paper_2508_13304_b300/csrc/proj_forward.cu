@@ -586,9 +586,20 @@ __global__ void k_forward_grad_reduce(const InstTable* __restrict__ inst, const 
 
 // ---------------------------------------------------------------- K7
 
+// Vector reduction into global memory (no return value): four FP32 adds to
+// one 16-byte-aligned record, one L2 operation.
+__device__ __forceinline__ void red_add4(float4* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+// The transpose scatters into cell records laid out like the forward march's
+// (x fastest, no pair interleave): record (x, y, z) accumulates the weights of
+// the four corners of cell (x, y, z)'s xy face, so a sample adds its 8
+// corner weights with two vector reductions (its record and the record one
+// slice up); k_unrecord then sums the four records that share each voxel.
 __global__ void __launch_bounds__(kMarchThreads) k_forward_adjoint(const InstTable* __restrict__ inst, int n_tiles,
                                                                    int tiles_u, Geo g, const float* __restrict__ y,
-                                                                   float* __restrict__ acc) {
+                                                                   float4* __restrict__ acc) {
   const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
   int iu, iv;
   if (!tile_pixel(tile, tiles_u, g, iu, iv)) return;
@@ -597,30 +608,15 @@ __global__ void __launch_bounds__(kMarchThreads) k_forward_adjoint(const InstTab
   Ray r;
   if (yi == 0.f || !T.valid || !ray_setup(T, g, iu, iv, r)) return;
   const int pxy = g.px * g.py;
-  // Samples 0.5 voxel apart often fall in the same cell, or in a cell that
-  // shares a face with the previous one.  The 8 corner weights (corner q =
-  // offsets (q & 1, (q >> 1) & 1, q >> 2)) are summed in registers while the
-  // cell is unchanged; on a step to a face neighbour the 4 shared corners
-  // carry over and only the 4 left behind are added to the volume; any
-  // other step adds all 8.
+  // The 8 corner weights (corner q = offsets (q & 1, (q >> 1) & 1, q >> 2))
+  // are summed in registers while the ray stays in one cell.  On a step to
+  // the cell above or below, the shared face's record is the new cell's too,
+  // so its 4 weights carry over and only the face left behind is reduced;
+  // any other step reduces both faces.
   int cur = -1;
   float w[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const int off[8] = {0, 1, g.px, g.px + 1, pxy, pxy + 1, pxy + g.px, pxy + g.px + 1};
-  auto put = [&](int idx, int q) {
-    atomicAdd(acc + idx + off[q], yi * w[q]);
-    w[q] = 0.f;
-  };
-  // move along one axis: corners with bit `bit` == from go to the volume,
-  // corners with bit == 1 - from shift into their place
-  auto step_axis = [&](int bit, int from) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (((q >> bit) & 1) == from) {
-        const int o = q ^ (1 << bit);
-        put(cur, q);
-        w[q] = w[o];
-        w[o] = 0.f;
-      }
+  auto face = [&](int rec, int q) {
+    red_add4(acc + rec, yi * w[q], yi * w[q + 1], yi * w[q + 2], yi * w[q + 3]);
   };
   for (int k = r.k0; k <= r.k1; ++k) {
     const float kf = (float)k;
@@ -628,21 +624,25 @@ __global__ void __launch_bounds__(kMarchThreads) k_forward_adjoint(const InstTab
     if (c.idx != cur) {
       const int d = c.idx - cur;
       if (cur < 0) {
-      } else if (d == 1) {
-        step_axis(0, 0);
-      } else if (d == -1) {
-        step_axis(0, 1);
-      } else if (d == g.px) {
-        step_axis(1, 0);
-      } else if (d == -g.px) {
-        step_axis(1, 1);
       } else if (d == pxy) {
-        step_axis(2, 0);
-      } else if (d == -pxy) {
-        step_axis(2, 1);
-      } else {
+        face(cur, 0);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) put(cur, q);
+        for (int q = 0; q < 4; ++q) {
+          w[q] = w[q + 4];
+          w[q + 4] = 0.f;
+        }
+      } else if (d == -pxy) {
+        face(cur + pxy, 4);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          w[q + 4] = w[q];
+          w[q] = 0.f;
+        }
+      } else {
+        face(cur, 0);
+        face(cur + pxy, 4);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w[q] = 0.f;
       }
       cur = c.idx;
     }
@@ -657,18 +657,21 @@ __global__ void __launch_bounds__(kMarchThreads) k_forward_adjoint(const InstTab
     w[7] += c.ax * c.ay * c.az;
   }
   if (cur >= 0) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) put(cur, q);
+    face(cur, 0);
+    face(cur + pxy, 4);
   }
 }
 
-// Interior of the padded accumulation volume -> [nz][ny][nx].
-__global__ void k_unpad(const float* __restrict__ acc, Geo g, float* __restrict__ vol) {
+// Voxel (i, j, k) is padded point (i+1, j+1, k+1): corner 0 of record
+// (i+1, j+1), corner 1 of record (i, j+1), corner 2 of record (i+1, j) and
+// corner 3 of record (i, j), all in slice k+1.  Writes [nz][ny][nx].
+__global__ void k_unrecord(const float4* __restrict__ acc, Geo g, float* __restrict__ vol) {
   const long long n = (long long)g.nx * g.ny * g.nz;
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(p % g.nx), j = (int)((p / g.nx) % g.ny), k = (int)(p / ((long long)g.nx * g.ny));
-    vol[p] = acc[((size_t)(k + 1) * g.py + (j + 1)) * g.px + (i + 1)];
+    const float4* a = acc + ((size_t)(k + 1) * g.py + j) * g.px + i;
+    vol[p] = (__ldg(a + g.px + 1).x + __ldg(a + g.px).y) + (__ldg(a + 1).z + __ldg(a).w);
   }
 }
 
@@ -838,17 +841,17 @@ cudaError_t launch_forward_grad_reduce(const InstTable* d_inst, const PoseTable*
   return cudaGetLastError();
 }
 
-cudaError_t launch_forward_adjoint(const InstTable* d_inst, int n_inst, Geo geo, const float* d_y, float* d_acc,
+cudaError_t launch_forward_adjoint(const InstTable* d_inst, int n_inst, Geo geo, const float* d_y, float4* d_acc,
                                    float* d_vol, cudaStream_t s) {
   const long long npad = (long long)geo.px * geo.py * geo.pz;
-  cudaError_t e = cudaMemsetAsync(d_acc, 0, sizeof(float) * npad, s);
+  cudaError_t e = cudaMemsetAsync(d_acc, 0, sizeof(float4) * npad, s);
   if (e != cudaSuccess) return e;
   const int nt = tiles_of(geo);
   k_forward_adjoint<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo, d_y, d_acc);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long n = (long long)geo.nx * geo.ny * geo.nz;
-  k_unpad<<<elementwise_grid(n), 256, 0, s>>>(d_acc, geo, d_vol);
+  k_unrecord<<<elementwise_grid(n), 256, 0, s>>>(d_acc, geo, d_vol);
   return cudaGetLastError();
 }
 

@@ -136,7 +136,7 @@ cudaError_t launch_forward_grad_batch(const BatchProblem* d_probs, int n_probs, 
                                       unsigned long long* d_counter, int n_blocks, int loss_all, cudaStream_t s);
 int forward_grad_batch_blocks_per_sm(int loss_all);
 cudaError_t launch_forward_adjoint(const InstTable* d_inst, int n_inst, Geo geo, const float* d_y,
-                                   float* d_acc, float* d_vol, cudaStream_t s);
+                                   float4* d_acc, float* d_vol, cudaStream_t s);
 cudaError_t launch_detector_prep(const float* d_proj, int n_inst, Geo geo, float4* d_det4, cudaStream_t s);
 cudaError_t launch_back(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float* d_proj,
                         float* d_vol, cudaStream_t s);
