@@ -248,8 +248,14 @@ def secondary(pb, torch, dev, w, mu_d, flush):
     gradb = torch.empty((360, 6), device=dev)
     vv = 360 * 256 ** 3
     ms = _timed(lambda: pb.proj_back(Pb.plan, img, motion, pb.PROJ_W_FDK, volb, Pb.ws), Pb.plan, pb, flush)
-    out["back"] = {"kernel": "k_back", "config": "256^3, 360 views of 512^2, FDK weight", "kernel_ms": ms,
-                   "voxel_view_updates_per_s": vv / (ms * 1e-3)}
+    out["back"] = {"kernel": "k_detector_records + k_back", "config": "256^3, 360 views of 512^2, FDK weight",
+                   "kernel_ms": ms, "voxel_view_updates_per_s": vv / (ms * 1e-3)}
+    imgb = torch.empty_like(img)
+    ms = _timed(lambda: pb.proj_back_adjoint(Pb.plan, volb, motion, pb.PROJ_W_FDK, imgb, Pb.ws), Pb.plan, pb, flush)
+    out["back_adjoint"] = {"kernel": "k_back_adjoint + k_detector_unrecord",
+                           "config": "256^3, 360 views of 512^2, FDK weight", "kernel_ms": ms,
+                           "voxel_view_updates_per_s": vv / (ms * 1e-3)}
+    del imgb
     ms = _timed(lambda: pb.proj_back_pose_grad(Pb.plan, img, motion, pb.PROJ_W_FDK, wvol, gradb, Pb.ws), Pb.plan,
                 pb, flush)
     out["back_pose_grad"] = {"kernel": "k_back_grad", "config": "256^3, 360 views of 512^2, FDK weight",

@@ -141,8 +141,8 @@ typedef struct proj_plan_s *proj_plan;
  *   inst_pose  host [n_inst], pose of each instance in [0, n_pose).
  *   ops        OR of PROJ_OP_* the plan must support.
  *   out        receives the plan.
- * Limits: ny, nz, nv <= 65000; with PROJ_OP_BACK_GRAD at most 65535
- * instances; padded volumes below 2^31 voxels.
+ * Limits: ny, nz, nv <= 65000; with PROJ_OP_BACK or PROJ_OP_BACK_GRAD at
+ * most 65535 instances; padded volumes below 2^31 voxels.
  * Errors: PROJ_E_ARG (bad sizes, indices, non-finite or degenerate
  * geometry, singular detector basis, limits above), PROJ_E_CUDA (table
  * allocation). */

@@ -63,7 +63,7 @@ struct proj_plan_s {
   // workspace layout (byte offsets; 0 = buffer absent, the status word sits at 0)
   size_t off_status = 0, off_inst = 0, off_ptab = 0, off_volq = 0, off_volqy = 0, off_vol4 = 0, off_vol4y = 0, off_part_f = 0,
          off_det4 = 0,
-         off_part_b = 0, off_acc = 0, off_sharp_m = 0, off_sharp_part = 0, ws_bytes = 0;
+         off_part_b = 0, off_detq = 0, off_acc = 0, off_sharp_m = 0, off_sharp_part = 0, ws_bytes = 0;
 };
 
 namespace {
@@ -82,6 +82,7 @@ struct WsView {
   float4* det4 = nullptr;
   float* part_b = nullptr;
   float4* acc = nullptr;
+  float4* detq = nullptr;
 };
 
 int check_ws(const proj_plan_s* p, void* d_ws, size_t ws_bytes, WsView* w) {
@@ -101,6 +102,7 @@ int check_ws(const proj_plan_s* p, void* d_ws, size_t ws_bytes, WsView* w) {
   w->det4 = p->off_det4 ? reinterpret_cast<float4*>(b + p->off_det4) : nullptr;
   w->part_b = p->off_part_b ? reinterpret_cast<float*>(b + p->off_part_b) : nullptr;
   w->acc = p->off_acc ? reinterpret_cast<float4*>(b + p->off_acc) : nullptr;
+  w->detq = p->off_detq ? reinterpret_cast<float4*>(b + p->off_detq) : nullptr;
   return PROJ_OK;
 }
 
@@ -166,8 +168,8 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   // launch grids put volume rows / slices, detector rows and (for the detector stack) instances in
   // the y and z grid dimensions
   if (G.ny > 65000 || G.nz > 65000 || G.nv > 65000) return fail(PROJ_E_ARG, "ny, nz and nv must be <= 65000");
-  if ((ops & PROJ_OP_BACK_GRAD) && n_inst > 65535)
-    return fail(PROJ_E_ARG, "PROJ_OP_BACK_GRAD supports at most 65535 instances per plan");
+  if ((ops & (PROJ_OP_BACK | PROJ_OP_BACK_GRAD)) && n_inst > 65535)
+    return fail(PROJ_E_ARG, "PROJ_OP_BACK and PROJ_OP_BACK_GRAD support at most 65535 instances per plan");
   for (int v = 0; v < G.n_views; ++v) {
     const double* w = G.views + 12 * v;
     for (int a = 0; a < 12; ++a)
@@ -270,6 +272,7 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   p->off_part_f = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float) * kRec * (size_t)n_inst * p->n_tiles) : 0;
   p->off_det4 = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float4) * (size_t)n_inst * (G.nu + 4) * (G.nv + 4)) : 0;
   p->off_part_b = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float) * 12 * (size_t)n_inst * p->bp_blocks) : 0;
+  p->off_detq = (ops & PROJ_OP_BACK) ? take(sizeof(float4) * (size_t)n_inst * (G.nu + 1) * (G.nv + 1)) : 0;
   p->off_acc = (ops & PROJ_OP_ADJOINT) ? take(sizeof(float4) * npad_sz) : 0;
   if (ops & PROJ_OP_SHARPNESS) {
     p->off_sharp_m = take(sizeof(float) * (size_t)G.nx * G.ny * G.nz);
@@ -439,7 +442,7 @@ int proj_back(proj_plan p, const float* d_proj, const float* d_pose, int weight,
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = setup(p, d_pose, w, s))) return rc;
   mark(p, true, s);
-  cudaError_t e = launch_back(w.inst, p->n_inst, p->geo, weight, d_proj, d_vol, s);
+  cudaError_t e = launch_back(w.inst, p->n_inst, p->geo, weight, d_proj, w.detq, d_vol, s);
   mark(p, false, s);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "back-projection launch");
 }
@@ -458,7 +461,7 @@ int proj_back_adjoint(proj_plan p, const float* d_vol, const float* d_pose, int 
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = setup(p, d_pose, w, s))) return rc;
   mark(p, true, s);
-  cudaError_t e = launch_back_adjoint(w.inst, p->n_inst, p->geo, weight, d_vol, d_proj, s);
+  cudaError_t e = launch_back_adjoint(w.inst, p->n_inst, p->geo, weight, d_vol, w.detq, d_proj, s);
   mark(p, false, s);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "back-projection adjoint launch");
 }

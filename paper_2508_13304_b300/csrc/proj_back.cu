@@ -38,10 +38,42 @@ __global__ void k_detector_prep(const float* __restrict__ proj, int n_inst, Geo 
   det4[((size_t)in * qv + y) * qu + x] = make_float4(l, du, dv, 0.f);
 }
 
+// Detector cell records, [n_inst][nv+1][nu+1] float4: record (x, y) holds
+// the four pixels of the bilinear cell whose lower corner is pixel
+// (x-1, y-1), (l(x-1, y-1), l(x, y-1), l(x-1, y), l(x, y)), zero outside the
+// image, so a bilinear sample anywhere in (-1, nu) x (-1, nv) reads its 4
+// corners with one 128-bit load and no edge tests.
+__global__ void k_detector_records(const float* __restrict__ proj, Geo g, float4* __restrict__ detq) {
+  const int ru = g.nu + 1, rv = g.nv + 1;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, in = blockIdx.z;
+  if (x >= ru) return;
+  const int iu = x - 1, iv = y - 1;
+  const float* img = proj + (size_t)in * g.nu * g.nv;
+  detq[((size_t)in * rv + y) * ru + x] = make_float4(pix(img, g.nu, g.nv, iu, iv), pix(img, g.nu, g.nv, iu + 1, iv),
+                                                     pix(img, g.nu, g.nv, iu, iv + 1),
+                                                     pix(img, g.nu, g.nv, iu + 1, iv + 1));
+}
+
+// Pixel (i, j) = lane 0 of record (i+1, j+1), lane 1 of (i, j+1), lane 2 of
+// (i+1, j) and lane 3 of (i, j): the transpose of k_detector_records, which
+// gathers the back-projector transpose's record sums into [n_inst][nv][nu].
+__global__ void k_detector_unrecord(const float4* __restrict__ detq, Geo g, float* __restrict__ proj) {
+  const int ru = g.nu + 1, rv = g.nv + 1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, in = blockIdx.z;
+  if (i >= g.nu) return;
+  const float4* r = detq + ((size_t)in * rv + j) * ru + i;
+  proj[((size_t)in * g.nv + j) * g.nu + i] = (__ldg(r + ru + 1).x + __ldg(r + ru).y) + (__ldg(r + 1).z + __ldg(r).w);
+}
+
+// Vector reduction (no return value): four FP32 adds to one 16-byte record.
+__device__ __forceinline__ void red_add4(float4* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
 // ---------------------------------------------------------------- K5
 
 __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict__ inst, int n_inst, Geo g,
-                                                     int weight, const float* __restrict__ proj,
+                                                     int weight, const float4* __restrict__ detq,
                                                      float* __restrict__ vol) {
   const int ix = blockIdx.x * kBpX + (threadIdx.x & 31);
   const int iy = blockIdx.y * kBpY + (threadIdx.x >> 5);
@@ -59,7 +91,7 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
     const float bv = fmaf(T.Q[4], fy, fmaf(T.Q[1], fx, T.Q[10]));
     const float bw = fmaf(T.Q[5], fy, fmaf(T.Q[2], fx, T.Q[11]));
     const float qz0 = T.Q[6], qz1 = T.Q[7], qz2 = T.Q[8], w0 = T.w0;
-    const float* img = proj + (size_t)n * g.nu * g.nv;
+    const float4* rec = detq + (size_t)n * (g.nu + 1) * (g.nv + 1);
 #pragma unroll
     for (int z = 0; z < kZChunk; ++z) {
       const float fz = (float)(iz0 + z) - g.cz;
@@ -69,17 +101,12 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
       const float u = fmaf(qz0, fz, bu) * rw, v = fmaf(qz1, fz, bv) * rw;
       if (!(u > -1.f && u < fu && v > -1.f && v < fvv)) continue;
       // u in (-1, nu) and v in (-1, nv): the lower corner is in [-1, n-1],
-      // so only the four edges need a test (zero padding outside the image).
+      // record (i0 + 1, j0 + 1)
       const float flu = floorf(u), flv = floorf(v);
       const int i0 = (int)flu, j0 = (int)flv;
       const float au = u - flu, av = v - flv;
-      const bool xl = i0 >= 0, xh = i0 < g.nu - 1, yl = j0 >= 0, yh = j0 < g.nv - 1;
-      const int o = j0 * g.nu + i0;
-      const float v00 = (xl && yl) ? __ldg(img + o) : 0.f;
-      const float v10 = (xh && yl) ? __ldg(img + o + 1) : 0.f;
-      const float v01 = (xl && yh) ? __ldg(img + o + g.nu) : 0.f;
-      const float v11 = (xh && yh) ? __ldg(img + o + g.nu + 1) : 0.f;
-      float val = lerp(lerp(v00, v10, au), lerp(v01, v11, au), av);
+      const float4 q = __ldg(rec + (j0 + 1) * (g.nu + 1) + (i0 + 1));
+      float val = lerp(lerp(q.x, q.y, au), lerp(q.z, q.w, au), av);
       if (weight != PROJ_W_NONE) {
         const float r = w0 * rw;
         val *= r * r;
@@ -265,7 +292,7 @@ __global__ void k_back_grad_reduce(const PoseTable* __restrict__ ptab, const int
 // zeroed by the launcher; float atomics (order-dependent in the last bits).
 __global__ void __launch_bounds__(kBpThreads) k_back_adjoint(const InstTable* __restrict__ inst, int n_inst, Geo g,
                                                              int weight, const float* __restrict__ y,
-                                                             float* __restrict__ proj) {
+                                                             float4* __restrict__ detq) {
   const int ix = blockIdx.x * kBpX + (threadIdx.x & 31);
   const int iy = blockIdx.y * kBpY + (threadIdx.x >> 5);
   const int iz0 = blockIdx.z * kZChunk;
@@ -282,7 +309,7 @@ __global__ void __launch_bounds__(kBpThreads) k_back_adjoint(const InstTable* __
     const float bu = fmaf(T.Q[3], fy, fmaf(T.Q[0], fx, T.Q[9]));
     const float bv = fmaf(T.Q[4], fy, fmaf(T.Q[1], fx, T.Q[10]));
     const float bw = fmaf(T.Q[5], fy, fmaf(T.Q[2], fx, T.Q[11]));
-    float* img = proj + (size_t)n * g.nu * g.nv;
+    float4* rec = detq + (size_t)n * (g.nu + 1) * (g.nv + 1);
 #pragma unroll
     for (int z = 0; z < kZChunk; ++z) {
       if (yv[z] == 0.f) continue;
@@ -300,11 +327,11 @@ __global__ void __launch_bounds__(kBpThreads) k_back_adjoint(const InstTable* __
         const float r = T.w0 * rw;
         val *= r * r;
       }
-      const int o = j0 * g.nu + i0;
-      if (i0 >= 0 && j0 >= 0) atomicAdd(img + o, val * (1.f - au) * (1.f - av));
-      if (i0 < g.nu - 1 && j0 >= 0) atomicAdd(img + o + 1, val * au * (1.f - av));
-      if (i0 >= 0 && j0 < g.nv - 1) atomicAdd(img + o + g.nu, val * (1.f - au) * av);
-      if (i0 < g.nu - 1 && j0 < g.nv - 1) atomicAdd(img + o + g.nu + 1, val * au * av);
+      // the 4 corner weights go to record (i0 + 1, j0 + 1) in one vector
+      // reduction; weights of corners outside the image land in border lanes
+      // that k_detector_unrecord never reads
+      red_add4(rec + (j0 + 1) * (g.nu + 1) + (i0 + 1), val * (1.f - au) * (1.f - av), val * au * (1.f - av),
+               val * (1.f - au) * av, val * au * av);
     }
   }
 }
@@ -319,18 +346,24 @@ cudaError_t launch_detector_prep(const float* d_proj, int n_inst, Geo geo, float
 }
 
 cudaError_t launch_back(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float* d_proj,
-                        float* d_vol, cudaStream_t s) {
+                        float4* d_detq, float* d_vol, cudaStream_t s) {
+  k_detector_records<<<dim3(ceil_div(geo.nu + 1, 128), geo.nv + 1, n_inst), 128, 0, s>>>(d_proj, geo, d_detq);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   dim3 grid(ceil_div(geo.nx, kBpX), ceil_div(geo.ny, kBpY), ceil_div(geo.nz, kZChunk));
-  k_back<<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_proj, d_vol);
+  k_back<<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_detq, d_vol);
   return cudaGetLastError();
 }
 
 cudaError_t launch_back_adjoint(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float* d_y,
-                                float* d_proj, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(d_proj, 0, sizeof(float) * (size_t)n_inst * geo.nu * geo.nv, s);
+                                float4* d_detq, float* d_proj, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(d_detq, 0, sizeof(float4) * (size_t)n_inst * (geo.nu + 1) * (geo.nv + 1), s);
   if (e != cudaSuccess) return e;
   dim3 grid(ceil_div(geo.nx, kBpX), ceil_div(geo.ny, kBpY), ceil_div(geo.nz, kZChunk));
-  k_back_adjoint<<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_y, d_proj);
+  k_back_adjoint<<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_y, d_detq);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_detector_unrecord<<<dim3(ceil_div(geo.nu, 128), geo.nv, n_inst), 128, 0, s>>>(d_detq, geo, d_proj);
   return cudaGetLastError();
 }
 

@@ -138,10 +138,11 @@ int forward_grad_batch_blocks_per_sm(int loss_all);
 cudaError_t launch_forward_adjoint(const InstTable* d_inst, int n_inst, Geo geo, const float* d_y,
                                    float4* d_acc, float* d_vol, cudaStream_t s);
 cudaError_t launch_detector_prep(const float* d_proj, int n_inst, Geo geo, float4* d_det4, cudaStream_t s);
+// d_detq: detector cell records, [n_inst][nv+1][nu+1] float4 scratch
 cudaError_t launch_back(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float* d_proj,
-                        float* d_vol, cudaStream_t s);
+                        float4* d_detq, float* d_vol, cudaStream_t s);
 cudaError_t launch_back_adjoint(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float* d_y,
-                                float* d_proj, cudaStream_t s);
+                                float4* d_detq, float* d_proj, cudaStream_t s);
 cudaError_t launch_back_grad(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float4* d_det4,
                              const float* d_wvol, float* d_part, int n_blocks, cudaStream_t s);
 cudaError_t launch_back_grad_reduce(const PoseTable* d_ptab, int n_pose, const int* d_pose_ptr,
