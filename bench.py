@@ -811,14 +811,16 @@ def main():
         w0 = workload(64)
         g0 = w0["geom"]
         iv0, ip0 = instance_maps(64, g0.n_views)
-        P0 = pb.Projector(g0, n_pose=64, inst_view=iv0, inst_pose=ip0, ops=pb.PROJ_OP_FORWARD)
+        P0 = pb.Projector(g0, n_pose=64, inst_view=iv0, inst_pose=ip0, ops=pb.PROJ_OP_FORWARD | pb.PROJ_OP_ADJOINT)
         pb.proj_enable_kernel_timing(P0.plan)
         P0.set_volume(torch.from_numpy(w0["mu"]).to(dev0))
         pose0 = torch.from_numpy(w0["poses"]).to(dev0)
         out0 = torch.empty((P0.n_inst, g0.nv, g0.nu), device=dev0)
         ms0 = _timed(lambda: pb.proj_forward(P0.plan, pose0, out0, P0.ws), P0.plan, pb, fl)
+        vol0 = torch.empty((g0.nz, g0.ny, g0.nx), device=dev0)
+        ms1 = _timed(lambda: pb.proj_forward_adjoint(P0.plan, out0, pose0, vol0, P0.ws), P0.plan, pb, fl)
         print(json.dumps({"section": "forward", "kernel": "k_forward", "kernel_ms": ms0,
-                          "config": "256^3, 128 view instances of 384^2"}), flush=True)
+                          "k_forward_adjoint_ms": ms1, "config": "256^3, 128 view instances of 384^2"}), flush=True)
         return
     if args.section == "c1":
         dev0 = torch.device("cuda", local)
@@ -861,7 +863,9 @@ def main():
         ms_b = _timed(lambda: pb.proj_back(Pb.plan, img, motion, pb.PROJ_W_FDK, volb, Pb.ws), Pb.plan, pb, fl)
         ms_g = _timed(lambda: pb.proj_back_pose_grad(Pb.plan, img, motion, pb.PROJ_W_FDK, wvol, gradb, Pb.ws),
                       Pb.plan, pb, fl)
-        print(json.dumps({"section": "back", "k_back_ms": ms_b, "k_back_grad_ms": ms_g,
+        imgb = torch.empty_like(img)
+        ms_a = _timed(lambda: pb.proj_back_adjoint(Pb.plan, volb, motion, pb.PROJ_W_FDK, imgb, Pb.ws), Pb.plan, pb, fl)
+        print(json.dumps({"section": "back", "k_back_ms": ms_b, "k_back_grad_ms": ms_g, "k_back_adjoint_ms": ms_a,
                           "config": "256^3, 360 views of 512^2, FDK weight"}), flush=True)
         return
     if args.section == "gemm":

@@ -45,6 +45,17 @@ __device__ __forceinline__ bool tile_pixel(int tile, int tiles_u, const Geo& g, 
   return iu < g.nu && iv < g.nv;
 }
 
+// Band-major block order for the scalar march and its transpose: the grid
+// runs through every instance's tiles of one row of tiles before the next
+// row.  Detector v runs along the orbit axis z, so the blocks resident at any
+// time touch one slab of the volume's cell records, which stays in L2.
+__device__ __forceinline__ void band_major_tile(int n_tiles, int tiles_u, int& n, int& tile) {
+  const int n_inst = gridDim.x / n_tiles;
+  const int b = blockIdx.x, tu = b % tiles_u, rest = b / tiles_u;
+  n = rest % n_inst;
+  tile = (rest / n_inst) * tiles_u + tu;
+}
+
 struct Ray {
   float ax, ay, az;  // padded index coordinates of the source (sample k = 0)
   float dx, dy, dz;  // index units per step
@@ -228,7 +239,8 @@ __device__ __forceinline__ float drr_ray(const InstTable& T, const Geo& g, int i
 __global__ void __launch_bounds__(kMarchThreads) k_forward(const InstTable* __restrict__ inst, int n_tiles,
                                                            int tiles_u, Geo g, const float4* __restrict__ volq,
                                                            const float4* __restrict__ volqy, float* __restrict__ proj) {
-  const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
+  int n, tile;
+  band_major_tile(n_tiles, tiles_u, n, tile);
   int iu, iv;
   if (!tile_pixel(tile, tiles_u, g, iu, iv)) return;
   const InstTable& T = inst[n];
@@ -600,7 +612,8 @@ __device__ __forceinline__ void red_add4(float4* p, float a, float b, float c, f
 __global__ void __launch_bounds__(kMarchThreads) k_forward_adjoint(const InstTable* __restrict__ inst, int n_tiles,
                                                                    int tiles_u, Geo g, const float* __restrict__ y,
                                                                    float4* __restrict__ acc) {
-  const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
+  int n, tile;
+  band_major_tile(n_tiles, tiles_u, n, tile);
   int iu, iv;
   if (!tile_pixel(tile, tiles_u, g, iu, iv)) return;
   const InstTable& T = inst[n];
