@@ -45,7 +45,7 @@ __device__ __forceinline__ bool tile_pixel(int tile, int tiles_u, const Geo& g, 
   return iu < g.nu && iv < g.nv;
 }
 
-// Band-major block order for the scalar march and its transpose: the grid
+// Band-major block order for the marches and the forward transpose: the grid
 // runs through every instance's tiles of one row of tiles before the next
 // row.  Detector v runs along the orbit axis z, so the blocks resident at any
 // time touch one slab of the volume's cell records, which stays in L2.
@@ -392,7 +392,8 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
                    const float4* __restrict__ vol, const float4* __restrict__ voly, const float* __restrict__ ref,
                    float* __restrict__ proj, float* __restrict__ part) {
   __shared__ float red[kMarchThreads / 32][kRec];
-  const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
+  int n, tile;
+  band_major_tile(n_tiles, tiles_u, n, tile);
   if (voly && inst[n].yfast)  // uniform per block
     march_tile<LOSS, WU, 1>(inst, n, tile, n_tiles, tiles_u, g, voly, ref, proj, part, red);
   else
@@ -434,7 +435,8 @@ __device__ __forceinline__ float probe_ray(const InstTable& T, const Geo& g, int
 __global__ void __launch_bounds__(kMarchThreads, 4)
     k_gather_probe(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g, const float4* __restrict__ vol,
                    const float4* __restrict__ voly, float* __restrict__ sink) {
-  const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
+  int n, tile;
+  band_major_tile(n_tiles, tiles_u, n, tile);  // the fused march's block order
   int iu, iv;
   const bool on = tile_pixel<4>(tile, tiles_u, g, iu, iv);
   float acc = 0.f;
