@@ -688,7 +688,7 @@ int proj_batch_create(int n, const proj_plan* plans, const int* loss, const floa
     B.n_tiles = p->n_tiles;
     B.tiles_u = ceil_div(p->geo.nu, kTileU);
     B.loss = loss[i];
-    B.pad = 0;
+    B.n_inst = p->n_inst;
     // per-tile cost ~ samples per ray ~ volume diagonal / step
     const double dx = p->geo.nx * (double)p->geo.vx, dy = p->geo.ny * (double)p->geo.vy,
                  dz = p->geo.nz * (double)p->geo.vz;

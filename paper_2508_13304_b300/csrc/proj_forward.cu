@@ -470,8 +470,9 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
     int p = 0;
     while (p + 1 < n_probs && probs[p + 1].item_begin <= item) ++p;
     const BatchProblem& B = probs[p];
-    const int local = (int)(item - B.item_begin);
-    const int n = local / B.n_tiles, tile = local % B.n_tiles;
+    // band-major within the problem, as in k_forward_grad
+    const int local = (int)(item - B.item_begin), tu = local % B.tiles_u, rest = local / B.tiles_u;
+    const int n = rest % B.n_inst, tile = (rest / B.n_inst) * B.tiles_u + tu;
     const bool yf = B.vol4y && B.inst[n].yfast;
     if constexpr (LOSS >= 0) {
       if (yf)

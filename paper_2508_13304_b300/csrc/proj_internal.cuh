@@ -48,7 +48,7 @@ static_assert(sizeof(PoseTable) % 8 == 0, "PoseTable layout");
 // Static geometry shared by all kernels of a plan (passed by value).
 struct Geo {
   int nx, ny, nz;       // voxels
-  int px, py, pz;       // sizes with a 1-voxel border (n + 2): the mu copy
+  int px, py, pz;       // sizes with a 1-voxel border (n + 2): the cell records of mu (z rounded up to even)
   int qx, qy, qz;       // pitches of the (mu, grad mu) volume (2-voxel border, >= n + 4; qz even): element
                         // (x, y, z) at (((z >> 1) * qy + y) * qx + x) * 2 + (z & 1), i.e. x fastest with
                         // the two slices of a z pair interleaved element by element
@@ -78,7 +78,7 @@ struct BatchProblem {
   const float4* vol4y;  // y-fast copy, or null
   const float* ref;
   float* part;
-  int n_tiles, tiles_u, loss, pad;
+  int n_tiles, tiles_u, loss, n_inst;
   long long item_begin;  // first global work item of this problem
 };
 
