@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 256 << 20
 # ncu capture of the 8-instance case (profiles/k_forward_grad_ncc_...md,
 # 1.903 GB) scaled by 128/8 instances, since every instance re-streams the
 # volume.  Set to None whenever the kernel changes until it is re-measured.
-TRAFFIC_PER_LAUNCH = 31.9e9   # ncu dram__bytes_read+write of the 4-candidate launch (1.996 GB) x 128/8 instances
+TRAFFIC_PER_LAUNCH = 21.57e9  # ncu dram__bytes_read+write of one full-size launch (one-pass metrics): 21.55 GB + 19 MB
 
 
 def load_peaks():
