@@ -55,9 +55,15 @@ def f32(a):
 
 # --------------------------------------------------------------- small ragged
 
-def ragged_case(seed=101):
+# two ragged grids: even and odd slice counts (the volume copies store z slices
+# in pairs), detector sizes that are not multiples of the 16-pixel tile
+RAGGED = {"even_z": ((40, 36, 44), (50, 37)), "odd_z": ((37, 42, 33), (41, 46))}
+
+
+def ragged_case(seed=101, shape="even_z"):
     rng = np.random.default_rng(seed)
-    g = small_geom(n=(40, 36, 44), vox=(1.0, 1.1, 0.9), det=(50, 37), pix=1.6, n_views=3,
+    n, det = RAGGED[shape]
+    g = small_geom(n=n, vox=(1.0, 1.1, 0.9), det=det, pix=1.6, n_views=3,
                    off=(1.5, -0.7, 0.4), step=0.5)
     mu = f32(smooth_volume(g, rng, n_blobs=8) + 0.3 * (rng.uniform(0, 1, g.vol_shape) > 0.97))
     poses = f32(np.concatenate([rng.uniform(-3, 3, (2, 3)), rng.uniform(-0.15, 0.15, (2, 3))], axis=1))
@@ -66,9 +72,9 @@ def ragged_case(seed=101):
     return g, mu, poses, inst_view, inst_pose, rng
 
 
-@pytest.fixture(scope="module")
-def ragged():
-    g, mu, poses, iv, ip, rng = ragged_case()
+@pytest.fixture(scope="module", params=sorted(RAGGED))
+def ragged(request):
+    g, mu, poses, iv, ip, rng = ragged_case(shape=request.param)
     P = pb.Projector(g, n_pose=2, inst_view=iv, inst_pose=ip)
     P.set_volume(mu)
     return dict(g=g, mu=mu, poses=poses, iv=iv, ip=ip, rng=rng, P=P)
