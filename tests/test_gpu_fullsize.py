@@ -194,3 +194,41 @@ def test_uneven_batch_full_size():
         gref, _ = oracle.forward_grad(g, mu.astype(np.float64), pose[v].astype(np.float64), w, [v], [0])
         assert grad_rel(got[k][0][v], gref[0]) <= TOL_GRAD, (k, v, got[k][0][v], gref[0])
         assert abs(got[k][1][v] - L[0]) <= 1e-4 * abs(L[0]), (k, v)
+
+
+def test_odd_sizes_records_and_transposes():
+    """Large odd sizes for the cell-record layouts: a 257 x 300 x 259 volume
+    (odd slice count, anisotropic voxels) and 513 x 385 detectors, 6 views
+    with their own poses.  Forward projection at 1500 sampled pixels and
+    back-projection at 1500 sampled voxels against the oracle; both
+    transposes through the adjoint identities <A x, y> = <x, A^T y> against
+    the GPU's own forward and back-projection."""
+    rng = np.random.default_rng(77)
+    views = synth.circular_views(6, synth.SAD, synth.SDD, 0.7, 0.65)
+    g = synth.Geometry(257, 300, 259, 0.8, 0.75, 0.7, 513, 385, views, 0.375, (1.0, -2.0, 0.5))
+    mu = f32(rng.random((259, 300, 257), dtype=np.float32))
+    poses = np.zeros((6, 6))
+    poses[:, :3] = rng.normal(0.0, 2.0, (6, 3))
+    poses[:, 3:] = np.deg2rad(rng.normal(0.0, 3.0, (6, 3)))
+    poses = f32(poses)
+    iv = np.arange(6, dtype=np.int32)
+    P = pb.Projector(g, n_pose=6, inst_view=iv, inst_pose=iv,
+                     ops=pb.PROJ_OP_FORWARD | pb.PROJ_OP_ADJOINT | pb.PROJ_OP_BACK)
+    P.set_volume(mu)
+    proj = P.forward(poses).cpu().numpy()
+    pix = np.stack([rng.integers(0, 6, 1500), rng.integers(0, 513, 1500), rng.integers(0, 385, 1500)], axis=1)
+    ref = oracle.forward_pixels(g, mu.astype(np.float64), poses.astype(np.float64), pix, iv, iv)
+    assert rel(proj[pix[:, 0], pix[:, 2], pix[:, 1]], ref) <= TOL_IMG
+    img = f32(rng.random((6, 385, 513), dtype=np.float32))
+    vol = P.back(img, poses, pb.PROJ_W_FDK).cpu().numpy()
+    vox = np.stack([rng.integers(0, 257, 1500), rng.integers(0, 300, 1500), rng.integers(0, 259, 1500)], axis=1)
+    refb = oracle.back_voxels(g, img.astype(np.float64), poses.astype(np.float64), vox, iv, iv, weight=oracle.W_FDK)
+    assert rel(vol[vox[:, 2], vox[:, 1], vox[:, 0]], refb) <= TOL_IMG
+    # <A mu, img> = <mu, A^T img>, <B img, x> = <img, B^T x>
+    at = P.forward_adjoint(img, poses).cpu().numpy()
+    lhs, rhs = np.vdot(proj.astype(np.float64), img), np.vdot(mu.astype(np.float64), at)
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    x = f32(rng.standard_normal((259, 300, 257), dtype=np.float32))
+    bt = P.back_adjoint(x, poses, pb.PROJ_W_FDK).cpu().numpy()
+    lhs, rhs = np.vdot(vol.astype(np.float64), x), np.vdot(img, bt.astype(np.float64))
+    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(vol) * np.linalg.norm(x)
