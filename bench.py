@@ -336,6 +336,55 @@ def secondary(pb, torch, dev, w, mu_d, flush):
     out["posenet"] = posenet_measure(pb, torch, dev, flush, g, mu_d, load_peaks())
     out["uneven_batch_small"] = uneven_batch(pb, torch, dev, flush, with_large=False)
     out["uneven_batch_c4"] = uneven_batch(pb, torch, dev, flush, with_large=True)
+    out["cpu_baseline_subsets"] = oracle_subset_rates(out)   # CPU-baseline leg: the oracle beside the GPU
+    return out
+
+
+def oracle_subset_rates(sec):
+    """The FP64 oracle (all host cores) on seeded subsets of the
+    motion-compensated and calibration workloads, its rate per voxel-view or
+    ray sample extrapolated to the full call, beside the GPU's rate on the
+    full call: FDK back-projection on 32 of the 360 views, its pose gradient
+    on 8, and the fused L2 pose gradient of the 512^3 / 768^2 problem on the
+    64 central detector rows of 4 of its 720 views."""
+    import oracle
+    out = {"threads": oracle.max_threads(), "kind": "oracle"}
+    rng = np.random.default_rng(1003)
+    gm = synth.Geometry(256, 256, 256, 0.8, 0.8, 0.8, 512, 512,
+                        synth.circular_views(360, synth.SAD, synth.SDD, 0.6, 0.6), 0.4)
+    motion = synth.smooth_motion(rng, 360, 2.0, 3.0)
+    views = np.arange(0, 360, 360 // 32)[:32]
+    img = rng.random((32, 512, 512))
+    t0 = time.perf_counter()
+    oracle.back(gm, img, motion[views], inst_view=views, inst_pose=np.arange(32), weight=oracle.W_FDK)
+    r = 32 * 256 ** 3 / (time.perf_counter() - t0)
+    gpu = sec["back"]["voxel_view_updates_per_s"]
+    out["fdk_back_projection"] = {"sample": "32 of 360 views", "oracle_voxel_view_updates_per_s": r,
+                                  "gpu_voxel_view_updates_per_s": gpu, "speedup": gpu / r}
+    wvol = rng.standard_normal((256, 256, 256))
+    t0 = time.perf_counter()
+    oracle.back_grad(gm, img[:8], motion[views[:8]], wvol, inst_view=views[:8], inst_pose=np.arange(8),
+                     weight=oracle.W_FDK)
+    r = 8 * 256 ** 3 / (time.perf_counter() - t0)
+    gpu = sec["back_pose_grad"]["voxel_view_updates_per_s"]
+    out["fdk_back_projection_pose_grad"] = {"sample": "8 of 360 views", "oracle_voxel_view_updates_per_s": r,
+                                            "gpu_voxel_view_updates_per_s": gpu, "speedup": gpu / r}
+    q = synth.workload_uneven(with_large=True, n_extra=0)[0]
+    g4 = q["geom"]
+    vsel = np.array([0, 180, 360, 540])
+    band = synth.Geometry(g4.nx, g4.ny, g4.nz, g4.vx, g4.vy, g4.vz, g4.nu, 64, g4.views[vsel], g4.step)
+    mu4 = rng.random((g4.nz, g4.ny, g4.nx))
+    pose = q["poses"][vsel]
+    iv = np.arange(4)
+    _, ns = oracle.forward(band, mu4, pose, iv, iv, return_samples=True)
+    resid = rng.standard_normal((4, 64, g4.nu))
+    t0 = time.perf_counter()
+    oracle.forward_grad(band, mu4, pose, resid, iv, iv)
+    r = float(np.sum(ns)) / (time.perf_counter() - t0)
+    gpu = sec["uneven_batch_c4"]["batched_ray_samples_per_s"]
+    out["calibration_pose_grad"] = {"sample": "64 central rows of 4 of the 720 views of 768^2 (512^3)",
+                                    "oracle_ray_samples_per_s": r, "gpu_ray_samples_per_s": gpu, "speedup": gpu / r,
+                                    "oracle_s_per_full_eval_extrapolated": sec["uneven_batch_c4"]["ray_samples"] / r}
     return out
 
 
