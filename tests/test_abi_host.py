@@ -107,6 +107,29 @@ def test_instance_indices_are_checked(L, iv, ip, n_pose, msg):
     assert rc == pb.PROJ_E_ARG and msg in pb.proj_last_error()
 
 
+def test_empty_instance_list_is_rejected(L):
+    rc, h = create(tiny_geom(), inst_view=(), inst_pose=())
+    assert rc == pb.PROJ_E_ARG and not h.value and "n_inst" in pb.proj_last_error()
+
+
+@pytest.mark.parametrize("sizes,msg", [
+    (dict(ny=65001), "<= 65000"), (dict(nz=65001), "<= 65000"), (dict(nv=65001), "<= 65000"),
+    (dict(nx=2000, ny=2000, nz=600), "volume too large"),   # padded voxel count >= 2^31
+])
+def test_size_limits_are_enforced_on_the_host(L, sizes, msg):
+    rc, h = create(tiny_geom(**sizes))
+    assert rc == pb.PROJ_E_ARG and not h.value and msg in pb.proj_last_error()
+
+
+def test_instance_limit_of_the_voxel_driven_calls(L):
+    n = 65536
+    iv, ip = np.zeros(n, dtype=np.int32), np.zeros(n, dtype=np.int32)
+    rc, _ = create(tiny_geom(), inst_view=iv, inst_pose=ip, ops=pb.PROJ_OP_BACK)
+    assert rc == pb.PROJ_E_ARG and "65535" in pb.proj_last_error()
+    rc, _ = create(tiny_geom(), inst_view=iv, inst_pose=ip, ops=pb.PROJ_OP_BACK_GRAD)
+    assert rc == pb.PROJ_E_ARG and "65535" in pb.proj_last_error()
+
+
 def test_bad_ops_and_null_arguments(L):
     rc, _ = create(tiny_geom(), ops=0)
     assert rc == pb.PROJ_E_ARG
