@@ -248,6 +248,32 @@ def test_single_voxel_single_pixel():
     assert rel_l2(np32(P.back(img, pose)), oracle.back(g, img, pose)) <= TOL_IMG
 
 
+def test_source_inside_the_volume():
+    """A degenerate geometry: the source sits inside the volume (10 mm from
+    the isocentre of a 40 mm grid).  Rays start at the source (sample k = 0);
+    voxels behind the source (w' <= 0) receive nothing from the
+    back-projector.  Every call against the oracle."""
+    rng = np.random.default_rng(21)
+    g = small_geom(n=(40, 38, 36), vox=(1.0, 1.0, 1.0), det=(45, 40), pix=2.5, n_views=2, sad=10.0, sdd=60.0)
+    mu = f32(smooth_volume(g, rng, n_blobs=6))
+    poses = f32([[0.5, -0.3, 0.2, 0.02, -0.03, 0.01]])
+    P = pb.Projector(g)
+    P.set_volume(mu)
+    ref = oracle.forward(g, mu, poses)
+    assert rel_l2(np32(P.forward(poses)), ref) <= TOL_IMG
+    w = f32(rng.standard_normal(ref.shape))
+    gth, _ = oracle.forward_grad(g, mu, poses, w, mode=oracle.GRAD_ANALYTIC)
+    assert grad_rel(np32(P.forward_pose_grad(poses, pb.PROJ_LOSS_RESIDUAL, w)[0]), gth) <= TOL_GRAD
+    img = f32(rng.uniform(0, 1, ref.shape))
+    for weight in (pb.PROJ_W_NONE, pb.PROJ_W_FDK):
+        vref = oracle.back(g, img, poses, weight=weight)
+        assert np.any(vref == 0) and np.any(vref != 0)       # some voxels lie behind the source
+        assert rel_l2(np32(P.back(img, poses, weight)), vref) <= TOL_IMG
+    wv = f32(rng.standard_normal(g.vol_shape))
+    gb, _ = oracle.back_grad(g, img, poses, wv, weight=pb.PROJ_W_NONE, mode=oracle.GRAD_ANALYTIC)
+    assert grad_rel(np32(P.back_pose_grad(img, poses, wv, pb.PROJ_W_NONE)), gb) <= TOL_GRAD
+
+
 # --------------------------------------------------------------- C1 (64^3) full
 
 @pytest.fixture(scope="module")
