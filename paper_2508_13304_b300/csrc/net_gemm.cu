@@ -440,6 +440,8 @@ __device__ __forceinline__ void mbar_arrive_remote(uint32_t bar_cluster) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
 }
 
+constexpr int kGroupM = 8;
+
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPersistThreads, 1)
     k_gemm_bf16_pair_persistent(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
                                 int M, int N, int K, int kb_per_split, int m_pairs, int n_tiles, int n_work,
@@ -491,11 +493,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPersistThreads, 1)
   const uint32_t tmem_d = *tmem_slot;
   int fail = 0;
 
-  // work item w -> (split z, N tile, M pair), M pairs fastest
+  // work item w -> (split z, N tile, M pair): groups of kGroupM M pairs, M
+  // fastest inside a group, then N, then the next group, so the tiles the
+  // clusters hold at one time share a few A and B panels in L2
   auto decode = [&](int w, int& mp, int& nt, int& z) {
-    mp = w % m_pairs;
-    nt = (w / m_pairs) % n_tiles;
-    z = w / (m_pairs * n_tiles);
+    const int per_z = m_pairs * n_tiles;
+    z = w / per_z;
+    const int local = w - z * per_z;
+    const int grp = local / (kGroupM * n_tiles), in = local - grp * (kGroupM * n_tiles);
+    const int gsize = min(kGroupM, m_pairs - grp * kGroupM);
+    mp = grp * kGroupM + in % gsize;
+    nt = in / gsize;
   };
   auto kb_range = [&](int z, int& kb0, int& nkb) {
     kb0 = z * kb_per_split;
