@@ -189,7 +189,8 @@ int proj_forward_pose_grad(proj_plan plan, const float *d_pose, int loss, const 
                            float *d_loss, float *d_proj, void *d_ws, size_t ws_bytes, proj_stream stream);
 
 /* Voxel-driven back-projection (Eq. back) of one image per instance.
- *   d_proj  [n_inst][nv][nu] FP32.
+ *   d_proj  [n_inst][nv][nu] FP32; copied first into zero-bordered cell
+ *           records in the workspace (the 4 pixels of each bilinear cell).
  *   weight  PROJ_W_NONE or PROJ_W_FDK (FDK_CONST behaves as FDK here).
  *   d_vol   out [nz][ny][nx] FP32 (sum over all instances). */
 int proj_back(proj_plan plan, const float *d_proj, const float *d_pose, int weight, float *d_vol, void *d_ws,
@@ -200,8 +201,10 @@ int proj_back(proj_plan plan, const float *d_proj, const float *d_pose, int weig
  * the 4 bilinear corners of its projection in every instance.
  *   d_vol   [nz][ny][nx] FP32 (dL/dmu).
  *   weight  PROJ_W_NONE or PROJ_W_FDK (FDK_CONST behaves as FDK).
- *   d_proj  out [n_inst][nv][nu] FP32 (zeroed, then accumulated with float
- *           atomics: the last bits depend on the order). */
+ *   d_proj  out [n_inst][nv][nu] FP32: the weights are accumulated with
+ *           float vector reductions into detector cell records in the
+ *           workspace, then the 4 records sharing each pixel are summed
+ *           (the last bits depend on the order of the reductions). */
 int proj_back_adjoint(proj_plan plan, const float *d_vol, const float *d_pose, int weight, float *d_proj, void *d_ws,
                       size_t ws_bytes, proj_stream stream);
 
@@ -274,7 +277,11 @@ int proj_batch_destroy(proj_batch batch);
 /* Exact transpose of proj_forward for the given poses: each sample spreads
  * step * y_i over its 8 trilinear corners.
  *   d_y    [n_inst][nv][nu] FP32.
- *   d_vol  out [nz][ny][nx] FP32. */
+ *   d_vol  out [nz][ny][nx] FP32: the weights are accumulated with float
+ *          vector reductions into cell records in the workspace (the 4
+ *          corners of each cell's xy face), then the 4 records sharing each
+ *          voxel are summed (the last bits depend on the order of the
+ *          reductions).  Needs PROJ_OP_ADJOINT. */
 int proj_forward_adjoint(proj_plan plan, const float *d_y, const float *d_pose, float *d_vol, void *d_ws,
                          size_t ws_bytes, proj_stream stream);
 
@@ -315,12 +322,13 @@ int proj_count_samples(proj_plan plan, const float *d_pose, long long *d_count, 
                        proj_stream stream);
 
 /* Kernel timing for benchmarks.  While enabled, every call records two
- * CUDA events on its stream, immediately before and after its main kernel
- * (the march of proj_forward / proj_forward_pose_grad /
- * proj_forward_adjoint, the voxel kernel of proj_back /
- * proj_back_pose_grad); proj_kernel_time_ms waits for the second event and
- * returns the elapsed time of the last call's main kernel.  The events are
- * created by the first enable (not on the compute path). */
+ * CUDA events on its stream, immediately before and after its main kernels
+ * (the march of proj_forward / proj_forward_pose_grad, the record pass and
+ * voxel kernel of proj_back, the voxel kernel of proj_back_pose_grad, the
+ * clearing, scatter and record-summing passes of the two transposes);
+ * proj_kernel_time_ms waits for the second event and returns the elapsed
+ * time of the last call's main kernels.  The events are created by the
+ * first enable (not on the compute path). */
 int proj_enable_kernel_timing(proj_plan plan, int enable);
 int proj_kernel_time_ms(proj_plan plan, float *ms);
 
