@@ -167,8 +167,10 @@ __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo&
 
 // volq: mu with a 1-voxel zero border, (n+2)^3 cells, each cell holding the
 // 2 x 2 corners of its xy face, (mu(x, y), mu(x+1, y), mu(x, y+1),
-// mu(x+1, y+1)) at its own z: a trilinear sample reads its 8 corners as two
-// 16-byte loads (this cell and the one above).  vol4: (mu, grad mu) with a
+// mu(x+1, y+1)) at its own z, z slices interleaved in pairs: a trilinear
+// sample reads its 8 corners as two 16-byte loads (this cell and the one
+// above); launch_records_yfast then writes its copy with rows along y.
+// vol4: (mu, grad mu) with a
 // 2-voxel border, (n+4)^3; grad mu = central differences of the zero-padded
 // volume, non-zero up to one voxel outside the grid and zero on the outer
 // border layer.
