@@ -1061,6 +1061,9 @@ def main():
         pipe.submit(mu_h, target_h, pose_h, grad_o, loss_o)
     pipe.synchronize()
     flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -1068,7 +1071,11 @@ def main():
         pipe.submit(mu_h, target_h, pose_h, grad_o, loss_o)
     e1.record(stream)
     e1.synchronize()
-    em = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        dist.barrier()
+    # whole job: every rank's candidates over the slowest rank's time
+    em = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
+    em_serial = max_over_ranks(em_serial, dist, dev)
     h2d = mu_h.numel() * 4 + target_h.numel() * 4 + pose_h.numel() * 4
     d2h = grad_o.numel() * 4 + loss_o.numel() * 4
 
@@ -1112,13 +1119,14 @@ def main():
                      "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                              "frac": hbm_achieved / hbm_peak, "compulsory_bytes": hbm_bytes,
                              "peak_from": "MEASURED_PEAKS.json hbm_gbs"}},
-        "e2e": {"value": args.n_cand / (em * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": em,
+        "e2e": {"value": world * args.n_cand / (em * 1e-3), "unit": UNIT, "h2d_bytes_per_step": world * h2d,
+                "d2h_bytes_per_step": world * d2h, "ms_per_step": em,
                 "what": "PoseGradPipeline: pinned host volume, targets and poses copied in and gradients and "
                         "losses copied out every step; step k+1's copies overlap step k's compute; no L2 flush "
                         "between steps (the two 285 MB (mu, grad mu) copies exceed L2)",
-                "serial_value": args.n_cand / (em_serial * 1e-3), "serial_ms_per_step": em_serial},
-        "gpu_launches": 5 * args.steps,   # per step: k_volume_prep, k_volume_yfast, k_setup, k_forward_grad, reduce
+                "serial_value": world * args.n_cand / (em_serial * 1e-3), "serial_ms_per_step": em_serial},
+        # per step and rank: k_volume_prep, k_transpose_xy (the y-fast copy), k_setup, k_forward_grad, its reduce
+        "gpu_launches": 5 * args.steps * world,
         "clocks": clk,
         "wall_s_timed_region": wall,
     }
