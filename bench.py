@@ -261,6 +261,11 @@ def secondary(pb, torch, dev, w, mu_d, flush):
     out["back_pose_grad"] = {"kernel": "k_back_grad", "config": "256^3, 360 views of 512^2, FDK weight",
                              "kernel_ms": ms, "voxel_view_updates_per_s": vv / (ms * 1e-3),
                              "pose_gradient_evals_per_s": 360 / (ms * 1e-3)}
+    shape, bt = pb.proj_autotune_back_grad(Pb.plan, img, motion, pb.PROJ_W_FDK, wvol, Pb.ws, reps=2)
+    out["brick_shape_autotune"] = {"config": "256^3, 360 views of 512^2, FDK weight",
+                                   "ms_per_launch": {"%dx%dx%d/%d views" % (32, 8, gz, nv): bt[k]
+                                                     for k, (gz, nv) in enumerate(pb.BRICK_SHAPES)},
+                                   "chosen": "%dx%dx%d/%d views" % ((32, 8) + pb.BRICK_SHAPES[shape])}
     # one motion-compensated FDK iteration at the same size (BP, sharpness, BP gradient, Adam step)
     from paper_2508_13304_b300.registration import Adam
     Pm = pb.Projector(gm, n_pose=360, inst_view=np.arange(360), inst_pose=np.arange(360),

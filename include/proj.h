@@ -248,6 +248,27 @@ int proj_get_warp_shape(proj_plan plan, int *warp_width);
 int proj_autotune_forward_grad(proj_plan plan, const float *d_pose, int loss, const float *d_ref, void *d_ws,
                                size_t ws_bytes, proj_stream stream, int reps, float *times_ms, int *warp_width);
 
+/* Brick shape of the back-projection gradient (a library facility; the
+ * paper fixes none): a block owns 32 x 8 voxel columns of gz voxels and a
+ * chunk of instances.  Shapes: 0 = gz 16, 8 instances (default);
+ * 1 = gz 8, 8; 2 = gz 16, 16; 3 = gz 8, 16.  Results of different shapes
+ * differ only in the order of the FP32 partial sums.
+ * Errors: PROJ_E_ARG (NULL plan or pointer, shape out of range). */
+int proj_set_brick_shape(proj_plan plan, int shape);
+int proj_get_brick_shape(proj_plan plan, int *shape);
+
+/* Times proj_back_pose_grad's voxel kernel under every brick shape on the
+ * caller's data (CUDA events, one warm-up and `reps` launches each), keeps
+ * the fastest in the plan and returns it in *shape (may be NULL) and the
+ * times in times_ms[4] (ms per launch, may be NULL).  Arguments as
+ * proj_back_pose_grad without d_grad: writes only the workspace.
+ * Synchronises the stream (not for capture).  Needs PROJ_OP_BACK_GRAD;
+ * reps in 1..1000.
+ * Errors: PROJ_E_ARG, PROJ_E_UNSUPPORTED, PROJ_E_WORKSPACE, PROJ_E_CUDA. */
+int proj_autotune_back_grad(proj_plan plan, const float *d_proj, const float *d_pose, int weight,
+                            const float *d_vol_resid, void *d_ws, size_t ws_bytes, proj_stream stream, int reps,
+                            float *times_ms, int *shape);
+
 /* Batches: several independent forward pose-gradient problems (each a plan
  * with its own volume, detector, views, poses and workspace, e.g. registration
  * problems of uneven size) run by one persistent launch.  Resident blocks

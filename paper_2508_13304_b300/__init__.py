@@ -73,6 +73,10 @@ _SIGS = {
     "proj_get_warp_shape": [_P, ctypes.POINTER(_I)],
     "proj_autotune_forward_grad": [_P, _P, _I, _P, _P, _SZ, _P, _I, ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(_I)],
+    "proj_set_brick_shape": [_P, _I],
+    "proj_get_brick_shape": [_P, ctypes.POINTER(_I)],
+    "proj_autotune_back_grad": [_P, _P, _P, _I, _P, _P, _SZ, _P, _I, ctypes.POINTER(ctypes.c_float),
+                                ctypes.POINTER(_I)],
     "proj_batch_create": [_I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P),
                           ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_SZ),
                           ctypes.POINTER(_P)],
@@ -373,6 +377,34 @@ def proj_autotune_forward_grad(plan: Plan, pose, loss, ref, ws, reps=3, stream=N
     return int(w.value), dict(zip(WARP_WIDTHS, [float(t) for t in times]))
 
 
+# brick shapes of the back-projection gradient: (voxels per thread along z, instances per block)
+BRICK_SHAPES = ((16, 8), (8, 8), (16, 16), (8, 16))
+
+
+def proj_set_brick_shape(plan: Plan, shape: int):
+    _check(lib().proj_set_brick_shape(plan.handle, int(shape)))
+
+
+def proj_get_brick_shape(plan: Plan) -> int:
+    b = ctypes.c_int()
+    _check(lib().proj_get_brick_shape(plan.handle, ctypes.byref(b)))
+    return int(b.value)
+
+
+def proj_autotune_back_grad(plan: Plan, proj, pose, weight, vol_resid, ws, reps=3, stream=None):
+    """Time the back-projection gradient per brick shape on this data, keep
+    the fastest in the plan; returns (shape, {shape: ms per launch})."""
+    import torch
+    p, nb = _ws(ws)
+    times = (ctypes.c_float * 4)()
+    b = ctypes.c_int()
+    _check(lib().proj_autotune_back_grad(plan.handle, _ptr(proj, torch.float32, plan.n_inst * plan.img_numel, "proj"),
+                                         _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"), int(weight),
+                                         _ptr(vol_resid, torch.float32, plan.vol_numel, "vol_resid"), p, nb,
+                                         _stream(stream), int(reps), times, ctypes.byref(b)))
+    return int(b.value), {k: float(t) for k, t in enumerate(times)}
+
+
 class Batch:
     """Handle of a proj_batch; keeps the bound plans and tensors alive."""
 
@@ -577,6 +609,10 @@ class Projector:
 
     def autotune(self, pose, loss, ref, reps=3):
         return proj_autotune_forward_grad(self.plan, self._t(pose), loss, self._t(ref), self.ws, reps)
+
+    def autotune_back(self, proj, pose, vol_resid, weight=PROJ_W_NONE, reps=3):
+        return proj_autotune_back_grad(self.plan, self._t(proj), self._t(pose), weight, self._t(vol_resid), self.ws,
+                                       reps)
 
     def back(self, proj, pose, weight=PROJ_W_NONE):
         import torch

@@ -45,7 +45,8 @@ struct proj_plan_s {
   int n_views, n_pose, n_inst, ops;
   int device;
   int n_tiles;        // ray tiles per instance
-  int bp_blocks;      // voxel bricks of the back-projection gradient (records per instance)
+  int bp_blocks;      // most voxel bricks of the back-projection gradient over the brick shapes (records per instance)
+  int bp_shape = 0;   // brick shape of the back-projection gradient (0..kBrickShapes-1)
   std::vector<double> views;
   std::vector<int> inst_view, inst_pose;
   // device tables owned by the plan
@@ -250,7 +251,8 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
     return cuda_fail(e, "device query");
   }
   // records of the back-projection gradient: one per voxel brick and instance
-  p->bp_blocks = ceil_div(G.nx, kGbX) * ceil_div(G.ny, kGbY) * ceil_div(G.nz, kGbZ);
+  p->bp_blocks = 0;
+  for (int b = 0; b < kBrickShapes; ++b) p->bp_blocks = std::max(p->bp_blocks, back_grad_blocks(p->geo, b));
   (void)n_sm;
 
   // Workspace layout.
@@ -482,10 +484,11 @@ int proj_back_pose_grad(proj_plan p, const float* d_proj, const float* d_pose, i
   cudaError_t e = launch_detector_prep(d_proj, p->n_inst, p->geo, w.det4, s);
   if (e != cudaSuccess) return cuda_fail(e, "detector-gradient launch");
   mark(p, true, s);
-  e = launch_back_grad(w.inst, p->n_inst, p->geo, weight, w.det4, d_vol_resid, w.part_b, p->bp_blocks, s);
+  e = launch_back_grad(w.inst, p->n_inst, p->geo, weight, w.det4, d_vol_resid, w.part_b, p->bp_shape, s);
   mark(p, false, s);
   if (e != cudaSuccess) return cuda_fail(e, "back-projection gradient launch");
-  e = launch_back_grad_reduce(w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_inst, p->bp_blocks, p->geo,
+  e = launch_back_grad_reduce(w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_inst,
+                              back_grad_blocks(p->geo, p->bp_shape), p->geo,
                               w.part_b, d_grad, s);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "back-projection gradient reduction launch");
 }
@@ -534,6 +537,64 @@ int proj_set_warp_shape(proj_plan p, int warp_width) {
 int proj_get_warp_shape(proj_plan p, int* warp_width) {
   if (!p || !warp_width) return fail(PROJ_E_ARG, "plan or warp_width is NULL");
   *warp_width = p->warp_width;
+  return PROJ_OK;
+}
+
+int proj_set_brick_shape(proj_plan p, int shape) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (shape < 0 || shape >= kBrickShapes) return fail(PROJ_E_ARG, "brick shape %d is not in 0..%d", shape, kBrickShapes - 1);
+  p->bp_shape = shape;
+  return PROJ_OK;
+}
+
+int proj_get_brick_shape(proj_plan p, int* shape) {
+  if (!p || !shape) return fail(PROJ_E_ARG, "plan or shape is NULL");
+  *shape = p->bp_shape;
+  return PROJ_OK;
+}
+
+int proj_autotune_back_grad(proj_plan p, const float* d_proj, const float* d_pose, int weight,
+                            const float* d_vol_resid, void* d_ws, size_t ws_bytes, proj_stream stream, int reps,
+                            float* times_ms, int* shape) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_proj || !d_pose || !d_vol_resid) return fail(PROJ_E_ARG, "proj_autotune_back_grad: NULL argument");
+  if (weight != PROJ_W_NONE && weight != PROJ_W_FDK && weight != PROJ_W_FDK_CONST)
+    return fail(PROJ_E_ARG, "unknown weight %d", weight);
+  if (reps < 1 || reps > 1000) return fail(PROJ_E_ARG, "reps must be in 1..1000");
+  int rc = need_op(p, PROJ_OP_BACK_GRAD, "proj_autotune_back_grad");
+  if (rc) return rc;
+  WsView w;
+  if ((rc = check_ws(p, d_ws, ws_bytes, &w))) return rc;
+  if ((rc = check_device(p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = setup(p, d_pose, w, s))) return rc;
+  cudaError_t e = launch_detector_prep(d_proj, p->n_inst, p->geo, w.det4, s);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  float best = 0.f;
+  int pick = p->bp_shape;
+  for (int i = 0; i < kBrickShapes && e == cudaSuccess; ++i) {
+    e = launch_back_grad(w.inst, p->n_inst, p->geo, weight, w.det4, d_vol_resid, w.part_b, i, s);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(a, s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r)
+      e = launch_back_grad(w.inst, p->n_inst, p->geo, weight, w.det4, d_vol_resid, w.part_b, i, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    ms /= (float)reps;
+    if (times_ms) times_ms[i] = ms;
+    if (e == cudaSuccess && (i == 0 || ms < best)) {
+      best = ms;
+      pick = i;
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(e, "brick-shape autotune launches");
+  p->bp_shape = pick;
+  if (shape) *shape = pick;
   return PROJ_OK;
 }
 

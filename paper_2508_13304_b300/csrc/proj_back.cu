@@ -128,9 +128,9 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
 // dL/dmu_j the 12 sums wj rho and wj rho f~^T (f~ = centred voxel index)
 // give dL/dM of the instance.
 //
-// Work decomposition: a block owns one brick of kGbX x kGbY x kGbZ voxels
-// (one thread per (x, y) column holding its kGbZ residual weights in
-// registers) and a chunk of kGbViews consecutive instances; blocks of the same
+// Work decomposition: a block owns one brick of kGbX x kGbY x GZ voxels
+// (one thread per (x, y) column holding its GZ residual weights in
+// registers) and a chunk of `views` consecutive instances; blocks of the same
 // chunk run together, so that chunk's detector stacks stay in L2.  The inner
 // loop over z is branch-free - a voxel that projects outside the image, lies
 // behind the source or has wj = 0 gets weight 0 and gathers from a clamped,
@@ -144,25 +144,26 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+template <int GZ>
 __global__ void __launch_bounds__(kBpThreads, 3)
     k_back_grad(const InstTable* __restrict__ inst, int n_inst, Geo g, int weight, const float4* __restrict__ det4,
-                const float* __restrict__ wvol, float* __restrict__ part, int bricks_x, int bricks_y) {
+                const float* __restrict__ wvol, float* __restrict__ part, int bricks_x, int bricks_y, int views) {
   __shared__ float sred[kBpThreads / 32][12];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n_bricks = gridDim.x;
   const int brick = blockIdx.x;
   const int bx = brick % bricks_x, by = (brick / bricks_x) % bricks_y, bz = brick / (bricks_x * bricks_y);
-  const int ix = bx * kGbX + lane, iy = by * kGbY + warp, iz0 = bz * kGbZ;
+  const int ix = bx * kGbX + lane, iy = by * kGbY + warp, iz0 = bz * GZ;
   const bool col = ix < g.nx && iy < g.ny;
-  float wj[kGbZ];
+  float wj[GZ];
 #pragma unroll
-  for (int z = 0; z < kGbZ; ++z)
+  for (int z = 0; z < GZ; ++z)
     wj[z] = (col && iz0 + z < g.nz) ? __ldg(wvol + ((size_t)(iz0 + z) * g.ny + iy) * g.nx + ix) : 0.f;
   const float fx = (float)ix - g.cx, fy = (float)iy - g.cy;
   const int qu = g.nu + 4;
   const size_t det_stride = (size_t)(g.nu + 4) * (g.nv + 4);
   const float fu = (float)g.nu + 1.f, fvv = (float)g.nv + 1.f;
-  const int n0 = blockIdx.y * kGbViews, n1 = min(n_inst, n0 + kGbViews);
+  const int n0 = blockIdx.y * views, n1 = min(n_inst, n0 + views);
   for (int n = n0; n < n1; ++n) {
     const InstTable& T = inst[n];
     float a[12];
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(kBpThreads, 3)
       const float P1x = T.P3[3], P1y = T.P3[4], P1z = T.P3[5];
       const float P2x = T.P3[6], P2y = T.P3[7], P2z = T.P3[8];
 #pragma unroll
-      for (int z = 0; z < kGbZ; ++z) {
+      for (int z = 0; z < GZ; ++z) {
         const float fz = (float)(iz0 + z) - g.cz;
         const float hw = fmaf(T.Q[8], fz, bw);
         const float rw = 1.0f / hw;
@@ -368,11 +369,14 @@ cudaError_t launch_back_adjoint(const InstTable* d_inst, int n_inst, Geo geo, in
 }
 
 cudaError_t launch_back_grad(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float4* d_det4,
-                             const float* d_wvol, float* d_part, int n_blocks, cudaStream_t s) {
-  const int bx = ceil_div(geo.nx, kGbX), by = ceil_div(geo.ny, kGbY), bz = ceil_div(geo.nz, kGbZ);
-  (void)n_blocks;  // = bx * by * bz, the record count per instance
-  dim3 grid(bx * by * bz, ceil_div(n_inst, kGbViews));
-  k_back_grad<<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_det4, d_wvol, d_part, bx, by);
+                             const float* d_wvol, float* d_part, int shape, cudaStream_t s) {
+  const int gz = brick_gz(shape), views = brick_views(shape);
+  const int bx = ceil_div(geo.nx, kGbX), by = ceil_div(geo.ny, kGbY), bz = ceil_div(geo.nz, gz);
+  dim3 grid(bx * by * bz, ceil_div(n_inst, views));  // = back_grad_blocks(geo, shape) records per instance
+  if (gz == 8)
+    k_back_grad<8><<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_det4, d_wvol, d_part, bx, by, views);
+  else
+    k_back_grad<16><<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_det4, d_wvol, d_part, bx, by, views);
   return cudaGetLastError();
 }
 

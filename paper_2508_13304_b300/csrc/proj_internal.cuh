@@ -100,11 +100,16 @@ constexpr int kBpX = 32;
 constexpr int kBpY = 8;
 constexpr int kZChunk = 8;
 constexpr int kBpThreads = kBpX * kBpY;
-// Back-projection gradient: bricks of 32 x 8 x 16 voxels, 8 instances per block.
+// Back-projection gradient: bricks of 32 x 8 x gz voxels (one thread per
+// column of gz voxels), `views` instances per block; the shape is chosen per
+// plan (proj_set_brick_shape, proj_autotune_back_grad):
+//   0: gz 16, 8 views (default)   1: gz 8, 8 views
+//   2: gz 16, 16 views            3: gz 8, 16 views
 constexpr int kGbX = 32;
 constexpr int kGbY = 8;
-constexpr int kGbZ = 16;
-constexpr int kGbViews = 8;
+constexpr int kBrickShapes = 4;
+__host__ __device__ constexpr int brick_gz(int shape) { return (shape & 1) ? 8 : 16; }
+__host__ __device__ constexpr int brick_views(int shape) { return shape >= 2 ? 16 : 8; }
 
 // Launchers (defined in the .cu files; return cudaError_t of the launch).
 cudaError_t launch_setup(const float* d_pose, int n_pose, const double* d_views, const int* d_inst_view,
@@ -143,8 +148,9 @@ cudaError_t launch_back(const InstTable* d_inst, int n_inst, Geo geo, int weight
                         float4* d_detq, float* d_vol, cudaStream_t s);
 cudaError_t launch_back_adjoint(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float* d_y,
                                 float4* d_detq, float* d_proj, cudaStream_t s);
+// shape: brick shape 0..3 (see brick_gz / brick_views); records per instance = back_grad_blocks(geo, shape)
 cudaError_t launch_back_grad(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float4* d_det4,
-                             const float* d_wvol, float* d_part, int n_blocks, cudaStream_t s);
+                             const float* d_wvol, float* d_part, int shape, cudaStream_t s);
 cudaError_t launch_back_grad_reduce(const PoseTable* d_ptab, int n_pose, const int* d_pose_ptr,
                                     const int* d_pose_idx, int n_inst, int n_blocks, Geo geo, const float* d_part,
                                     float* d_grad, cudaStream_t s);
@@ -188,5 +194,10 @@ cudaError_t launch_sharpness(const float* d_mu, Geo geo, float* d_m, double* d_p
 void record_error(const char* msg);
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Bricks (records per instance) of the back-projection gradient for a brick shape.
+inline int back_grad_blocks(const Geo& g, int shape) {
+  return ceil_div(g.nx, kGbX) * ceil_div(g.ny, kGbY) * ceil_div(g.nz, brick_gz(shape));
+}
 
 }  // namespace projk

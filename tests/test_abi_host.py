@@ -162,6 +162,9 @@ def test_bad_ops_and_null_arguments(L):
     assert L.proj_gather_probe(None, None, None, 0, None) == pb.PROJ_E_ARG
     assert L.proj_get_warp_shape(None, None) == pb.PROJ_E_ARG
     assert L.proj_autotune_forward_grad(None, None, 0, None, None, 0, None, 1, None, None) == pb.PROJ_E_ARG
+    assert L.proj_set_brick_shape(None, 0) == pb.PROJ_E_ARG
+    assert L.proj_get_brick_shape(None, None) == pb.PROJ_E_ARG
+    assert L.proj_autotune_back_grad(None, None, None, 0, None, None, 0, None, 1, None, None) == pb.PROJ_E_ARG
 
 
 def test_valid_plan_without_a_gpu_reports_a_cuda_error(L):

@@ -152,6 +152,40 @@ def test_autotune_picks_a_shape_and_keeps_results(ragged):
     assert grad_rel(np32(grad), np32(base)) <= 1e-5
 
 
+@pytest.mark.parametrize("shape", range(len(pb.BRICK_SHAPES)))
+def test_back_pose_grad_brick_shapes(ragged, shape):
+    d = ragged
+    g = d["g"]
+    rng = np.random.default_rng(16)
+    img = f32(oracle.forward(g, d["mu"], np.zeros(6), d["iv"], np.zeros(5, dtype=np.int32))
+              + 0.05 * rng.uniform(0, 1, (5, g.nv, g.nu)))
+    wvol = f32(rng.standard_normal(g.vol_shape))
+    gth, _ = oracle.back_grad(g, img, d["poses"], wvol, d["iv"], d["ip"], weight=pb.PROJ_W_FDK,
+                              mode=oracle.GRAD_ANALYTIC)
+    P = pb.Projector(g, n_pose=2, inst_view=d["iv"], inst_pose=d["ip"], ops=pb.PROJ_OP_BACK_GRAD)
+    pb.proj_set_brick_shape(P.plan, shape)
+    assert pb.proj_get_brick_shape(P.plan) == shape
+    got = np32(P.back_pose_grad(img, d["poses"], wvol, pb.PROJ_W_FDK))
+    assert grad_rel(got, gth) <= TOL_GRAD, (shape, got, gth)
+
+
+def test_brick_autotune_picks_a_shape_and_keeps_results(ragged):
+    d = ragged
+    g = d["g"]
+    rng = np.random.default_rng(17)
+    img = f32(rng.uniform(0, 1, (5, g.nv, g.nu)))
+    wvol = f32(rng.standard_normal(g.vol_shape))
+    P = pb.Projector(g, n_pose=2, inst_view=d["iv"], inst_pose=d["ip"], ops=pb.PROJ_OP_BACK_GRAD)
+    base = np32(P.back_pose_grad(img, d["poses"], wvol, pb.PROJ_W_FDK))
+    shape, times = P.autotune_back(img, d["poses"], wvol, pb.PROJ_W_FDK, reps=2)
+    assert shape in range(len(pb.BRICK_SHAPES)) and pb.proj_get_brick_shape(P.plan) == shape
+    assert all(t > 0 for t in times.values()) and times[shape] == min(times.values())
+    got = np32(P.back_pose_grad(img, d["poses"], wvol, pb.PROJ_W_FDK))
+    assert grad_rel(got, base) <= 1e-5
+    with pytest.raises(pb.ProjError):
+        pb.proj_set_brick_shape(P.plan, len(pb.BRICK_SHAPES))
+
+
 def test_forward_pose_grad_is_deterministic(ragged):
     d = ragged
     w = f32(np.random.default_rng(3).standard_normal((5, d["g"].nv, d["g"].nu)))
