@@ -665,9 +665,9 @@ def registration_500(pb, torch, dev, n_prob=500, max_iter=200):
 def moco_quality(pb, torch, dev):
     """Motion-compensated FDK on the 360-view workload (256^3 at 0.8 mm,
     512^2 at 0.6 mm, smooth per-view motion rot <= 2 deg, trans <= 3 mm):
-    projections rendered at the moving poses, then 80 iterations of the
-    sharpness loss with a centred 24-node spline motion model
-    (translations).  Errors are relative L2 distances to the FDK of
+    projections rendered at the moving poses, then 240 iterations of the
+    sharpness loss with a centred 24-node spline motion model (translations
+    and rotations).  Errors are relative L2 distances to the FDK of
     motion-free projections."""
     from paper_2508_13304_b300 import moco
     w = synth.workload_moco()
@@ -686,15 +686,17 @@ def moco_quality(pb, torch, dev):
     def rel(a):
         return float((a - ref).norm() / ref.norm())
 
-    out = moco.moco_fdk(g, proj.cpu().numpy(), n_iter=80, lr=[0.05] * 3 + [0.0] * 3, spline_nodes=24,
-                        device=dev)
+    out = moco.moco_fdk(g, proj.cpu().numpy(), n_iter=240, lr=[0.05] * 3 + [math.radians(0.02)] * 3,
+                        spline_nodes=24, device=dev)
     d = out["poses"] - motion
-    return {"config": "256^3, 360 views of 512^2, 24-node spline (translations), 80 iterations",
+    return {"config": "256^3, 360 views of 512^2, 24-node spline (translations and rotations), 240 iterations",
             "recon_err_uncompensated": rel(torch.from_numpy(out["fdk0"]).to(dev)),
             "recon_err_compensated": rel(torch.from_numpy(out["fdk"]).to(dev)),
             "recon_err_true_motion": rel(best),
             "trans_rms_mm_before_after": [float(np.sqrt((motion[:, :3] ** 2).mean())),
                                           float(np.sqrt((d[:, :3] ** 2).mean()))],
+            "rot_rms_deg_before_after": [float(np.degrees(np.sqrt((motion[:, 3:] ** 2).mean()))),
+                                         float(np.degrees(np.sqrt((d[:, 3:] ** 2).mean())))],
             "sharpness_before_after": [float(out["sharpness"][0]), float(out["sharpness"][-1])],
             "seconds": out["seconds"]}
 
