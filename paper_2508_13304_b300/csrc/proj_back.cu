@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
 //
 // Work decomposition: a block owns one brick of kGbX x kGbY x GZ voxels
 // (one thread per (x, y) column holding its GZ residual weights in
-// registers) and a chunk of `views` consecutive instances; blocks of the same
+// registers) and a chunk of VIEWS consecutive instances; blocks of the same
 // chunk run together, so that chunk's detector stacks stay in L2.  The inner
 // loop over z is branch-free - a voxel that projects outside the image, lies
 // behind the source or has wj = 0 gets weight 0 and gathers from a clamped,
@@ -144,10 +144,10 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-template <int GZ>
+template <int GZ, int VIEWS>
 __global__ void __launch_bounds__(kBpThreads, 3)
     k_back_grad(const InstTable* __restrict__ inst, int n_inst, Geo g, int weight, const float4* __restrict__ det4,
-                const float* __restrict__ wvol, float* __restrict__ part, int bricks_x, int bricks_y, int views) {
+                const float* __restrict__ wvol, float* __restrict__ part, int bricks_x, int bricks_y) {
   __shared__ float sred[kBpThreads / 32][12];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n_bricks = gridDim.x;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kBpThreads, 3)
   const int qu = g.nu + 4;
   const size_t det_stride = (size_t)(g.nu + 4) * (g.nv + 4);
   const float fu = (float)g.nu + 1.f, fvv = (float)g.nv + 1.f;
-  const int n0 = blockIdx.y * views, n1 = min(n_inst, n0 + views);
+  const int n0 = blockIdx.y * VIEWS, n1 = min(n_inst, n0 + VIEWS);
   for (int n = n0; n < n1; ++n) {
     const InstTable& T = inst[n];
     float a[12];
@@ -373,10 +373,12 @@ cudaError_t launch_back_grad(const InstTable* d_inst, int n_inst, Geo geo, int w
   const int gz = brick_gz(shape), views = brick_views(shape);
   const int bx = ceil_div(geo.nx, kGbX), by = ceil_div(geo.ny, kGbY), bz = ceil_div(geo.nz, gz);
   dim3 grid(bx * by * bz, ceil_div(n_inst, views));  // = back_grad_blocks(geo, shape) records per instance
-  if (gz == 8)
-    k_back_grad<8><<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_det4, d_wvol, d_part, bx, by, views);
-  else
-    k_back_grad<16><<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_det4, d_wvol, d_part, bx, by, views);
+  switch (shape) {
+    case 1: k_back_grad<8, 8><<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_det4, d_wvol, d_part, bx, by); break;
+    case 2: k_back_grad<16, 16><<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_det4, d_wvol, d_part, bx, by); break;
+    case 3: k_back_grad<8, 16><<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_det4, d_wvol, d_part, bx, by); break;
+    default: k_back_grad<16, 8><<<grid, kBpThreads, 0, s>>>(d_inst, n_inst, geo, weight, d_det4, d_wvol, d_part, bx, by); break;
+  }
   return cudaGetLastError();
 }
 
