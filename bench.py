@@ -41,6 +41,7 @@ L2_FLUSH_BYTES = 256 << 20
 # ncu capture of the 8-instance case (profiles/k_forward_grad_ncc_...md,
 # 1.903 GB) scaled by 128/8 instances, since every instance re-streams the
 # volume.  Set to None whenever the kernel changes until it is re-measured.
+NCU_L1_WAVEFRONT_PCT = 88.7    # ncu l1tex__data_pipe_lsu_wavefronts of the fused march (small case, same kernel)
 TRAFFIC_PER_LAUNCH = 21.57e9  # ncu dram__bytes_read+write of one full-size launch (one-pass metrics): 21.55 GB + 19 MB
 
 
@@ -1118,6 +1119,12 @@ def main():
                              "%d B/clk x %.0f MHz" % (L1_BYTES_PER_SAMPLE, n_sm, L1_BYTES_PER_CLK_SM, sm_max),
                      "alu": {"achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
                              "frac": alu_achieved / alu_peak, "flop_per_sample": FLOP_PER_SAMPLE},
+                     # the unit that binds, from the committed ncu capture of the same kernel (a small case of
+                     # this launch; not measured live)
+                     "ncu_l1_wavefront_utilisation": {
+                         "pct_of_peak": NCU_L1_WAVEFRONT_PCT,
+                         "source": "profiles/k_forward_grad_ncc_registration_256c_2x384.md "
+                                   "(l1tex__data_pipe_lsu_wavefronts, 8-instance case)"},
                      "empirical_gather_ceiling": {
                          "kernel_ms": probe_ms, "ray_samples_per_s": samples / (probe_ms * 1e-3),
                          "frac": probe_ms / k_ms,
