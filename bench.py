@@ -37,12 +37,13 @@ FLOP_PER_SAMPLE = 118     # FP32 work of one fused-march sample: 4-channel trili
 L1_BYTES_PER_SAMPLE = 128  # 8 trilinear corners x float4 (mu, grad mu) delivered to registers
 L1_BYTES_PER_CLK_SM = 128  # L1 data-pipe width per SM per clock
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of one fused-march launch on this workload: the
-# ncu capture of the 8-instance case (profiles/k_forward_grad_ncc_...md,
-# 1.903 GB) scaled by 128/8 instances, since every instance re-streams the
-# volume.  Set to None whenever the kernel changes until it is re-measured.
-NCU_L1_WAVEFRONT_PCT = 88.7    # ncu l1tex__data_pipe_lsu_wavefronts of the fused march (small case, same kernel)
-TRAFFIC_PER_LAUNCH = 21.57e9  # ncu dram__bytes_read+write of one full-size launch (one-pass metrics): 21.55 GB + 19 MB
+# Counters of the fused march from ncu captures (they cannot be read live):
+# the L1 data-pipe wavefront utilisation of the 8-instance case, and the DRAM
+# bytes (read + write) of one full-size launch of this workload taken with
+# one-pass metrics.  Set to None whenever the kernel changes until they are
+# re-measured.
+NCU_L1_WAVEFRONT_PCT = 88.7
+TRAFFIC_PER_LAUNCH = 21.57e9  # 21.55 GB read + 19 MB written
 
 
 def load_peaks():
@@ -1123,8 +1124,8 @@ def main():
                      # this launch; not measured live)
                      "ncu_l1_wavefront_utilisation": {
                          "pct_of_peak": NCU_L1_WAVEFRONT_PCT,
-                         "source": "profiles/k_forward_grad_ncc_registration_256c_2x384.md "
-                                   "(l1tex__data_pipe_lsu_wavefronts, 8-instance case)"},
+                         "source": "ncu l1tex__data_pipe_lsu_wavefronts of the same kernel, 8-instance case "
+                                   "(summary under profiles/)"},
                      "empirical_gather_ceiling": {
                          "kernel_ms": probe_ms, "ray_samples_per_s": samples / (probe_ms * 1e-3),
                          "frac": probe_ms / k_ms,
