@@ -7,7 +7,7 @@ Per iteration: FDK back-projection of the filtered projections at the
 current poses (proj_back, FDK weight), the sharpness S = -Var(|grad mu|) and
 dS/dmu (proj_sharpness), the per-view pose gradient (proj_back_pose_grad
 with the FDK weight derivative), and an Adam step on the [n_views, 6] poses.
-The paper uses gradient entropy as the sharpness criterion; this build uses
+The paper uses gradient entropy as the sharpness criterion; this module uses
 the negative variance of the gradient magnitude.
 
 With spline_nodes = K the per-view poses are not free: the motion is a
