@@ -572,10 +572,15 @@ def paper_tables(pb, torch, dev, flush):
         # Table III: one view, 100 iterations of loss + pose gradient + update
         g1 = synth.Geometry(n, n, n, vox, vox, vox, d, d, synth.circular_views(1, synth.SAD, synth.SDD, pix, pix),
                             0.5 * vox)
+        # the target is rendered by a plan of its own, so the measured workspace is the gradient path's
+        Pt = pb.Projector(g1, n_pose=1, inst_view=np.zeros(1, np.int32), inst_pose=np.zeros(1, np.int32),
+                          ops=pb.PROJ_OP_FORWARD)
+        Pt.set_volume(mu)
+        target = Pt.forward(torch.zeros((1, 6), device=dev)).contiguous()
+        del Pt
         P1 = pb.Projector(g1, n_pose=1, inst_view=np.zeros(1, np.int32), inst_pose=np.zeros(1, np.int32),
-                          ops=pb.PROJ_OP_FORWARD | pb.PROJ_OP_FORWARD_GRAD)
+                          ops=pb.PROJ_OP_FORWARD_GRAD)
         P1.set_volume(mu)
-        target = P1.forward(torch.zeros((1, 6), device=dev)).contiguous()
         pose = torch.tensor([[2.0, -1.0, 1.5, 0.02, -0.03, 0.01]], device=dev)
         gbuf = torch.empty((1, 6), device=dev)
         lbuf = torch.empty(1, device=dev)
