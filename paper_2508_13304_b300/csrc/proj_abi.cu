@@ -272,9 +272,16 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   p->off_vol4 = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float4) * (size_t)npad2) : 0;
   p->off_vol4y = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float4) * (size_t)npad2y) : 0;
   p->off_part_f = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float) * kRec * (size_t)n_inst * p->n_tiles) : 0;
-  p->off_det4 = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float4) * (size_t)n_inst * (G.nu + 4) * (G.nv + 4)) : 0;
+  // the detector scratch of proj_back (cell records) and of proj_back_pose_grad (the (l, d_u l, d_v l)
+  // stack) are never needed by the same call: one region serves both
+  {
+    const size_t det4_bytes = (ops & PROJ_OP_BACK_GRAD) ? sizeof(float4) * (size_t)n_inst * (G.nu + 4) * (G.nv + 4) : 0;
+    const size_t detq_bytes = (ops & PROJ_OP_BACK) ? sizeof(float4) * (size_t)n_inst * (G.nu + 1) * (G.nv + 1) : 0;
+    const size_t off_det = (det4_bytes || detq_bytes) ? take(std::max(det4_bytes, detq_bytes)) : 0;
+    p->off_det4 = det4_bytes ? off_det : 0;
+    p->off_detq = detq_bytes ? off_det : 0;
+  }
   p->off_part_b = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float) * 12 * (size_t)n_inst * p->bp_blocks) : 0;
-  p->off_detq = (ops & PROJ_OP_BACK) ? take(sizeof(float4) * (size_t)n_inst * (G.nu + 1) * (G.nv + 1)) : 0;
   p->off_acc = (ops & PROJ_OP_ADJOINT) ? take(sizeof(float4) * npad_sz) : 0;
   if (ops & PROJ_OP_SHARPNESS) {
     p->off_sharp_m = take(sizeof(float) * (size_t)G.nx * G.ny * G.nz);
