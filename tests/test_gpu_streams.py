@@ -1,4 +1,4 @@
-"""Two plans with their own workspaces on two CUDA streams, launched
+"""Streams and graphs.  Two plans with their own workspaces on two CUDA streams, launched
 interleaved so that their kernels can overlap: every result equals the one
 of the same calls run one after another on the default stream (the library
 keeps no state outside the plan and the caller's workspace)."""
@@ -66,3 +66,25 @@ def test_two_plans_on_two_streams_match_sequential_runs():
     for got, want in ((oa, seq[0]), (ob, seq[1])):
         for k in ("grad", "loss", "proj", "vol", "bgrad"):
             assert torch.equal(got[k], want[k]), k
+
+
+def test_calls_replay_from_a_cuda_graph():
+    """Every hot-path call is asynchronous and allocation-free, so a step of
+    them can be captured once and replayed; the replay reproduces the eager
+    results bit for bit."""
+    c = make(3, (40, 36, 42), (48, 40), 2, 2)
+    want = run(c, None)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        run(c, s)                            # warm-up on the capture stream
+    s.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        got = run(c, s)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    for k in ("grad", "loss", "proj", "vol", "bgrad"):
+        assert torch.equal(got[k], want[k]), k
