@@ -67,10 +67,14 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other kernels' measurements")
     ap.add_argument("--section", default=None,
-                    choices=["gemm", "forward", "back", "accuracy", "tables", "registration500", "moco", "c1"],
+                    choices=["gemm", "forward", "back", "accuracy", "tables", "registration500", "moco", "c1",
+                             "batch"],
                     help="run only one secondary measurement and print it (gemm: the tensor-core GEMM shapes; "
                          "forward: forward projection of the 128 registration instances; back: FDK "
-                         "back-projection and its pose gradient, 360 views of 512^2 on 256^3)")
+                         "back-projection and its pose gradient, 360 views of 512^2 on 256^3; batch: the "
+                         "uneven single-view problems in one persistent launch)")
+    ap.add_argument("--batch-problems", type=int, default=24,
+                    help="--section batch: how many of the 24 single-view problems")
     ap.add_argument("--posenet-eval", action="store_true",
                     help="also train the pose-proposal network on 200k DRRs and compare proposal + registration "
                          "with 16-start registration (about 3 minutes)")
@@ -412,12 +416,13 @@ def _event_ms(torch, fn, flush, reps=2):
     return float(np.median(ts))
 
 
-def uneven_batch(pb, torch, dev, flush, with_large):
+def uneven_batch(pb, torch, dev, flush, with_large, n_extra=24):
     """Independent L2 pose-gradient problems of uneven size: one persistent
     batched launch (proj_batch_run) against one proj_forward_pose_grad call
     per problem on the same stream.  Both include the pose set-ups and the
-    reductions."""
-    probs = synth.workload_uneven(with_large=with_large)
+    reductions.  n_extra: how many of the single-view problems (the first
+    ones of the same seeded sequence)."""
+    probs = synth.workload_uneven(with_large=with_large, n_extra=n_extra)
     gen = torch.Generator(device=dev)
     gen.manual_seed(1004)
     items, keep, samples = [], [], 0
@@ -884,6 +889,12 @@ def main():
         ms1 = _timed(lambda: pb.proj_forward_adjoint(P0.plan, out0, pose0, vol0, P0.ws), P0.plan, pb, fl)
         print(json.dumps({"section": "forward", "kernel": "k_forward", "kernel_ms": ms0,
                           "k_forward_adjoint_ms": ms1, "config": "256^3, 128 view instances of 384^2"}), flush=True)
+        return
+    if args.section == "batch":
+        dev0 = torch.device("cuda", local)
+        fl = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev0)
+        print(json.dumps({"section": "batch", **uneven_batch(pb, torch, dev0, fl, False, args.batch_problems)}),
+              flush=True)
         return
     if args.section == "c1":
         dev0 = torch.device("cuda", local)
