@@ -371,7 +371,12 @@ int proj_kernel_time_ms(proj_plan plan, float *ms);
  *          proj_forward_pose_grad (d_loss may be NULL).
  * The result equals proj_forward_pose_grad's for the same inputs.  The first
  * call on a device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream capture.
+ * with that device current) and caches it; make that first call before any
+ * stream capture, and do not reset the device (cudaDeviceReset) after it.
+ * Every call copies the host tables (views, instance maps) into the array
+ * with cudaMemcpyAsync from pageable memory that lives only for the call, so
+ * a call on a stream that is capturing a CUDA graph is refused with
+ * PROJ_E_ARG before anything is enqueued.
  * Every call on a device shares the one array and overwrites it, so calls
  * that overlap on the GPU (other streams or threads) race: serialise them.
  * Non-finite poses give zero gradients (no status word is kept). */

@@ -315,6 +315,11 @@ def proj_forward_pose_grad_static(geom, n_pose, inst_view, inst_pose, mu, pose, 
     ip = np.ascontiguousarray(inst_pose, dtype=np.int32)
     if iv.shape != ip.shape:
         raise ValueError("inst_view and inst_pose differ in length")
+    # the library uses the current device's scratch and stream: every tensor must live there
+    cur = torch.cuda.current_device()
+    for t, nm in ((mu, "mu"), (pose, "pose"), (ref, "ref"), (grad, "grad"), (loss_out, "loss")):
+        if isinstance(t, torch.Tensor) and t.is_cuda and t.device.index != cur:
+            raise ValueError("%s is on cuda:%d, the current device is cuda:%d" % (nm, t.device.index, cur))
     n_img = int(geom.nu) * int(geom.nv)
     n_ref = (iv.size if loss == PROJ_LOSS_RESIDUAL else views.shape[0]) * n_img
     _check(lib().proj_forward_pose_grad_static(

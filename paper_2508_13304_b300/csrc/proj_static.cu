@@ -63,7 +63,9 @@ std::mutex g_mutex;
 unsigned char* g_addr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch on the current device, looked up once per
-// device with that device current.
+// device with that device current.  The cached address belongs to the
+// context that was current then: a cudaDeviceReset after the first call
+// (which unloads this module) is not supported.
 int scratch_address(unsigned char** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -110,9 +112,10 @@ int proj_forward_pose_grad_static(const proj_geometry* geom, int n_pose, int n_i
   if (npad > kMaxPadVoxels)
     return fail(PROJ_E_ARG, "volume %d x %d x %d exceeds the static scratch limit (%lld padded voxels > %d)", G.nx,
                 G.ny, G.nz, npad, kMaxPadVoxels);
-  if (n_inst > kMaxInst || n_pose > kMaxPose || G.n_views > kMaxViews)
-    return fail(PROJ_E_ARG, "n_inst %d, n_pose %d, n_views %d exceed the static scratch limit of %d each", n_inst,
-                n_pose, G.n_views, kMaxInst);
+  if (n_inst > kMaxInst) return fail(PROJ_E_ARG, "n_inst %d exceeds the static scratch limit of %d", n_inst, kMaxInst);
+  if (n_pose > kMaxPose) return fail(PROJ_E_ARG, "n_pose %d exceeds the static scratch limit of %d", n_pose, kMaxPose);
+  if (G.n_views > kMaxViews)
+    return fail(PROJ_E_ARG, "n_views %d exceeds the static scratch limit of %d", G.n_views, kMaxViews);
   if (n_inst * n_tiles > kMaxRecords)
     return fail(PROJ_E_ARG, "n_inst x detector tiles (%lld) exceeds the static scratch limit of %d",
                 (long long)n_inst * n_tiles, kMaxRecords);
@@ -172,10 +175,21 @@ int proj_forward_pose_grad_static(const proj_geometry* geom, int n_pose, int n_i
   g.nv = G.nv;
   g.step = (float)G.step;
 
+  // Each call copies its host tables (the caller's view table and instance
+  // maps, and CSR arrays on this function's stack) with cudaMemcpyAsync.
+  // A graph captured from such a call would read those host buffers again
+  // at every replay, long after they are gone, so a capturing stream is
+  // refused before anything is enqueued.
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+  if (ce != cudaSuccess) return fail(PROJ_E_CUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(ce));
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(PROJ_E_ARG, "the stream is capturing a CUDA graph; this entry point cannot be captured");
+
   unsigned char* base = nullptr;
   int rc = scratch_address(&base);
   if (rc) return rc;
-  cudaStream_t s = (cudaStream_t)stream;
   int* status = reinterpret_cast<int*>(base + kOffStatus);
   double* views = reinterpret_cast<double*>(base + kOffViews);
   int* d_iv = reinterpret_cast<int*>(base + kOffInstView);
