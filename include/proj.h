@@ -116,9 +116,23 @@ enum {
   PROJ_OP_ALL = 63
 };
 
+/* Option flags, ORed into the ops argument of proj_plan_create (a library
+ * facility; the paper fixes no memory layout). */
+enum {
+  /* Keep one copy of the prepared volume (rows along x) instead of two
+   * (rows along x and along y, each instance marching the copy whose rows
+   * run closest to its detector u axis).  Halves the volume part of the
+   * workspace (the float4 (mu, grad mu) volume is 16 B per voxel of the
+   * padded grid, the cell records of the DRR march 16 B per voxel) at the
+   * cost of slower gathers for instances whose u axis runs along y.
+   * Results are identical to the two-copy plan's. */
+  PROJ_FLAG_ONE_COPY = 256
+};
+
 /* Device status bits (proj_check). */
 enum {
-  PROJ_STATUS_BAD_POSE = 1 /* a pose had a non-finite entry */
+  PROJ_STATUS_BAD_POSE = 1, /* a pose had a non-finite entry */
+  PROJ_STATUS_BAD_INDEX = 2 /* a pose list held an index outside [-1, n_pose) */
 };
 
 typedef struct {
@@ -187,6 +201,27 @@ int proj_forward(proj_plan plan, const float *d_pose, float *d_proj, void *d_ws,
  *   d_proj      out [n_inst][nv][nu] FP32 projections, or NULL. */
 int proj_forward_pose_grad(proj_plan plan, const float *d_pose, int loss, const float *d_ref, float *d_grad,
                            float *d_loss, float *d_proj, void *d_ws, size_t ws_bytes, proj_stream stream);
+
+/* proj_forward_pose_grad for a subset of the plan's poses, chosen per call
+ * (a library facility for multi-start registration: starts that have
+ * converged or failed leave the launch, new starts take their slots).
+ *   d_pose_list  device [n_list] int32: pose indices in [0, n_pose), or -1
+ *                for an empty slot.  The kernels read it when they run, so
+ *                a caller may rewrite it on the stream between calls (also
+ *                inside a captured CUDA graph).  An entry outside
+ *                [-1, n_pose) is skipped and sets PROJ_STATUS_BAD_INDEX; a
+ *                pose listed twice is evaluated twice with identical results.
+ *   n_list       >= 1 (slots; the launch grid has n_list x the largest
+ *                number of instances of one pose x ray tiles blocks, which
+ *                must stay below 2^31).
+ * Every instance of each listed pose is marched.  Rows of d_grad and d_loss
+ * belong to the poses (as in proj_forward_pose_grad); only the rows of
+ * listed poses are written, the others are left as they were.  d_proj rows
+ * of the marched instances are written, the others left as they were.
+ * Other arguments and errors as proj_forward_pose_grad. */
+int proj_forward_pose_grad_list(proj_plan plan, const float *d_pose, const int *d_pose_list, int n_list, int loss,
+                                const float *d_ref, float *d_grad, float *d_loss, float *d_proj, void *d_ws,
+                                size_t ws_bytes, proj_stream stream);
 
 /* Voxel-driven back-projection (Eq. back) of one image per instance.
  *   d_proj  [n_inst][nv][nu] FP32; copied first into zero-bordered cell

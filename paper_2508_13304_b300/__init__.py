@@ -27,7 +27,9 @@ PROJ_W_NONE, PROJ_W_FDK, PROJ_W_FDK_CONST = 0, 1, 2
 PROJ_OP_FORWARD, PROJ_OP_FORWARD_GRAD, PROJ_OP_BACK, PROJ_OP_BACK_GRAD, PROJ_OP_ADJOINT = 1, 2, 4, 8, 16
 PROJ_OP_SHARPNESS = 32
 PROJ_OP_ALL = 63
+PROJ_FLAG_ONE_COPY = 256
 PROJ_STATUS_BAD_POSE = 1
+PROJ_STATUS_BAD_INDEX = 2
 
 
 class ProjError(RuntimeError):
@@ -58,6 +60,7 @@ _SIGS = {
     "proj_set_volume": [_P, _P, _P, _SZ, _P],
     "proj_forward": [_P, _P, _P, _P, _SZ, _P],
     "proj_forward_pose_grad": [_P, _P, _I, _P, _P, _P, _P, _P, _SZ, _P],
+    "proj_forward_pose_grad_list": [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P, _SZ, _P],
     "proj_back": [_P, _P, _P, _I, _P, _P, _SZ, _P],
     "proj_back_pose_grad": [_P, _P, _P, _I, _P, _P, _P, _SZ, _P],
     "proj_back_adjoint": [_P, _P, _P, _I, _P, _P, _SZ, _P],
@@ -248,6 +251,23 @@ def proj_forward_pose_grad(plan: Plan, pose, loss, ref, grad, loss_out=None, pro
     _check(lib().proj_forward_pose_grad(
         plan.handle, _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"), int(loss),
         _ptr(ref, torch.float32, n_ref, "ref"), _ptr(grad, torch.float32, 6 * plan.n_pose, "grad"),
+        _ptr(loss_out, torch.float32, plan.n_pose, "loss", allow_none=True),
+        _ptr(proj_out, torch.float32, plan.n_inst * plan.img_numel, "proj", allow_none=True), p, nb,
+        _stream(stream)))
+
+
+def proj_forward_pose_grad_list(plan: Plan, pose, pose_list, loss, ref, grad, loss_out=None, proj_out=None, ws=None,
+                                stream=None):
+    """Pose gradient of the poses in pose_list (int32 CUDA tensor, -1 = empty
+    slot); rows of grad / loss_out / proj_out of other poses are untouched."""
+    import torch
+    p, nb = _ws(ws)
+    n_ref = (plan.n_inst if loss == PROJ_LOSS_RESIDUAL else plan.geom.n_views) * plan.img_numel
+    n_list = pose_list.numel() if pose_list is not None else 0
+    _check(lib().proj_forward_pose_grad_list(
+        plan.handle, _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"), _ptr(pose_list, torch.int32, None, "pose_list"),
+        int(n_list), int(loss), _ptr(ref, torch.float32, n_ref, "ref"),
+        _ptr(grad, torch.float32, 6 * plan.n_pose, "grad"),
         _ptr(loss_out, torch.float32, plan.n_pose, "loss", allow_none=True),
         _ptr(proj_out, torch.float32, plan.n_inst * plan.img_numel, "proj", allow_none=True), p, nb,
         _stream(stream)))

@@ -45,6 +45,7 @@ struct proj_plan_s {
   int n_views, n_pose, n_inst, ops;
   int device;
   int n_tiles;        // ray tiles per instance
+  int ipp = 1;        // most instances of any one pose (grid slots per pose of a pose list)
   int bp_blocks;      // most voxel bricks of the back-projection gradient over the brick shapes (records per instance)
   int bp_shape = 0;   // brick shape of the back-projection gradient (0..kBrickShapes-1)
   std::vector<double> views;
@@ -236,12 +237,15 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
 
   // CSR list of instances per pose (ascending instance order).
   std::vector<int> ptr(n_pose + 1, 0), idx(n_inst);
+  int p_ipp = 1;
   for (int i = 0; i < n_inst; ++i) ptr[inst_pose[i] + 1]++;
   for (int q = 0; q < n_pose; ++q) ptr[q + 1] += ptr[q];
+  for (int q = 0; q < n_pose; ++q) p_ipp = std::max(p_ipp, ptr[q + 1] - ptr[q]);
   {
     std::vector<int> fill(ptr.begin(), ptr.end() - 1);
     for (int i = 0; i < n_inst; ++i) idx[fill[inst_pose[i]]++] = i;
   }
+  p->ipp = p_ipp;
 
   cudaError_t e = cudaGetDevice(&p->device);
   int n_sm = 148;
@@ -434,6 +438,35 @@ int proj_forward_pose_grad(proj_plan p, const float* d_pose, int loss, const flo
   if (e != cudaSuccess) return cuda_fail(e, "forward pose-gradient launch");
   e = launch_forward_grad_reduce(w.inst, w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_tiles, p->geo, loss,
                                  w.part_f, d_grad, d_loss, s);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "forward pose-gradient reduction launch");
+}
+
+int proj_forward_pose_grad_list(proj_plan p, const float* d_pose, const int* d_pose_list, int n_list, int loss,
+                                const float* d_ref, float* d_grad, float* d_loss, float* d_proj, void* d_ws,
+                                size_t ws_bytes, proj_stream stream) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_pose || !d_pose_list || !d_ref || !d_grad)
+    return fail(PROJ_E_ARG, "proj_forward_pose_grad_list: NULL pose, pose list, reference or grad");
+  if (n_list < 1) return fail(PROJ_E_ARG, "proj_forward_pose_grad_list: n_list must be >= 1");
+  if ((long long)n_list * p->ipp * p->n_tiles > 0x7fffffffLL)
+    return fail(PROJ_E_ARG, "proj_forward_pose_grad_list: n_list x instances per pose x tiles exceeds 2^31 - 1");
+  if (loss != PROJ_LOSS_RESIDUAL && loss != PROJ_LOSS_L2 && loss != PROJ_LOSS_NCC)
+    return fail(PROJ_E_ARG, "unknown loss mode %d", loss);
+  int rc = need_op(p, PROJ_OP_FORWARD_GRAD, "proj_forward_pose_grad_list");
+  if (rc) return rc;
+  WsView w;
+  if ((rc = check_ws(p, d_ws, ws_bytes, &w))) return rc;
+  if ((rc = check_device(p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = setup(p, d_pose, w, s))) return rc;
+  PoseList L{d_pose_list, n_list, p->ipp, p->n_pose, p->d_pose_ptr, p->d_pose_idx, w.status};
+  mark(p, true, s);
+  cudaError_t e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, d_proj, w.part_f, s,
+                                      p->warp_width, &L);
+  mark(p, false, s);
+  if (e != cudaSuccess) return cuda_fail(e, "forward pose-gradient launch");
+  e = launch_forward_grad_reduce(w.inst, w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_tiles, p->geo, loss,
+                                 w.part_f, d_grad, d_loss, s, d_pose_list, n_list);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "forward pose-gradient reduction launch");
 }
 

@@ -388,14 +388,39 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
   __syncthreads();  // red is reused by the next tile of a persistent block
 }
 
+// Block -> (instance, tile) when a pose list selects the poses to march: the
+// grid has n_list x ipp virtual instances (slot, j) per row of tiles, in the
+// band-major order of band_major_tile; virtual instance (slot, j) is the j-th
+// instance of pose list[slot].  Returns false for blocks with nothing to do.
+__device__ __forceinline__ bool listed_tile(const PoseList& L, int n_tiles, int tiles_u, int& n, int& tile) {
+  const int nv = L.n_list * L.ipp;
+  const int b = blockIdx.x, tu = b % tiles_u, rest = b / tiles_u;
+  const int q = rest % nv, slot = q / L.ipp, j = q % L.ipp;
+  tile = (rest / nv) * tiles_u + tu;
+  const int p = L.list[slot];
+  if (p < 0) return false;
+  if (p >= L.n_pose) {
+    if (threadIdx.x == 0 && j == 0 && tile == 0) atomicOr(L.status, PROJ_STATUS_BAD_INDEX);
+    return false;
+  }
+  const int e0 = L.pose_ptr[p];
+  if (j >= L.pose_ptr[p + 1] - e0) return false;
+  n = L.pose_idx[e0 + j];
+  return true;
+}
+
 template <int LOSS, int WU>
 __global__ void __launch_bounds__(kMarchThreads, 4)
     k_forward_grad(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g,
                    const float4* __restrict__ vol, const float4* __restrict__ voly, const float* __restrict__ ref,
-                   float* __restrict__ proj, float* __restrict__ part) {
+                   float* __restrict__ proj, float* __restrict__ part, PoseList L) {
   __shared__ float red[kMarchThreads / 32][kRec];
   int n, tile;
-  band_major_tile(n_tiles, tiles_u, n, tile);
+  if (L.list) {
+    if (!listed_tile(L, n_tiles, tiles_u, n, tile)) return;  // uniform per block
+  } else {
+    band_major_tile(n_tiles, tiles_u, n, tile);
+  }
   if (voly && inst[n].yfast)  // uniform per block
     march_tile<LOSS, WU, 1>(inst, n, tile, n_tiles, tiles_u, g, voly, ref, proj, part, red);
   else
@@ -518,11 +543,13 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
 __global__ void k_forward_grad_reduce(const InstTable* __restrict__ inst, const PoseTable* __restrict__ ptab,
                                       const int* __restrict__ pose_ptr, const int* __restrict__ pose_idx,
                                       int n_tiles, Geo g, int loss, const float* __restrict__ part,
-                                      float* __restrict__ grad, float* __restrict__ loss_out) {
+                                      float* __restrict__ grad, float* __restrict__ loss_out,
+                                      const int* __restrict__ pose_list, int n_pose) {
   constexpr int kGroups = 5;
   __shared__ double sp[kGroups][kRec];
   __shared__ double rec[kRec];
-  const int p = blockIdx.x;
+  const int p = pose_list ? pose_list[blockIdx.x] : (int)blockIdx.x;
+  if (p < 0 || p >= n_pose) return;  // empty slot (or an index the march reported)
   const int t = threadIdx.x;
   double acc[12];
   double L = 0.0;
@@ -730,19 +757,19 @@ namespace {
 template <int WU>
 void launch_forward_grad_w(const InstTable* d_inst, int grid, int nt, int tu, const Geo& geo, const float4* d_vol4,
                            const float4* d_vol4y, int loss, const float* d_ref, float* d_proj, float* d_part,
-                           cudaStream_t s) {
+                           const PoseList& L, cudaStream_t s) {
   switch (loss) {
     case PROJ_LOSS_RESIDUAL:
       k_forward_grad<PROJ_LOSS_RESIDUAL, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_vol4y,
-                                                                            d_ref, d_proj, d_part);
+                                                                            d_ref, d_proj, d_part, L);
       break;
     case PROJ_LOSS_L2:
       k_forward_grad<PROJ_LOSS_L2, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_vol4y, d_ref,
-                                                                      d_proj, d_part);
+                                                                      d_proj, d_part, L);
       break;
     default:
       k_forward_grad<PROJ_LOSS_NCC, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_vol4y, d_ref,
-                                                                       d_proj, d_part);
+                                                                       d_proj, d_part, L);
       break;
   }
 }
@@ -750,16 +777,21 @@ void launch_forward_grad_w(const InstTable* d_inst, int grid, int nt, int tu, co
 
 cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
                                 const float4* d_vol4y, int loss, const float* d_ref, float* d_proj, float* d_part,
-                                cudaStream_t s, int warp_width) {
+                                cudaStream_t s, int warp_width, const PoseList* pl) {
   const int nt = tiles_of(geo), tu = tiles_u_of(geo);
-  const int grid = n_inst * nt;
+  PoseList L{};
+  if (pl && pl->list) L = *pl;
+  const long long grid_ll = L.list ? (long long)L.n_list * L.ipp * nt : (long long)n_inst * nt;
+  if (grid_ll < 1) return cudaSuccess;
+  if (grid_ll > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const int grid = (int)grid_ll;
   switch (warp_width) {
-    case 2: launch_forward_grad_w<2>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, s); break;
-    case 8: launch_forward_grad_w<8>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, s); break;
+    case 2: launch_forward_grad_w<2>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, L, s); break;
+    case 8: launch_forward_grad_w<8>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, L, s); break;
     case 16:
-      launch_forward_grad_w<16>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, s);
+      launch_forward_grad_w<16>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, L, s);
       break;
-    default: launch_forward_grad_w<4>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, s); break;
+    default: launch_forward_grad_w<4>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, L, s); break;
   }
   return cudaGetLastError();
 }
@@ -853,9 +885,11 @@ int forward_grad_batch_blocks_per_sm(int loss_all) {
 cudaError_t launch_forward_grad_reduce(const InstTable* d_inst, const PoseTable* d_ptab, int n_pose,
                                        const int* d_pose_ptr, const int* d_pose_idx, int n_tiles, Geo geo,
                                        int loss, const float* d_part, float* d_grad, float* d_loss,
-                                       cudaStream_t s) {
-  k_forward_grad_reduce<<<n_pose, 256, 0, s>>>(d_inst, d_ptab, d_pose_ptr, d_pose_idx, n_tiles, geo, loss, d_part,
-                                               d_grad, d_loss);
+                                       cudaStream_t s, const int* d_pose_list, int n_list) {
+  const int blocks = d_pose_list ? n_list : n_pose;
+  if (blocks < 1) return cudaSuccess;
+  k_forward_grad_reduce<<<blocks, 256, 0, s>>>(d_inst, d_ptab, d_pose_ptr, d_pose_idx, n_tiles, geo, loss, d_part,
+                                               d_grad, d_loss, d_pose_list, n_pose);
   return cudaGetLastError();
 }
 

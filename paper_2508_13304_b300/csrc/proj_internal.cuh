@@ -82,6 +82,19 @@ struct BatchProblem {
   long long item_begin;  // first global work item of this problem
 };
 
+// Optional per-call subset of a plan's poses for the fused march and its
+// reduction (proj_forward_pose_grad_list).  With list == nullptr every
+// instance of the plan is marched and every pose reduced.
+struct PoseList {
+  const int* list;      // device [n_list]: pose indices, or -1 for an empty slot
+  int n_list;
+  int ipp;              // most instances of any one pose (grid slots per listed pose)
+  int n_pose;
+  const int* pose_ptr;  // the plan's instances per pose (CSR)
+  const int* pose_idx;
+  int* status;          // PROJ_STATUS_BAD_INDEX for entries outside [-1, n_pose)
+};
+
 // Record of one K3 block (ray tile) partial: see kRec* offsets.
 constexpr int kRec = 48;
 constexpr int kRecG = 0;      // 12: sum of w * G   (RESIDUAL, L2)  or sum G (NCC)
@@ -123,19 +136,21 @@ cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const f
 cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long* d_count, cudaStream_t s);
 // warp_width: rays per warp row of the 16x16 tile (2, 4, 8 or 16; other values use 4)
 // d_vol4y: the y-fast copy (instances with yfast set march it), or null (all march d_vol4)
+// pl: optional pose subset (nullptr or pl->list == nullptr: all n_inst instances)
 cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
                                 const float4* d_vol4y, int loss, const float* d_ref, float* d_proj, float* d_part,
-                                cudaStream_t s, int warp_width = 4);
+                                cudaStream_t s, int warp_width = 4, const PoseList* pl = nullptr);
 // the fused march's gathers without its arithmetic (empirical gather ceiling)
 cudaError_t launch_gather_probe(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
                                 const float4* d_vol4y, float* d_sink, cudaStream_t s);
 // y-fast copy of the pitched (mu, grad mu) volume (tiled transpose of every z slice)
 cudaError_t launch_volume_yfast(const float4* d_vol4, Geo geo, float4* d_vol4y, cudaStream_t s);
 cudaError_t launch_records_yfast(const float4* d_volq, Geo geo, float4* d_volqy, cudaStream_t s);
+// d_pose_list: optional [n_list] poses to reduce (-1 = skip); nullptr = all n_pose
 cudaError_t launch_forward_grad_reduce(const InstTable* d_inst, const PoseTable* d_ptab, int n_pose,
                                        const int* d_pose_ptr, const int* d_pose_idx, int n_tiles, Geo geo,
                                        int loss, const float* d_part, float* d_grad, float* d_loss,
-                                       cudaStream_t s);
+                                       cudaStream_t s, const int* d_pose_list = nullptr, int n_list = 0);
 // loss_all: the loss shared by every problem, or -1 for a batch of mixed losses
 cudaError_t launch_forward_grad_batch(const BatchProblem* d_probs, int n_probs, long long n_items,
                                       unsigned long long* d_counter, int n_blocks, int loss_all, cudaStream_t s);

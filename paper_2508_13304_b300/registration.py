@@ -35,15 +35,18 @@ class Adam:
         self.eps = eps
         self.m = torch.zeros((n, 6), device=device)
         self.v = torch.zeros((n, 6), device=device)
-        self.t = torch.zeros((), dtype=torch.float32, device=device)   # step count, on the device
+        # step count of each pose, on the device: a pose's bias correction counts only its own
+        # updates, so a start that joins a running batch later follows its own trajectory
+        self.t = torch.zeros((n, 1), dtype=torch.float32, device=device)
 
     def step(self, pose, grad, active):
-        self.t.add_(1.0)
         a = active.float().reshape(-1, 1)
+        self.t.add_(a)
+        tc = self.t.clamp(min=1.0)              # rows never updated have m = v = 0
         self.m.mul_(1 - a * (1 - self.b1)).add_(a * (1 - self.b1) * grad)
         self.v.mul_(1 - a * (1 - self.b2)).add_(a * (1 - self.b2) * grad * grad)
-        mh = self.m / (1 - torch.pow(self.b1, self.t))
-        vh = self.v / (1 - torch.pow(self.b2, self.t))
+        mh = self.m / (1 - torch.pow(self.b1, tc))
+        vh = self.v / (1 - torch.pow(self.b2, tc))
         pose.sub_(a * self.lr * mh / (torch.sqrt(vh) + self.eps))
 
 
@@ -52,7 +55,8 @@ def paper_step_sizes():
 
 
 def register(geom, mu, target, init_poses, max_iter=200, lr=None, ncc_stop=0.999, dloss_stop=1e-5,
-             batched=True, device="cuda", true_pose=None, tol=(0.5, 0.5), graph_steps=0, inst_view=None):
+             batched=True, device="cuda", true_pose=None, tol=(0.5, 0.5), graph_steps=0, inst_view=None,
+             wave=None, stop_at_hit=False):
     """Register every start pose in init_poses [n][6] to the target images
     ([n_views][nv][nu]).  By default every pose sees every view; with
     inst_view ([n] view indices) pose i sees only view inst_view[i], i.e. n
@@ -61,7 +65,12 @@ def register(geom, mu, target, init_poses, max_iter=200, lr=None, ncc_stop=0.999
     first_hit_s: wall time at which any candidate was first seen within
     tol = (mm, deg) of it, or None; true_pose may be [6] or [n][6]).
     graph_steps > 0 replays CUDA graphs of that many iterations (checked
-    once per replay)."""
+    once per replay).  wave=B runs at most B starts at a time (see
+    register_waves); stop_at_hit ends the run at the first hit."""
+    if wave is not None and inst_view is None:
+        return register_waves(geom, mu, target, init_poses, wave, max_iter=max_iter, lr=lr, ncc_stop=ncc_stop,
+                              dloss_stop=dloss_stop, device=device, true_pose=true_pose, tol=tol,
+                              stop_at_hit=stop_at_hit)
     lr = paper_step_sizes() if lr is None else lr
     init = torch.as_tensor(np.asarray(init_poses, dtype=np.float32), device=device)
     n = init.shape[0]
@@ -125,12 +134,89 @@ def register(geom, mu, target, init_poses, max_iter=200, lr=None, ncc_stop=0.999
         it += k
         if true_pose is not None and first_hit is None and bool(hit_any):
             first_hit = time.perf_counter() - t0
+            if stop_at_hit:
+                break
         if not bool(active.any()):
             break
     torch.cuda.synchronize()
     seconds = time.perf_counter() - t0
     return dict(poses=pose.cpu().numpy(), ncc=(-loss).cpu().numpy(), iters=iters.cpu().numpy(), seconds=seconds,
                 first_hit_s=first_hit)
+
+
+def register_waves(geom, mu, target, init_poses, wave, max_iter=200, lr=None, ncc_stop=0.999, dloss_stop=1e-5,
+                   device="cuda", true_pose=None, tol=(0.5, 0.5), stop_at_hit=False):
+    """Multi-start registration with at most `wave` starts in flight: one plan
+    holds every start as a pose, and each iteration marches only the poses in
+    a device-resident slot list (proj_forward_pose_grad_list).  A start that
+    stops (NCC above ncc_stop, loss change below dloss_stop, or max_iter
+    updates) leaves its slot and the next start in order takes it, on the
+    device, without a host round trip.  Each start follows exactly the
+    trajectory it has when registered alone (its Adam state and step count are
+    its own).  Returns the dict of register() plus `started` (starts begun)."""
+    from . import proj_forward_pose_grad_list
+    lr = paper_step_sizes() if lr is None else lr
+    init = torch.as_tensor(np.asarray(init_poses, dtype=np.float32), device=device)
+    n = init.shape[0]
+    B = max(1, min(int(wave), n))
+    nv = geom.views.shape[0]
+    mu_d = torch.as_tensor(np.asarray(mu, dtype=np.float32), device=device).contiguous()
+    tgt = torch.as_tensor(np.asarray(target, dtype=np.float32), device=device).contiguous()
+    P = Projector(geom, n_pose=n, inst_view=np.tile(np.arange(nv), n), inst_pose=np.repeat(np.arange(n), nv),
+                  ops=PROJ_OP_FORWARD_GRAD, device=device)
+    proj_set_volume(P.plan, mu_d, P.ws)
+    pose = init.clone()
+    opt = Adam(n, lr, device=device)
+    alive = torch.ones(n, dtype=torch.bool, device=device)     # not yet stopped
+    last = torch.full((n,), float("inf"), device=device)
+    grad = torch.zeros((n, 6), device=device)
+    loss = torch.zeros((n,), device=device)
+    iters = torch.zeros(n, dtype=torch.int64, device=device)
+    slots = torch.arange(B, dtype=torch.int32, device=device)    # pose of each slot, -1 = empty
+    nxt = torch.full((), B, dtype=torch.int64, device=device)    # next start to begin
+    hit_any = torch.zeros((), dtype=torch.bool, device=device)
+    listed_buf = torch.zeros(n + 1, dtype=torch.bool, device=device)
+    if true_pose is not None:
+        tp = torch.as_tensor(np.asarray(true_pose, dtype=np.float32), device=device).reshape(-1, 6)
+
+    def iteration():
+        proj_forward_pose_grad_list(P.plan, pose, slots, PROJ_LOSS_NCC, tgt, grad, loss, None, P.ws)
+        sl = slots.long()
+        listed_buf.zero_()
+        listed_buf.index_fill_(0, torch.where(sl >= 0, sl, n), True)
+        listed = listed_buf[:n]
+        if true_pose is not None:
+            d = (pose - tp).abs()
+            hit = listed & (d[:, :3].amax(1) <= tol[0]) & (torch.rad2deg(d[:, 3:]).amax(1) <= tol[1])
+            hit_any.logical_or_(hit.any())
+        done = listed & ((-loss >= ncc_stop) | ((last - loss).abs() < dloss_stop) | (iters >= max_iter))
+        alive.logical_and_(~done)
+        upd = alive & listed
+        iters.add_(upd)
+        opt.step(pose, grad, upd)
+        last.copy_(torch.where(listed, loss, last))
+        # refill the slots of stopped starts (and empty ones) with the next starts, in order
+        free = (sl < 0) | ~alive[sl.clamp(min=0)]
+        cand = nxt + torch.cumsum(free.long(), 0) - 1
+        take = free & (cand < n)
+        slots.copy_(torch.where(take, cand, torch.where(free, torch.full_like(cand, -1), sl)).int())
+        nxt.add_(take.long().sum())
+
+    first_hit = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while True:
+        iteration()
+        if true_pose is not None and first_hit is None and bool(hit_any):
+            first_hit = time.perf_counter() - t0
+            if stop_at_hit:
+                break
+        if not bool((slots >= 0).any()):
+            break
+    torch.cuda.synchronize()
+    seconds = time.perf_counter() - t0
+    return dict(poses=pose.cpu().numpy(), ncc=(-loss).cpu().numpy(), iters=iters.cpu().numpy(), seconds=seconds,
+                first_hit_s=first_hit, started=int(min(int(nxt.item()), n)))
 
 
 def pose_error(a, b):
