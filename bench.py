@@ -599,6 +599,14 @@ def paper_tables(pb, torch, dev, flush):
         ms3 = _event_ms(torch, t3, flush, reps=2)
         ws3 = pb.proj_workspace_size(P1.plan)
         del P1
+        # the same with one copy of the prepared volume (PROJ_FLAG_ONE_COPY): the memory-lean plan
+        pose.copy_(torch.tensor([[2.0, -1.0, 1.5, 0.02, -0.03, 0.01]], device=dev))
+        P1 = pb.Projector(g1, n_pose=1, inst_view=np.zeros(1, np.int32), inst_pose=np.zeros(1, np.int32),
+                          ops=pb.PROJ_OP_FORWARD_GRAD | pb.PROJ_FLAG_ONE_COPY)
+        P1.set_volume(mu)
+        ms3c = _event_ms(torch, t3, flush, reps=2)
+        ws3c = pb.proj_workspace_size(P1.plan)
+        del P1
         # Table IV: 256 views, one iteration of back-projection, image loss, pose gradient, update
         g4 = synth.Geometry(n, n, n, vox, vox, vox, d, d, synth.circular_views(256, synth.SAD, synth.SDD, pix, pix),
                             0.5 * vox)

@@ -153,7 +153,8 @@ typedef struct proj_plan_s *proj_plan;
  *   n_inst     number of instances, >= 1.
  *   inst_view  host [n_inst], view of each instance in [0, n_views).
  *   inst_pose  host [n_inst], pose of each instance in [0, n_pose).
- *   ops        OR of PROJ_OP_* the plan must support.
+ *   ops        OR of PROJ_OP_* the plan must support (at least one), plus
+ *              optional PROJ_FLAG_* options.
  *   out        receives the plan.
  * Limits: ny, nz, nv <= 65000; with PROJ_OP_BACK or PROJ_OP_BACK_GRAD at
  * most 65535 instances; padded volumes below 2^31 voxels.

@@ -166,7 +166,8 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   if (G.n_views < 1 || !G.views) return fail(PROJ_E_ARG, "need n_views >= 1 and a view table");
   if (n_pose < 1) return fail(PROJ_E_ARG, "n_pose must be >= 1");
   if (n_inst < 1 || !inst_view || !inst_pose) return fail(PROJ_E_ARG, "need n_inst >= 1 and instance maps");
-  if (ops <= 0 || (ops & ~PROJ_OP_ALL)) return fail(PROJ_E_ARG, "ops must be a non-empty OR of PROJ_OP_*");
+  if ((ops & PROJ_OP_ALL) == 0 || (ops & ~(PROJ_OP_ALL | PROJ_FLAG_ONE_COPY)))
+    return fail(PROJ_E_ARG, "ops must be a non-empty OR of PROJ_OP_* (plus PROJ_FLAG_* options)");
   // launch grids put volume rows / slices, detector rows and (for the detector stack) instances in
   // the y and z grid dimensions
   if (G.ny > 65000 || G.nz > 65000 || G.nv > 65000) return fail(PROJ_E_ARG, "ny, nz and nv must be <= 65000");
@@ -272,9 +273,10 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   const size_t npad_sz = (size_t)npad;
   const size_t nrec = (size_t)(G.nx + 2) * (G.ny + 2) * record_slices(G.nz);
   p->off_volq = (ops & PROJ_OP_FORWARD) ? take(sizeof(float4) * nrec) : 0;
-  p->off_volqy = (ops & PROJ_OP_FORWARD) ? take(sizeof(float4) * nrec) : 0;
+  const bool two_copies = !(ops & PROJ_FLAG_ONE_COPY);
+  p->off_volqy = ((ops & PROJ_OP_FORWARD) && two_copies) ? take(sizeof(float4) * nrec) : 0;
   p->off_vol4 = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float4) * (size_t)npad2) : 0;
-  p->off_vol4y = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float4) * (size_t)npad2y) : 0;
+  p->off_vol4y = ((ops & PROJ_OP_FORWARD_GRAD) && two_copies) ? take(sizeof(float4) * (size_t)npad2y) : 0;
   p->off_part_f = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float) * kRec * (size_t)n_inst * p->n_tiles) : 0;
   // the detector scratch of proj_back (cell records) and of proj_back_pose_grad (the (l, d_u l, d_v l)
   // stack) are never needed by the same call: one region serves both

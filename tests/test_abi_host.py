@@ -135,6 +135,9 @@ def test_bad_ops_and_null_arguments(L):
     assert rc == pb.PROJ_E_ARG
     rc, _ = create(tiny_geom(), ops=128)
     assert rc == pb.PROJ_E_ARG
+    rc, _ = create(tiny_geom(), ops=pb.PROJ_FLAG_ONE_COPY)       # an option flag alone enables no operation
+    assert rc == pb.PROJ_E_ARG and "non-empty" in pb.proj_last_error()
+    assert L.proj_forward_pose_grad_list(None, None, None, 1, 0, None, None, None, None, None, 0, None) == pb.PROJ_E_ARG
     assert L.proj_plan_create(None, 1, 1, None, None, 1, None) == pb.PROJ_E_ARG
     n = ctypes.c_size_t()
     assert L.proj_workspace_size(None, ctypes.byref(n)) == pb.PROJ_E_ARG

@@ -373,3 +373,26 @@ def test_yfast_volume_copy_gives_identical_results():
         torch.cuda.synchronize()
         assert torch.equal(grad, g2), (grad, g2)
         assert torch.equal(L, L2)
+
+
+def test_one_copy_plan_gives_identical_results(ragged):
+    """PROJ_FLAG_ONE_COPY keeps only the rows-along-x copies of the prepared
+    volume: a smaller workspace and the same projections and pose gradients
+    bit for bit (the instances whose u axis runs along y march the x copy)."""
+    d = ragged
+    g, mu, poses, iv, ip = d["g"], d["mu"], d["poses"], d["iv"], d["ip"]
+    target = f32(oracle.forward(g, mu, f32([[1.0, -1.0, 0.5, 0.05, -0.02, 0.03]]), inst_view=[0, 1, 2],
+                                inst_pose=[0, 0, 0]))
+    ops = pb.PROJ_OP_FORWARD | pb.PROJ_OP_FORWARD_GRAD
+    P2 = pb.Projector(g, n_pose=2, inst_view=iv, inst_pose=ip, ops=ops)
+    P1 = pb.Projector(g, n_pose=2, inst_view=iv, inst_pose=ip, ops=ops | pb.PROJ_FLAG_ONE_COPY)
+    assert pb.proj_workspace_size(P1.plan) < pb.proj_workspace_size(P2.plan)
+    for P in (P1, P2):
+        P.set_volume(mu)
+    for loss in (pb.PROJ_LOSS_L2, pb.PROJ_LOSS_NCC):
+        g1, l1 = P1.forward_pose_grad(poses, loss, target)
+        g2, l2 = P2.forward_pose_grad(poses, loss, target)
+        np.testing.assert_array_equal(np32(g1), np32(g2))
+        np.testing.assert_array_equal(np32(l1), np32(l2))
+    np.testing.assert_array_equal(np32(P1.forward(poses)), np32(P2.forward(poses)))
+    assert rel_l2(np32(P1.forward(poses)), oracle.forward(g, mu, poses, iv, ip)) <= TOL_IMG
