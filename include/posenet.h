@@ -104,9 +104,23 @@ int pn_to_bf16(const float *src, long long n, void *dst, proj_stream stream);
 /* Synchronise the stream, return and clear the status word of the current
  * device: 0 = clean; bit 1: a TMA stage never filled, bit 2: an
  * accumulator never completed, bit 4: a stage was never released (each
- * after a 2 s bound on the wait; the CTA then released its tensor memory
- * and returned, and the output of that launch is undefined). */
+ * after a bound on the wait, 2 s unless pn_gemm_test_hooks lowers it; the
+ * CTA then released its tensor memory and returned, and the output of that
+ * launch is undefined). */
 int pn_status(proj_stream stream, int *status);
+
+/* Test hook for the GEMM's failure path (no counterpart in the paper).
+ * Every mbarrier wait of the GEMM kernels gives up after wait_ns of the
+ * global timer (0 restores the default, 2 s), sets a pn_status bit and lets
+ * the CTA skip its stores, free its tensor memory and return.  With
+ * stall_tma non-zero, GEMMs run on 1-SM tiles and the TMA producer arms each
+ * stage barrier for its bytes but issues no copy, so the waits on those
+ * barriers run out: the call then returns normally, its output is left
+ * unwritten, and pn_status reports bit 1 (a stage never filled) and, with
+ * more K blocks than pipeline stages, bit 4 (a stage never released).  No
+ * copy is left in flight.  Settings are process-wide and apply to GEMMs
+ * launched afterwards; for tests of the failure path only.  Returns PROJ_OK. */
+int pn_gemm_test_hooks(unsigned long long wait_ns, int stall_tma);
 
 #ifdef __cplusplus
 }

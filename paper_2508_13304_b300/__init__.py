@@ -97,6 +97,7 @@ _SIGS = {
     "pn_mse_loss": [_P, _I, _I, _I, _P, _P, _P, _I, _P],
     "pn_to_bf16": [_P, ctypes.c_longlong, _P, _P],
     "pn_status": [_P, ctypes.POINTER(_I)],
+    "pn_gemm_test_hooks": [ctypes.c_ulonglong, _I],
     "proj_enable_kernel_timing": [_P, _I],
     "proj_kernel_time_ms": [_P, ctypes.POINTER(ctypes.c_float)],
     "proj_last_error": [],
@@ -581,6 +582,11 @@ def pn_mse_loss(y, B, n_out, ldy, target, loss=None, dy=None, lddy=None, stream=
 
 def pn_to_bf16(src, dst, stream=None):
     _check(lib().pn_to_bf16(_f32(src, name="src"), src.numel(), _bf(dst, src.numel(), "dst"), _stream(stream)))
+
+
+def pn_gemm_test_hooks(wait_ns=0, stall_tma=False):
+    """Failure-path test hook of the GEMM (see include/posenet.h)."""
+    _check(lib().pn_gemm_test_hooks(int(wait_ns), 1 if stall_tma else 0))
 
 
 def pn_status(stream=None) -> int:

@@ -39,6 +39,11 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 std::mutex g_mu;
 EncodeTiledFn g_encode = nullptr;
 int g_use_pair = 2;
+// limit of every mbarrier wait of the GEMM kernels, and the test hook that
+// stalls the 1-SM kernel's TMA producer (pn_gemm_test_hooks)
+constexpr unsigned long long kDefaultWaitNs = 2000000000ULL;  // 2 s
+unsigned long long g_wait_ns = kDefaultWaitNs;
+int g_stall_tma = 0;
 int* g_status_addr[64] = {};
 int g_n_sm[64] = {};
 
@@ -120,6 +125,12 @@ int pn_gemm_use_pair_tiles(int mode) {
   return old;
 }
 
+int pn_gemm_test_hooks(unsigned long long wait_ns, int stall_tma) {
+  g_wait_ns = wait_ns ? wait_ns : kDefaultWaitNs;
+  g_stall_tma = stall_tma ? 1 : 0;
+  return PROJ_OK;
+}
+
 int pn_gemm_split_hint(int M, int N, int K) {
   if (M < 1 || N < 1 || K < 1) return 1;
   const int bn = bn_for(N);
@@ -147,7 +158,7 @@ int pn_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int
   int* status = status_word();
   if (!status) return fail(PROJ_E_CUDA, "pn_gemm_bf16: no device status word");
   const int bn = bn_for(N);
-  const int pair = (bn == 256 && M > kBM) ? g_use_pair : 0;
+  const int pair = (bn == 256 && M > kBM && !g_stall_tma) ? g_use_pair : 0;
   CUtensorMap ta, tb;
   int rc = make_map(&ta, A, M, K, lda, kBM);
   if (rc) return rc;
@@ -164,6 +175,8 @@ int pn_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int
   epi.d16 = static_cast<__nv_bfloat16*>(D16);
   epi.ldd = ldd;
   epi.part = split > 1 ? part : nullptr;
+  epi.wait_ns = g_wait_ns;
+  epi.stall_tma = g_stall_tma;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = launch_gemm(ta, tb, M, N, K, bn, pair, split, kbs, epi, status, s);
   if (e != cudaSuccess) return cuda_fail(e, "GEMM launch");

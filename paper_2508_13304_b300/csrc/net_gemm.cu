@@ -21,8 +21,6 @@ namespace pnk {
 
 namespace {
 
-constexpr unsigned long long kWaitNs = 2000000000ULL;  // 2 s per wait
-
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -53,13 +51,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the completion of the phase with the given parity, at most kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait for the completion of the phase with the given parity, at most
+// limit_ns of the global timer (GemmEpi::wait_ns: 2 s unless a test lowers it).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 
@@ -230,11 +229,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   if (warp == 0 && lane == 0) {
     for (int i = 0; i < nkb; ++i) {
       const int s = i % kStages;
-      if (i >= kStages && !mbar_wait(empty(s), ((i / kStages) - 1) & 1)) {
+      if (i >= kStages && !mbar_wait(empty(s), ((i / kStages) - 1) & 1, epi.wait_ns)) {
         fail = kStatusTimeoutFree;
         break;
       }
       mbar_expect_tx(full(s), kBytesA + kBytesB);
+      if (epi.stall_tma) continue;  // test hook: the stage is armed but never filled
       tma_load_2d(sA + s * kBytesA, &ta, full(s), (kb0 + i) * kBK, m0);
       tma_load_2d(sB + s * kBytesB, &tb, full(s), (kb0 + i) * kBK, n0);
     }
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     constexpr uint32_t idesc = idesc_bf16(BN);
     for (int i = 0; i < nkb; ++i) {
       const int s = i % kStages;
-      if (!mbar_wait(full(s), (i / kStages) & 1)) {
+      if (!mbar_wait(full(s), (i / kStages) & 1, epi.wait_ns)) {
         fail = kStatusTimeoutTma;
         break;
       }
@@ -256,12 +256,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     umma_commit(done);
   }
   __syncwarp();
-  const bool ok = mbar_wait(done, 0);
+  const bool ok = mbar_wait(done, 0, epi.wait_ns);
   if (!ok && threadIdx.x == 0) fail |= kStatusTimeoutMma;
   if (fail) atomicOr(status, fail);
+  // a producer or MMA timeout leaves the accumulator incomplete: no thread stores it
+  const bool any_fail = __syncthreads_or(fail != 0 || !ok) != 0;
   tc_fence_after();
 
-  if (ok) epilogue<BN>(tmem_d, m0, n0, M, N, blockIdx.z, epi, warp);
+  if (!any_fail) epilogue<BN>(tmem_d, m0, n0, M, N, blockIdx.z, epi, warp);
 
   tc_fence_before();
   __syncthreads();
@@ -383,7 +385,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
   if (warp == 0 && lane == 0) {
     for (int i = 0; i < nkb; ++i) {
       const int s = i % kStagesPair;
-      if (i >= kStagesPair && !mbar_wait(empty(s), ((i / kStagesPair) - 1) & 1)) {
+      if (i >= kStagesPair && !mbar_wait(empty(s), ((i / kStagesPair) - 1) & 1, epi.wait_ns)) {
         fail = kStatusTimeoutFree;
         break;
       }
@@ -396,7 +398,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
     constexpr uint32_t idesc = idesc_bf16_pair();
     for (int i = 0; i < nkb; ++i) {
       const int s = i % kStagesPair;
-      if (!mbar_wait(full(s), (i / kStagesPair) & 1)) {
+      if (!mbar_wait(full(s), (i / kStagesPair) & 1, epi.wait_ns)) {
         fail = kStatusTimeoutTma;
         break;
       }
@@ -410,7 +412,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
     umma_commit_pair(done);
   }
   __syncwarp();
-  const bool ok = mbar_wait(done, 0);
+  const bool ok = mbar_wait(done, 0, epi.wait_ns);
   if (!ok && threadIdx.x == 0) fail |= kStatusTimeoutMma;
   if (fail) atomicOr(status, fail);
   tc_fence_after();
@@ -521,7 +523,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPersistThreads, 1)
         for (int i = 0; i < nkb; ++i, ++g) {
           const int s = (int)(g % kStagesPair);
           const long long u = g / kStagesPair;
-          if (u > 0 && !mbar_wait(empty(s), (uint32_t)((u - 1) & 1))) {
+          if (u > 0 && !mbar_wait(empty(s), (uint32_t)((u - 1) & 1), epi.wait_ns)) {
             fail = kStatusTimeoutFree;
             break;
           }
@@ -542,7 +544,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPersistThreads, 1)
         decode(w, mp, nt, z);
         kb_range(z, kb0, nkb);
         const int b = j & 1, ub = j >> 1;
-        if (ub > 0 && !mbar_wait(tmem_empty(b), (uint32_t)((ub - 1) & 1))) {
+        if (ub > 0 && !mbar_wait(tmem_empty(b), (uint32_t)((ub - 1) & 1), epi.wait_ns)) {
           fail = kStatusTimeoutMma;
           break;
         }
@@ -550,7 +552,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPersistThreads, 1)
         const uint32_t acc = tmem_d + (uint32_t)(b * 256);
         for (int i = 0; i < nkb; ++i, ++g) {
           const int s = (int)(g % kStagesPair);
-          if (!mbar_wait(full(s), (uint32_t)((g / kStagesPair) & 1))) {
+          if (!mbar_wait(full(s), (uint32_t)((g / kStagesPair) & 1), epi.wait_ns)) {
             fail = kStatusTimeoutTma;
             break;
           }
@@ -571,7 +573,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPersistThreads, 1)
       int mp, nt, z;
       decode(w, mp, nt, z);
       const int b = j & 1;
-      const bool ok = mbar_wait(tmem_full(b), (uint32_t)((j >> 1) & 1));
+      const bool ok = mbar_wait(tmem_full(b), (uint32_t)((j >> 1) & 1), epi.wait_ns);
       if (!ok) {
         fail = kStatusTimeoutMma;
         *epi_abort = 1;

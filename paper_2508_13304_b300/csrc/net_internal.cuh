@@ -31,6 +31,8 @@ struct GemmEpi {
   __nv_bfloat16* d16;           // [M][ldd] BF16 output, or null
   int ldd;
   float* part;                  // split-K partials [split][M][N] (raw sums), or null
+  unsigned long long wait_ns;   // limit of every mbarrier wait (global-timer ns)
+  int stall_tma;                // test hook: the 1-SM kernel arms its stage barriers but issues no TMA
 };
 
 size_t gemm_smem_bytes(int bn);

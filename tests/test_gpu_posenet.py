@@ -110,6 +110,36 @@ def test_gemm_epilogue_bias_relu_mask_bf16():
     assert np.all(f64(D16)[f64(mask) <= 0] == 0)
 
 
+def test_gemm_bounded_waits_run_out_and_report():
+    """Failure path of the tensor-core GEMM, made on purpose without a fault:
+    with a 1 ms wait limit and the TMA producer stalled (each stage barrier
+    armed for its bytes, no copy issued), the call returns, the bounded
+    mbarrier waits report through pn_status, no CTA stores its incomplete
+    accumulator, and the next GEMM in the same process is exact."""
+    import time
+    rng = np.random.default_rng(9)
+    M, N, K = 256, 128, 512          # 8 K blocks > 4 stages: the producer also waits for a free stage
+    A, B = bf16(rng, (M, K)), bf16(rng, (N, K))
+    assert pb.pn_status() == 0
+    D = torch.full((M, N), float("nan"), device="cuda")
+    pb.pn_gemm_test_hooks(wait_ns=1_000_000, stall_tma=True)
+    try:
+        t0 = time.perf_counter()
+        pb.pn_gemm_bf16(M, N, K, A, K, B, K, D32=D)
+        torch.cuda.synchronize()
+        elapsed = time.perf_counter() - t0
+    finally:
+        pb.pn_gemm_test_hooks(0, False)
+    st = pb.pn_status()
+    assert (st & 1) and (st & 4), st
+    assert torch.isnan(D).all()
+    assert elapsed < 1.0, elapsed
+    pb.pn_gemm_bf16(M, N, K, A, K, B, K, D32=D)
+    torch.cuda.synchronize()
+    assert pb.pn_status() == 0
+    assert rel(D.cpu().numpy(), f64(A) @ f64(B).T) <= 1e-5
+
+
 def test_gemm_rejects_bad_arguments():
     A = torch.zeros((8, 24), device="cuda", dtype=torch.bfloat16)
     D = torch.zeros((8, 8), device="cuda")
