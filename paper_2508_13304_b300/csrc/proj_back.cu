@@ -4,10 +4,14 @@
 // dis_back) with a deterministic two-stage reduction.
 //
 // Layout: a 256-thread block covers 32 (x) x 8 (y) voxel columns and
-// kZChunk voxels along z; each warp is one row of 32 x-adjacent columns, so
-// their projections are adjacent on the detector.  Each thread projects its
-// voxels with the instance's 3x4 matrix Q (centred voxel index -> (u',v',w')),
-// one FMA chain per voxel.
+// kZChunk voxels along z; each warp covers 4 (x) x 8 (y) columns, so the 8
+// lanes that the L1 data pipe serves together for 16-byte loads (a
+// quarter-warp) form a 4 x 2 patch.  Whichever of x and y runs along the
+// detector u axis in a view, that patch projects into a few neighbouring
+// pixels; a row of 8 x-adjacent columns would spread over 16 pixels (two
+// lines at the same bank slots) in the views where x runs along u.  Each
+// thread projects its voxels with the instance's 3x4 matrix Q (centred voxel
+// index -> (u',v',w')), one FMA chain per voxel.
 #include "proj_internal.cuh"
 
 namespace projk {
@@ -15,6 +19,13 @@ namespace projk {
 namespace {
 
 __device__ __forceinline__ float lerp(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+// Voxel column (x, y offsets in the block's 32 x 8 tile) of this thread:
+// warp w takes x in [4w, 4w + 4), lane l takes x offset l & 3 and y = l >> 2.
+__device__ __forceinline__ int col_x() { return ((threadIdx.x >> 5) << 2) + (threadIdx.x & 3); }
+__device__ __forceinline__ int col_y() { return (threadIdx.x & 31) >> 2; }
+static_assert(kBpX == 32 && kBpY == 8 && kGbX == 32 && kGbY == 8 && kBpThreads == 256,
+              "col_x / col_y map 8 warps of 4 x 8 columns onto a 32 x 8 tile");
 
 __device__ __forceinline__ float pix(const float* __restrict__ img, int nu, int nv, int iu, int iv) {
   return (iu >= 0 && iu < nu && iv >= 0 && iv < nv) ? __ldg(img + (size_t)iv * nu + iu) : 0.f;
@@ -75,8 +86,8 @@ __device__ __forceinline__ void red_add4(float4* p, float a, float b, float c, f
 __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict__ inst, int n_inst, Geo g,
                                                      int weight, const float4* __restrict__ detq,
                                                      float* __restrict__ vol) {
-  const int ix = blockIdx.x * kBpX + (threadIdx.x & 31);
-  const int iy = blockIdx.y * kBpY + (threadIdx.x >> 5);
+  const int ix = blockIdx.x * kBpX + col_x();
+  const int iy = blockIdx.y * kBpY + col_y();
   const int iz0 = blockIdx.z * kZChunk;
   if (ix >= g.nx || iy >= g.ny) return;
   const float fx = (float)ix - g.cx, fy = (float)iy - g.cy;
@@ -153,7 +164,7 @@ __global__ void __launch_bounds__(kBpThreads, 3)
   const int n_bricks = gridDim.x;
   const int brick = blockIdx.x;
   const int bx = brick % bricks_x, by = (brick / bricks_x) % bricks_y, bz = brick / (bricks_x * bricks_y);
-  const int ix = bx * kGbX + lane, iy = by * kGbY + warp, iz0 = bz * GZ;
+  const int ix = bx * kGbX + col_x(), iy = by * kGbY + col_y(), iz0 = bz * GZ;
   const bool col = ix < g.nx && iy < g.ny;
   float wj[GZ];
 #pragma unroll
