@@ -40,10 +40,23 @@ L2_FLUSH_BYTES = 256 << 20
 # Counters of the fused march from ncu captures (they cannot be read live):
 # the L1 data-pipe wavefront utilisation of the 8-instance case, and the DRAM
 # bytes (read + write) of one full-size launch of this workload taken with
-# one-pass metrics.  Set to None whenever the kernel changes until they are
-# re-measured.
+# one-pass metrics.  NCU_SOURCE_SHA16 is the hash (kernel_source_sha16) of
+# the march's sources they were taken on; when the built sources hash
+# differently the line reports them as null.
+NCU_SOURCE_SHA16 = "ba21f7b51388d206"
 NCU_L1_WAVEFRONT_PCT = 88.7
 TRAFFIC_PER_LAUNCH = 21.57e9  # 21.55 GB read + 19 MB written
+MARCH_SOURCES = ("paper_2508_13304_b300/csrc/proj_forward.cu", "paper_2508_13304_b300/csrc/proj_internal.cuh")
+
+
+def kernel_source_sha16():
+    """First 16 hex digits of the SHA-256 of the fused march's source files."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in MARCH_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def load_peaks():
@@ -312,24 +325,35 @@ def secondary(pb, torch, dev, w, mu_d, flush):
     mu_h = mu_d.cpu().numpy()
     # one untimed call first: the first registration in a process pays one-off set-up costs
     reg.register(g, mu_h, tgt, starts[:2], max_iter=3, batched=True, true_pose=true)
+    reg.register(g, mu_h, tgt, starts[:4], max_iter=3, wave=2, true_pose=true)
     rb = reg.register(g, mu_h, tgt, starts, max_iter=150, batched=True, true_pose=true)
-    t_plain, found, tried = 0.0, None, 0
+    t_plain, found, tried, plain_iters = 0.0, None, 0, []
     for c in range(len(starts)):
         rp = reg.register(g, mu_h, tgt, starts[c:c + 1], max_iter=150, batched=True, true_pose=true)
+        plain_iters.append(int(rp["iters"][0]))
         if found is None:
             tried += 1
             if rp["first_hit_s"] is not None:
                 found = t_plain + rp["first_hit_s"]
         t_plain += rp["seconds"]
+    waves = {}
+    for B in (4, 8, 16):
+        rw = reg.register(g, mu_h, tgt, starts, max_iter=150, wave=B, true_pose=true, stop_at_hit=True)
+        waves[str(B)] = {"time_to_pose_s": rw["first_hit_s"], "starts_begun": rw["started"]}
     te, re = reg.pose_error(rb["poses"], true)
     out["registration"] = {
-        "config": "256^3, 2 views of 384^2, %d starts (rot +-15 deg, trans +-20 mm), NCC, Adam 10 mm / 2 deg" % len(starts),
-        "batched_time_to_pose_s": rb["first_hit_s"], "batched_total_s": rb["seconds"],
-        "batched_within_tol_at_end": int(np.sum((te <= 0.5) & (re <= 0.5))),
+        "config": "256^3, 2 views of 384^2, %d starts (rot +-15 deg, trans +-20 mm), NCC, Adam 10 mm / 2 deg, "
+                  "stop at dloss < 1e-5 or NCC > 0.999 or 150 iterations; time to the first pose within "
+                  "0.5 mm / 0.5 deg of the truth" % len(starts),
+        "batched_waves_time_to_pose_s": waves["8"]["time_to_pose_s"], "waves": waves,
+        "batched_all_time_to_pose_s": rb["first_hit_s"], "batched_all_total_s": rb["seconds"],
+        "batched_all_within_tol_at_end": int(np.sum((te <= 0.5) & (re <= 0.5))),
         "plain_time_to_pose_s": found, "plain_starts_tried_to_first_hit": tried,
+        "plain_iterations_per_start": plain_iters[:tried],
         "plain_total_s_all_starts": t_plain,
-        "note": "plain = one start per launch, starts run one after another; batched = all starts in one launch "
-                "per iteration"}
+        "note": "plain = one start per launch, starts run one after another; batched waves = at most B starts "
+                "in flight in one launch per iteration (proj_forward_pose_grad_list), a stopped start's slot "
+                "taken by the next start on the device; batched all = every start in one launch"}
     # ray-tile shape autotuner on the benchmark's own launch (64 candidates x 2 views)
     Pa = pb.Projector(g, n_pose=nc, inst_view=iv, inst_pose=ip, ops=pb.PROJ_OP_FORWARD_GRAD)
     Pa.set_volume(mu_d)
@@ -630,6 +654,7 @@ def paper_tables(pb, torch, dev, flush):
         rows.append({"volume": n, "detector": d,
                      "table3_100_iter_s": ms3 * 1e-3, "table3_paper_s": t3_paper, "table3_ratio": t3_paper / (ms3 * 1e-3),
                      "table3_workspace_gb": ws3 / 1e9,
+                     "table3_one_copy_100_iter_s": ms3c * 1e-3, "table3_one_copy_workspace_gb": ws3c / 1e9,
                      "table4_iter_s": ms4 * 1e-3, "table4_paper_s": t4_paper, "table4_ratio": t4_paper / (ms4 * 1e-3),
                      "table4_workspace_gb": ws4 / 1e9})
     return {"rows": rows, "note": "paper: RTX 4090, whole autograd steps in PyTorch with the authors' kernels and "
@@ -963,6 +988,11 @@ def main():
     dev = torch.device("cuda", local)
 
     w = workload(args.n_cand)
+    if world > 1 and rank > 0:
+        # every rank registers its own candidates against the same target: rank 0 keeps the
+        # single-GPU workload's, the others draw theirs from seeds of their own (same ranges)
+        w["poses"] = np.ascontiguousarray(
+            synth.random_poses(np.random.default_rng(1002 + 7919 * rank), args.n_cand, 15.0, 20.0), dtype=np.float32)
     g = w["geom"]
     iv, ip = instance_maps(args.n_cand, g.n_views)
     P = pb.Projector(g, n_pose=args.n_cand, inst_view=iv, inst_pose=ip, ops=pb.PROJ_OP_FORWARD_GRAD)
@@ -1128,6 +1158,8 @@ def main():
     npad = (g.nx + 2) * (g.ny + 2) * (g.nz + 2)
     hbm_bytes = npad * 16 + g.n_views * g.nu * g.nv * 4 + args.n_cand * 6 * 4  # compulsory: float4 volume, targets
     hbm_achieved = hbm_bytes / (k_ms * 1e-3) / 1e9
+    src_sha = kernel_source_sha16()
+    ncu_current = src_sha == NCU_SOURCE_SHA16
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -1138,7 +1170,8 @@ def main():
         "kernel_ms": k_ms,
         "plain": plain,
         "roofline": {"bound": "l1", "achieved": l1_achieved, "peak": l1_peak, "unit": "GB/s",
-                     "frac": l1_achieved / l1_peak, "traffic": TRAFFIC_PER_LAUNCH,
+                     "frac": l1_achieved / l1_peak, "traffic": TRAFFIC_PER_LAUNCH if ncu_current else None,
+                     "ncu_source_sha16": NCU_SOURCE_SHA16, "built_source_sha16": src_sha,
                      "kernel": "k_forward_grad<NCC> (fused pose-gradient march)",
                      "what": "L1->register gather bytes: %d B per ray sample (8 corners x float4); peak = %d SMs x "
                              "%d B/clk x %.0f MHz" % (L1_BYTES_PER_SAMPLE, n_sm, L1_BYTES_PER_CLK_SM, sm_max),
@@ -1147,7 +1180,7 @@ def main():
                      # the unit that binds, from the committed ncu capture of the same kernel (a small case of
                      # this launch; not measured live)
                      "ncu_l1_wavefront_utilisation": {
-                         "pct_of_peak": NCU_L1_WAVEFRONT_PCT,
+                         "pct_of_peak": NCU_L1_WAVEFRONT_PCT if ncu_current else None,
                          "source": "ncu l1tex__data_pipe_lsu_wavefronts of the same kernel, 8-instance case "
                                    "(summary under profiles/)"},
                      "empirical_gather_ceiling": {
