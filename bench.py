@@ -842,6 +842,41 @@ def gemm_throughput(pb, torch, dev, flush, bf16_peak, shapes=GEMM_SHAPES):
     return out
 
 
+# convolution layers 2..6 of the pose network at batch 256: (input side, input channels, output channels)
+CONV_LAYERS = ((64, 32, 64), (32, 64, 128), (16, 128, 128), (8, 128, 128), (4, 128, 128))
+
+
+def conv_layers(pb, torch, dev, flush, bf16_peak, B=256):
+    """The network's 3x3 stride-2 convolutions (bias + ReLU, BF16 out): im2col
+    + GEMM against the implicit-GEMM kernel that gathers the patches itself."""
+    out = []
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(8)
+    for H, C, Co in CONV_LAYERS:
+        Ho = (H + 1) // 2
+        M, K = B * Ho * Ho, 9 * C
+        x = torch.randn((B, H, H, C), device=dev, generator=gen).bfloat16()
+        w = torch.randn((Co, K), device=dev, generator=gen).bfloat16()
+        bias = torch.zeros(Co, device=dev)
+        col = torch.empty((M, K), device=dev, dtype=torch.bfloat16)
+        y = torch.empty((M, Co), device=dev, dtype=torch.bfloat16)
+
+        def explicit():
+            pb.pn_im2col_3x3s2(x, B, H, H, C, K, col)
+            pb.pn_gemm_bf16(M, Co, K, col, K, w, K, bias=bias, relu=True, D16=y)
+
+        ms_e = _event_ms(torch, explicit, flush, reps=5)
+        ms_i = _event_ms(torch, lambda: pb.pn_conv3x3s2_bf16(x, B, H, H, C, w, Co, bias=bias, relu=True, y16=y),
+                         flush, reps=5)
+        fl = 2.0 * M * Co * K
+        out.append({"input": "%dx%dx%dx%d" % (B, H, H, C), "cout": Co, "gemm_MNK": [M, Co, K],
+                    "im2col_gemm_ms": ms_e, "implicit_ms": ms_i, "implicit_tflops": fl / (ms_i * 1e-3) / 1e12,
+                    "implicit_frac_of_bf16_peak": fl / (ms_i * 1e-3) / 1e12 / bf16_peak,
+                    "col_matrix_bytes_avoided": M * K * 2})
+        del x, w, col, y
+    return out
+
+
 def posenet_measure(pb, torch, dev, flush, g, mu_d, peaks):
     """Pose-proposal network: GEMM roofline, DRR batch generation, network
     training step (batch 256, 2 views of 128^2 from 384^2 DRRs)."""
@@ -862,8 +897,12 @@ def posenet_measure(pb, torch, dev, flush, g, mu_d, peaks):
 
     ms_net = _event_ms(torch, step, flush, reps=5)
     ms_fwd = _event_ms(torch, net.forward, flush, reps=5)
+    net.implicit = False
+    ms_fwd_explicit = _event_ms(torch, net.forward, flush, reps=5)
+    net.implicit = True
+    convs = conv_layers(pb, torch, dev, flush, bf16_peak)
     status = pb.pn_status()
-    return {"gemm": gem,
+    return {"gemm": gem, "conv_layers": convs,
             "roofline": {"bound": "tensor", "kernel": "k_gemm_bf16 (tcgen05.mma kind::f16, TMEM accumulator, TMA)",
                          "achieved": top["tflops"], "peak": bf16_peak, "unit": "TFLOP/s",
                          "frac": top["tflops"] / bf16_peak,
@@ -871,6 +910,7 @@ def posenet_measure(pb, torch, dev, flush, g, mu_d, peaks):
                          "peak_from": "MEASURED_PEAKS.json bf16_tflops (cuBLAS 8192^3 burst)"},
             "drr_batch_ms": ms_drr, "drr_batch": "256 poses x 2 views of 384^2 (K2), box-downsampled to 128^2",
             "net_train_step_ms": ms_net, "net_forward_ms": ms_fwd,
+            "net_forward_ms_im2col_gemm": ms_fwd_explicit,
             "training_drrs_per_s": B / ((ms_drr + ms_net) * 1e-3),
             "device_status": status}
 
@@ -978,8 +1018,9 @@ def main():
     if args.section == "gemm":
         dev0 = torch.device("cuda", local)
         fl = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev0)
-        print(json.dumps({"section": "gemm", "gemm": gemm_throughput(
-            pb, torch, dev0, fl, float(load_peaks().get("bf16_tflops", 1800.0)))}), flush=True)
+        pk = float(load_peaks().get("bf16_tflops", 1800.0))
+        print(json.dumps({"section": "gemm", "gemm": gemm_throughput(pb, torch, dev0, fl, pk),
+                          "conv_layers": conv_layers(pb, torch, dev0, fl, pk)}), flush=True)
         return
     dist = None
     if world > 1:

@@ -101,6 +101,21 @@ int pn_mse_loss(const float *y, int B, int n_out, int ldy, const float *target, 
 /* dst = BF16(src), round to nearest even, n elements. */
 int pn_to_bf16(const float *src, long long n, void *dst, proj_stream stream);
 
+/* 3x3, stride-2, padding-1 convolution as an implicit GEMM on the tensor
+ * cores: the same products and accumulation order as pn_im2col_3x3s2 (kp =
+ * 9 C) followed by pn_gemm_bf16 on 1-SM tiles, hence the same results, but
+ * the (pixel x tap x channel) matrix is never written: the kernel gathers
+ * each 128 x 64 operand tile from x into shared memory itself.
+ *   x      BF16 NHWC [B][H][W][C], C a multiple of 8, 16-byte aligned.
+ *   w      BF16 [cout][9 C] (k = (kh * 3 + kw) * C + c), 16-byte aligned.
+ *   bias   [cout] FP32 or NULL; relu: max(0, .) after the bias.
+ *   y32, y16  outputs [B][Ho][Wo][cout] (FP32 / BF16; at least one),
+ *          Ho = (H + 1) / 2, Wo = (W + 1) / 2.
+ * Errors: PROJ_E_ARG (shapes, alignment, C not a multiple of 8),
+ * PROJ_E_CUDA.  Waits are bounded as in pn_gemm_bf16 (pn_status). */
+int pn_conv3x3s2_bf16(const void *x, int B, int H, int W, int C, const void *w, int cout, const float *bias,
+                      int relu, float *y32, void *y16, proj_stream stream);
+
 /* Synchronise the stream, return and clear the status word of the current
  * device: 0 = clean; bit 1: a TMA stage never filled, bit 2: an
  * accumulator never completed, bit 4: a stage was never released (each

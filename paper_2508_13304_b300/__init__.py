@@ -89,6 +89,7 @@ _SIGS = {
     "pn_gemm_split_hint": [_I, _I, _I],
     "pn_gemm_use_pair_tiles": [_I],
     "pn_im2col_3x3s2": [_P, _I, _I, _I, _I, _I, _P, _P],
+    "pn_conv3x3s2_bf16": [_P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _P, _P],
     "pn_col2im_3x3s2": [_P, _I, _I, _I, _I, _I, _P, _P, _P, _P],
     "pn_transpose_bf16": [_P, _I, _I, _P, _I, _P],
     "pn_colsum_scratch_floats": [_I, _I],
@@ -534,6 +535,15 @@ def pn_gemm_use_pair_tiles(mode=2) -> int:
 
 def pn_gemm_split_hint(M, N, K) -> int:
     return int(lib().pn_gemm_split_hint(int(M), int(N), int(K)))
+
+
+def pn_conv3x3s2_bf16(x, B, H, W, C, w, cout, bias=None, relu=False, y32=None, y16=None, stream=None):
+    """Implicit-GEMM 3x3 stride-2 convolution (see include/posenet.h)."""
+    Ho, Wo = (H + 1) // 2, (W + 1) // 2
+    _check(lib().pn_conv3x3s2_bf16(_bf(x, B * H * W * C, "x"), B, H, W, C, _bf(w, cout * 9 * C, "w"), int(cout),
+                                   _f32(bias, cout, "bias", allow_none=True), 1 if relu else 0,
+                                   _f32(y32, B * Ho * Wo * cout, "y32", allow_none=True),
+                                   _bf(y16, B * Ho * Wo * cout, "y16", allow_none=True), _stream(stream)))
 
 
 def pn_im2col_3x3s2(x, B, H, W, C, kp, col, stream=None):

@@ -188,6 +188,37 @@ int pn_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int
   return PROJ_OK;
 }
 
+int pn_conv3x3s2_bf16(const void* x, int B, int H, int W, int C, const void* w, int cout, const float* bias,
+                      int relu, float* y32, void* y16, proj_stream stream) {
+  if (!x || !w || (!y32 && !y16)) return fail(PROJ_E_ARG, "pn_conv3x3s2_bf16: NULL input, weights or output");
+  if (B < 1 || H < 1 || W < 1 || cout < 1) return fail(PROJ_E_ARG, "pn_conv3x3s2_bf16: empty shape");
+  if (C < 8 || C % 8) return fail(PROJ_E_ARG, "pn_conv3x3s2_bf16: C = %d must be a positive multiple of 8", C);
+  if (!aligned16(x) || !aligned16(w)) return fail(PROJ_E_ARG, "pn_conv3x3s2_bf16: x and w must be 16-byte aligned");
+  const long long M = (long long)B * ((H + 1) / 2) * ((W + 1) / 2);
+  if (M > 0x7fffffffLL || (long long)B * H * W * C > (1LL << 40))
+    return fail(PROJ_E_ARG, "pn_conv3x3s2_bf16: shape too large");
+  int* status = status_word();
+  if (!status) return fail(PROJ_E_CUDA, "pn_conv3x3s2_bf16: no device status word");
+  const int bn = bn_for(cout);
+  CUtensorMap tw;
+  int rc = make_map(&tw, w, cout, 9 * C, 9 * C, bn);
+  if (rc) return rc;
+  GemmEpi epi;
+  epi.bias = bias;
+  epi.mask = nullptr;
+  epi.ldm = 0;
+  epi.relu = relu;
+  epi.d32 = y32;
+  epi.d16 = static_cast<__nv_bfloat16*>(y16);
+  epi.ldd = cout;
+  epi.part = nullptr;
+  epi.wait_ns = g_wait_ns;
+  epi.stall_tma = 0;
+  cudaError_t e = launch_conv_implicit(static_cast<const __nv_bfloat16*>(x), B, H, W, C, tw, cout, bn, epi, status,
+                                       (cudaStream_t)stream);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "implicit convolution launch");
+}
+
 int pn_im2col_3x3s2(const void* x, int B, int H, int W, int C, int kp, void* col, proj_stream stream) {
   if (!x || !col) return fail(PROJ_E_ARG, "pn_im2col_3x3s2: NULL argument");
   if (B < 1 || H < 1 || W < 1 || C < 1) return fail(PROJ_E_ARG, "pn_im2col_3x3s2: empty shape");

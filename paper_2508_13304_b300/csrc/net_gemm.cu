@@ -661,6 +661,175 @@ cudaError_t launch_pair_persistent(const CUtensorMap& ta, const CUtensorMap& tb,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- implicit-GEMM convolution
+//
+// 3x3, stride-2, padding-1 convolution of an NHWC BF16 activation as a GEMM
+// whose A operand (output pixels x (tap, channel)) is never written to
+// memory: warps 0-3 gather each 128 x 64 A stage straight from the
+// activation, one output pixel (tile row) per thread, as eight 16-byte
+// cp.async copies placed at their 128-byte-swizzled positions (zero fill for
+// taps in the padding and for rows past M).  The weights [Cout][9 C] arrive
+// by TMA as in k_gemm_bf16 (warp 4), one lane of warp 5 issues the MMAs, and
+// warps 0-3 run the same epilogue.  K runs tap-major, k = tap * C + c, as in
+// k_im2col, so the accumulation order and the results equal those of im2col
+// followed by the 1-SM GEMM.  A gathering thread keeps kStages - 1 stages of
+// copies in flight; it signals a stage's "full" barrier (with a proxy fence,
+// the MMA reads shared memory through the async proxy) once that stage's
+// copies are complete.  Every wait is bounded as in the GEMM kernels.
+
+constexpr int kConvThreads = 192;
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kConvThreads, 1)
+    k_conv3x3s2_implicit(const __nv_bfloat16* __restrict__ x, int H, int W, int C,
+                         const __grid_constant__ CUtensorMap tb, int M, int N, GemmEpi epi, int* status) {
+  constexpr uint32_t kBytesA = kBM * kBK * 2, kBytesB = BN * kBK * 2;
+  constexpr int kAhead = kStages - 1;  // stages of copies a gathering thread keeps in flight
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* const gbase = smem_raw + (base - raw);
+  const uint32_t sA = base, sB = base + kStages * kBytesA;
+  const uint32_t bars = sB + kStages * kBytesB;  // full[kStages], empty[kStages], done
+  uint64_t* const bar_ptr = reinterpret_cast<uint64_t*>(gbase + (bars - base));
+  uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bar_ptr + 2 * kStages + 1);
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (kStages + s); };
+  const uint32_t done = bars + 8u * (2 * kStages);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  const int nkb = (9 * C + kBK - 1) / kBK;
+  const int Ho = (H + 1) / 2, Wo = (W + 1) / 2;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full(s), 1 + kBM);  // the weight TMA's expect_tx arrive + one arrive per gathered row
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(tmem_cols<BN>())
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_d = *tmem_slot;
+  int fail = 0;
+
+  if (warp < 4) {
+    const int t = threadIdx.x;  // row of the A tile
+    const int m = m0 + t;
+    const bool row_ok = m < M;
+    const int wo = row_ok ? m % Wo : 0, ho = row_ok ? (m / Wo) % Ho : 0, b = row_ok ? m / (Wo * Ho) : 0;
+    const int hi0 = 2 * ho - 1, wi0 = 2 * wo - 1;
+    const __nv_bfloat16* xb = x + (size_t)b * H * W * C;
+    const uint32_t row_off = (uint32_t)t * 128u, swz = (uint32_t)(t & 7);
+    int i = 0;
+    for (; i < nkb; ++i) {
+      const int s = i % kStages;
+      if (i >= kStages && !mbar_wait(empty(s), ((i / kStages) - 1) & 1, epi.wait_ns)) {
+        fail = kStatusTimeoutFree;
+        break;
+      }
+      const int k = i * kBK;
+      int tap = k / C, c = k - tap * C;
+      const uint32_t dst = sA + s * kBytesA + row_off;
+#pragma unroll
+      for (int j = 0; j < kBK / 8; ++j) {  // 16-byte chunk j of the row: k .. k + 7 of tap `tap`
+        const int hi = hi0 + tap / 3, wi = wi0 + tap % 3;
+        const bool ok = row_ok && tap < 9 && hi >= 0 && hi < H && wi >= 0 && wi < W;
+        cp_async16(dst + (((uint32_t)j ^ swz) << 4), ok ? xb + ((size_t)hi * W + wi) * C + c : x, ok ? 16u : 0u);
+        c += 8;
+        if (c == C) {
+          c = 0;
+          ++tap;
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      if (i >= kAhead) {
+        asm volatile("cp.async.wait_group %0;" ::"n"(kAhead) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(full((i - kAhead) % kStages));
+      }
+    }
+    // no copy may still be writing this CTA's shared memory when it moves on
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (!fail)
+      for (int q = max(0, nkb - kAhead); q < nkb; ++q) mbar_arrive(full(q % kStages));
+  } else if (warp == 4 && lane == 0) {
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % kStages;
+      if (i >= kStages && !mbar_wait(empty(s), ((i / kStages) - 1) & 1, epi.wait_ns)) {
+        fail = kStatusTimeoutFree;
+        break;
+      }
+      mbar_expect_tx(full(s), kBytesB);
+      tma_load_2d(sB + s * kBytesB, &tb, full(s), i * kBK, n0);
+    }
+  } else if (warp == 5 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(BN);
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % kStages;
+      if (!mbar_wait(full(s), (i / kStages) & 1, epi.wait_ns)) {
+        fail = kStatusTimeoutTma;
+        break;
+      }
+      tc_fence_after();
+      const uint64_t da = sw128_desc(sA + s * kBytesA), db = sw128_desc(sB + s * kBytesB);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk)
+        umma_bf16(tmem_d, da + 2 * kk, db + 2 * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+      umma_commit(empty(s));
+    }
+    umma_commit(done);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(done, 0, epi.wait_ns);
+  if (!ok && threadIdx.x == 0) fail |= kStatusTimeoutMma;
+  if (fail) atomicOr(status, fail);
+  const bool any_fail = __syncthreads_or(fail != 0 || !ok) != 0;
+  tc_fence_after();
+
+  if (!any_fail && warp < 4) epilogue<BN>(tmem_d, m0, n0, M, N, 0, epi, warp);
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 5) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(tmem_cols<BN>())
+                 : "memory");
+  }
+}
+
+template <int BN>
+cudaError_t launch_conv_bn(const __nv_bfloat16* x, int B, int H, int W, int C, const CUtensorMap& tb, int N,
+                           const GemmEpi& epi, int* status, cudaStream_t s) {
+  const size_t smem = gemm_smem_bytes(BN);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_conv3x3s2_implicit<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long M = (long long)B * ((H + 1) / 2) * ((W + 1) / 2);
+  if (M > 0x7fffffffLL) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((M + kBM - 1) / kBM), (N + BN - 1) / BN, 1);
+  k_conv3x3s2_implicit<BN><<<grid, kConvThreads, smem, s>>>(x, H, W, C, tb, (int)M, N, epi, status);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t gemm_smem_bytes(int bn) {
@@ -676,6 +845,17 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int
     case 64: return launch_bn<64>(ta, tb, M, N, K, split, kb_per_split, epi, status, s);
     case 128: return launch_bn<128>(ta, tb, M, N, K, split, kb_per_split, epi, status, s);
     case 256: return launch_bn<256>(ta, tb, M, N, K, split, kb_per_split, epi, status, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_conv_implicit(const __nv_bfloat16* x, int B, int H, int W, int C, const CUtensorMap& tw, int cout,
+                                 int bn, const GemmEpi& epi, int* status, cudaStream_t s) {
+  switch (bn) {
+    case 32: return launch_conv_bn<32>(x, B, H, W, C, tw, cout, epi, status, s);
+    case 64: return launch_conv_bn<64>(x, B, H, W, C, tw, cout, epi, status, s);
+    case 128: return launch_conv_bn<128>(x, B, H, W, C, tw, cout, epi, status, s);
+    case 256: return launch_conv_bn<256>(x, B, H, W, C, tw, cout, epi, status, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -41,6 +41,10 @@ size_t gemm_smem_bytes(int bn);
 cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int bn, int pair,
                         int split, int kb_per_split, const GemmEpi& epi, int* status, cudaStream_t s);
 cudaError_t launch_split_reduce(const float* part, int split, int M, int N, const GemmEpi& epi, cudaStream_t s);
+// implicit-GEMM 3x3 stride-2 pad-1 convolution: x NHWC [B][H][W][C] (C % 8 == 0), weights by the tensor map tw
+// ([cout][9 C], boxes of bn rows), output through epi (rows = output pixels, columns = output channels)
+cudaError_t launch_conv_implicit(const __nv_bfloat16* x, int B, int H, int W, int C, const CUtensorMap& tw, int cout,
+                                 int bn, const GemmEpi& epi, int* status, cudaStream_t s);
 
 cudaError_t launch_im2col(const __nv_bfloat16* x, int B, int H, int W, int C, int kp, __nv_bfloat16* col,
                           cudaStream_t s);

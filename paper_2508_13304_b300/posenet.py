@@ -11,10 +11,12 @@ padding-1 convolutions with ReLU (default 2 -> 32 -> 64 -> 128 -> 128 ->
 connected layer of 256 with ReLU and a linear output of 6 (normalised pose:
 translations / t_range, rotations / r_range).  Loss: mean squared error.
 
-Every forward and backward step runs in the library's kernels: im2col +
-GEMM (bias and ReLU fused) forward; GEMM + col2im (ReLU mask fused) for the
-input gradients; transposes + split-K GEMM for the weight gradients; column
-sums for the bias gradients.  Parameters are FP32 masters updated by Adam
+Every forward and backward step runs in the library's kernels: implicit-
+GEMM convolutions (the tensor-core kernel gathers the 3x3 patches itself;
+bias and ReLU fused) forward for layers whose input has a multiple of 8
+channels and at least 8192 output pixels, im2col + GEMM for the others; GEMM + col2im (ReLU mask fused)
+for the input gradients; im2col, transposes + split-K GEMM for the weight
+gradients; column sums for the bias gradients.  Parameters are FP32 masters updated by Adam
 (a few torch elementwise operations, as in the registration loop) and
 converted to BF16 (and transposed) for the GEMMs after every update.
 """
@@ -27,8 +29,8 @@ import numpy as np
 import torch
 
 from . import (PROJ_OP_FORWARD, Projector, pn_col2im_3x3s2, pn_colsum_bf16, pn_colsum_scratch_floats,
-               pn_gemm_bf16, pn_gemm_split_hint, pn_im2col_3x3s2, pn_mse_loss, pn_prepare_images, pn_to_bf16,
-               pn_transpose_bf16, proj_forward)
+               pn_conv3x3s2_bf16, pn_gemm_bf16, pn_gemm_split_hint, pn_im2col_3x3s2, pn_mse_loss, pn_prepare_images,
+               pn_to_bf16, pn_transpose_bf16, proj_forward)
 
 BF = torch.bfloat16
 
@@ -43,8 +45,9 @@ class PoseNet:
     gradients of one batch into .grads (FP32, same shapes as .params)."""
 
     def __init__(self, batch, in_hw=128, n_views=2, channels=(32, 64, 128, 128, 128, 128), hidden=256, n_out=6,
-                 device="cuda", seed=0):
+                 device="cuda", seed=0, implicit=True):
         self.B, self.hw, self.n_views, self.n_out = batch, in_hw, n_views, n_out
+        self.implicit = implicit
         self.dev = torch.device(device)
         g = torch.Generator(device="cpu").manual_seed(seed)
         self.layers = []
@@ -134,9 +137,16 @@ class PoseNet:
         B = self.B
         a, cin = self.x, self.n_views
         for L in self.layers:
-            pn_im2col_3x3s2(a, B, L["H"], L["H"], cin, L["kp"], L["col"])
-            pn_gemm_bf16(L["M"], L["cout"], L["kp"], L["col"], L["kp"], L["wb"], L["kp"], bias=L["b"], relu=True,
-                         D16=L["a"])
+            # implicit GEMM where its grid has at least 64 tiles of 128 output pixels: on the two smallest
+            # layers of the default network (8 and 32 tiles) im2col + GEMM measured faster
+            if self.implicit and cin % 8 == 0 and L["M"] >= 64 * 128:
+                pn_conv3x3s2_bf16(a, B, L["H"], L["H"], cin, L["wb"], L["cout"], bias=L["b"], relu=True, y16=L["a"])
+                L["col_ready"] = False
+            else:
+                pn_im2col_3x3s2(a, B, L["H"], L["H"], cin, L["kp"], L["col"])
+                pn_gemm_bf16(L["M"], L["cout"], L["kp"], L["col"], L["kp"], L["wb"], L["kp"], bias=L["b"],
+                             relu=True, D16=L["a"])
+                L["col_ready"] = True
             a, cin = L["a"], L["cout"]
         F1, F2 = self.fc
         pn_gemm_bf16(B, F1["n"], F1["n_in"], a, F1["n_in"], F1["wb"], F1["n_in"], bias=F1["b"], relu=True,
@@ -177,6 +187,10 @@ class PoseNet:
         # convolutions, last to first
         for i in reversed(range(len(self.layers))):
             L = self.layers[i]
+            if not L.get("col_ready", False):     # the implicit forward did not store the patches
+                inp = self.x if i == 0 else self.layers[i - 1]["a"]
+                pn_im2col_3x3s2(inp, B, L["H"], L["H"], L["cin"], L["kp"], L["col"])
+                L["col_ready"] = True
             self._wgrad(L["d"], L["M"], L["cout"], L["col"], L["kp"], L["gw"], L["split"])
             pn_colsum_bf16(L["d"], L["M"], L["cout"], L["cout"], L["gb"], self.cs)
             if i > 0:

@@ -193,6 +193,66 @@ def test_conv_forward_im2col_gemm(B, H, W, Ci, Co):
     assert rel(y.cpu().numpy().reshape(ref.shape), ref) <= 1e-5
 
 
+@pytest.mark.parametrize("B,H,W,Ci,Co", [(2, 32, 32, 8, 16), (3, 31, 17, 32, 64), (4, 16, 16, 64, 128),
+                                        (2, 8, 8, 128, 128), (1, 5, 7, 16, 32), (5, 9, 33, 128, 40)])
+def test_conv_implicit_gemm_equals_im2col_gemm(B, H, W, Ci, Co):
+    """The implicit-GEMM convolution gathers the 3x3 patches itself: its
+    FP32 and BF16 outputs equal im2col + the 1-SM GEMM bit for bit (same
+    products, same K order) and match the FP64 convolution.  Odd sizes leave
+    ragged last M and N tiles and padding taps on every border."""
+    rng = np.random.default_rng(B * H + Ci + Co)
+    x, w = conv_case(rng, B, H, W, Ci, Co)
+    b = torch.from_numpy(0.1 * rng.standard_normal(Co).astype(np.float32)).cuda()
+    kp = kpad(Ci)
+    Ho, Wo = (H + 1) // 2, (W + 1) // 2
+    M = B * Ho * Wo
+    col = torch.empty((M, kp), device="cuda", dtype=torch.bfloat16)
+    pb.pn_im2col_3x3s2(x, B, H, W, Ci, kp, col)
+    Wm = weight_matrix(w, kp)
+    y32 = torch.full((M, Co), float("nan"), device="cuda")
+    y16 = torch.full((M, Co), float("nan"), device="cuda", dtype=torch.bfloat16)
+    pb.pn_gemm_bf16(M, Co, kp, col, kp, Wm, kp, bias=b, relu=True, D32=y32, D16=y16)
+    z32 = torch.full((M, Co), float("nan"), device="cuda")
+    z16 = torch.full((M, Co), float("nan"), device="cuda", dtype=torch.bfloat16)
+    pb.pn_conv3x3s2_bf16(x, B, H, W, Ci, Wm, Co, bias=b, relu=True, y32=z32, y16=z16)
+    torch.cuda.synchronize()
+    assert pb.pn_status() == 0
+    assert torch.equal(z32, y32) and torch.equal(z16, y16)
+    ref = np.maximum(on.conv3x3s2(f64(x), f64(w), b.cpu().numpy()), 0.0)
+    assert rel(z32.cpu().numpy().reshape(ref.shape), ref) <= 1e-5
+
+
+def test_conv_implicit_gemm_rejects_bad_arguments():
+    x = torch.zeros((1, 8, 8, 12), device="cuda", dtype=torch.bfloat16)
+    w = torch.zeros((16, 108), device="cuda", dtype=torch.bfloat16)
+    y = torch.empty((1, 4, 4, 16), device="cuda", dtype=torch.bfloat16)
+    with pytest.raises(pb.ProjError):                     # C must be a multiple of 8
+        pb.pn_conv3x3s2_bf16(x, 1, 8, 8, 12, w, 16, y16=y)
+
+
+def test_network_forward_implicit_equals_explicit():
+    """PoseNet with implicit-GEMM convolutions and with im2col + GEMM give the
+    same outputs and the same gradients (the backward pass materialises the
+    patches for the weight gradients in both)."""
+    from paper_2508_13304_b300 import posenet as pn
+    rng = np.random.default_rng(21)
+    B = 64                                   # layer 2 has 64 x 16 x 16 = 16384 output pixels: implicit GEMM
+    nets = [pn.PoseNet(B, in_hw=64, n_views=2, channels=(16, 32, 32, 32), hidden=64, seed=5, implicit=imp)
+            for imp in (True, False)]
+    x = torch.from_numpy(rng.standard_normal((B, 64, 64, 2)).astype(np.float32)).cuda().bfloat16()
+    t = torch.from_numpy(rng.uniform(-1, 1, (B, 6)).astype(np.float32)).cuda()
+    outs, grads = [], []
+    for net in nets:
+        outs.append(net.forward(x).clone())
+        net.loss_grad(t)
+        net.backward()
+        grads.append([g.clone() for g in net.grads])
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1])
+    for g0, g1 in zip(*grads):
+        assert torch.equal(g0, g1)
+
+
 @pytest.mark.parametrize("B,H,W,Ci,Co", [(3, 16, 16, 2, 32), (2, 18, 14, 32, 64), (2, 8, 8, 128, 128)])
 def test_conv_backward_pieces(B, H, W, Ci, Co):
     """dx = col2im(dy . W) with the ReLU mask of x; dW = dy^T . col via
