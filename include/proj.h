@@ -177,7 +177,8 @@ int proj_workspace_size(proj_plan plan, size_t *bytes);
  * four corners of each cell's xy face, two copies with rows along x and y)
  * and, when PROJ_OP_FORWARD_GRAD is enabled, a float4
  * (mu, d mu/dx', d mu/dy', d mu/dz') volume (per mm, object frame) on the
- * index grid [-1, n]^3 and its copy with rows along y.
+ * index grid [-1, n]^3 and its copy with rows along y; for either, the
+ * occupancy bricks of the empty-space skipping (proj_set_skip_brick).
  *   d_mu  [nz][ny][nx] FP32.
  * Must run before proj_forward / proj_forward_pose_grad; stays valid until
  * the workspace is reused for another volume. */
@@ -283,6 +284,34 @@ int proj_set_warp_shape(proj_plan plan, int warp_width);
 int proj_get_warp_shape(proj_plan plan, int *warp_width);
 int proj_autotune_forward_grad(proj_plan plan, const float *d_pose, int loss, const float *d_ref, void *d_ws,
                                size_t ws_bytes, proj_stream stream, int reps, float *times_ms, int *warp_width);
+
+/* Empty-space skipping in proj_forward and the fused pose-gradient marches
+ * (a library facility; the paper has none).  proj_set_volume also records,
+ * for bricks of 8^3 and of 16^3 cells of the 2-voxel-bordered grid, whether
+ * a brick holds, or lies within one cell of, a cell with a non-zero corner in
+ * (mu, grad mu).  Before marching, each ray walks the bricks it crosses and
+ * keeps only its samples from two before the first to two after the last
+ * occupied brick.  A sample left out reads eight zero corners and adds exact
+ * zeros to every sum, and the kept samples are summed in the same order, so
+ * results are bit-identical with and without skipping; only the time
+ * changes (most for volumes with much empty space around the object).  The
+ * exact transposes never skip (they do not read mu).
+ * proj_set_skip_brick: edge 8 (default), 16, or 0 (off); PROJ_E_ARG
+ * otherwise.  proj_autotune_march: like proj_autotune_forward_grad over the
+ * 3 x 4 combinations of brick edge (0, 8, 16) and warp shape (2, 4, 8, 16);
+ * keeps the fastest pair in the plan and returns it in *warp_width and
+ * *brick_edge (may be NULL) with the times in times_ms[12] (index 4 * edge
+ * position + shape position; may be NULL).  proj_count_marched_samples: like
+ * proj_count_samples, but counts the samples the fused march gathers with
+ * the plan's setting (the gradient grid's box (-2, n+1), clipped to the
+ * occupied bricks); needs PROJ_OP_FORWARD_GRAD. */
+int proj_set_skip_brick(proj_plan plan, int edge);
+int proj_get_skip_brick(proj_plan plan, int *edge);
+int proj_autotune_march(proj_plan plan, const float *d_pose, int loss, const float *d_ref, void *d_ws,
+                        size_t ws_bytes, proj_stream stream, int reps, float *times_ms, int *warp_width,
+                        int *brick_edge);
+int proj_count_marched_samples(proj_plan plan, const float *d_pose, long long *d_count, void *d_ws, size_t ws_bytes,
+                               proj_stream stream);
 
 /* Brick shape of the back-projection gradient (a library facility; the
  * paper fixes none): a block owns 32 x 8 voxel columns of gz voxels and a

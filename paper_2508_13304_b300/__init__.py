@@ -76,6 +76,11 @@ _SIGS = {
     "proj_get_warp_shape": [_P, ctypes.POINTER(_I)],
     "proj_autotune_forward_grad": [_P, _P, _I, _P, _P, _SZ, _P, _I, ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(_I)],
+    "proj_set_skip_brick": [_P, _I],
+    "proj_get_skip_brick": [_P, ctypes.POINTER(_I)],
+    "proj_autotune_march": [_P, _P, _I, _P, _P, _SZ, _P, _I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I),
+                            ctypes.POINTER(_I)],
+    "proj_count_marched_samples": [_P, _P, _P, _P, _SZ, _P],
     "proj_set_brick_shape": [_P, _I],
     "proj_get_brick_shape": [_P, ctypes.POINTER(_I)],
     "proj_autotune_back_grad": [_P, _P, _P, _I, _P, _P, _SZ, _P, _I, ctypes.POINTER(ctypes.c_float),
@@ -404,6 +409,42 @@ def proj_autotune_forward_grad(plan: Plan, pose, loss, ref, ws, reps=3, stream=N
     return int(w.value), dict(zip(WARP_WIDTHS, [float(t) for t in times]))
 
 
+SKIP_BRICK_EDGES = (0, 8, 16)
+
+
+def proj_set_skip_brick(plan: Plan, edge: int):
+    """Empty-space skipping of the forward marches: brick edge 8, 16 or 0 (off)."""
+    _check(lib().proj_set_skip_brick(plan.handle, int(edge)))
+
+
+def proj_get_skip_brick(plan: Plan) -> int:
+    e = ctypes.c_int()
+    _check(lib().proj_get_skip_brick(plan.handle, ctypes.byref(e)))
+    return int(e.value)
+
+
+def proj_autotune_march(plan: Plan, pose, loss, ref, ws, reps=3, stream=None):
+    """Time the fused march per (skip brick edge, warp shape) on this data, keep
+    the fastest in the plan; returns (warp_width, brick_edge, {(edge, width): ms})."""
+    import torch
+    p, nb = _ws(ws)
+    n_ref = (plan.n_inst if loss == PROJ_LOSS_RESIDUAL else plan.geom.n_views) * plan.img_numel
+    times = (ctypes.c_float * 12)()
+    w, e = ctypes.c_int(), ctypes.c_int()
+    _check(lib().proj_autotune_march(plan.handle, _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"), int(loss),
+                                     _ptr(ref, torch.float32, n_ref, "ref"), p, nb, _stream(stream), int(reps), times,
+                                     ctypes.byref(w), ctypes.byref(e)))
+    tt = {(SKIP_BRICK_EDGES[j], WARP_WIDTHS[i]): float(times[4 * j + i]) for j in range(3) for i in range(4)}
+    return int(w.value), int(e.value), tt
+
+
+def proj_count_marched_samples(plan: Plan, pose, count, ws, stream=None):
+    import torch
+    p, nb = _ws(ws)
+    _check(lib().proj_count_marched_samples(plan.handle, _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"),
+                                            _ptr(count, torch.int64, plan.n_inst, "count"), p, nb, _stream(stream)))
+
+
 # brick shapes of the back-projection gradient: (voxels per thread along z, instances per block)
 BRICK_SHAPES = ((16, 8), (8, 8), (16, 16), (8, 16))
 
@@ -699,6 +740,12 @@ class Projector:
         import torch
         c = torch.empty((self.n_inst,), dtype=torch.int64, device=self.device)
         proj_count_samples(self.plan, self._t(pose), c, self.ws)
+        return c
+
+    def count_marched_samples(self, pose):
+        import torch
+        c = torch.empty((self.n_inst,), dtype=torch.int64, device=self.device)
+        proj_count_marched_samples(self.plan, self._t(pose), c, self.ws)
         return c
 
     def check(self):

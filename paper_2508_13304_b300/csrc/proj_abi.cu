@@ -59,13 +59,16 @@ struct proj_plan_s {
   FdkView* d_fdk = nullptr;  // per instance
   // rays per warp row in the fused pose-gradient march (2, 4, 8 or 16)
   int warp_width = 4;
+  // empty-space skipping in the forward marches: log2 of the occupancy brick edge (3: 8 cells, 4: 16), 0 = off
+  int skip_shift = 3;
   // optional timing of the main kernel of each call
   bool timing = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // workspace layout (byte offsets; 0 = buffer absent, the status word sits at 0)
   size_t off_status = 0, off_inst = 0, off_ptab = 0, off_volq = 0, off_volqy = 0, off_vol4 = 0, off_vol4y = 0, off_part_f = 0,
          off_det4 = 0,
-         off_part_b = 0, off_detq = 0, off_acc = 0, off_sharp_m = 0, off_sharp_part = 0, ws_bytes = 0;
+         off_part_b = 0, off_detq = 0, off_acc = 0, off_sharp_m = 0, off_sharp_part = 0, off_occ8 = 0, off_occ16 = 0,
+         ws_bytes = 0;
 };
 
 namespace {
@@ -85,6 +88,8 @@ struct WsView {
   float* part_b = nullptr;
   float4* acc = nullptr;
   float4* detq = nullptr;
+  unsigned char* occ8 = nullptr;
+  unsigned char* occ16 = nullptr;
 };
 
 int check_ws(const proj_plan_s* p, void* d_ws, size_t ws_bytes, WsView* w) {
@@ -105,7 +110,22 @@ int check_ws(const proj_plan_s* p, void* d_ws, size_t ws_bytes, WsView* w) {
   w->part_b = p->off_part_b ? reinterpret_cast<float*>(b + p->off_part_b) : nullptr;
   w->acc = p->off_acc ? reinterpret_cast<float4*>(b + p->off_acc) : nullptr;
   w->detq = p->off_detq ? reinterpret_cast<float4*>(b + p->off_detq) : nullptr;
+  w->occ8 = p->off_occ8 ? reinterpret_cast<unsigned char*>(b + p->off_occ8) : nullptr;
+  w->occ16 = p->off_occ16 ? reinterpret_cast<unsigned char*>(b + p->off_occ16) : nullptr;
   return PROJ_OK;
+}
+
+// The occupancy bricks the forward marches skip with, per the plan's setting (or none).
+Occ occ_of(const proj_plan_s* p, const WsView& w, int shift) {
+  Occ o{};
+  unsigned char* m = shift == 3 ? w.occ8 : (shift == 4 ? w.occ16 : nullptr);
+  if (!m) return o;
+  o.map = m;
+  o.shift = shift;
+  o.nb[0] = occ_bricks(p->geo.nx, shift);
+  o.nb[1] = occ_bricks(p->geo.ny, shift);
+  o.nb[2] = occ_bricks(p->geo.nz, shift);
+  return o;
 }
 
 int need_op(const proj_plan_s* p, int op, const char* name) {
@@ -289,6 +309,10 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   }
   p->off_part_b = (ops & PROJ_OP_BACK_GRAD) ? take(sizeof(float) * 12 * (size_t)n_inst * p->bp_blocks) : 0;
   p->off_acc = (ops & PROJ_OP_ADJOINT) ? take(sizeof(float4) * npad_sz) : 0;
+  if (ops & (PROJ_OP_FORWARD | PROJ_OP_FORWARD_GRAD)) {
+    p->off_occ8 = take((size_t)occ_bricks(G.nx, 3) * occ_bricks(G.ny, 3) * occ_bricks(G.nz, 3));
+    p->off_occ16 = take((size_t)occ_bricks(G.nx, 4) * occ_bricks(G.ny, 4) * occ_bricks(G.nz, 4));
+  }
   if (ops & PROJ_OP_SHARPNESS) {
     p->off_sharp_m = take(sizeof(float) * (size_t)G.nx * G.ny * G.nz);
     p->off_sharp_part = take(sizeof(double) * (2 * (size_t)sharpness_blocks(g) + 2));
@@ -385,6 +409,7 @@ int proj_set_volume(proj_plan p, const float* d_mu, void* d_ws, size_t ws_bytes,
   if (rc) return rc;
   if ((rc = check_device(p))) return rc;
   cudaError_t e = launch_volume_prep(d_mu, p->geo, w.volq, w.vol4, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = launch_occupancy(d_mu, p->geo, w.occ8, w.occ16, (cudaStream_t)stream);
   if (e == cudaSuccess && w.vol4y) e = launch_volume_yfast(w.vol4, p->geo, w.vol4y, (cudaStream_t)stream);
   if (e == cudaSuccess && w.volqy) e = launch_records_yfast(w.volq, p->geo, w.volqy, (cudaStream_t)stream);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "volume preparation launch");
@@ -401,7 +426,7 @@ int proj_forward(proj_plan p, const float* d_pose, float* d_proj, void* d_ws, si
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = setup(p, d_pose, w, s))) return rc;
   mark(p, true, s);
-  cudaError_t e = launch_forward(w.inst, p->n_inst, p->geo, w.volq, w.volqy, d_proj, s);
+  cudaError_t e = launch_forward(w.inst, p->n_inst, p->geo, w.volq, w.volqy, d_proj, s, occ_of(p, w, p->skip_shift));
   mark(p, false, s);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "forward launch");
 }
@@ -435,7 +460,8 @@ int proj_forward_pose_grad(proj_plan p, const float* d_pose, int loss, const flo
   if ((rc = setup(p, d_pose, w, s))) return rc;
   mark(p, true, s);
   cudaError_t e =
-      launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, d_proj, w.part_f, s, p->warp_width);
+      launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, d_proj, w.part_f, s, p->warp_width,
+                          nullptr, occ_of(p, w, p->skip_shift));
   mark(p, false, s);
   if (e != cudaSuccess) return cuda_fail(e, "forward pose-gradient launch");
   e = launch_forward_grad_reduce(w.inst, w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_tiles, p->geo, loss,
@@ -464,7 +490,7 @@ int proj_forward_pose_grad_list(proj_plan p, const float* d_pose, const int* d_p
   PoseList L{d_pose_list, n_list, p->ipp, p->n_pose, p->d_pose_ptr, p->d_pose_idx, w.status};
   mark(p, true, s);
   cudaError_t e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, d_proj, w.part_f, s,
-                                      p->warp_width, &L);
+                                      p->warp_width, &L, occ_of(p, w, p->skip_shift));
   mark(p, false, s);
   if (e != cudaSuccess) return cuda_fail(e, "forward pose-gradient launch");
   e = launch_forward_grad_reduce(w.inst, w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_tiles, p->geo, loss,
@@ -563,7 +589,8 @@ int proj_gather_probe(proj_plan p, const float* d_pose, void* d_ws, size_t ws_by
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = setup(p, d_pose, w, s))) return rc;
   mark(p, true, s);
-  cudaError_t e = launch_gather_probe(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, w.part_f, s);
+  cudaError_t e = launch_gather_probe(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, w.part_f, s,
+                                      occ_of(p, w, p->skip_shift));
   mark(p, false, s);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "gather probe launch");
 }
@@ -661,12 +688,13 @@ int proj_autotune_forward_grad(proj_plan p, const float* d_pose, int loss, const
   float best = 0.f;
   int pick = p->warp_width;
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+    const Occ occ = occ_of(p, w, p->skip_shift);
     e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, nullptr, w.part_f, s,
-                            widths[i]);
+                            widths[i], nullptr, occ);
     if (e == cudaSuccess) e = cudaEventRecord(a, s);
     for (int r = 0; r < reps && e == cudaSuccess; ++r)
       e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, nullptr, w.part_f, s,
-                            widths[i]);
+                              widths[i], nullptr, occ);
     if (e == cudaSuccess) e = cudaEventRecord(b, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(b);
     float ms = 0.f;
@@ -683,6 +711,90 @@ int proj_autotune_forward_grad(proj_plan p, const float* d_pose, int loss, const
   if (e != cudaSuccess) return cuda_fail(e, "autotune launches");
   p->warp_width = pick;
   if (warp_width) *warp_width = pick;
+  return PROJ_OK;
+}
+
+int proj_count_marched_samples(proj_plan p, const float* d_pose, long long* d_count, void* d_ws, size_t ws_bytes,
+                               proj_stream stream) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_pose || !d_count) return fail(PROJ_E_ARG, "proj_count_marched_samples: NULL pose or output");
+  int rc = need_op(p, PROJ_OP_FORWARD_GRAD, "proj_count_marched_samples");
+  if (rc) return rc;
+  WsView w;
+  if ((rc = check_ws(p, d_ws, ws_bytes, &w))) return rc;
+  if ((rc = check_device(p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = setup(p, d_pose, w, s))) return rc;
+  // the fused march's samples: the gradient grid's box, clipped to the occupied bricks when skipping is on
+  cudaError_t e = launch_count(w.inst, p->n_inst, p->geo, d_count, s, occ_of(p, w, p->skip_shift), 1);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "count launch");
+}
+
+int proj_set_skip_brick(proj_plan p, int edge) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (edge != 0 && edge != 8 && edge != 16) return fail(PROJ_E_ARG, "brick edge %d is not one of 0, 8, 16", edge);
+  p->skip_shift = edge == 8 ? 3 : (edge == 16 ? 4 : 0);
+  return PROJ_OK;
+}
+
+int proj_get_skip_brick(proj_plan p, int* edge) {
+  if (!p || !edge) return fail(PROJ_E_ARG, "plan or edge is NULL");
+  *edge = p->skip_shift ? 1 << p->skip_shift : 0;
+  return PROJ_OK;
+}
+
+int proj_autotune_march(proj_plan p, const float* d_pose, int loss, const float* d_ref, void* d_ws, size_t ws_bytes,
+                        proj_stream stream, int reps, float* times_ms, int* warp_width, int* brick_edge) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (!d_pose || !d_ref) return fail(PROJ_E_ARG, "proj_autotune_march: NULL pose or reference");
+  if (loss != PROJ_LOSS_RESIDUAL && loss != PROJ_LOSS_L2 && loss != PROJ_LOSS_NCC)
+    return fail(PROJ_E_ARG, "unknown loss mode %d", loss);
+  if (reps < 1 || reps > 1000) return fail(PROJ_E_ARG, "reps must be in 1..1000");
+  int rc = need_op(p, PROJ_OP_FORWARD_GRAD, "proj_autotune_march");
+  if (rc) return rc;
+  WsView w;
+  if ((rc = check_ws(p, d_ws, ws_bytes, &w))) return rc;
+  if ((rc = check_device(p))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = setup(p, d_pose, w, s))) return rc;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  const int widths[4] = {2, 4, 8, 16};
+  const int shifts[3] = {0, 3, 4};
+  float best = 0.f;
+  int pick_w = p->warp_width, pick_s = p->skip_shift;
+  bool have = false;
+  for (int j = 0; j < 3 && e == cudaSuccess; ++j) {
+    const Occ occ = occ_of(p, w, shifts[j]);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+      e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, nullptr, w.part_f, s,
+                              widths[i], nullptr, occ);
+      if (e == cudaSuccess) e = cudaEventRecord(a, s);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r)
+        e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, nullptr, w.part_f, s,
+                                widths[i], nullptr, occ);
+      if (e == cudaSuccess) e = cudaEventRecord(b, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      ms /= (float)reps;
+      if (times_ms) times_ms[4 * j + i] = ms;
+      if (e == cudaSuccess && (!have || ms < best)) {
+        best = ms;
+        pick_w = widths[i];
+        pick_s = shifts[j];
+        have = true;
+      }
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune launches");
+  p->warp_width = pick_w;
+  p->skip_shift = pick_s;
+  if (warp_width) *warp_width = pick_w;
+  if (brick_edge) *brick_edge = pick_s ? 1 << pick_s : 0;
   return PROJ_OK;
 }
 
@@ -786,6 +898,7 @@ int proj_batch_create(int n, const proj_plan* plans, const int* loss, const floa
     B.inst = w.inst;
     B.vol4 = w.vol4;
     B.vol4y = w.vol4y;
+    B.occ = occ_of(p, w, p->skip_shift);
     B.ref = d_ref[i];
     B.part = w.part_f;
     B.n_tiles = p->n_tiles;

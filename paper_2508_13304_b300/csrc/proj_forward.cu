@@ -105,6 +105,65 @@ __device__ __forceinline__ bool ray_setup(const InstTable& T, const Geo& g, int 
   return ray_setup_m<1>(T, g, iu, iv, r);
 }
 
+// Empty-space skipping.  Narrows the inclusive sample range [k0, k1] of a ray
+// to the samples between the first and the last occupied brick (Occ) that
+// the ray crosses, widened by two samples at each end.  Sample k sits at
+// (ax, ay, az) + k (dx, dy, dz) in cell coordinates of the 2-voxel-bordered
+// grid (cell c covers [c, c + 1)); (gx, gy, gz) = n + 2 is the largest cell
+// index.  The walk steps from brick face to brick face in the sample
+// parameter (a 3-D DDA) from sample k0 until it passes sample k1.  Samples
+// left out lie in bricks that hold no cell with a non-zero corner within one
+// cell, so even with the rounding of their FP32 positions they read eight
+// zero corners and add exact zeros.  Returns false when no occupied brick is
+// crossed.
+__device__ __forceinline__ bool occ_clip(const Occ& o, float ax, float ay, float az, float dx, float dy, float dz,
+                                         int gx, int gy, int gz, int& k0, int& k1) {
+  const int sh = o.shift;
+  const float edge = (float)(1 << sh), big = 3.0e30f;
+  const float t0 = (float)k0, t1 = (float)k1;
+  int bx = min(max(__float2int_rd(fmaf(t0, dx, ax)), 0), gx) >> sh;
+  int by = min(max(__float2int_rd(fmaf(t0, dy, ay)), 0), gy) >> sh;
+  int bz = min(max(__float2int_rd(fmaf(t0, dz, az)), 0), gz) >> sh;
+  const int stx = dx > 0.f ? 1 : -1, sty = dy > 0.f ? 1 : -1, stz = dz > 0.f ? 1 : -1;
+  // parameter of the next brick face along each axis, and the parameter span of one brick
+  float tx = dx != 0.f ? ((float)((bx + (dx > 0.f ? 1 : 0)) << sh) - ax) / dx : big;
+  float ty = dy != 0.f ? ((float)((by + (dy > 0.f ? 1 : 0)) << sh) - ay) / dy : big;
+  float tz = dz != 0.f ? ((float)((bz + (dz > 0.f ? 1 : 0)) << sh) - az) / dz : big;
+  const float ix = dx != 0.f ? edge / fabsf(dx) : big;
+  const float iy = dy != 0.f ? edge / fabsf(dy) : big;
+  const float iz = dz != 0.f ? edge / fabsf(dz) : big;
+  float t_in = t0, t_first = 0.f, t_last = 0.f;
+  bool found = false;
+  const int max_steps = o.nb[0] + o.nb[1] + o.nb[2] + 3;
+  for (int step = 0; step < max_steps; ++step) {
+    const float t_out = fminf(tx, fminf(ty, tz));
+    if (__ldg(o.map + (bz * o.nb[1] + by) * o.nb[0] + bx)) {
+      if (!found) t_first = t_in;
+      found = true;
+      t_last = t_out;
+    }
+    if (t_out > t1) break;
+    if (tx <= ty && tx <= tz) {
+      bx += stx;
+      tx += ix;
+      if ((unsigned)bx >= (unsigned)o.nb[0]) break;
+    } else if (ty <= tz) {
+      by += sty;
+      ty += iy;
+      if ((unsigned)by >= (unsigned)o.nb[1]) break;
+    } else {
+      bz += stz;
+      tz += iz;
+      if ((unsigned)bz >= (unsigned)o.nb[2]) break;
+    }
+    t_in = t_out;
+  }
+  if (!found) return false;
+  k0 = max(k0, __float2int_rd(t_first) - 2);
+  k1 = min(k1, __float2int_ru(fminf(t_last, t1)) + 2);
+  return k0 <= k1;
+}
+
 // Cell of padded index point (fx, fy, fz): lower corner clamped to
 // [0, n] (1-voxel border) or [0, n + 2] (2-voxel border) so the 8 corners
 // stay inside the padded array; fractions are taken from the clamped corner
@@ -215,6 +274,33 @@ __global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ m
   }
 }
 
+// Occupancy bricks (Occ): one thread per voxel; a non-zero voxel (i, j, k)
+// is a non-zero corner of the bordered-grid cells i .. i+3 (its mu and the
+// central differences on both sides), which with the one-cell apron marks
+// the bricks holding cells i-1 .. i+4 along each axis.  Every writer stores
+// the same value 1, so the unordered stores need no atomics.
+__device__ __forceinline__ void occ_mark(unsigned char* map, int sh, int nb0, int nb1, int x0, int x1, int y0, int y1,
+                                         int z0, int z1) {
+  for (int bz = z0 >> sh; bz <= (z1 >> sh); ++bz)
+    for (int by = y0 >> sh; by <= (y1 >> sh); ++by)
+      for (int bx = x0 >> sh; bx <= (x1 >> sh); ++bx) map[(bz * nb1 + by) * nb0 + bx] = 1;
+}
+
+__global__ void k_occupancy(const float* __restrict__ mu, Geo g, unsigned char* __restrict__ occ8,
+                            unsigned char* __restrict__ occ16) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    if (__ldg(mu + p) == 0.f) continue;
+    const int i = (int)(p % g.nx), j = (int)((p / g.nx) % g.ny), k = (int)(p / ((long long)g.nx * g.ny));
+    const int x0 = max(i - 1, 0), x1 = min(i + 4, g.nx + 2);
+    const int y0 = max(j - 1, 0), y1 = min(j + 4, g.ny + 2);
+    const int z0 = max(k - 1, 0), z1 = min(k + 4, g.nz + 2);
+    if (occ8) occ_mark(occ8, 3, occ_bricks(g.nx, 3), occ_bricks(g.ny, 3), x0, x1, y0, y1, z0, z1);
+    if (occ16) occ_mark(occ16, 4, occ_bricks(g.nx, 4), occ_bricks(g.ny, 4), x0, x1, y0, y1, z0, z1);
+  }
+}
+
 // ---------------------------------------------------------------- K2
 
 // Corners of a sample's cell: the xy face at z in one 16-byte cell record,
@@ -222,10 +308,14 @@ __global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ m
 // for an even slice, the next pair's slot for an odd one).
 template <int YF>
 __device__ __forceinline__ float drr_ray(const InstTable& T, const Geo& g, int iu, int iv,
-                                         const float4* __restrict__ volq) {
+                                         const float4* __restrict__ volq, const Occ& occ) {
   float acc = 0.f;
   Ray r;
   if (!ray_setup(T, g, iu, iv, r)) return acc;
+  // the records' 1-voxel border: cell coordinates of the 2-voxel-bordered grid are one more
+  if (occ.map && !occ_clip(occ, r.ax + 1.f, r.ay + 1.f, r.az + 1.f, r.dx, r.dy, r.dz, g.nx + 2, g.ny + 2, g.nz + 2,
+                           r.k0, r.k1))
+    return acc;
   const int szp = 2 * g.px * g.py;
   for (int k = r.k0; k <= r.k1; ++k) {
     const float kf = (float)k;
@@ -240,27 +330,40 @@ __device__ __forceinline__ float drr_ray(const InstTable& T, const Geo& g, int i
 
 __global__ void __launch_bounds__(kMarchThreads) k_forward(const InstTable* __restrict__ inst, int n_tiles,
                                                            int tiles_u, Geo g, const float4* __restrict__ volq,
-                                                           const float4* __restrict__ volqy, float* __restrict__ proj) {
+                                                           const float4* __restrict__ volqy, float* __restrict__ proj,
+                                                           Occ occ) {
   int n, tile;
   band_major_tile(n_tiles, tiles_u, n, tile);
   int iu, iv;
   if (!tile_pixel(tile, tiles_u, g, iu, iv)) return;
   const InstTable& T = inst[n];
   float acc = 0.f;
-  if (T.valid) acc = (volqy && T.yfast) ? drr_ray<1>(T, g, iu, iv, volqy) : drr_ray<0>(T, g, iu, iv, volq);
+  if (T.valid)
+    acc = (volqy && T.yfast) ? drr_ray<1>(T, g, iu, iv, volqy, occ) : drr_ray<0>(T, g, iu, iv, volq, occ);
   proj[((size_t)n * g.nv + iv) * g.nu + iu] = g.step * acc;
 }
 
 // ---------------------------------------------------------------- count
 
+// Samples per instance: grad_box 0, those in the open box (-1, n) of mu~
+// (the sum of Eq. forward); grad_box 1, those the fused march gathers: the
+// gradient grid's box (-2, n+1), clipped to the occupied bricks when occ.map
+// is set.
 __global__ void k_count(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g,
-                        unsigned long long* __restrict__ count) {
+                        unsigned long long* __restrict__ count, Occ occ, int grad_box) {
   const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
   int iu, iv;
   unsigned long long c = 0;
   Ray r;
-  if (tile_pixel(tile, tiles_u, g, iu, iv) && inst[n].valid && ray_setup(inst[n], g, iu, iv, r))
-    c = (unsigned long long)(r.k1 - r.k0 + 1);
+  if (tile_pixel(tile, tiles_u, g, iu, iv) && inst[n].valid) {
+    if (!grad_box) {
+      if (ray_setup(inst[n], g, iu, iv, r)) c = (unsigned long long)(r.k1 - r.k0 + 1);
+    } else if (ray_setup_m<2>(inst[n], g, iu, iv, r) &&
+               (!occ.map ||
+                occ_clip(occ, r.ax, r.ay, r.az, r.dx, r.dy, r.dz, g.nx + 2, g.ny + 2, g.nz + 2, r.k0, r.k1))) {
+      c = (unsigned long long)(r.k1 - r.k0 + 1);
+    }
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(count + n, c);
@@ -283,7 +386,7 @@ template <int LOSS, int WU = 4, int YF = 0>
 __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, int n, int tile, int n_tiles,
                                            int tiles_u, const Geo& g, const float4* __restrict__ vol,
                                            const float* __restrict__ ref, float* __restrict__ proj,
-                                           float* __restrict__ part, float (*red)[kRec]) {
+                                           float* __restrict__ part, float (*red)[kRec], const Occ& occ) {
   int iu, iv;
   const bool on_det = tile_pixel<WU>(tile, tiles_u, g, iu, iv);
   const InstTable& T = inst[n];
@@ -291,7 +394,8 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
   float s0[3] = {0.f, 0.f, 0.f};
   float s1[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   Ray r;
-  if (on_det && T.valid && ray_setup_m<2>(T, g, iu, iv, r)) {
+  if (on_det && T.valid && ray_setup_m<2>(T, g, iu, iv, r) &&
+      (!occ.map || occ_clip(occ, r.ax, r.ay, r.az, r.dx, r.dy, r.dz, g.nx + 2, g.ny + 2, g.nz + 2, r.k0, r.k1))) {
     // element strides of +1 voxel along x, y, z in the marched copy
     const int sx = YF ? 2 * g.rqy : 2, sy = YF ? 2 : 2 * g.qx, szp = YF ? 2 * g.rqx * g.rqy : 2 * g.qx * g.qy;
     const float ox = g.cx + 2.0f, oy = g.cy + 2.0f, oz = g.cz + 2.0f;
@@ -413,7 +517,7 @@ template <int LOSS, int WU>
 __global__ void __launch_bounds__(kMarchThreads, 4)
     k_forward_grad(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g,
                    const float4* __restrict__ vol, const float4* __restrict__ voly, const float* __restrict__ ref,
-                   float* __restrict__ proj, float* __restrict__ part, PoseList L) {
+                   float* __restrict__ proj, float* __restrict__ part, PoseList L, Occ occ) {
   __shared__ float red[kMarchThreads / 32][kRec];
   int n, tile;
   if (L.list) {
@@ -422,9 +526,9 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
     band_major_tile(n_tiles, tiles_u, n, tile);
   }
   if (voly && inst[n].yfast)  // uniform per block
-    march_tile<LOSS, WU, 1>(inst, n, tile, n_tiles, tiles_u, g, voly, ref, proj, part, red);
+    march_tile<LOSS, WU, 1>(inst, n, tile, n_tiles, tiles_u, g, voly, ref, proj, part, red, occ);
   else
-    march_tile<LOSS, WU, 0>(inst, n, tile, n_tiles, tiles_u, g, vol, ref, proj, part, red);
+    march_tile<LOSS, WU, 0>(inst, n, tile, n_tiles, tiles_u, g, vol, ref, proj, part, red, occ);
 }
 
 // ---------------------------------------------------------------- gather probe
@@ -443,10 +547,13 @@ __device__ __forceinline__ float ld_probe(const float4* p) {
 }
 
 template <int YF>
-__device__ __forceinline__ float probe_ray(const InstTable& T, const Geo& g, int iu, int iv, const float4* vol) {
+__device__ __forceinline__ float probe_ray(const InstTable& T, const Geo& g, int iu, int iv, const float4* vol,
+                                           const Occ& occ) {
   Ray r;
   float acc = 0.f;
   if (!(T.valid && ray_setup_m<2>(T, g, iu, iv, r))) return acc;
+  if (occ.map && !occ_clip(occ, r.ax, r.ay, r.az, r.dx, r.dy, r.dz, g.nx + 2, g.ny + 2, g.nz + 2, r.k0, r.k1))
+    return acc;
   const int sx = YF ? 2 * g.rqy : 2, sy = YF ? 2 : 2 * g.qx, szp = YF ? 2 * g.rqx * g.rqy : 2 * g.qx * g.qy;
   for (int k = r.k0; k <= r.k1; ++k) {
     const float kf = (float)k;
@@ -461,13 +568,15 @@ __device__ __forceinline__ float probe_ray(const InstTable& T, const Geo& g, int
 
 __global__ void __launch_bounds__(kMarchThreads, 4)
     k_gather_probe(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g, const float4* __restrict__ vol,
-                   const float4* __restrict__ voly, float* __restrict__ sink) {
+                   const float4* __restrict__ voly, float* __restrict__ sink, Occ occ) {
   int n, tile;
   band_major_tile(n_tiles, tiles_u, n, tile);  // the fused march's block order
   int iu, iv;
   const bool on = tile_pixel<4>(tile, tiles_u, g, iu, iv);
   float acc = 0.f;
-  if (on) acc = (voly && inst[n].yfast) ? probe_ray<1>(inst[n], g, iu, iv, voly) : probe_ray<0>(inst[n], g, iu, iv, vol);
+  if (on)
+    acc = (voly && inst[n].yfast) ? probe_ray<1>(inst[n], g, iu, iv, voly, occ)
+                                  : probe_ray<0>(inst[n], g, iu, iv, vol, occ);
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0 && acc == 1.2345e-30f) sink[0] = acc;  // keeps the loads live; never taken in practice
 }
@@ -503,35 +612,35 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
     const bool yf = B.vol4y && B.inst[n].yfast;
     if constexpr (LOSS >= 0) {
       if (yf)
-        march_tile<LOSS, 4, 1>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4y, B.ref, nullptr, B.part, red);
+        march_tile<LOSS, 4, 1>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4y, B.ref, nullptr, B.part, red, B.occ);
       else
-        march_tile<LOSS, 4, 0>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr, B.part, red);
+        march_tile<LOSS, 4, 0>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr, B.part, red, B.occ);
       continue;
     }
     switch (B.loss * 2 + (yf ? 1 : 0)) {
       case PROJ_LOSS_RESIDUAL * 2:
         march_tile<PROJ_LOSS_RESIDUAL, 4, 0>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr,
-                                             B.part, red);
+                                             B.part, red, B.occ);
         break;
       case PROJ_LOSS_RESIDUAL * 2 + 1:
         march_tile<PROJ_LOSS_RESIDUAL, 4, 1>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4y, B.ref, nullptr,
-                                             B.part, red);
+                                             B.part, red, B.occ);
         break;
       case PROJ_LOSS_L2 * 2:
         march_tile<PROJ_LOSS_L2, 4, 0>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr, B.part,
-                                       red);
+                                       red, B.occ);
         break;
       case PROJ_LOSS_L2 * 2 + 1:
         march_tile<PROJ_LOSS_L2, 4, 1>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4y, B.ref, nullptr, B.part,
-                                       red);
+                                       red, B.occ);
         break;
       case PROJ_LOSS_NCC * 2 + 1:
         march_tile<PROJ_LOSS_NCC, 4, 1>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4y, B.ref, nullptr,
-                                        B.part, red);
+                                        B.part, red, B.occ);
         break;
       default:
         march_tile<PROJ_LOSS_NCC, 4, 0>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr,
-                                        B.part, red);
+                                        B.part, red, B.occ);
         break;
     }
   }
@@ -730,6 +839,20 @@ int elementwise_grid(long long n) {
 
 }  // namespace
 
+cudaError_t launch_occupancy(const float* d_mu, Geo geo, unsigned char* d_occ8, unsigned char* d_occ16,
+                             cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (d_occ8)
+    e = cudaMemsetAsync(d_occ8, 0,
+                        (size_t)occ_bricks(geo.nx, 3) * occ_bricks(geo.ny, 3) * occ_bricks(geo.nz, 3), s);
+  if (e == cudaSuccess && d_occ16)
+    e = cudaMemsetAsync(d_occ16, 0,
+                        (size_t)occ_bricks(geo.nx, 4) * occ_bricks(geo.ny, 4) * occ_bricks(geo.nz, 4), s);
+  if (e != cudaSuccess) return e;
+  k_occupancy<<<elementwise_grid((long long)geo.nx * geo.ny * geo.nz), 256, 0, s>>>(d_mu, geo, d_occ8, d_occ16);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float4* d_vol4, cudaStream_t s) {
   // the pitched extents (qx, qy, qz) exceed the 1-padded ones (n + 2) in every axis
   dim3 grid(ceil_div(geo.qx, 32), ceil_div(geo.qy, 8), ceil_div(geo.qz, kPrepZChunk));
@@ -738,18 +861,19 @@ cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float
 }
 
 cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_volq, const float4* d_volqy,
-                           float* d_proj, cudaStream_t s) {
+                           float* d_proj, cudaStream_t s, Occ occ) {
   const int nt = tiles_of(geo);
-  k_forward<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo, d_volq, d_volqy, d_proj);
+  k_forward<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo, d_volq, d_volqy, d_proj, occ);
   return cudaGetLastError();
 }
 
-cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long* d_count, cudaStream_t s) {
+cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long* d_count, cudaStream_t s, Occ occ,
+                         int grad_box) {
   cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(long long) * n_inst, s);
   if (e != cudaSuccess) return e;
   const int nt = tiles_of(geo);
   k_count<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo,
-                                                reinterpret_cast<unsigned long long*>(d_count));
+                                                reinterpret_cast<unsigned long long*>(d_count), occ, grad_box);
   return cudaGetLastError();
 }
 
@@ -757,19 +881,19 @@ namespace {
 template <int WU>
 void launch_forward_grad_w(const InstTable* d_inst, int grid, int nt, int tu, const Geo& geo, const float4* d_vol4,
                            const float4* d_vol4y, int loss, const float* d_ref, float* d_proj, float* d_part,
-                           const PoseList& L, cudaStream_t s) {
+                           const PoseList& L, const Occ& occ, cudaStream_t s) {
   switch (loss) {
     case PROJ_LOSS_RESIDUAL:
       k_forward_grad<PROJ_LOSS_RESIDUAL, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_vol4y,
-                                                                            d_ref, d_proj, d_part, L);
+                                                                            d_ref, d_proj, d_part, L, occ);
       break;
     case PROJ_LOSS_L2:
       k_forward_grad<PROJ_LOSS_L2, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_vol4y, d_ref,
-                                                                      d_proj, d_part, L);
+                                                                      d_proj, d_part, L, occ);
       break;
     default:
       k_forward_grad<PROJ_LOSS_NCC, WU><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_vol4, d_vol4y, d_ref,
-                                                                       d_proj, d_part, L);
+                                                                       d_proj, d_part, L, occ);
       break;
   }
 }
@@ -777,7 +901,7 @@ void launch_forward_grad_w(const InstTable* d_inst, int grid, int nt, int tu, co
 
 cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
                                 const float4* d_vol4y, int loss, const float* d_ref, float* d_proj, float* d_part,
-                                cudaStream_t s, int warp_width, const PoseList* pl) {
+                                cudaStream_t s, int warp_width, const PoseList* pl, Occ occ) {
   const int nt = tiles_of(geo), tu = tiles_u_of(geo);
   PoseList L{};
   if (pl && pl->list) L = *pl;
@@ -786,20 +910,21 @@ cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, co
   if (grid_ll > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   const int grid = (int)grid_ll;
   switch (warp_width) {
-    case 2: launch_forward_grad_w<2>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, L, s); break;
-    case 8: launch_forward_grad_w<8>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, L, s); break;
+    case 2: launch_forward_grad_w<2>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, L, occ, s); break;
+    case 8: launch_forward_grad_w<8>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, L, occ, s); break;
     case 16:
-      launch_forward_grad_w<16>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, L, s);
+      launch_forward_grad_w<16>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, L, occ, s);
       break;
-    default: launch_forward_grad_w<4>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, L, s); break;
+    default: launch_forward_grad_w<4>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, L, occ, s); break;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_probe(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
-                                const float4* d_vol4y, float* d_sink, cudaStream_t s) {
+                                const float4* d_vol4y, float* d_sink, cudaStream_t s, Occ occ) {
   const int nt = tiles_of(geo);
-  k_gather_probe<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo, d_vol4, d_vol4y, d_sink);
+  k_gather_probe<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo, d_vol4, d_vol4y, d_sink,
+                                                       occ);
   return cudaGetLastError();
 }
 

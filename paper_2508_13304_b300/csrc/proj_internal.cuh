@@ -70,6 +70,21 @@ struct FdkView {
   float pad[3];
 };
 
+// Occupancy bricks for empty-space skipping in the marches.  Cells are
+// those of the 2-voxel-bordered (mu, grad mu) grid (lower corner 0 .. n + 2
+// per axis); a brick is 2^shift cells on a side.  Byte b of map is non-zero
+// when brick b holds, or lies within one cell of, a cell with a non-zero
+// corner in (mu, grad mu), i.e. a cell within 2..4 cells of a non-zero
+// voxel.  A sample whose cell has only zero corners adds exact zeros to every
+// sum of the marches, so a ray's samples before the first and after the last
+// occupied brick it crosses can be left out without changing any result.
+struct Occ {
+  const unsigned char* map;  // nullptr: no skipping
+  int shift;                 // 3 (8-cell bricks) or 4 (16-cell bricks)
+  int nb[3];                 // bricks per axis
+};
+__host__ __device__ constexpr int occ_bricks(int n, int shift) { return (n + 3 + (1 << shift) - 1) >> shift; }
+
 // One problem of a persistent multi-problem fused march (proj_batch_*).
 struct BatchProblem {
   Geo geo;
@@ -78,6 +93,7 @@ struct BatchProblem {
   const float4* vol4y;  // y-fast copy, or null
   const float* ref;
   float* part;
+  Occ occ;
   int n_tiles, tiles_u, loss, n_inst;
   long long item_begin;  // first global work item of this problem
 };
@@ -129,20 +145,26 @@ cudaError_t launch_setup(const float* d_pose, int n_pose, const double* d_views,
                          const int* d_inst_pose, int n_inst, Geo geo, InstTable* d_inst, PoseTable* d_ptab,
                          int* d_status, cudaStream_t s);
 cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float4* d_vol4, cudaStream_t s);
+// occupancy bricks of both edges (8 and 16 cells) for the volume d_mu; either map may be null
+cudaError_t launch_occupancy(const float* d_mu, Geo geo, unsigned char* d_occ8, unsigned char* d_occ16,
+                             cudaStream_t s);
 // d_volqy: the copy of the cell records with rows along y (instances with yfast
 // set march it), or null (all march d_volq)
 cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_volq, const float4* d_volqy,
-                           float* d_proj, cudaStream_t s);
-cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long* d_count, cudaStream_t s);
+                           float* d_proj, cudaStream_t s, Occ occ = Occ{});
+// grad_box 0: samples in the box (-1, n) of mu~ (the projector's sum); 1: samples the fused march gathers,
+// those in the gradient grid's box (-2, n+1), clipped to the occupied bricks of occ when occ.map is set
+cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long* d_count, cudaStream_t s,
+                         Occ occ = Occ{}, int grad_box = 0);
 // warp_width: rays per warp row of the 16x16 tile (2, 4, 8 or 16; other values use 4)
 // d_vol4y: the y-fast copy (instances with yfast set march it), or null (all march d_vol4)
 // pl: optional pose subset (nullptr or pl->list == nullptr: all n_inst instances)
 cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
                                 const float4* d_vol4y, int loss, const float* d_ref, float* d_proj, float* d_part,
-                                cudaStream_t s, int warp_width = 4, const PoseList* pl = nullptr);
+                                cudaStream_t s, int warp_width = 4, const PoseList* pl = nullptr, Occ occ = Occ{});
 // the fused march's gathers without its arithmetic (empirical gather ceiling)
 cudaError_t launch_gather_probe(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
-                                const float4* d_vol4y, float* d_sink, cudaStream_t s);
+                                const float4* d_vol4y, float* d_sink, cudaStream_t s, Occ occ = Occ{});
 // y-fast copy of the pitched (mu, grad mu) volume (tiled transpose of every z slice)
 cudaError_t launch_volume_yfast(const float4* d_vol4, Geo geo, float4* d_vol4y, cudaStream_t s);
 cudaError_t launch_records_yfast(const float4* d_volq, Geo geo, float4* d_volqy, cudaStream_t s);
