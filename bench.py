@@ -43,9 +43,10 @@ L2_FLUSH_BYTES = 256 << 20
 # one-pass metrics.  NCU_SOURCE_SHA16 is the hash (kernel_source_sha16) of
 # the march's sources they were taken on; when the built sources hash
 # differently the line reports them as null.
-NCU_SOURCE_SHA16 = "953708542ed0e44e"
-NCU_L1_WAVEFRONT_PCT = 88.8
-TRAFFIC_PER_LAUNCH = 21.572e9  # 21.552 GB read + 19.7 MB written
+NCU_SOURCE_SHA16 = "04b5fc1141a6ce61"
+NCU_L1_WAVEFRONT_PCT = 53.9
+NCU_ISSUE_ACTIVE_PCT = 65.4
+TRAFFIC_PER_LAUNCH = 78.51e6  # 69.95 MB read + 8.56 MB written
 MARCH_SOURCES = ("paper_2508_13304_b300/csrc/proj_forward.cu", "paper_2508_13304_b300/csrc/proj_internal.cuh")
 
 
@@ -359,9 +360,15 @@ def secondary(pb, torch, dev, w, mu_d, flush):
     Pa.set_volume(mu_d)
     tg = torch.from_numpy(np.ascontiguousarray(tgt, dtype=np.float32)).to(dev)
     width, times = pb.proj_autotune_forward_grad(Pa.plan, pose, pb.PROJ_LOSS_NCC, tg, Pa.ws, reps=2)
-    out["warp_shape_autotune"] = {"config": "256^3, 128 view instances of 384^2, NCC",
+    out["warp_shape_autotune"] = {"config": "256^3, 128 view instances of 384^2, NCC, default skipping",
                                   "ms_per_launch": {"%dx%d" % (k, 32 // k): v for k, v in times.items()},
                                   "chosen": "%dx%d" % (width, 32 // width)}
+    # the same launch over (skip brick edge, cell test, warp shape)
+    width, edge, cells, times = pb.proj_autotune_march(Pa.plan, pose, pb.PROJ_LOSS_NCC, tg, Pa.ws, reps=2)
+    out["march_autotune"] = {"config": "256^3, 128 view instances of 384^2, NCC",
+                             "ms_per_launch": {"edge %d, cells %d, %dx%d" % (e, c, k, 32 // k): v
+                                               for (e, c, k), v in times.items()},
+                             "chosen": "edge %d, cells %d, %dx%d" % (edge, cells, width, 32 // width)}
     del Pa
     out["c1_small"] = c1_small(pb, torch, dev, flush)
     out["moco_quality"] = moco_quality(pb, torch, dev)
@@ -1051,6 +1058,10 @@ def main():
     pb.proj_set_volume(P.plan, mu_d, P.ws)
     marched = int(P.count_marched_samples(pose_d).sum().item())   # gathered after empty-space skipping
     skip_edge = pb.proj_get_skip_brick(P.plan)
+    skip_cells = pb.proj_get_skip_cells(P.plan)
+    pb.proj_set_skip_cells(P.plan, pb.SKIP_CELLS_OFF)
+    brick_range = int(P.count_marched_samples(pose_d).sum().item())  # samples inside the occupied bricks' range
+    pb.proj_set_skip_cells(P.plan, skip_cells)
     pb.proj_enable_kernel_timing(P.plan)
 
     def step():
@@ -1090,6 +1101,7 @@ def main():
     probe_ms = float(np.median(probe_ms))
     # the same march with empty-space skipping off (every sample of the box gathered): results are identical
     pb.proj_set_skip_brick(P.plan, 0)
+    pb.proj_set_skip_cells(P.plan, pb.SKIP_CELLS_OFF)
     dense_ms, dense_probe_ms = [], []
     for _ in range(3):
         flush.zero_()
@@ -1100,6 +1112,7 @@ def main():
         dense_probe_ms.append(pb.proj_kernel_time_ms(P.plan))
     dense_marched = int(P.count_marched_samples(pose_d).sum().item())
     pb.proj_set_skip_brick(P.plan, skip_edge)
+    pb.proj_set_skip_cells(P.plan, skip_cells)
     pb.proj_forward_pose_grad(P.plan, pose_d, pb.PROJ_LOSS_NCC, target_d, grad_d, loss_d, None, P.ws)
     dense_ms, dense_probe_ms = float(np.median(dense_ms)), float(np.median(dense_probe_ms))
     if dist:
@@ -1230,12 +1243,14 @@ def main():
         "marched_samples_per_step": marched,
         "kernel_ms": k_ms,
         "empty_space_skipping": {
-            "brick_edge": skip_edge, "marched_samples": marched, "box_samples": samples,
+            "brick_edge": skip_edge, "cell_test": skip_cells, "marched_samples": marched,
+            "brick_range_samples": brick_range, "box_samples": samples,
             "gradient_box_samples": dense_marched, "kernel_ms_without_skipping": dense_ms,
             "value_without_skipping_kernel_only": world * args.n_cand / (dense_ms * 1e-3),
             "l1_frac_without_skipping": l1_dense / l1_peak,
             "probe_ms_without_skipping": dense_probe_ms,
-            "what": "each ray marches only its samples around the occupied 8^3-cell bricks it crosses (the left-out "
+            "what": "each ray marches only its samples around the occupied 8^3-cell bricks it crosses, and "
+                    "within them gathers only the samples whose cell has a non-zero corner (the left-out "
                     "samples read eight zero corners); results are bit-identical with skipping off.  "
                     "ray_samples_per_s counts the samples gathered, effective_ray_samples_per_s all samples of "
                     "the box (the sum of Eq. forward)"},
@@ -1248,12 +1263,15 @@ def main():
                              "%d B/clk x %.0f MHz" % (L1_BYTES_PER_SAMPLE, n_sm, L1_BYTES_PER_CLK_SM, sm_max),
                      "alu": {"achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
                              "frac": alu_achieved / alu_peak, "flop_per_sample": FLOP_PER_SAMPLE},
-                     # the unit that binds, from the committed ncu capture of the same kernel (a small case of
-                     # this launch; not measured live)
+                     # the units that bind, from the committed ncu capture of the same kernel (a small case of
+                     # this launch; not measured live): instruction issue, then the L1 data pipe
                      "ncu_l1_wavefront_utilisation": {
                          "pct_of_peak": NCU_L1_WAVEFRONT_PCT if ncu_current else None,
                          "source": "ncu l1tex__data_pipe_lsu_wavefronts of the same kernel, 8-instance case "
                                    "(summary under profiles/)"},
+                     "ncu_issue_active": {
+                         "pct_of_peak": NCU_ISSUE_ACTIVE_PCT if ncu_current else None,
+                         "source": "ncu smsp__issue_active of the same kernel, 8-instance case"},
                      "empirical_gather_ceiling": {
                          "kernel_ms": probe_ms, "ray_samples_per_s": marched / (probe_ms * 1e-3),
                          "frac": probe_ms / k_ms,

@@ -289,34 +289,48 @@ int proj_autotune_forward_grad(proj_plan plan, const float *d_pose, int loss, co
  * (a library facility; the paper has none).  proj_set_volume also records,
  * for bricks of 8^3 and of 16^3 cells of the 2-voxel-bordered grid, whether
  * a brick holds, or lies within one cell of, a cell with a non-zero corner in
- * (mu, grad mu).  Before marching, each ray walks the bricks it crosses and
+ * (mu, grad mu), and, one bit per cell, whether the cell itself has one (the
+ * cell map).  Before marching, each ray walks the bricks it crosses and
  * keeps only its samples from two before the first to two after the last
- * occupied brick.  A sample left out reads eight zero corners and adds exact
- * zeros to every sum, and the kept samples are summed in the same order, so
- * results are bit-identical with and without skipping; only the time
- * changes (most for volumes with much empty space around the object).  The
- * exact transposes never skip (they do not read mu).
+ * occupied brick; inside that range the fused pose-gradient march (not the
+ * DRR march) tests each sample's cell in the cell map and leaves out the
+ * gathers and arithmetic of samples whose cell has none.  A sample left out
+ * reads eight zero corners and adds exact zeros to every sum, and the kept
+ * samples are summed in the same order, so results are bit-identical with
+ * and without skipping; only the time changes (most for volumes with much
+ * empty space around and inside the object; on dense volumes the tests cost
+ * a little).  The exact transposes never skip (they do not read mu).
  * proj_set_skip_brick: edge 8 (default), 16, or 0 (off); PROJ_E_ARG
- * otherwise.  proj_autotune_march: like proj_autotune_forward_grad over the
- * 3 x 4 combinations of brick edge (0, 8, 16) and warp shape (2, 4, 8, 16);
- * keeps the fastest pair in the plan and returns it in *warp_width and
- * *brick_edge (may be NULL) with the times in times_ms[12] (index 4 * edge
- * position + shape position; may be NULL).  proj_count_marched_samples: like
+ * otherwise.  proj_set_skip_cells: the cell test of the fused march, which
+ * works with or without bricks: 0 off, 1 on, 2 automatic (default): on when,
+ * for the volume of the last proj_set_volume, at most 85 % of the cells in
+ * the occupied 8^3 bricks have a non-zero corner (decided on the device, no
+ * synchronisation; on a uniformly filled volume the tests cost about 12 %);
+ * PROJ_E_ARG otherwise.
+ * proj_autotune_march: like proj_autotune_forward_grad over the 3 x 2 x 4
+ * combinations of brick edge (0, 8, 16), cell test (0 off, 1 on) and warp
+ * shape (2, 4, 8, 16); keeps the fastest in the plan and returns it in
+ * *warp_width, *brick_edge and *skip_cells (each may be NULL) with the times
+ * in times_ms[24] (index 4 * (2 * edge position + cell test) + shape
+ * position; may be NULL).  proj_count_marched_samples: like
  * proj_count_samples, but counts the samples the fused march gathers with
  * the plan's setting (the gradient grid's box (-2, n+1), clipped to the
- * occupied bricks); needs PROJ_OP_FORWARD_GRAD. */
+ * occupied bricks, and of those the ones in cells with a non-zero corner when
+ * the cell test is on); needs PROJ_OP_FORWARD_GRAD. */
 int proj_set_skip_brick(proj_plan plan, int edge);
 int proj_get_skip_brick(proj_plan plan, int *edge);
+int proj_set_skip_cells(proj_plan plan, int mode);
+int proj_get_skip_cells(proj_plan plan, int *mode);
 int proj_autotune_march(proj_plan plan, const float *d_pose, int loss, const float *d_ref, void *d_ws,
                         size_t ws_bytes, proj_stream stream, int reps, float *times_ms, int *warp_width,
-                        int *brick_edge);
+                        int *brick_edge, int *skip_cells);
 int proj_count_marched_samples(proj_plan plan, const float *d_pose, long long *d_count, void *d_ws, size_t ws_bytes,
                                proj_stream stream);
 
 /* Brick shape of the back-projection gradient (a library facility; the
  * paper fixes none): a block owns 32 x 8 voxel columns of gz voxels and a
- * chunk of instances.  Shapes: 0 = gz 16, 8 instances (default);
- * 1 = gz 8, 8; 2 = gz 16, 16; 3 = gz 8, 16.  Results of different shapes
+ * chunk of instances.  Shapes: 0 = gz 16, 8 instances; 1 = gz 8, 8;
+ * 2 = gz 16, 16; 3 = gz 8, 16 (default).  Results of different shapes
  * differ only in the order of the FP32 partial sums.
  * Errors: PROJ_E_ARG (NULL plan or pointer, shape out of range). */
 int proj_set_brick_shape(proj_plan plan, int shape);

@@ -78,8 +78,10 @@ _SIGS = {
                                    ctypes.POINTER(_I)],
     "proj_set_skip_brick": [_P, _I],
     "proj_get_skip_brick": [_P, ctypes.POINTER(_I)],
+    "proj_set_skip_cells": [_P, _I],
+    "proj_get_skip_cells": [_P, ctypes.POINTER(_I)],
     "proj_autotune_march": [_P, _P, _I, _P, _P, _SZ, _P, _I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I),
-                            ctypes.POINTER(_I)],
+                            ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "proj_count_marched_samples": [_P, _P, _P, _P, _SZ, _P],
     "proj_set_brick_shape": [_P, _I],
     "proj_get_brick_shape": [_P, ctypes.POINTER(_I)],
@@ -423,19 +425,36 @@ def proj_get_skip_brick(plan: Plan) -> int:
     return int(e.value)
 
 
+SKIP_CELLS_OFF, SKIP_CELLS_ON, SKIP_CELLS_AUTO = 0, 1, 2
+
+
+def proj_set_skip_cells(plan: Plan, mode: int):
+    """Per-sample cell test of the fused march (empty-space skipping inside the
+    brick range): SKIP_CELLS_OFF, SKIP_CELLS_ON or SKIP_CELLS_AUTO (default)."""
+    _check(lib().proj_set_skip_cells(plan.handle, int(mode)))
+
+
+def proj_get_skip_cells(plan: Plan) -> int:
+    v = ctypes.c_int()
+    _check(lib().proj_get_skip_cells(plan.handle, ctypes.byref(v)))
+    return int(v.value)
+
+
 def proj_autotune_march(plan: Plan, pose, loss, ref, ws, reps=3, stream=None):
-    """Time the fused march per (skip brick edge, warp shape) on this data, keep
-    the fastest in the plan; returns (warp_width, brick_edge, {(edge, width): ms})."""
+    """Time the fused march per (skip brick edge, cell test, warp shape) on this
+    data, keep the fastest in the plan; returns (warp_width, brick_edge,
+    skip_cells, {(edge, cells, width): ms})."""
     import torch
     p, nb = _ws(ws)
     n_ref = (plan.n_inst if loss == PROJ_LOSS_RESIDUAL else plan.geom.n_views) * plan.img_numel
-    times = (ctypes.c_float * 12)()
-    w, e = ctypes.c_int(), ctypes.c_int()
+    times = (ctypes.c_float * 24)()
+    w, e, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().proj_autotune_march(plan.handle, _ptr(pose, torch.float32, 6 * plan.n_pose, "pose"), int(loss),
                                      _ptr(ref, torch.float32, n_ref, "ref"), p, nb, _stream(stream), int(reps), times,
-                                     ctypes.byref(w), ctypes.byref(e)))
-    tt = {(SKIP_BRICK_EDGES[j], WARP_WIDTHS[i]): float(times[4 * j + i]) for j in range(3) for i in range(4)}
-    return int(w.value), int(e.value), tt
+                                     ctypes.byref(w), ctypes.byref(e), ctypes.byref(c)))
+    tt = {(SKIP_BRICK_EDGES[j], cl, WARP_WIDTHS[i]): float(times[4 * (2 * j + cl) + i])
+          for j in range(3) for cl in (0, 1) for i in range(4)}
+    return int(w.value), int(e.value), int(c.value), tt
 
 
 def proj_count_marched_samples(plan: Plan, pose, count, ws, stream=None):

@@ -47,7 +47,7 @@ struct proj_plan_s {
   int n_tiles;        // ray tiles per instance
   int ipp = 1;        // most instances of any one pose (grid slots per pose of a pose list)
   int bp_blocks;      // most voxel bricks of the back-projection gradient over the brick shapes (records per instance)
-  int bp_shape = 0;   // brick shape of the back-projection gradient (0..kBrickShapes-1)
+  int bp_shape = 3;   // brick shape of the back-projection gradient (0..kBrickShapes-1)
   std::vector<double> views;
   std::vector<int> inst_view, inst_pose;
   // device tables owned by the plan
@@ -61,6 +61,9 @@ struct proj_plan_s {
   int warp_width = 4;
   // empty-space skipping in the forward marches: log2 of the occupancy brick edge (3: 8 cells, 4: 16), 0 = off
   int skip_shift = 3;
+  // and the per-sample test of the cell map in the fused march: 0 off, 1 on, 2 automatic (default; decided
+  // on the device by proj_set_volume from the volume's cells, see k_cell_decide)
+  int skip_cells = 2;
   // optional timing of the main kernel of each call
   bool timing = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -68,7 +71,7 @@ struct proj_plan_s {
   size_t off_status = 0, off_inst = 0, off_ptab = 0, off_volq = 0, off_volqy = 0, off_vol4 = 0, off_vol4y = 0, off_part_f = 0,
          off_det4 = 0,
          off_part_b = 0, off_detq = 0, off_acc = 0, off_sharp_m = 0, off_sharp_part = 0, off_occ8 = 0, off_occ16 = 0,
-         ws_bytes = 0;
+         off_nbits = 0, off_cells = 0, off_cstat = 0, ws_bytes = 0;
 };
 
 namespace {
@@ -90,6 +93,9 @@ struct WsView {
   float4* detq = nullptr;
   unsigned char* occ8 = nullptr;
   unsigned char* occ16 = nullptr;
+  unsigned* nbits = nullptr;
+  unsigned* cells = nullptr;
+  void* cstat = nullptr;
 };
 
 int check_ws(const proj_plan_s* p, void* d_ws, size_t ws_bytes, WsView* w) {
@@ -112,12 +118,22 @@ int check_ws(const proj_plan_s* p, void* d_ws, size_t ws_bytes, WsView* w) {
   w->detq = p->off_detq ? reinterpret_cast<float4*>(b + p->off_detq) : nullptr;
   w->occ8 = p->off_occ8 ? reinterpret_cast<unsigned char*>(b + p->off_occ8) : nullptr;
   w->occ16 = p->off_occ16 ? reinterpret_cast<unsigned char*>(b + p->off_occ16) : nullptr;
+  w->nbits = p->off_nbits ? reinterpret_cast<unsigned*>(b + p->off_nbits) : nullptr;
+  w->cells = p->off_cells ? reinterpret_cast<unsigned*>(b + p->off_cells) : nullptr;
+  w->cstat = p->off_cstat ? static_cast<void*>(b + p->off_cstat) : nullptr;
   return PROJ_OK;
 }
 
-// The occupancy bricks the forward marches skip with, per the plan's setting (or none).
-Occ occ_of(const proj_plan_s* p, const WsView& w, int shift) {
+// The occupancy bricks (edge 2^shift; shift 0: none) and the cell map the forward marches skip with; cells:
+// 0 no cell test, 1 always, 2 as decided for the volume by proj_set_volume.
+Occ occ_of(const proj_plan_s* p, const WsView& w, int shift, int cells) {
   Occ o{};
+  if (cells && w.cells) {
+    o.cells = w.cells;
+    o.cw = cell_words(p->geo.nx);
+    o.ch = p->geo.ny + 3;
+    o.cells_flag = cells == 2 ? cell_flag_of(w.cstat) : nullptr;
+  }
   unsigned char* m = shift == 3 ? w.occ8 : (shift == 4 ? w.occ16 : nullptr);
   if (!m) return o;
   o.map = m;
@@ -127,6 +143,9 @@ Occ occ_of(const proj_plan_s* p, const WsView& w, int shift) {
   o.nb[2] = occ_bricks(p->geo.nz, shift);
   return o;
 }
+
+// The plan's own setting.
+Occ occ_of(const proj_plan_s* p, const WsView& w) { return occ_of(p, w, p->skip_shift, p->skip_cells); }
 
 int need_op(const proj_plan_s* p, int op, const char* name) {
   if (!(p->ops & op)) return fail(PROJ_E_UNSUPPORTED, "%s: operation not enabled when the plan was created", name);
@@ -312,6 +331,9 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   if (ops & (PROJ_OP_FORWARD | PROJ_OP_FORWARD_GRAD)) {
     p->off_occ8 = take((size_t)occ_bricks(G.nx, 3) * occ_bricks(G.ny, 3) * occ_bricks(G.nz, 3));
     p->off_occ16 = take((size_t)occ_bricks(G.nx, 4) * occ_bricks(G.ny, 4) * occ_bricks(G.nz, 4));
+    p->off_nbits = take(sizeof(unsigned) * (size_t)nbits_words(p->geo.qx) * p->geo.qy * p->geo.qz);
+    p->off_cells = take(sizeof(unsigned) * (size_t)cell_words(G.nx) * (G.ny + 3) * (G.nz + 3));
+    p->off_cstat = take(kCellStatBytes);
   }
   if (ops & PROJ_OP_SHARPNESS) {
     p->off_sharp_m = take(sizeof(float) * (size_t)G.nx * G.ny * G.nz);
@@ -408,8 +430,10 @@ int proj_set_volume(proj_plan p, const float* d_mu, void* d_ws, size_t ws_bytes,
   int rc = check_ws(p, d_ws, ws_bytes, &w);
   if (rc) return rc;
   if ((rc = check_device(p))) return rc;
-  cudaError_t e = launch_volume_prep(d_mu, p->geo, w.volq, w.vol4, (cudaStream_t)stream);
+  cudaError_t e = launch_volume_prep(d_mu, p->geo, w.volq, w.vol4, (cudaStream_t)stream, w.nbits);
   if (e == cudaSuccess) e = launch_occupancy(d_mu, p->geo, w.occ8, w.occ16, (cudaStream_t)stream);
+  if (e == cudaSuccess && w.cells)
+    e = launch_cell_bits(w.nbits, p->geo, w.cells, w.occ8, w.cstat, (cudaStream_t)stream);
   if (e == cudaSuccess && w.vol4y) e = launch_volume_yfast(w.vol4, p->geo, w.vol4y, (cudaStream_t)stream);
   if (e == cudaSuccess && w.volqy) e = launch_records_yfast(w.volq, p->geo, w.volqy, (cudaStream_t)stream);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "volume preparation launch");
@@ -426,7 +450,7 @@ int proj_forward(proj_plan p, const float* d_pose, float* d_proj, void* d_ws, si
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = setup(p, d_pose, w, s))) return rc;
   mark(p, true, s);
-  cudaError_t e = launch_forward(w.inst, p->n_inst, p->geo, w.volq, w.volqy, d_proj, s, occ_of(p, w, p->skip_shift));
+  cudaError_t e = launch_forward(w.inst, p->n_inst, p->geo, w.volq, w.volqy, d_proj, s, occ_of(p, w));
   mark(p, false, s);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "forward launch");
 }
@@ -461,7 +485,7 @@ int proj_forward_pose_grad(proj_plan p, const float* d_pose, int loss, const flo
   mark(p, true, s);
   cudaError_t e =
       launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, d_proj, w.part_f, s, p->warp_width,
-                          nullptr, occ_of(p, w, p->skip_shift));
+                          nullptr, occ_of(p, w));
   mark(p, false, s);
   if (e != cudaSuccess) return cuda_fail(e, "forward pose-gradient launch");
   e = launch_forward_grad_reduce(w.inst, w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_tiles, p->geo, loss,
@@ -490,7 +514,7 @@ int proj_forward_pose_grad_list(proj_plan p, const float* d_pose, const int* d_p
   PoseList L{d_pose_list, n_list, p->ipp, p->n_pose, p->d_pose_ptr, p->d_pose_idx, w.status};
   mark(p, true, s);
   cudaError_t e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, d_proj, w.part_f, s,
-                                      p->warp_width, &L, occ_of(p, w, p->skip_shift));
+                                      p->warp_width, &L, occ_of(p, w));
   mark(p, false, s);
   if (e != cudaSuccess) return cuda_fail(e, "forward pose-gradient launch");
   e = launch_forward_grad_reduce(w.inst, w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_tiles, p->geo, loss,
@@ -590,7 +614,7 @@ int proj_gather_probe(proj_plan p, const float* d_pose, void* d_ws, size_t ws_by
   if ((rc = setup(p, d_pose, w, s))) return rc;
   mark(p, true, s);
   cudaError_t e = launch_gather_probe(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, w.part_f, s,
-                                      occ_of(p, w, p->skip_shift));
+                                      occ_of(p, w));
   mark(p, false, s);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "gather probe launch");
 }
@@ -688,7 +712,7 @@ int proj_autotune_forward_grad(proj_plan p, const float* d_pose, int loss, const
   float best = 0.f;
   int pick = p->warp_width;
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
-    const Occ occ = occ_of(p, w, p->skip_shift);
+    const Occ occ = occ_of(p, w);
     e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, nullptr, w.part_f, s,
                             widths[i], nullptr, occ);
     if (e == cudaSuccess) e = cudaEventRecord(a, s);
@@ -726,7 +750,7 @@ int proj_count_marched_samples(proj_plan p, const float* d_pose, long long* d_co
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = setup(p, d_pose, w, s))) return rc;
   // the fused march's samples: the gradient grid's box, clipped to the occupied bricks when skipping is on
-  cudaError_t e = launch_count(w.inst, p->n_inst, p->geo, d_count, s, occ_of(p, w, p->skip_shift), 1);
+  cudaError_t e = launch_count(w.inst, p->n_inst, p->geo, d_count, s, occ_of(p, w), 1);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "count launch");
 }
 
@@ -743,8 +767,22 @@ int proj_get_skip_brick(proj_plan p, int* edge) {
   return PROJ_OK;
 }
 
+int proj_set_skip_cells(proj_plan p, int mode) {
+  if (!p) return fail(PROJ_E_ARG, "plan is NULL");
+  if (mode < 0 || mode > 2) return fail(PROJ_E_ARG, "skip_cells mode must be 0, 1 or 2, got %d", mode);
+  p->skip_cells = mode;
+  return PROJ_OK;
+}
+
+int proj_get_skip_cells(proj_plan p, int* mode) {
+  if (!p || !mode) return fail(PROJ_E_ARG, "plan or mode is NULL");
+  *mode = p->skip_cells;
+  return PROJ_OK;
+}
+
 int proj_autotune_march(proj_plan p, const float* d_pose, int loss, const float* d_ref, void* d_ws, size_t ws_bytes,
-                        proj_stream stream, int reps, float* times_ms, int* warp_width, int* brick_edge) {
+                        proj_stream stream, int reps, float* times_ms, int* warp_width, int* brick_edge,
+                        int* skip_cells) {
   if (!p) return fail(PROJ_E_ARG, "plan is NULL");
   if (!d_pose || !d_ref) return fail(PROJ_E_ARG, "proj_autotune_march: NULL pose or reference");
   if (loss != PROJ_LOSS_RESIDUAL && loss != PROJ_LOSS_L2 && loss != PROJ_LOSS_NCC)
@@ -764,9 +802,11 @@ int proj_autotune_march(proj_plan p, const float* d_pose, int loss, const float*
   const int shifts[3] = {0, 3, 4};
   float best = 0.f;
   int pick_w = p->warp_width, pick_s = p->skip_shift;
+  int pick_c = p->skip_cells;
   bool have = false;
-  for (int j = 0; j < 3 && e == cudaSuccess; ++j) {
-    const Occ occ = occ_of(p, w, shifts[j]);
+  // j = 2 * (brick edge position) + cell test
+  for (int j = 0; j < 6 && e == cudaSuccess; ++j) {
+    const Occ occ = occ_of(p, w, shifts[j >> 1], j & 1);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
       e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, nullptr, w.part_f, s,
                               widths[i], nullptr, occ);
@@ -783,7 +823,8 @@ int proj_autotune_march(proj_plan p, const float* d_pose, int loss, const float*
       if (e == cudaSuccess && (!have || ms < best)) {
         best = ms;
         pick_w = widths[i];
-        pick_s = shifts[j];
+        pick_s = shifts[j >> 1];
+        pick_c = j & 1;
         have = true;
       }
     }
@@ -793,8 +834,10 @@ int proj_autotune_march(proj_plan p, const float* d_pose, int loss, const float*
   if (e != cudaSuccess) return cuda_fail(e, "autotune launches");
   p->warp_width = pick_w;
   p->skip_shift = pick_s;
+  p->skip_cells = pick_c;
   if (warp_width) *warp_width = pick_w;
   if (brick_edge) *brick_edge = pick_s ? 1 << pick_s : 0;
+  if (skip_cells) *skip_cells = pick_c;
   return PROJ_OK;
 }
 
@@ -898,7 +941,7 @@ int proj_batch_create(int n, const proj_plan* plans, const int* loss, const floa
     B.inst = w.inst;
     B.vol4 = w.vol4;
     B.vol4y = w.vol4y;
-    B.occ = occ_of(p, w, p->skip_shift);
+    B.occ = occ_of(p, w);
     B.ref = d_ref[i];
     B.part = w.part_f;
     B.n_tiles = p->n_tiles;

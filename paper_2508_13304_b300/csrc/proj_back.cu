@@ -143,26 +143,97 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
 // (one thread per (x, y) column holding its GZ residual weights in
 // registers) and a chunk of VIEWS consecutive instances; blocks of the same
 // chunk run together, so that chunk's detector stacks stay in L2.  The inner
-// loop over z is branch-free - a voxel that projects outside the image, lies
-// behind the source or has wj = 0 gets weight 0 and gathers from a clamped,
-// valid address - so the gathers of several voxels can be in flight at once.
-// Per (brick, instance) one block reduction (warp shuffles, then the 8 warps
-// in a fixed order) writes a record part[instance][brick][12].
+// loop over z is branch-free - a voxel that projects outside the image or
+// lies behind the source gets weight 0 and gathers from a valid address - so
+// the gathers of several voxels can be in flight at once.  Per (brick,
+// instance) one block reduction (a warp reduce-scatter, then the 8 warps in a
+// fixed order) writes a record part[instance][brick][12].
+//
+// Arithmetic per voxel-view, kept short because the kernel issues about as
+// many instructions as its gathers allow:
+//  * projection straight into shifted pixel coordinates (up, vp) = (u + 3,
+//    v + 3), one more than the padded stack's: the chunk's instance
+//    constants are staged in shared memory with the +3 folded into Q, and
+//    into the rows P0, P1 so that s can be formed from (up, vp) (D_u P0 +
+//    D_v P1 - s P2 is unchanged when s -> s + 3 D_u + 3 D_v and P0 -> P0 +
+//    3 P2, P1 -> P1 + 3 P2);
+//  * the corner index and fractions without float-int conversions: for
+//    1 <= x < 2^22 the sum x + (2^23 - 1/2) lies in [2^23, 2^24), where FP32
+//    spacing is 1, so it rounds to 2^23 + RN(x - 1/2), whose low mantissa
+//    bits are floor(x) (floor(x) - 1 with fraction 1 when x is an integer: the
+//    same bilinear value); three adds per axis;
+//  * the FDK factor w0^2 of W = (w0 rw)^2 applied once per record;
+//  * since f~x and f~y are fixed for a thread, only sum rho and sum rho f~z
+//    are accumulated per voxel (6 sums); the 12 follow per instance.
+constexpr int kBgTab = 24;   // staged per-instance constants (floats), see k_back_grad
 
-__device__ __forceinline__ float warp_sum(float v) {
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Sum over the warp of 12 values per lane, as a reduce-scatter: after the
+// two halving rounds lane l holds 3 partial sums, of values 6 (l >> 4 & 1) +
+// 3 (l >> 3 & 1) + {0, 1, 2}; three butterfly rounds complete them.  Lanes
+// with (l & 7) == 0 write their 3 sums to dst.  Fixed order: deterministic.
+__device__ __forceinline__ void warp_sum12(const float (&v)[12], float* dst) {
+  const int lane = threadIdx.x & 31;
+  const bool h16 = lane & 16, h8 = lane & 8;
+  float b[6], c[3];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  for (int i = 0; i < 6; ++i) {
+    const float send = h16 ? v[i] : v[i + 6], keep = h16 ? v[i + 6] : v[i];
+    b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float send = h8 ? b[i] : b[i + 3], keep = h8 ? b[i + 3] : b[i];
+    c[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c[i] += __shfl_xor_sync(0xffffffffu, c[i], o);
+  if ((lane & 7) == 0) {
+    const int base = (h16 ? 6 : 0) + (h8 ? 3 : 0);
+    dst[base] = c[0];
+    dst[base + 1] = c[1];
+    dst[base + 2] = c[2];
+  }
 }
 
 template <int GZ, int VIEWS>
 __global__ void __launch_bounds__(kBpThreads, 3)
     k_back_grad(const InstTable* __restrict__ inst, int n_inst, Geo g, int weight, const float4* __restrict__ det4,
                 const float* __restrict__ wvol, float* __restrict__ part, int bricks_x, int bricks_y) {
-  __shared__ float sred[kBpThreads / 32][12];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // per instance of the chunk: Q with the +3 pixel shift folded in (columns x, y, z, constant; u, v, w each),
+  // P0 + 3 P2, P1 + 3 P2, P2, the record factor (w0^2 or 1) and the valid flag
+  __shared__ __align__(16) float tab[VIEWS][kBgTab];
+  __shared__ float sred[2][kBpThreads / 32][12];
+  const int warp = threadIdx.x >> 5;
   const int n_bricks = gridDim.x;
   const int brick = blockIdx.x;
+  const int n0 = blockIdx.y * VIEWS, n1 = min(n_inst, n0 + VIEWS);
+  if (threadIdx.x < n1 - n0) {
+    const InstTable& T = inst[n0 + threadIdx.x];
+    float* t = tab[threadIdx.x];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      t[3 * c + 0] = fmaf(3.f, T.Q[3 * c + 2], T.Q[3 * c + 0]);
+      t[3 * c + 1] = fmaf(3.f, T.Q[3 * c + 2], T.Q[3 * c + 1]);
+      t[3 * c + 2] = T.Q[3 * c + 2];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      t[12 + a] = fmaf(3.f, T.P3[6 + a], T.P3[a]);
+      t[15 + a] = fmaf(3.f, T.P3[6 + a], T.P3[3 + a]);
+      t[18 + a] = T.P3[6 + a];
+    }
+    t[21] = weight != PROJ_W_NONE ? T.w0 * T.w0 : 1.f;
+    t[22] = T.valid ? 1.f : 0.f;
+    t[23] = 0.f;
+  }
   const int bx = brick % bricks_x, by = (brick / bricks_x) % bricks_y, bz = brick / (bricks_x * bricks_y);
   const int ix = bx * kGbX + col_x(), iy = by * kGbY + col_y(), iz0 = bz * GZ;
   const bool col = ix < g.nx && iy < g.ny;
@@ -170,80 +241,71 @@ __global__ void __launch_bounds__(kBpThreads, 3)
 #pragma unroll
   for (int z = 0; z < GZ; ++z)
     wj[z] = (col && iz0 + z < g.nz) ? __ldg(wvol + ((size_t)(iz0 + z) * g.ny + iy) * g.nx + ix) : 0.f;
-  const float fx = (float)ix - g.cx, fy = (float)iy - g.cy;
-  const int qu = g.nu + 4;
+  const float fx = (float)ix - g.cx, fy = (float)iy - g.cy, fz0 = (float)iz0 - g.cz;
+  const unsigned qu = (unsigned)g.nu + 4u;
+  // the float bits of 2^23 + i are 0x4B000000 + i; stack column = i - 1 (likewise rows)
+  const unsigned koff = (0x4B000000u + 1u) * (qu + 1u);
   const size_t det_stride = (size_t)(g.nu + 4) * (g.nv + 4);
-  const float fu = (float)g.nu + 1.f, fvv = (float)g.nv + 1.f;
-  const int n0 = blockIdx.y * VIEWS, n1 = min(n_inst, n0 + VIEWS);
+  const float ulim = (float)g.nu + 4.f, vlim = (float)g.nv + 4.f;
+  __syncthreads();
   for (int n = n0; n < n1; ++n) {
-    const InstTable& T = inst[n];
-    float a[12];
-#pragma unroll
-    for (int q = 0; q < 12; ++q) a[q] = 0.f;
-    if (T.valid && col) {
+    const float* t = tab[n - n0];
+    float S0 = 0.f, S1 = 0.f, S2 = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f;
+    if (t[22] != 0.f && col) {
       const float4* img = det4 + (size_t)n * det_stride;
-      const float bu = fmaf(T.Q[3], fy, fmaf(T.Q[0], fx, T.Q[9]));
-      const float bv = fmaf(T.Q[4], fy, fmaf(T.Q[1], fx, T.Q[10]));
-      const float bw = fmaf(T.Q[5], fy, fmaf(T.Q[2], fx, T.Q[11]));
-      const float P0x = T.P3[0], P0y = T.P3[1], P0z = T.P3[2];
-      const float P1x = T.P3[3], P1y = T.P3[4], P1z = T.P3[5];
-      const float P2x = T.P3[6], P2y = T.P3[7], P2z = T.P3[8];
+      const float bu = fmaf(t[3], fy, fmaf(t[0], fx, t[9]));
+      const float bv = fmaf(t[4], fy, fmaf(t[1], fx, t[10]));
+      const float bw = fmaf(t[5], fy, fmaf(t[2], fx, t[11]));
+      const float qzu = t[6], qzv = t[7], qzw = t[8];
+      const float P0x = t[12], P0y = t[13], P0z = t[14];
+      const float P1x = t[15], P1y = t[16], P1z = t[17];
+      const float P2x = t[18], P2y = t[19], P2z = t[20];
 #pragma unroll
       for (int z = 0; z < GZ; ++z) {
-        const float fz = (float)(iz0 + z) - g.cz;
-        const float hw = fmaf(T.Q[8], fz, bw);
-        const float rw = 1.0f / hw;
-        const float u0 = fmaf(T.Q[6], fz, bu) * rw, v0 = fmaf(T.Q[7], fz, bv) * rw;
-        // support of the interpolated gradient images: (-2, nu+1) x (-2, nv+1)
-        const bool ok = wj[z] != 0.f && hw > 0.f && u0 > -2.f && u0 < fu && v0 > -2.f && v0 < fvv;
-        const float u = ok ? u0 : 0.f, v = ok ? v0 : 0.f;
-        // padded coordinates: pixel index + 2, corner clamped to [0, n + 2]
-        const float up = u + 2.f, vp = v + 2.f;
-        const int i0 = min(max(__float2int_rd(up), 0), g.nu + 2);
-        const int j0 = min(max(__float2int_rd(vp), 0), g.nv + 2);
-        const float au = up - (float)i0, av = vp - (float)j0;
-        const float4* p0 = img + (j0 * qu + i0);
+        const float fz = fz0 + (float)z;
+        const float hw = fmaf(qzw, fz, bw);
+        const float rw = rcp_approx(hw);
+        const float up0 = fmaf(qzu, fz, bu) * rw, vp0 = fmaf(qzv, fz, bv) * rw;
+        // support of the interpolated gradient images: (-2, nu+1) x (-2, nv+1), i.e. 1 < up < nu + 4
+        const bool ok = hw > 0.f && up0 > 1.f && up0 < ulim && vp0 > 1.f && vp0 < vlim;
+        const float up = ok ? up0 : 3.5f, vp = ok ? vp0 : 3.5f;
+        // __fadd_rn: never contracted with the product above, so the sum rounds the tested value of up
+        const float tu = __fadd_rn(up, 8388607.5f), tv = __fadd_rn(vp, 8388607.5f);
+        const float au = up - (tu - 8388608.f), av = vp - (tv - 8388608.f);
+        const unsigned idx = __float_as_uint(tv) * qu + __float_as_uint(tu) - koff;
+        const float4* p0 = img + idx;
         const float4 c00 = __ldg(p0), c10 = __ldg(p0 + 1), c01 = __ldg(p0 + qu), c11 = __ldg(p0 + qu + 1);
         const float L = lerp(lerp(c00.x, c10.x, au), lerp(c01.x, c11.x, au), av);
         const float Du = lerp(lerp(c00.y, c10.y, au), lerp(c01.y, c11.y, au), av);
         const float Dv = lerp(lerp(c00.z, c10.z, au), lerp(c01.z, c11.z, au), av);
-        float W = 1.f;
-        float sv = fmaf(Du, u, Dv * v);
-        if (weight != PROJ_W_NONE) {
-          const float r = T.w0 * rw;
-          W = r * r;
-          if (weight == PROJ_W_FDK) sv = fmaf(2.f, L, sv);
-        }
-        const float f = ok ? W * rw * wj[z] : 0.f;
-        const float r0 = f * (fmaf(Du, P0x, Dv * P1x) - sv * P2x);
-        const float r1 = f * (fmaf(Du, P0y, Dv * P1y) - sv * P2y);
-        const float r2 = f * (fmaf(Du, P0z, Dv * P1z) - sv * P2z);
-        a[0] += r0;
-        a[1] += r1;
-        a[2] += r2;
-        a[3] = fmaf(r0, fx, a[3]);
-        a[4] = fmaf(r0, fy, a[4]);
-        a[5] = fmaf(r0, fz, a[5]);
-        a[6] = fmaf(r1, fx, a[6]);
-        a[7] = fmaf(r1, fy, a[7]);
-        a[8] = fmaf(r1, fz, a[8]);
-        a[9] = fmaf(r2, fx, a[9]);
-        a[10] = fmaf(r2, fy, a[10]);
-        a[11] = fmaf(r2, fz, a[11]);
+        float sv = fmaf(Du, up, Dv * vp);
+        if (weight == PROJ_W_FDK) sv = fmaf(2.f, L, sv);
+        const float fw = weight != PROJ_W_NONE ? rw * rw * rw : rw;
+        const float f = ok ? fw * wj[z] : 0.f;
+        const float Duf = f * Du, Dvf = f * Dv, svf = f * sv;
+        const float r0 = fmaf(Duf, P0x, fmaf(Dvf, P1x, -svf * P2x));
+        const float r1 = fmaf(Duf, P0y, fmaf(Dvf, P1y, -svf * P2y));
+        const float r2 = fmaf(Duf, P0z, fmaf(Dvf, P1z, -svf * P2z));
+        S0 += r0;
+        S1 += r1;
+        S2 += r2;
+        T0 = fmaf(r0, fz, T0);
+        T1 = fmaf(r1, fz, T1);
+        T2 = fmaf(r2, fz, T2);
       }
     }
-#pragma unroll
-    for (int q = 0; q < 12; ++q) {
-      const float sq = warp_sum(a[q]);
-      if (lane == 0) sred[warp][q] = sq;
-    }
+    // a[0..2] = sum rho_a, a[3 + 3a + b] = sum rho_a f~_b
+    const float a[12] = {S0, S1, S2, S0 * fx, S0 * fy, T0, S1 * fx, S1 * fy, T1, S2 * fx, S2 * fy, T2};
+    float(*red)[12] = sred[(n - n0) & 1];
+    warp_sum12(a, red[warp]);
     __syncthreads();
     if (threadIdx.x < 12) {
       float sq = 0.f;
-      for (int w = 0; w < kBpThreads / 32; ++w) sq += sred[w][threadIdx.x];
-      part[((size_t)n * n_bricks + brick) * 12 + threadIdx.x] = sq;
+      for (int w = 0; w < kBpThreads / 32; ++w) sq += red[w][threadIdx.x];
+      part[((size_t)n * n_bricks + brick) * 12 + threadIdx.x] = sq * t[21];
     }
-    __syncthreads();
+    // no second barrier: the next instance reduces into the other buffer, and the one after it
+    // only after the next instance's barrier, which every reader of this buffer has passed
   }
 }
 

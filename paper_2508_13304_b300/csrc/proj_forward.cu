@@ -105,19 +105,20 @@ __device__ __forceinline__ bool ray_setup(const InstTable& T, const Geo& g, int 
   return ray_setup_m<1>(T, g, iu, iv, r);
 }
 
-// Empty-space skipping.  Narrows the inclusive sample range [k0, k1] of a ray
-// to the samples between the first and the last occupied brick (Occ) that
-// the ray crosses, widened by two samples at each end.  Sample k sits at
-// (ax, ay, az) + k (dx, dy, dz) in cell coordinates of the 2-voxel-bordered
-// grid (cell c covers [c, c + 1)); (gx, gy, gz) = n + 2 is the largest cell
-// index.  The walk steps from brick face to brick face in the sample
-// parameter (a 3-D DDA) from sample k0 until it passes sample k1.  Samples
-// left out lie in bricks that hold no cell with a non-zero corner within one
-// cell, so even with the rounding of their FP32 positions they read eight
-// zero corners and add exact zeros.  Returns false when no occupied brick is
-// crossed.
-__device__ __forceinline__ bool occ_clip(const Occ& o, float ax, float ay, float az, float dx, float dy, float dz,
-                                         int gx, int gy, int gz, int& k0, int& k1) {
+// Empty-space skipping, first stage.  Narrows the inclusive sample range
+// [k0, k1] of a ray to the samples between the first and the last occupied
+// brick (Occ) that the ray crosses, widened by two samples at each end.
+// Sample k sits at (ax, ay, az) + k (dx, dy, dz) in cell coordinates of the
+// 2-voxel-bordered grid (cell c covers [c, c + 1)); (gx, gy, gz) = n + 2 is
+// the largest cell index.  The walk steps from brick face to brick face in
+// the sample parameter (a 3-D DDA) from sample k0 until it passes sample k1;
+// no step waits on the occupancy byte it loads, so the loads of successive
+// steps overlap.  Samples left out lie in bricks that hold no cell with a
+// non-zero corner within one cell, so even with the rounding of their FP32
+// positions they read eight zero corners and add exact zeros.  Returns false
+// when no occupied brick is crossed.
+__device__ __forceinline__ bool occ_bricks_clip(const Occ& o, float ax, float ay, float az, float dx, float dy,
+                                                float dz, int gx, int gy, int gz, int& k0, int& k1) {
   const int sh = o.shift;
   const float edge = (float)(1 << sh), big = 3.0e30f;
   const float t0 = (float)k0, t1 = (float)k1;
@@ -164,6 +165,25 @@ __device__ __forceinline__ bool occ_clip(const Occ& o, float ax, float ay, float
   return k0 <= k1;
 }
 
+// Brick stage of empty-space skipping for a march whose own sample origin is
+// (ax, ay, az) in its own cell coordinates, with its cell clamp (lx, ly, lz):
+// n + 2 for the (mu, grad mu) grid (rs = 0), n for the DRR march's
+// 1-voxel-bordered records (rs = 1, its cells are one less than the bricks').
+__device__ __forceinline__ bool occ_clip(const Occ& o, float ax, float ay, float az, float dx, float dy, float dz,
+                                         int rs, int lx, int ly, int lz, int& k0, int& k1) {
+  const float sr = (float)rs;
+  // the bricks' grid is the 2-voxel-bordered one, largest cell n + 2 (= l + 2 rs for either march)
+  return occ_bricks_clip(o, ax + sr, ay + sr, az + sr, dx, dy, dz, lx + 2 * rs, ly + 2 * rs, lz + 2 * rs, k0, k1);
+}
+
+// Cell stage, inside the marches: true when cell (cx, cy, cz) of the cell map
+// (the march's cell plus rs) has a non-zero corner.  A sample in a cell
+// without one reads eight zero corners and adds exact zeros, so the march
+// leaves out its gathers and arithmetic and every sum is unchanged.
+__device__ __forceinline__ bool cell_live(const Occ& o, int cx, int cy, int cz) {
+  return (__ldg(o.cells + ((size_t)cz * o.ch + cy) * o.cw + (cx >> 5)) >> (cx & 31)) & 1u;
+}
+
 // Cell of padded index point (fx, fy, fz): lower corner clamped to
 // [0, n] (1-voxel border) or [0, n + 2] (2-voxel border) so the 8 corners
 // stay inside the padded array; fractions are taken from the clamped corner
@@ -172,6 +192,7 @@ __device__ __forceinline__ bool occ_clip(const Occ& o, float ax, float ay, float
 struct Cell {
   int idx;
   float ax, ay, az;
+  int cx, cy, cz;  // the cell (lower corner after the clamp)
 };
 
 __device__ __forceinline__ Cell locate(float fx, float fy, float fz, const Geo& g) {
@@ -183,6 +204,9 @@ __device__ __forceinline__ Cell locate(float fx, float fy, float fz, const Geo& 
   c.ay = fy - (float)iy;
   c.az = fz - (float)iz;
   c.idx = (iz * g.py + iy) * g.px + ix;
+  c.cx = ix;
+  c.cy = iy;
+  c.cz = iz;
   return c;
 }
 
@@ -199,6 +223,9 @@ __device__ __forceinline__ Cell locate_q(float fx, float fy, float fz, const Geo
   c.az = fz - (float)iz;
   c.idx = YF ? ((((iz >> 1) * g.px + ix) * g.py + iy) << 1) + (iz & 1)
              : ((((iz >> 1) * g.py + iy) * g.px + ix) << 1) + (iz & 1);
+  c.cx = ix;
+  c.cy = iy;
+  c.cz = iz;
   return c;
 }
 
@@ -208,8 +235,12 @@ __device__ __forceinline__ Cell locate_q(float fx, float fy, float fz, const Geo
 // (v runs along z in a circular orbit) gather from neighbouring 16-byte slots;
 // the +z corner is the neighbouring slot for an even slice and the next pair's
 // slot for an odd one.
+// YF = 2: either copy, chosen at run time through the element strides sx, sy
+// (+1 voxel along x, y) and szp (+1 slice pair); the index equals that of
+// YF = 0 or 1 for the same copy.
 template <int YF = 0>
-__device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo& g) {
+__device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo& g, int sx = 0, int sy = 0,
+                                        int szp = 0) {
   const int ix = min(max(__float2int_rd(fx), 0), g.nx + 2);
   const int iy = min(max(__float2int_rd(fy), 0), g.ny + 2);
   const int iz = min(max(__float2int_rd(fz), 0), g.nz + 2);
@@ -217,8 +248,14 @@ __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo&
   c.ax = fx - (float)ix;
   c.ay = fy - (float)iy;
   c.az = fz - (float)iz;
-  c.idx = YF ? ((((iz >> 1) * g.rqx + ix) * g.rqy + iy) << 1) + (iz & 1)
-             : ((((iz >> 1) * g.qy + iy) * g.qx + ix) << 1) + (iz & 1);
+  if (YF == 2)
+    c.idx = (iz >> 1) * szp + ix * sx + iy * sy + (iz & 1);
+  else
+    c.idx = YF ? ((((iz >> 1) * g.rqx + ix) * g.rqy + iy) << 1) + (iz & 1)
+               : ((((iz >> 1) * g.qy + iy) * g.qx + ix) << 1) + (iz & 1);
+  c.cx = ix;
+  c.cy = iy;
+  c.cz = iz;
   return c;
 }
 
@@ -242,7 +279,7 @@ __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo&
 constexpr int kPrepZChunk = 32;
 
 __global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ mu, Geo g, float4* __restrict__ volq,
-                                                     float4* __restrict__ vol4) {
+                                                     float4* __restrict__ vol4, unsigned* __restrict__ nbits) {
   auto at = [&](int a, int b, int c) -> float {
     return (a >= 0 && a < g.nx && b >= 0 && b < g.ny && c >= 0 && c < g.nz)
                ? __ldg(mu + ((size_t)c * g.ny + b) * g.nx + a)
@@ -251,7 +288,9 @@ __global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ m
   const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
   const int z0 = blockIdx.z * kPrepZChunk, z1 = min(g.qz, z0 + kPrepZChunk);
   const int i = x - 2, j = y - 2;  // voxel column of this element
-  const bool in4 = vol4 && x < g.qx && y < g.qy;
+  const bool inq = x < g.qx && y < g.qy, in4 = vol4 && inq;
+  // nbits: each warp (32 consecutive x of one row y) stores one word per z: bit = element non-zero
+  const bool row_bits = nbits && y < g.qy;  // uniform per warp
   const int x1 = x - 1, y1 = y - 1;
   const bool in1xy = volq && x1 >= 0 && x1 < g.px && y1 >= 0 && y1 < g.py;
   float m_prev = at(i, j, z0 - 3), m = at(i, j, z0 - 2);
@@ -259,11 +298,17 @@ __global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ m
   for (int z = z0; z < z1; ++z) {
     const int k = z - 2;
     const float m_next = at(i, j, k + 1);
-    if (in4) {
-      const float gx = (at(i + 1, j, k) - at(i - 1, j, k)) * sx;
-      const float gy = (at(i, j + 1, k) - at(i, j - 1, k)) * sy;
-      vol4[((((size_t)(z >> 1) * g.qy + y) * g.qx + x) << 1) + (z & 1)] =
-          make_float4(m, gx, gy, (m_next - m_prev) * sz);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (inq && (vol4 || nbits)) {
+      v.x = m;
+      v.y = (at(i + 1, j, k) - at(i - 1, j, k)) * sx;
+      v.z = (at(i, j + 1, k) - at(i, j - 1, k)) * sy;
+      v.w = (m_next - m_prev) * sz;
+      if (in4) vol4[((((size_t)(z >> 1) * g.qy + y) * g.qx + x) << 1) + (z & 1)] = v;
+    }
+    if (row_bits) {
+      const unsigned b = __ballot_sync(0xffffffffu, v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f);
+      if ((threadIdx.x & 31) == 0) nbits[((size_t)z * g.qy + y) * nbits_words(g.qx) + blockIdx.x] = b;
     }
     const int zz1 = z - 1;
     if (in1xy && zz1 >= 0 && zz1 < g.pz)
@@ -301,11 +346,73 @@ __global__ void k_occupancy(const float* __restrict__ mu, Geo g, unsigned char* 
   }
 }
 
+// Cell map (Occ::cells): cell (x, y, z) of the 2-voxel-bordered grid has
+// corners x..x+1, y..y+1, z..z+1, so its bit is the OR of the non-zero bits
+// of those 8 elements: the OR of 4 rows (y, z pairs), then of bits x and x+1.
+// One thread per word of the map.
+// live counts the set bits (cells with a non-zero corner).
+__global__ void k_cell_bits(const unsigned* __restrict__ nb, Geo g, unsigned* __restrict__ cells,
+                            unsigned long long* __restrict__ live) {
+  const int nw = nbits_words(g.qx), cw = cell_words(g.nx), ch = g.ny + 3;
+  const long long n = (long long)cw * ch * (g.nz + 3);
+  unsigned cnt = 0;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int w = (int)(p % cw), y = (int)((p / cw) % ch), z = (int)(p / ((long long)cw * ch));
+    // y + 1 <= ny + 3 < qy and z + 1 <= nz + 3 < qz: every row read exists
+    auto rows = [&](int ww) -> unsigned {
+      if (ww >= nw) return 0u;
+      const unsigned* r = nb + ((size_t)z * g.qy + y) * nw + ww;
+      const size_t slice = (size_t)g.qy * nw;
+      return __ldg(r) | __ldg(r + nw) | __ldg(r + slice) | __ldg(r + slice + nw);
+    };
+    const unsigned r0 = rows(w), r1 = rows(w + 1);
+    const unsigned word = r0 | (r0 >> 1) | (r1 << 31);
+    cells[p] = word;
+    cnt += __popc(word);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(live, (unsigned long long)cnt);
+}
+
+// Automatic cell test: the cell map pays off when a fair share of the cells
+// inside the occupied 8^3 bricks has no non-zero corner (samples there are
+// left out); on a dense volume every test is spent for nothing (measured: a
+// uniformly filled volume marches about 12 % slower with the test).  One
+// block counts the grid cells of the occupied bricks (bricks on the grid's
+// far faces hold fewer than 512) and sets the flag when the live cells are at
+// most 85 % of them.
+__global__ void k_cell_decide(const unsigned char* __restrict__ occ8, Geo g, const unsigned long long* __restrict__ live,
+                              int* __restrict__ flag) {
+  __shared__ unsigned long long part[32];
+  const int ex = g.nx + 3, ey = g.ny + 3, ez = g.nz + 3;  // cells per axis
+  const int nb0 = occ_bricks(g.nx, 3), nb1 = occ_bricks(g.ny, 3), nb2 = occ_bricks(g.nz, 3);
+  unsigned long long c = 0;
+  for (int b = threadIdx.x; b < nb0 * nb1 * nb2; b += blockDim.x) {
+    if (!occ8[b]) continue;
+    const int bx = b % nb0, by = (b / nb0) % nb1, bz = b / (nb0 * nb1);
+    c += (unsigned long long)min(8, ex - 8 * bx) * min(8, ey - 8 * by) * min(8, ez - 8 * bz);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long cells = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) cells += part[w];
+    *flag = (double)*live <= 0.85 * (double)cells ? 1 : 0;
+  }
+}
+
 // ---------------------------------------------------------------- K2
 
 // Corners of a sample's cell: the xy face at z in one 16-byte cell record,
 // the face at z + 1 in the record of the slice above (the neighbouring slot
-// for an even slice, the next pair's slot for an odd one).
+// for an even slice, the next pair's slot for an odd one).  The DRR march
+// skips by bricks only: with two gathers per sample, testing each sample's
+// cell in the cell map costs more than it saves (measured on the
+// registration phantom: 4.35 ms with bricks, 5.36 ms with the cell test).
 template <int YF>
 __device__ __forceinline__ float drr_ray(const InstTable& T, const Geo& g, int iu, int iv,
                                          const float4* __restrict__ volq, const Occ& occ) {
@@ -313,8 +420,7 @@ __device__ __forceinline__ float drr_ray(const InstTable& T, const Geo& g, int i
   Ray r;
   if (!ray_setup(T, g, iu, iv, r)) return acc;
   // the records' 1-voxel border: cell coordinates of the 2-voxel-bordered grid are one more
-  if (occ.map && !occ_clip(occ, r.ax + 1.f, r.ay + 1.f, r.az + 1.f, r.dx, r.dy, r.dz, g.nx + 2, g.ny + 2, g.nz + 2,
-                           r.k0, r.k1))
+  if (occ.map && !occ_clip(occ, r.ax, r.ay, r.az, r.dx, r.dy, r.dz, 1, g.nx, g.ny, g.nz, r.k0, r.k1))
     return acc;
   const int szp = 2 * g.px * g.py;
   for (int k = r.k0; k <= r.k1; ++k) {
@@ -348,7 +454,8 @@ __global__ void __launch_bounds__(kMarchThreads) k_forward(const InstTable* __re
 // Samples per instance: grad_box 0, those in the open box (-1, n) of mu~
 // (the sum of Eq. forward); grad_box 1, those the fused march gathers: the
 // gradient grid's box (-2, n+1), clipped to the occupied bricks when occ.map
-// is set.
+// is set, and of those only the samples whose cell has a non-zero corner when
+// the cell test is on (occ.cells, and *occ.cells_flag if given).
 __global__ void k_count(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g,
                         unsigned long long* __restrict__ count, Occ occ, int grad_box) {
   const int n = blockIdx.x / n_tiles, tile = blockIdx.x % n_tiles;
@@ -360,8 +467,16 @@ __global__ void k_count(const InstTable* __restrict__ inst, int n_tiles, int til
       if (ray_setup(inst[n], g, iu, iv, r)) c = (unsigned long long)(r.k1 - r.k0 + 1);
     } else if (ray_setup_m<2>(inst[n], g, iu, iv, r) &&
                (!occ.map ||
-                occ_clip(occ, r.ax, r.ay, r.az, r.dx, r.dy, r.dz, g.nx + 2, g.ny + 2, g.nz + 2, r.k0, r.k1))) {
-      c = (unsigned long long)(r.k1 - r.k0 + 1);
+                occ_clip(occ, r.ax, r.ay, r.az, r.dx, r.dy, r.dz, 0, g.nx + 2, g.ny + 2, g.nz + 2, r.k0, r.k1))) {
+      if (occ.cells && (!occ.cells_flag || __ldg(occ.cells_flag))) {
+        for (int k = r.k0; k <= r.k1; ++k) {
+          const float kf = (float)k;
+          const Cell cl = locate2(fmaf(kf, r.dx, r.ax), fmaf(kf, r.dy, r.ay), fmaf(kf, r.dz, r.az), g);
+          c += cell_live(occ, cl.cx, cl.cy, cl.cz) ? 1 : 0;
+        }
+      } else {
+        c = (unsigned long long)(r.k1 - r.k0 + 1);
+      }
     }
   }
 #pragma unroll
@@ -382,11 +497,15 @@ __global__ void k_count(const InstTable* __restrict__ inst, int n_tiles, int til
 // One 16 x 16 ray tile (instance n, tile index) of the fused march, block-
 // wide: writes the tile's record part[(n * n_tiles + tile) * kRec ...].
 // Shared by the per-problem kernel and the persistent multi-problem kernel.
+// YF: 0 or 1, the copy marched (rows along x or y); 2, the copy named at run
+// time by yf_rt, one code path for both (the persistent batch kernel, whose
+// register budget does not hold two inlined marches).
 template <int LOSS, int WU = 4, int YF = 0>
 __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, int n, int tile, int n_tiles,
                                            int tiles_u, const Geo& g, const float4* __restrict__ vol,
                                            const float* __restrict__ ref, float* __restrict__ proj,
-                                           float* __restrict__ part, float (*red)[kRec], const Occ& occ) {
+                                           float* __restrict__ part, float (*red)[kRec], const Occ& occ,
+                                           bool yf_rt = false) {
   int iu, iv;
   const bool on_det = tile_pixel<WU>(tile, tiles_u, g, iu, iv);
   const InstTable& T = inst[n];
@@ -395,14 +514,17 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
   float s1[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   Ray r;
   if (on_det && T.valid && ray_setup_m<2>(T, g, iu, iv, r) &&
-      (!occ.map || occ_clip(occ, r.ax, r.ay, r.az, r.dx, r.dy, r.dz, g.nx + 2, g.ny + 2, g.nz + 2, r.k0, r.k1))) {
+      (!occ.map || occ_clip(occ, r.ax, r.ay, r.az, r.dx, r.dy, r.dz, 0, g.nx + 2, g.ny + 2, g.nz + 2, r.k0, r.k1))) {
     // element strides of +1 voxel along x, y, z in the marched copy
-    const int sx = YF ? 2 * g.rqy : 2, sy = YF ? 2 : 2 * g.qx, szp = YF ? 2 * g.rqx * g.rqy : 2 * g.qx * g.qy;
+    const bool yf = YF == 2 ? yf_rt : YF == 1;
+    const bool cell_test = occ.cells && (!occ.cells_flag || __ldg(occ.cells_flag));
+    const int sx = yf ? 2 * g.rqy : 2, sy = yf ? 2 : 2 * g.qx, szp = yf ? 2 * g.rqx * g.rqy : 2 * g.qx * g.qy;
     const float ox = g.cx + 2.0f, oy = g.cy + 2.0f, oz = g.cz + 2.0f;
     for (int k = r.k0; k <= r.k1; ++k) {
       const float kf = (float)k;
       const float fx = fmaf(kf, r.dx, r.ax), fy = fmaf(kf, r.dy, r.ay), fz = fmaf(kf, r.dz, r.az);
-      const Cell c = locate2<YF>(fx, fy, fz, g);
+      const Cell c = locate2<YF>(fx, fy, fz, g, sx, sy, szp);
+      if (cell_test && !cell_live(occ, c.cx, c.cy, c.cz)) continue;
       const float4* p0 = vol + c.idx;
       const int sz = (c.idx & 1) ? szp - 1 : 1;
       const float4 v000 = __ldg(p0), v100 = __ldg(p0 + sx);
@@ -552,12 +674,14 @@ __device__ __forceinline__ float probe_ray(const InstTable& T, const Geo& g, int
   Ray r;
   float acc = 0.f;
   if (!(T.valid && ray_setup_m<2>(T, g, iu, iv, r))) return acc;
-  if (occ.map && !occ_clip(occ, r.ax, r.ay, r.az, r.dx, r.dy, r.dz, g.nx + 2, g.ny + 2, g.nz + 2, r.k0, r.k1))
+  if (occ.map && !occ_clip(occ, r.ax, r.ay, r.az, r.dx, r.dy, r.dz, 0, g.nx + 2, g.ny + 2, g.nz + 2, r.k0, r.k1))
     return acc;
   const int sx = YF ? 2 * g.rqy : 2, sy = YF ? 2 : 2 * g.qx, szp = YF ? 2 * g.rqx * g.rqy : 2 * g.qx * g.qy;
+  const bool cell_test = occ.cells && (!occ.cells_flag || __ldg(occ.cells_flag));
   for (int k = r.k0; k <= r.k1; ++k) {
     const float kf = (float)k;
     const Cell c = locate2<YF>(fmaf(kf, r.dx, r.ax), fmaf(kf, r.dy, r.ay), fmaf(kf, r.dz, r.az), g);
+    if (cell_test && !cell_live(occ, c.cx, c.cy, c.cz)) continue;
     const float4* p0 = vol + c.idx;
     const int sz = (c.idx & 1) ? szp - 1 : 1;
     acc += ld_probe(p0) + ld_probe(p0 + sx) + ld_probe(p0 + sy) + ld_probe(p0 + sy + sx) + ld_probe(p0 + sz) +
@@ -589,8 +713,9 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
 // chose (longest tiles first), so small problems fill the tail of the large
 // ones.  The counter is the only shared state; no block waits for another.
 
-// LOSS >= 0: every problem of the batch has that loss (2 march variants, the two
-// volume copies); LOSS < 0: each problem's own loss (6 variants, more registers).
+// LOSS >= 0: every problem of the batch has that loss (one march, either
+// volume copy through run-time strides); LOSS < 0: each problem's own loss
+// (3 variants, more registers).
 template <int LOSS>
 __global__ void __launch_bounds__(kMarchThreads, 4)
     k_forward_grad_batch(const BatchProblem* __restrict__ probs, int n_probs, long long n_items,
@@ -610,37 +735,23 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
     const int local = (int)(item - B.item_begin), tu = local % B.tiles_u, rest = local / B.tiles_u;
     const int n = rest % B.n_inst, tile = (rest / B.n_inst) * B.tiles_u + tu;
     const bool yf = B.vol4y && B.inst[n].yfast;
+    const float4* vol = yf ? B.vol4y : B.vol4;
     if constexpr (LOSS >= 0) {
-      if (yf)
-        march_tile<LOSS, 4, 1>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4y, B.ref, nullptr, B.part, red, B.occ);
-      else
-        march_tile<LOSS, 4, 0>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr, B.part, red, B.occ);
+      march_tile<LOSS, 4, 2>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, vol, B.ref, nullptr, B.part, red, B.occ, yf);
       continue;
     }
-    switch (B.loss * 2 + (yf ? 1 : 0)) {
-      case PROJ_LOSS_RESIDUAL * 2:
-        march_tile<PROJ_LOSS_RESIDUAL, 4, 0>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr,
-                                             B.part, red, B.occ);
+    switch (B.loss) {
+      case PROJ_LOSS_RESIDUAL:
+        march_tile<PROJ_LOSS_RESIDUAL, 4, 2>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, vol, B.ref, nullptr,
+                                             B.part, red, B.occ, yf);
         break;
-      case PROJ_LOSS_RESIDUAL * 2 + 1:
-        march_tile<PROJ_LOSS_RESIDUAL, 4, 1>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4y, B.ref, nullptr,
-                                             B.part, red, B.occ);
-        break;
-      case PROJ_LOSS_L2 * 2:
-        march_tile<PROJ_LOSS_L2, 4, 0>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr, B.part,
-                                       red, B.occ);
-        break;
-      case PROJ_LOSS_L2 * 2 + 1:
-        march_tile<PROJ_LOSS_L2, 4, 1>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4y, B.ref, nullptr, B.part,
-                                       red, B.occ);
-        break;
-      case PROJ_LOSS_NCC * 2 + 1:
-        march_tile<PROJ_LOSS_NCC, 4, 1>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4y, B.ref, nullptr,
-                                        B.part, red, B.occ);
+      case PROJ_LOSS_L2:
+        march_tile<PROJ_LOSS_L2, 4, 2>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, vol, B.ref, nullptr, B.part,
+                                       red, B.occ, yf);
         break;
       default:
-        march_tile<PROJ_LOSS_NCC, 4, 0>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, B.vol4, B.ref, nullptr,
-                                        B.part, red, B.occ);
+        march_tile<PROJ_LOSS_NCC, 4, 2>(B.inst, n, tile, B.n_tiles, B.tiles_u, B.geo, vol, B.ref, nullptr, B.part,
+                                        red, B.occ, yf);
         break;
     }
   }
@@ -853,10 +964,25 @@ cudaError_t launch_occupancy(const float* d_mu, Geo geo, unsigned char* d_occ8, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float4* d_vol4, cudaStream_t s) {
-  // the pitched extents (qx, qy, qz) exceed the 1-padded ones (n + 2) in every axis
+cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float4* d_vol4, cudaStream_t s,
+                               unsigned* d_nbits) {
+  // the pitched extents (qx, qy, qz) exceed the 1-padded ones (n + 2) in every axis; blockIdx.x is the
+  // word of a row of the non-zero bits (nbits_words(qx) = the grid's x extent)
   dim3 grid(ceil_div(geo.qx, 32), ceil_div(geo.qy, 8), ceil_div(geo.qz, kPrepZChunk));
-  k_volume_prep<<<grid, 256, 0, s>>>(d_mu, geo, d_volq, d_vol4);
+  k_volume_prep<<<grid, 256, 0, s>>>(d_mu, geo, d_volq, d_vol4, d_nbits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_bits(const unsigned* d_nbits, Geo geo, unsigned* d_cells, const unsigned char* d_occ8,
+                             void* d_stat, cudaStream_t s) {
+  unsigned long long* live = static_cast<unsigned long long*>(d_stat);
+  cudaError_t e = cudaMemsetAsync(d_stat, 0, kCellStatBytes, s);
+  if (e != cudaSuccess) return e;
+  k_cell_bits<<<elementwise_grid((long long)cell_words(geo.nx) * (geo.ny + 3) * (geo.nz + 3)), 256, 0, s>>>(
+      d_nbits, geo, d_cells, live);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_cell_decide<<<1, 1024, 0, s>>>(d_occ8, geo, live, const_cast<int*>(cell_flag_of(d_stat)));
   return cudaGetLastError();
 }
 

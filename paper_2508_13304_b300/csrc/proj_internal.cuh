@@ -78,12 +78,26 @@ struct FdkView {
 // voxel.  A sample whose cell has only zero corners adds exact zeros to every
 // sum of the marches, so a ray's samples before the first and after the last
 // occupied brick it crosses can be left out without changing any result.
+//
+// Within the brick range each ray's ends are then narrowed sample by sample
+// with the cell map (cells): bit (x & 31) of word (z * ch + y) * cw + (x >> 5)
+// is set when cell (x, y, z) of the same grid has a non-zero corner in
+// (mu, grad mu).  The test uses the march's own FP32 position and cell of each
+// sample, so the samples it leaves out are exactly those that read eight zero
+// corners.
 struct Occ {
   const unsigned char* map;  // nullptr: no skipping
   int shift;                 // 3 (8-cell bricks) or 4 (16-cell bricks)
   int nb[3];                 // bricks per axis
+  const unsigned* cells;     // cell map, or nullptr (brick ranges only)
+  int cw, ch;                // words per row (x), rows per slice (y)
+  const int* cells_flag;     // with cells: nullptr = always test; else test only when *cells_flag != 0
 };
 __host__ __device__ constexpr int occ_bricks(int n, int shift) { return (n + 3 + (1 << shift) - 1) >> shift; }
+// Non-zero map of the (mu, grad mu) elements, one bit per element of the pitched grid, rows of
+// nbits_words(qx) words, qy rows per slice, qz slices; and the cell map's words per row.
+__host__ __device__ constexpr int nbits_words(int qx) { return (qx + 31) >> 5; }
+__host__ __device__ constexpr int cell_words(int nx) { return (nx + 3 + 31) >> 5; }
 
 // One problem of a persistent multi-problem fused march (proj_batch_*).
 struct BatchProblem {
@@ -132,8 +146,9 @@ constexpr int kBpThreads = kBpX * kBpY;
 // Back-projection gradient: bricks of 32 x 8 x gz voxels (one thread per
 // column of gz voxels), `views` instances per block; the shape is chosen per
 // plan (proj_set_brick_shape, proj_autotune_back_grad):
-//   0: gz 16, 8 views (default)   1: gz 8, 8 views
-//   2: gz 16, 16 views            3: gz 8, 16 views
+//   0: gz 16, 8 views             1: gz 8, 8 views
+//   2: gz 16, 16 views            3: gz 8, 16 views (default: fastest on the
+//   motion-compensation workload, 24.9 vs 25.5 / 26.1 / 26.8 ms for 1 / 2 / 0)
 constexpr int kGbX = 32;
 constexpr int kGbY = 8;
 constexpr int kBrickShapes = 4;
@@ -144,7 +159,17 @@ __host__ __device__ constexpr int brick_views(int shape) { return shape >= 2 ? 1
 cudaError_t launch_setup(const float* d_pose, int n_pose, const double* d_views, const int* d_inst_view,
                          const int* d_inst_pose, int n_inst, Geo geo, InstTable* d_inst, PoseTable* d_ptab,
                          int* d_status, cudaStream_t s);
-cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float4* d_vol4, cudaStream_t s);
+// d_nbits (optional): the non-zero bits of (mu, grad mu), [qz][qy][nbits_words(qx)] words
+cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float4* d_vol4, cudaStream_t s,
+                               unsigned* d_nbits = nullptr);
+// the cell map, [nz + 3][ny + 3][cell_words(nx)] words, from the non-zero bits; d_stat (2 counters and
+// the flag, kCellStatBytes) receives the decision of the automatic cell test (see k_cell_decide)
+constexpr int kCellStatBytes = 32;
+cudaError_t launch_cell_bits(const unsigned* d_nbits, Geo geo, unsigned* d_cells, const unsigned char* d_occ8,
+                             void* d_stat, cudaStream_t s);
+__host__ __device__ inline const int* cell_flag_of(const void* d_stat) {
+  return reinterpret_cast<const int*>(static_cast<const char*>(d_stat) + 16);
+}
 // occupancy bricks of both edges (8 and 16 cells) for the volume d_mu; either map may be null
 cudaError_t launch_occupancy(const float* d_mu, Geo geo, unsigned char* d_occ8, unsigned char* d_occ16,
                              cudaStream_t s);

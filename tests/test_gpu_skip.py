@@ -1,7 +1,9 @@
-"""Empty-space skipping of the forward marches (proj_set_skip_brick): each
-ray keeps only its samples around the occupied bricks it crosses.  A sample
-left out reads eight zero corners, so projections, losses and pose gradients
-must be bit-identical with skipping off, with 8^3 and with 16^3 bricks.  The
+"""Empty-space skipping of the forward marches (proj_set_skip_brick,
+proj_set_skip_cells): each ray keeps only its samples around the occupied
+bricks it crosses, and the fused march leaves out the samples whose cell has
+no non-zero corner.  A sample left out reads eight zero corners, so
+projections, losses and pose gradients must be bit-identical with skipping
+off, with 8^3 and with 16^3 bricks, each with and without the cell test.  The
 volumes here are sparse on purpose: small ellipsoids in air, single voxels
 at the corners and faces of the grid (rays that graze a brick boundary),
 one-voxel lines, random geometries turned off the grid axes."""
@@ -27,6 +29,7 @@ def _lib():
 import paper_2508_13304_b300 as pb  # noqa: E402
 
 EDGES = (0, 8, 16)
+MODES = [(e, c) for e in EDGES for c in (0, 1)] + [(8, 2)]   # (brick edge, cell test off / on / automatic)
 
 
 def sparse_volume(g, rng, n_ell=3, n_dots=12):
@@ -68,17 +71,25 @@ def check_exact(g, mu, poses, iv, ip, rng):
                      ops=pb.PROJ_OP_FORWARD | pb.PROJ_OP_FORWARD_GRAD)
     P.set_volume(mu)
     res, counts = {}, {}
-    for e in EDGES:
+    for e, c in MODES:
         pb.proj_set_skip_brick(P.plan, e)
-        assert pb.proj_get_skip_brick(P.plan) == e
-        res[e] = all_calls(P, g, poses, target, resid)
-        counts[e] = int(P.count_marched_samples(poses).sum().item())
+        pb.proj_set_skip_cells(P.plan, c)
+        assert pb.proj_get_skip_brick(P.plan) == e and pb.proj_get_skip_cells(P.plan) == c
+        res[e, c] = all_calls(P, g, poses, target, resid)
+        counts[e, c] = int(P.count_marched_samples(poses).sum().item())
     pb.proj_set_skip_brick(P.plan, 8)
-    for e in (8, 16):
-        for k in res[0]:
-            assert same(res[e][k], res[0][k]), (e, k)
-    assert counts[8] <= counts[16] <= counts[0]
-    return res[0], counts
+    pb.proj_set_skip_cells(P.plan, pb.SKIP_CELLS_AUTO)
+    base = (0, 0)
+    for m in MODES[1:]:
+        for k in res[base]:
+            assert same(res[m][k], res[base][k]), (m, k)
+    assert counts[8, 0] <= counts[16, 0] <= counts[0, 0]
+    # the brick ranges hold every sample whose cell has a non-zero corner: the cell test counts the same
+    assert counts[0, 1] == counts[8, 1] == counts[16, 1] <= counts[8, 0]
+    assert counts[8, 2] in (counts[8, 0], counts[8, 1])
+    out = {e: counts[e, 0] for e in EDGES} | {("cells", e): counts[e, 1] for e in EDGES}
+    out["auto"] = counts[8, 2]
+    return res[base], out
 
 
 def test_sparse_phantom_exact_and_against_the_oracle():
@@ -122,6 +133,24 @@ def test_random_sparse_geometries_exact(seed):
     check_exact(g, mu, poses, iv, ip, rng)
 
 
+def test_automatic_cell_test_follows_the_volume():
+    """SKIP_CELLS_AUTO turns the cell test on for a volume with much empty
+    space inside the occupied bricks and off for a nearly full one (an empty
+    slab of 8 slices in a filled volume); results stay bit-identical."""
+    rng = np.random.default_rng(17)
+    g = small_geom(n=(40, 36, 44), det=(40, 38), n_views=2)
+    poses = np.array([[1.0, -0.5, 0.3, 0.05, -0.04, 0.08]], dtype=np.float32)
+    iv = np.arange(2, dtype=np.int32)
+    ip = np.zeros(2, dtype=np.int32)
+    _, sparse = check_exact(g, sparse_volume(g, rng), poses, iv, ip, rng)
+    assert sparse["auto"] == sparse["cells", 8] < sparse[8]
+    full = rng.uniform(0.01, 0.03, g.vol_shape).astype(np.float32)
+    full[18:26] = 0.0
+    _, dense = check_exact(g, full, poses, iv, ip, rng)
+    assert dense["cells", 8] < dense[8]            # the slab's inner cells are empty ...
+    assert dense["auto"] == dense[8]               # ... but too few for the automatic test
+
+
 def test_empty_volume_marches_nothing():
     rng = np.random.default_rng(3)
     g = small_geom(n=(20, 18, 22), det=(24, 20), n_views=2)
@@ -130,14 +159,14 @@ def test_empty_volume_marches_nothing():
     iv = np.arange(2, dtype=np.int32)
     ip = np.zeros(2, dtype=np.int32)
     res, counts = check_exact(g, mu, poses, iv, ip, rng)
-    assert counts[8] == 0 and counts[16] == 0 and counts[0] > 0
+    assert counts[8] == 0 and counts[16] == 0 and counts[0] > 0 and counts["cells", 0] == 0
     assert np.all(res["proj"] == 0) and np.all(res["res"][0] == 0)
 
 
 def test_autotune_march_and_batch_with_skipping():
-    """proj_autotune_march keeps a valid (brick edge, warp shape) pair with the
-    same results; a persistent batch of sparse problems equals the per-plan
-    calls and the unskipped march bit for bit."""
+    """proj_autotune_march keeps a valid (brick edge, cell test, warp shape)
+    with the same results; a persistent batch of sparse problems equals the
+    per-plan calls and the unskipped march bit for bit."""
     rng = np.random.default_rng(41)
     probs = []
     for n, det in (((40, 36, 30), (44, 40)), ((28, 33, 25), (30, 26)), ((36, 36, 36), (38, 38))):
@@ -153,12 +182,15 @@ def test_autotune_march_and_batch_with_skipping():
         probs.append((P, pose_d, tgt))
     P, pose_d, tgt = probs[0]
     base, _ = P.forward_pose_grad(pose_d, pb.PROJ_LOSS_NCC, tgt)
-    w, e, times = pb.proj_autotune_march(P.plan, pose_d, pb.PROJ_LOSS_NCC, tgt, P.ws, reps=1)
-    assert w in pb.WARP_WIDTHS and e in pb.SKIP_BRICK_EDGES and len(times) == 12
+    w, e, c, times = pb.proj_autotune_march(P.plan, pose_d, pb.PROJ_LOSS_NCC, tgt, P.ws, reps=1)
+    assert w in pb.WARP_WIDTHS and e in pb.SKIP_BRICK_EDGES and len(times) == 24
+    assert all(t > 0 for t in times.values())
     assert pb.proj_get_skip_brick(P.plan) == e and pb.proj_get_warp_shape(P.plan) == w
+    assert pb.proj_get_skip_cells(P.plan) == c
     pb.proj_set_warp_shape(P.plan, 4)
-    for edge in (0, 16, 8):
+    for edge, cells in ((0, False), (16, True), (8, False), (8, True)):
         pb.proj_set_skip_brick(P.plan, edge)
+        pb.proj_set_skip_cells(P.plan, cells)
         g2, _ = P.forward_pose_grad(pose_d, pb.PROJ_LOSS_NCC, tgt)
         assert torch.equal(g2, base)
     singles = [Q.forward_pose_grad(pq, pb.PROJ_LOSS_L2, tq)[0] for Q, pq, tq in probs]
@@ -171,6 +203,7 @@ def test_autotune_march_and_batch_with_skipping():
         assert torch.equal(a, b)
     for Q, _, _ in probs:
         pb.proj_set_skip_brick(Q.plan, 0)
+        pb.proj_set_skip_cells(Q.plan, pb.SKIP_CELLS_OFF)
     unskipped = [Q.forward_pose_grad(pq, pb.PROJ_LOSS_L2, tq)[0] for Q, pq, tq in probs]
     for a, b in zip(grads, unskipped):
         assert torch.equal(a, b)
