@@ -370,6 +370,28 @@ def secondary(pb, torch, dev, w, mu_d, flush):
                                                for (e, c, k), v in times.items()},
                              "chosen": "edge %d, cells %d, %dx%d" % (edge, cells, width, 32 // width)}
     del Pa
+    # volume layouts of the fused march on the same launch: rows along x and along y (default), rows along
+    # x only (PROJ_FLAG_ONE_COPY), bricks of 4^3 cells (PROJ_FLAG_BRICKS); march and gathers alone (probe),
+    # with the default skipping and without
+    layouts = {}
+    gl = torch.empty((nc, 6), device=dev)
+    ll = torch.empty((nc,), device=dev)
+    for name, flag in (("rows_x_and_y", 0), ("rows_x", pb.PROJ_FLAG_ONE_COPY), ("bricks_4", pb.PROJ_FLAG_BRICKS)):
+        Pl = pb.Projector(g, n_pose=nc, inst_view=iv, inst_pose=ip, ops=pb.PROJ_OP_FORWARD_GRAD | flag)
+        pb.proj_enable_kernel_timing(Pl.plan)
+        Pl.set_volume(mu_d)
+        row = {"workspace_gb": pb.proj_workspace_size(Pl.plan) / 1e9}
+        for tag in ("", "_without_skipping"):
+            if tag:
+                pb.proj_set_skip_brick(Pl.plan, 0)
+                pb.proj_set_skip_cells(Pl.plan, pb.SKIP_CELLS_OFF)
+            row["kernel_ms" + tag] = _timed(
+                lambda: pb.proj_forward_pose_grad(Pl.plan, pose, pb.PROJ_LOSS_NCC, tg, gl, ll, None, Pl.ws),
+                Pl.plan, pb, flush)
+            row["probe_ms" + tag] = _timed(lambda: pb.proj_gather_probe(Pl.plan, pose, Pl.ws), Pl.plan, pb, flush)
+        layouts[name] = row
+        del Pl
+    out["march_layouts"] = {"config": "256^3, 128 view instances of 384^2, NCC, 4x8 warps", **layouts}
     out["c1_small"] = c1_small(pb, torch, dev, flush)
     out["moco_quality"] = moco_quality(pb, torch, dev)
     out["gradient_accuracy"] = gradient_accuracy(pb, torch, dev, mu_d)

@@ -126,7 +126,17 @@ enum {
    * padded grid, the cell records of the DRR march 16 B per voxel) at the
    * cost of slower gathers for instances whose u axis runs along y.
    * Results are identical to the two-copy plan's. */
-  PROJ_FLAG_ONE_COPY = 256
+  PROJ_FLAG_ONE_COPY = 256,
+  /* Fused pose-gradient march over a bricked copy of the prepared volume:
+   * bricks of 4^3 cells, each storing the 5^3 (mu, grad mu) elements at its
+   * cells' corners (2 KB with padding), so a sample's 8 corners sit at fixed
+   * offsets inside one brick, in place of the rows-along-y copy.  Every
+   * instance marches the bricked copy with 4 x 8-pixel warps (the warp shape
+   * setting is ignored); results are identical to the other layouts'.  About
+   * 1.95x the volume memory of one row copy.  Kept as a measured
+   * alternative layout (the rows-along-x / rows-along-y pair is faster on
+   * the workloads measured). */
+  PROJ_FLAG_BRICKS = 512
 };
 
 /* Device status bits (proj_check). */

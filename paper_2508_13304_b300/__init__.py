@@ -28,6 +28,7 @@ PROJ_OP_FORWARD, PROJ_OP_FORWARD_GRAD, PROJ_OP_BACK, PROJ_OP_BACK_GRAD, PROJ_OP_
 PROJ_OP_SHARPNESS = 32
 PROJ_OP_ALL = 63
 PROJ_FLAG_ONE_COPY = 256
+PROJ_FLAG_BRICKS = 512
 PROJ_STATUS_BAD_POSE = 1
 PROJ_STATUS_BAD_INDEX = 2
 

@@ -71,7 +71,8 @@ struct proj_plan_s {
   size_t off_status = 0, off_inst = 0, off_ptab = 0, off_volq = 0, off_volqy = 0, off_vol4 = 0, off_vol4y = 0, off_part_f = 0,
          off_det4 = 0,
          off_part_b = 0, off_detq = 0, off_acc = 0, off_sharp_m = 0, off_sharp_part = 0, off_occ8 = 0, off_occ16 = 0,
-         off_nbits = 0, off_cells = 0, off_cstat = 0, ws_bytes = 0;
+         off_nbits = 0, off_cells = 0, off_cstat = 0, off_volb = 0,
+         ws_bytes = 0;
 };
 
 namespace {
@@ -96,6 +97,7 @@ struct WsView {
   unsigned* nbits = nullptr;
   unsigned* cells = nullptr;
   void* cstat = nullptr;
+  float4* volb = nullptr;
 };
 
 int check_ws(const proj_plan_s* p, void* d_ws, size_t ws_bytes, WsView* w) {
@@ -121,6 +123,7 @@ int check_ws(const proj_plan_s* p, void* d_ws, size_t ws_bytes, WsView* w) {
   w->nbits = p->off_nbits ? reinterpret_cast<unsigned*>(b + p->off_nbits) : nullptr;
   w->cells = p->off_cells ? reinterpret_cast<unsigned*>(b + p->off_cells) : nullptr;
   w->cstat = p->off_cstat ? static_cast<void*>(b + p->off_cstat) : nullptr;
+  w->volb = p->off_volb ? reinterpret_cast<float4*>(b + p->off_volb) : nullptr;
   return PROJ_OK;
 }
 
@@ -205,7 +208,7 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   if (G.n_views < 1 || !G.views) return fail(PROJ_E_ARG, "need n_views >= 1 and a view table");
   if (n_pose < 1) return fail(PROJ_E_ARG, "n_pose must be >= 1");
   if (n_inst < 1 || !inst_view || !inst_pose) return fail(PROJ_E_ARG, "need n_inst >= 1 and instance maps");
-  if ((ops & PROJ_OP_ALL) == 0 || (ops & ~(PROJ_OP_ALL | PROJ_FLAG_ONE_COPY)))
+  if ((ops & PROJ_OP_ALL) == 0 || (ops & ~(PROJ_OP_ALL | PROJ_FLAG_ONE_COPY | PROJ_FLAG_BRICKS)))
     return fail(PROJ_E_ARG, "ops must be a non-empty OR of PROJ_OP_* (plus PROJ_FLAG_* options)");
   // launch grids put volume rows / slices, detector rows and (for the detector stack) instances in
   // the y and z grid dimensions
@@ -312,10 +315,14 @@ int proj_plan_create(const proj_geometry* geom, int n_pose, int n_inst, const in
   const size_t npad_sz = (size_t)npad;
   const size_t nrec = (size_t)(G.nx + 2) * (G.ny + 2) * record_slices(G.nz);
   p->off_volq = (ops & PROJ_OP_FORWARD) ? take(sizeof(float4) * nrec) : 0;
+  const bool bricks = (ops & PROJ_FLAG_BRICKS) != 0;
   const bool two_copies = !(ops & PROJ_FLAG_ONE_COPY);
   p->off_volqy = ((ops & PROJ_OP_FORWARD) && two_copies) ? take(sizeof(float4) * nrec) : 0;
   p->off_vol4 = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float4) * (size_t)npad2) : 0;
-  p->off_vol4y = ((ops & PROJ_OP_FORWARD_GRAD) && two_copies) ? take(sizeof(float4) * (size_t)npad2y) : 0;
+  p->off_vol4y = ((ops & PROJ_OP_FORWARD_GRAD) && two_copies && !bricks) ? take(sizeof(float4) * (size_t)npad2y) : 0;
+  p->off_volb = ((ops & PROJ_OP_FORWARD_GRAD) && bricks)
+                    ? take(sizeof(float4) * (size_t)vb_n(G.nx) * vb_n(G.ny) * vb_n(G.nz) * kVbElems)
+                    : 0;
   p->off_part_f = (ops & PROJ_OP_FORWARD_GRAD) ? take(sizeof(float) * kRec * (size_t)n_inst * p->n_tiles) : 0;
   // the detector scratch of proj_back (cell records) and of proj_back_pose_grad (the (l, d_u l, d_v l)
   // stack) are never needed by the same call: one region serves both
@@ -435,6 +442,7 @@ int proj_set_volume(proj_plan p, const float* d_mu, void* d_ws, size_t ws_bytes,
   if (e == cudaSuccess && w.cells)
     e = launch_cell_bits(w.nbits, p->geo, w.cells, w.occ8, w.cstat, (cudaStream_t)stream);
   if (e == cudaSuccess && w.vol4y) e = launch_volume_yfast(w.vol4, p->geo, w.vol4y, (cudaStream_t)stream);
+  if (e == cudaSuccess && w.volb) e = launch_volume_bricks(w.vol4, p->geo, w.volb, (cudaStream_t)stream);
   if (e == cudaSuccess && w.volqy) e = launch_records_yfast(w.volq, p->geo, w.volqy, (cudaStream_t)stream);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "volume preparation launch");
 }
@@ -485,7 +493,7 @@ int proj_forward_pose_grad(proj_plan p, const float* d_pose, int loss, const flo
   mark(p, true, s);
   cudaError_t e =
       launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, d_proj, w.part_f, s, p->warp_width,
-                          nullptr, occ_of(p, w));
+                          nullptr, occ_of(p, w), w.volb);
   mark(p, false, s);
   if (e != cudaSuccess) return cuda_fail(e, "forward pose-gradient launch");
   e = launch_forward_grad_reduce(w.inst, w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_tiles, p->geo, loss,
@@ -514,7 +522,7 @@ int proj_forward_pose_grad_list(proj_plan p, const float* d_pose, const int* d_p
   PoseList L{d_pose_list, n_list, p->ipp, p->n_pose, p->d_pose_ptr, p->d_pose_idx, w.status};
   mark(p, true, s);
   cudaError_t e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, d_proj, w.part_f, s,
-                                      p->warp_width, &L, occ_of(p, w));
+                                      p->warp_width, &L, occ_of(p, w), w.volb);
   mark(p, false, s);
   if (e != cudaSuccess) return cuda_fail(e, "forward pose-gradient launch");
   e = launch_forward_grad_reduce(w.inst, w.ptab, p->n_pose, p->d_pose_ptr, p->d_pose_idx, p->n_tiles, p->geo, loss,
@@ -614,7 +622,7 @@ int proj_gather_probe(proj_plan p, const float* d_pose, void* d_ws, size_t ws_by
   if ((rc = setup(p, d_pose, w, s))) return rc;
   mark(p, true, s);
   cudaError_t e = launch_gather_probe(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, w.part_f, s,
-                                      occ_of(p, w));
+                                      occ_of(p, w), w.volb);
   mark(p, false, s);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "gather probe launch");
 }
@@ -714,11 +722,11 @@ int proj_autotune_forward_grad(proj_plan p, const float* d_pose, int loss, const
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
     const Occ occ = occ_of(p, w);
     e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, nullptr, w.part_f, s,
-                            widths[i], nullptr, occ);
+                            widths[i], nullptr, occ, w.volb);
     if (e == cudaSuccess) e = cudaEventRecord(a, s);
     for (int r = 0; r < reps && e == cudaSuccess; ++r)
       e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, nullptr, w.part_f, s,
-                              widths[i], nullptr, occ);
+                              widths[i], nullptr, occ, w.volb);
     if (e == cudaSuccess) e = cudaEventRecord(b, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(b);
     float ms = 0.f;
@@ -809,11 +817,11 @@ int proj_autotune_march(proj_plan p, const float* d_pose, int loss, const float*
     const Occ occ = occ_of(p, w, shifts[j >> 1], j & 1);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
       e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, nullptr, w.part_f, s,
-                              widths[i], nullptr, occ);
+                              widths[i], nullptr, occ, w.volb);
       if (e == cudaSuccess) e = cudaEventRecord(a, s);
       for (int r = 0; r < reps && e == cudaSuccess; ++r)
         e = launch_forward_grad(w.inst, p->n_inst, p->geo, w.vol4, w.vol4y, loss, d_ref, nullptr, w.part_f, s,
-                                widths[i], nullptr, occ);
+                                widths[i], nullptr, occ, w.volb);
       if (e == cudaSuccess) e = cudaEventRecord(b, s);
       if (e == cudaSuccess) e = cudaEventSynchronize(b);
       float ms = 0.f;

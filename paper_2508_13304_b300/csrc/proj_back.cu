@@ -204,7 +204,7 @@ __device__ __forceinline__ void warp_sum12(const float (&v)[12], float* dst) {
 }
 
 template <int GZ, int VIEWS>
-__global__ void __launch_bounds__(kBpThreads, 3)
+__global__ void __launch_bounds__(kBpThreads, GZ <= 8 ? 4 : 3)
     k_back_grad(const InstTable* __restrict__ inst, int n_inst, Geo g, int weight, const float4* __restrict__ det4,
                 const float* __restrict__ wvol, float* __restrict__ part, int bricks_x, int bricks_y) {
   // per instance of the chunk: Q with the +3 pixel shift folded in (columns x, y, z, constant; u, v, w each),

@@ -237,7 +237,7 @@ __device__ __forceinline__ Cell locate_q(float fx, float fy, float fz, const Geo
 // slot for an odd one.
 // YF = 2: either copy, chosen at run time through the element strides sx, sy
 // (+1 voxel along x, y) and szp (+1 slice pair); the index equals that of
-// YF = 0 or 1 for the same copy.
+// YF = 0 or 1 for the same copy.  YF = 3: the bricked copy (vb_n).
 template <int YF = 0>
 __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo& g, int sx = 0, int sy = 0,
                                         int szp = 0) {
@@ -248,7 +248,10 @@ __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo&
   c.ax = fx - (float)ix;
   c.ay = fy - (float)iy;
   c.az = fz - (float)iz;
-  if (YF == 2)
+  if (YF == 3)
+    c.idx = ((((iz >> 2) * vb_n(g.ny) + (iy >> 2)) * vb_n(g.nx) + (ix >> 2)) << 7) + (iz & 3) * 25 + (iy & 3) * 5 +
+            (ix & 3);
+  else if (YF == 2)
     c.idx = (iz >> 1) * szp + ix * sx + iy * sy + (iz & 1);
   else
     c.idx = YF ? ((((iz >> 1) * g.rqx + ix) * g.rqy + iy) << 1) + (iz & 1)
@@ -518,7 +521,9 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
     // element strides of +1 voxel along x, y, z in the marched copy
     const bool yf = YF == 2 ? yf_rt : YF == 1;
     const bool cell_test = occ.cells && (!occ.cells_flag || __ldg(occ.cells_flag));
-    const int sx = yf ? 2 * g.rqy : 2, sy = yf ? 2 : 2 * g.qx, szp = yf ? 2 * g.rqx * g.rqy : 2 * g.qx * g.qy;
+    // bricked copy: the corners sit at +1, +5, +25 inside the cell's brick
+    const int sx = YF == 3 ? 1 : (yf ? 2 * g.rqy : 2), sy = YF == 3 ? 5 : (yf ? 2 : 2 * g.qx);
+    const int szp = yf ? 2 * g.rqx * g.rqy : 2 * g.qx * g.qy;
     const float ox = g.cx + 2.0f, oy = g.cy + 2.0f, oz = g.cz + 2.0f;
     for (int k = r.k0; k <= r.k1; ++k) {
       const float kf = (float)k;
@@ -526,7 +531,7 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
       const Cell c = locate2<YF>(fx, fy, fz, g, sx, sy, szp);
       if (cell_test && !cell_live(occ, c.cx, c.cy, c.cz)) continue;
       const float4* p0 = vol + c.idx;
-      const int sz = (c.idx & 1) ? szp - 1 : 1;
+      const int sz = YF == 3 ? 25 : ((c.idx & 1) ? szp - 1 : 1);
       const float4 v000 = __ldg(p0), v100 = __ldg(p0 + sx);
       const float4 v010 = __ldg(p0 + sy), v110 = __ldg(p0 + sy + sx);
       const float4 v001 = __ldg(p0 + sz), v101 = __ldg(p0 + sz + sx);
@@ -653,6 +658,42 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
     march_tile<LOSS, WU, 0>(inst, n, tile, n_tiles, tiles_u, g, vol, ref, proj, part, red, occ);
 }
 
+// The fused march over the bricked copy (PROJ_FLAG_BRICKS), 4 x 8-pixel warps.
+template <int LOSS>
+__global__ void __launch_bounds__(kMarchThreads, 4)
+    k_forward_grad_bricks(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g,
+                          const float4* __restrict__ volb, const float* __restrict__ ref, float* __restrict__ proj,
+                          float* __restrict__ part, PoseList L, Occ occ) {
+  __shared__ float red[kMarchThreads / 32][kRec];
+  int n, tile;
+  if (L.list) {
+    if (!listed_tile(L, n_tiles, tiles_u, n, tile)) return;  // uniform per block
+  } else {
+    band_major_tile(n_tiles, tiles_u, n, tile);
+  }
+  march_tile<LOSS, 4, 3>(inst, n, tile, n_tiles, tiles_u, g, volb, ref, proj, part, red, occ);
+}
+
+// Bricked copy: one thread per element of a brick (128 per brick, 125 used);
+// element (i, j, k) of brick (bx, by, bz) is element (4 bx + i, 4 by + j,
+// 4 bz + k) of the pitched, pair-interleaved copy, zero outside it.
+__global__ void k_volume_bricks(const float4* __restrict__ vol4, Geo g, float4* __restrict__ volb) {
+  const int bnx = vb_n(g.nx), bny = vb_n(g.ny);
+  const long long n = (long long)bnx * bny * vb_n(g.nz) * kVbElems;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(p & (kVbElems - 1));
+    const long long b = p >> 7;
+    const int bx = (int)(b % bnx), by = (int)((b / bnx) % bny), bz = (int)(b / ((long long)bnx * bny));
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e < 125) {
+      const int x = 4 * bx + e % 5, y = 4 * by + (e / 5) % 5, z = 4 * bz + e / 25;
+      if (x < g.qx && y < g.qy && z < g.qz) v = __ldg(vol4 + ((((size_t)(z >> 1) * g.qy + y) * g.qx + x) << 1) + (z & 1));
+    }
+    volb[p] = v;
+  }
+}
+
 // ---------------------------------------------------------------- gather probe
 //
 // The fused march's memory access pattern without its arithmetic: the same
@@ -676,14 +717,15 @@ __device__ __forceinline__ float probe_ray(const InstTable& T, const Geo& g, int
   if (!(T.valid && ray_setup_m<2>(T, g, iu, iv, r))) return acc;
   if (occ.map && !occ_clip(occ, r.ax, r.ay, r.az, r.dx, r.dy, r.dz, 0, g.nx + 2, g.ny + 2, g.nz + 2, r.k0, r.k1))
     return acc;
-  const int sx = YF ? 2 * g.rqy : 2, sy = YF ? 2 : 2 * g.qx, szp = YF ? 2 * g.rqx * g.rqy : 2 * g.qx * g.qy;
+  const int sx = YF == 3 ? 1 : (YF ? 2 * g.rqy : 2), sy = YF == 3 ? 5 : (YF ? 2 : 2 * g.qx);
+  const int szp = YF ? 2 * g.rqx * g.rqy : 2 * g.qx * g.qy;
   const bool cell_test = occ.cells && (!occ.cells_flag || __ldg(occ.cells_flag));
   for (int k = r.k0; k <= r.k1; ++k) {
     const float kf = (float)k;
     const Cell c = locate2<YF>(fmaf(kf, r.dx, r.ax), fmaf(kf, r.dy, r.ay), fmaf(kf, r.dz, r.az), g);
     if (cell_test && !cell_live(occ, c.cx, c.cy, c.cz)) continue;
     const float4* p0 = vol + c.idx;
-    const int sz = (c.idx & 1) ? szp - 1 : 1;
+    const int sz = YF == 3 ? 25 : ((c.idx & 1) ? szp - 1 : 1);
     acc += ld_probe(p0) + ld_probe(p0 + sx) + ld_probe(p0 + sy) + ld_probe(p0 + sy + sx) + ld_probe(p0 + sz) +
            ld_probe(p0 + sz + sx) + ld_probe(p0 + sz + sy) + ld_probe(p0 + sz + sy + sx);
   }
@@ -692,15 +734,17 @@ __device__ __forceinline__ float probe_ray(const InstTable& T, const Geo& g, int
 
 __global__ void __launch_bounds__(kMarchThreads, 4)
     k_gather_probe(const InstTable* __restrict__ inst, int n_tiles, int tiles_u, Geo g, const float4* __restrict__ vol,
-                   const float4* __restrict__ voly, float* __restrict__ sink, Occ occ) {
+                   const float4* __restrict__ voly, float* __restrict__ sink, Occ occ,
+                   const float4* __restrict__ volb) {
   int n, tile;
   band_major_tile(n_tiles, tiles_u, n, tile);  // the fused march's block order
   int iu, iv;
   const bool on = tile_pixel<4>(tile, tiles_u, g, iu, iv);
   float acc = 0.f;
   if (on)
-    acc = (voly && inst[n].yfast) ? probe_ray<1>(inst[n], g, iu, iv, voly, occ)
-                                  : probe_ray<0>(inst[n], g, iu, iv, vol, occ);
+    acc = volb ? probe_ray<3>(inst[n], g, iu, iv, volb, occ)
+               : ((voly && inst[n].yfast) ? probe_ray<1>(inst[n], g, iu, iv, voly, occ)
+                                          : probe_ray<0>(inst[n], g, iu, iv, vol, occ));
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0 && acc == 1.2345e-30f) sink[0] = acc;  // keeps the loads live; never taken in practice
 }
@@ -973,6 +1017,12 @@ cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float
   return cudaGetLastError();
 }
 
+cudaError_t launch_volume_bricks(const float4* d_vol4, Geo geo, float4* d_volb, cudaStream_t s) {
+  k_volume_bricks<<<elementwise_grid((long long)vb_n(geo.nx) * vb_n(geo.ny) * vb_n(geo.nz) * kVbElems), 256, 0, s>>>(
+      d_vol4, geo, d_volb);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cell_bits(const unsigned* d_nbits, Geo geo, unsigned* d_cells, const unsigned char* d_occ8,
                              void* d_stat, cudaStream_t s) {
   unsigned long long* live = static_cast<unsigned long long*>(d_stat);
@@ -1027,7 +1077,7 @@ void launch_forward_grad_w(const InstTable* d_inst, int grid, int nt, int tu, co
 
 cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
                                 const float4* d_vol4y, int loss, const float* d_ref, float* d_proj, float* d_part,
-                                cudaStream_t s, int warp_width, const PoseList* pl, Occ occ) {
+                                cudaStream_t s, int warp_width, const PoseList* pl, Occ occ, const float4* d_volb) {
   const int nt = tiles_of(geo), tu = tiles_u_of(geo);
   PoseList L{};
   if (pl && pl->list) L = *pl;
@@ -1035,6 +1085,18 @@ cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, co
   if (grid_ll < 1) return cudaSuccess;
   if (grid_ll > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   const int grid = (int)grid_ll;
+  if (d_volb) {
+    if (loss == PROJ_LOSS_RESIDUAL)
+      k_forward_grad_bricks<PROJ_LOSS_RESIDUAL><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_volb, d_ref,
+                                                                               d_proj, d_part, L, occ);
+    else if (loss == PROJ_LOSS_L2)
+      k_forward_grad_bricks<PROJ_LOSS_L2><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_volb, d_ref, d_proj,
+                                                                         d_part, L, occ);
+    else
+      k_forward_grad_bricks<PROJ_LOSS_NCC><<<grid, kMarchThreads, 0, s>>>(d_inst, nt, tu, geo, d_volb, d_ref, d_proj,
+                                                                          d_part, L, occ);
+    return cudaGetLastError();
+  }
   switch (warp_width) {
     case 2: launch_forward_grad_w<2>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, L, occ, s); break;
     case 8: launch_forward_grad_w<8>(d_inst, grid, nt, tu, geo, d_vol4, d_vol4y, loss, d_ref, d_proj, d_part, L, occ, s); break;
@@ -1047,10 +1109,10 @@ cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, co
 }
 
 cudaError_t launch_gather_probe(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
-                                const float4* d_vol4y, float* d_sink, cudaStream_t s, Occ occ) {
+                                const float4* d_vol4y, float* d_sink, cudaStream_t s, Occ occ, const float4* d_volb) {
   const int nt = tiles_of(geo);
   k_gather_probe<<<n_inst * nt, kMarchThreads, 0, s>>>(d_inst, nt, tiles_u_of(geo), geo, d_vol4, d_vol4y, d_sink,
-                                                       occ);
+                                                       occ, d_volb);
   return cudaGetLastError();
 }
 

@@ -184,12 +184,23 @@ cudaError_t launch_count(const InstTable* d_inst, int n_inst, Geo geo, long long
 // warp_width: rays per warp row of the 16x16 tile (2, 4, 8 or 16; other values use 4)
 // d_vol4y: the y-fast copy (instances with yfast set march it), or null (all march d_vol4)
 // pl: optional pose subset (nullptr or pl->list == nullptr: all n_inst instances)
+// d_volb: the bricked copy (PROJ_FLAG_BRICKS); when given, every instance marches it with 4 x 8 warps
 cudaError_t launch_forward_grad(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
                                 const float4* d_vol4y, int loss, const float* d_ref, float* d_proj, float* d_part,
-                                cudaStream_t s, int warp_width = 4, const PoseList* pl = nullptr, Occ occ = Occ{});
+                                cudaStream_t s, int warp_width = 4, const PoseList* pl = nullptr, Occ occ = Occ{},
+                                const float4* d_volb = nullptr);
 // the fused march's gathers without its arithmetic (empirical gather ceiling)
 cudaError_t launch_gather_probe(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_vol4,
-                                const float4* d_vol4y, float* d_sink, cudaStream_t s, Occ occ = Occ{});
+                                const float4* d_vol4y, float* d_sink, cudaStream_t s, Occ occ = Occ{},
+                                const float4* d_volb = nullptr);
+// Bricked (mu, grad mu) volume (PROJ_FLAG_BRICKS): bricks of 4^3 cells of the 2-voxel-bordered grid, each
+// holding the 5^3 elements at its cells' corners (a one-element apron on the upper faces, so the 8 corners
+// of any cell sit at fixed offsets +1, +5, +25 from its lower corner), padded to 128 float4 (2 KB); brick
+// (bx, by, bz) starts at element ((bz * vb_n(ny) + by) * vb_n(nx) + bx) * 128 and holds element (i, j, k)
+// (0..4 each) at k * 25 + j * 5 + i.
+__host__ __device__ constexpr int vb_n(int n) { return (n + 6) >> 2; }  // ceil((n + 3) / 4) bricks per axis
+constexpr int kVbElems = 128;
+cudaError_t launch_volume_bricks(const float4* d_vol4, Geo geo, float4* d_volb, cudaStream_t s);
 // y-fast copy of the pitched (mu, grad mu) volume (tiled transpose of every z slice)
 cudaError_t launch_volume_yfast(const float4* d_vol4, Geo geo, float4* d_vol4y, cudaStream_t s);
 cudaError_t launch_records_yfast(const float4* d_volq, Geo geo, float4* d_volqy, cudaStream_t s);

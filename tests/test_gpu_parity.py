@@ -396,3 +396,44 @@ def test_one_copy_plan_gives_identical_results(ragged):
         np.testing.assert_array_equal(np32(l1), np32(l2))
     np.testing.assert_array_equal(np32(P1.forward(poses)), np32(P2.forward(poses)))
     assert rel_l2(np32(P1.forward(poses)), oracle.forward(g, mu, poses, iv, ip)) <= TOL_IMG
+
+
+@pytest.mark.parametrize("edge", [0, 8])
+def test_bricked_plan_gives_identical_results(ragged, edge):
+    """PROJ_FLAG_BRICKS marches a copy of the prepared volume stored in 4^3-cell
+    bricks with a one-element apron: the same corner values and fractions in
+    the same order, so pose gradients, losses, projections and pose-list calls
+    equal the row-layout plan's bit for bit, with and without skipping, and
+    the gradients stay within the oracle bars."""
+    d = ragged
+    g, mu, poses, iv, ip = d["g"], d["mu"], d["poses"], d["iv"], d["ip"]
+    target = f32(oracle.forward(g, mu, f32([[1.0, -1.0, 0.5, 0.05, -0.02, 0.03]]), inst_view=[0, 1, 2],
+                                inst_pose=[0, 0, 0]))
+    ops = pb.PROJ_OP_FORWARD | pb.PROJ_OP_FORWARD_GRAD
+    P2 = pb.Projector(g, n_pose=2, inst_view=iv, inst_pose=ip, ops=ops)
+    PB = pb.Projector(g, n_pose=2, inst_view=iv, inst_pose=ip, ops=ops | pb.PROJ_FLAG_BRICKS)
+    for P in (PB, P2):
+        pb.proj_set_skip_brick(P.plan, edge)
+        P.set_volume(mu)
+    resid = f32(np.random.default_rng(7).standard_normal((len(iv), g.nv, g.nu)))
+    for loss, ref in ((pb.PROJ_LOSS_L2, target), (pb.PROJ_LOSS_NCC, target), (pb.PROJ_LOSS_RESIDUAL, resid)):
+        gb, lb, pr_b = PB.forward_pose_grad(poses, loss, ref, want_proj=True)
+        g2, l2, pr_2 = P2.forward_pose_grad(poses, loss, ref, want_proj=True)
+        np.testing.assert_array_equal(np32(gb), np32(g2))
+        np.testing.assert_array_equal(np32(lb), np32(l2))
+        np.testing.assert_array_equal(np32(pr_b), np32(pr_2))
+    # a pose list (second pose only) on the bricked plan
+    pose_d = torch.from_numpy(np.asarray(poses, dtype=np.float32)).cuda()
+    tgt = torch.from_numpy(np.asarray(target, dtype=np.float32)).cuda()
+    gl = torch.zeros((2, 6), device="cuda")
+    ll = torch.zeros((2,), device="cuda")
+    pb.proj_forward_pose_grad_list(PB.plan, pose_d, torch.tensor([1], dtype=torch.int32, device="cuda"),
+                                   pb.PROJ_LOSS_L2, tgt, gl, ll, None, PB.ws)
+    g2, _ = P2.forward_pose_grad(poses, pb.PROJ_LOSS_L2, target)
+    assert torch.equal(gl[1], g2[1].cuda())
+    _, w = oracle.pose_loss_weights("l2", oracle.forward(g, mu, poses, iv, ip), target, iv, ip, 2)
+    gref, _ = oracle.forward_grad(g, mu, poses, w, iv, ip, mode=oracle.GRAD_ANALYTIC)
+    gb, _ = PB.forward_pose_grad(poses, pb.PROJ_LOSS_L2, target)
+    for p in range(2):
+        for blk in (slice(0, 3), slice(3, 6)):
+            assert rel_l2(np32(gb)[p, blk], gref[p, blk]) <= TOL_GRAD
