@@ -18,10 +18,6 @@ namespace {
 
 __device__ __forceinline__ float lerp(float a, float b, float t) { return fmaf(t, b - a, a); }
 
-__device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t) {
-  return make_float4(lerp(a.x, b.x, t), lerp(a.y, b.y, t), lerp(a.z, b.z, t), lerp(a.w, b.w, t));
-}
-
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -144,19 +140,17 @@ __device__ __forceinline__ bool occ_bricks_clip(const Occ& o, float ax, float ay
       t_last = t_out;
     }
     if (t_out > t1) break;
-    if (tx <= ty && tx <= tz) {
-      bx += stx;
-      tx += ix;
-      if ((unsigned)bx >= (unsigned)o.nb[0]) break;
-    } else if (ty <= tz) {
-      by += sty;
-      ty += iy;
-      if ((unsigned)by >= (unsigned)o.nb[1]) break;
-    } else {
-      bz += stz;
-      tz += iz;
-      if ((unsigned)bz >= (unsigned)o.nb[2]) break;
-    }
+    // step along the axis whose face comes first (x on ties, then y), without branches, so the
+    // lanes of a warp stepping along different axes run the same instructions
+    const bool ax_x = tx <= ty && tx <= tz, ax_y = !ax_x && ty <= tz, ax_z = !ax_x && !ax_y;
+    bx += ax_x ? stx : 0;
+    by += ax_y ? sty : 0;
+    bz += ax_z ? stz : 0;
+    tx += ax_x ? ix : 0.f;
+    ty += ax_y ? iy : 0.f;
+    tz += ax_z ? iz : 0.f;
+    if ((unsigned)bx >= (unsigned)o.nb[0] || (unsigned)by >= (unsigned)o.nb[1] || (unsigned)bz >= (unsigned)o.nb[2])
+      break;
     t_in = t_out;
   }
   if (!found) return false;
@@ -516,15 +510,22 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
   float s0[3] = {0.f, 0.f, 0.f};
   float s1[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   Ray r;
-  if (on_det && T.valid && ray_setup_m<2>(T, g, iu, iv, r) &&
-      (!occ.map || occ_clip(occ, r.ax, r.ay, r.az, r.dx, r.dy, r.dz, 0, g.nx + 2, g.ny + 2, g.nz + 2, r.k0, r.k1))) {
+  bool live = on_det && T.valid && ray_setup_m<2>(T, g, iu, iv, r);
+  // samples are numbered from the box entry kb whatever the skipping, so every kept sample's terms are
+  // the same with skipping on or off
+  const int kb = live ? r.k0 : 0;
+  if (live && occ.map)
+    live = occ_clip(occ, r.ax, r.ay, r.az, r.dx, r.dy, r.dz, 0, g.nx + 2, g.ny + 2, g.nz + 2, r.k0, r.k1);
+  if (live) {
     // element strides of +1 voxel along x, y, z in the marched copy
     const bool yf = YF == 2 ? yf_rt : YF == 1;
     const bool cell_test = occ.cells && (!occ.cells_flag || __ldg(occ.cells_flag));
     // bricked copy: the corners sit at +1, +5, +25 inside the cell's brick
     const int sx = YF == 3 ? 1 : (yf ? 2 * g.rqy : 2), sy = YF == 3 ? 5 : (yf ? 2 : 2 * g.qx);
     const int szp = yf ? 2 * g.rqx * g.rqy : 2 * g.qx * g.qy;
-    const float ox = g.cx + 2.0f, oy = g.cy + 2.0f, oz = g.cz + 2.0f;
+    const float kbf = (float)kb;
+    // sum_k g f~_k with f~_k = f~_kb + (k - kb) D: accumulate sum g and sum (k - kb) g, combine at the end
+    float t[3] = {0.f, 0.f, 0.f};
     for (int k = r.k0; k <= r.k1; ++k) {
       const float kf = (float)k;
       const float fx = fmaf(kf, r.dx, r.ax), fy = fmaf(kf, r.dy, r.ay), fz = fmaf(kf, r.dz, r.az);
@@ -536,23 +537,43 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
       const float4 v010 = __ldg(p0 + sy), v110 = __ldg(p0 + sy + sx);
       const float4 v001 = __ldg(p0 + sz), v101 = __ldg(p0 + sz + sx);
       const float4 v011 = __ldg(p0 + sz + sy), v111 = __ldg(p0 + sz + sy + sx);
-      const float4 c0 = lerp4(lerp4(v000, v100, c.ax), lerp4(v010, v110, c.ax), c.ay);
-      const float4 c1 = lerp4(lerp4(v001, v101, c.ax), lerp4(v011, v111, c.ax), c.ay);
-      const float4 v = lerp4(c0, c1, c.az);
-      const float cx = fx - ox, cy = fy - oy, cz = fz - oz;
-      a += v.x;
-      s0[0] += v.y;
-      s0[1] += v.z;
-      s0[2] += v.w;
-      s1[0] = fmaf(v.y, cx, s1[0]);
-      s1[1] = fmaf(v.y, cy, s1[1]);
-      s1[2] = fmaf(v.y, cz, s1[2]);
-      s1[3] = fmaf(v.z, cx, s1[3]);
-      s1[4] = fmaf(v.z, cy, s1[4]);
-      s1[5] = fmaf(v.z, cz, s1[5]);
-      s1[6] = fmaf(v.w, cx, s1[6]);
-      s1[7] = fmaf(v.w, cy, s1[7]);
-      s1[8] = fmaf(v.w, cz, s1[8]);
+      // trilinear weights once per sample, then 8 FMAs per channel
+      const float bx = 1.f - c.ax, by = 1.f - c.ay, bz = 1.f - c.az;
+      const float w00 = bx * by, w10 = c.ax * by, w01 = bx * c.ay, w11 = c.ax * c.ay;
+      const float q000 = w00 * bz, q100 = w10 * bz, q010 = w01 * bz, q110 = w11 * bz;
+      const float q001 = w00 * c.az, q101 = w10 * c.az, q011 = w01 * c.az, q111 = w11 * c.az;
+      auto tri = [&](float e000, float e100, float e010, float e110, float e001, float e101, float e011,
+                     float e111) {
+        float v = q000 * e000;
+        v = fmaf(q100, e100, v);
+        v = fmaf(q010, e010, v);
+        v = fmaf(q110, e110, v);
+        v = fmaf(q001, e001, v);
+        v = fmaf(q101, e101, v);
+        v = fmaf(q011, e011, v);
+        return fmaf(q111, e111, v);
+      };
+      const float vm = tri(v000.x, v100.x, v010.x, v110.x, v001.x, v101.x, v011.x, v111.x);
+      const float gx = tri(v000.y, v100.y, v010.y, v110.y, v001.y, v101.y, v011.y, v111.y);
+      const float gy = tri(v000.z, v100.z, v010.z, v110.z, v001.z, v101.z, v011.z, v111.z);
+      const float gz = tri(v000.w, v100.w, v010.w, v110.w, v001.w, v101.w, v011.w, v111.w);
+      const float j = kf - kbf;  // exact: |k| < 2^24
+      a += vm;
+      s0[0] += gx;
+      s0[1] += gy;
+      s0[2] += gz;
+      t[0] = fmaf(gx, j, t[0]);
+      t[1] = fmaf(gy, j, t[1]);
+      t[2] = fmaf(gz, j, t[2]);
+    }
+    // centred index coordinates of sample kb
+    const float fbx = fmaf(kbf, r.dx, r.ax) - (g.cx + 2.0f), fby = fmaf(kbf, r.dy, r.ay) - (g.cy + 2.0f),
+                fbz = fmaf(kbf, r.dz, r.az) - (g.cz + 2.0f);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      s1[3 * b + 0] = fmaf(r.dx, t[b], fbx * s0[b]);
+      s1[3 * b + 1] = fmaf(r.dy, t[b], fby * s0[b]);
+      s1[3 * b + 2] = fmaf(r.dz, t[b], fbz * s0[b]);
     }
   }
   const float l = g.step * a;
