@@ -111,6 +111,73 @@ def instance_maps(n_cand, n_views):
 
 # ------------------------------------------------------------------ clocks
 
+class NvmlClockSampler:
+    """SM clock, power and clock-event reasons read through NVML (the driver's
+    libnvidia-ml, called with ctypes) every 10 ms in a thread during the timed
+    region: read-only queries, so short timed regions still get many samples.
+    Same summary as ClockSampler."""
+
+    # clock-event reason bits of nvmlDeviceGetCurrentClocksEventReasons (nvml.h)
+    BITS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20, "sw_power_cap": 0x4}
+
+    def __init__(self, torch_device):
+        import ctypes
+        import threading
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.lib, self.ct = lib, ctypes
+        prop = __import__("torch").cuda.get_device_properties(torch_device)
+        h = ctypes.c_void_p()
+        bus = b"%08x:%02x:%02x.0" % (prop.pci_domain_id, prop.pci_bus_id, prop.pci_device_id)
+        if lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(h)) != 0:
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(torch_device.index or 0), ctypes.byref(h)) != 0:
+                raise OSError("no NVML handle")
+        self.h = h
+        self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx)) != 0:  # 1 = NVML_CLOCK_SM
+            raise OSError("nvmlDeviceGetMaxClockInfo failed")
+        self.smax = float(mx.value)
+        self.rows, self.stop = [], threading.Event()
+        self.thread = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        ct, lib, h = self.ct, self.lib, self.h
+        sm, pw, rs = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        while not self.stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(h, ct.c_int(1), ct.byref(sm)) == 0 and
+                    lib.nvmlDeviceGetPowerUsage(h, ct.byref(pw)) == 0 and self.reasons_fn(h, ct.byref(rs)) == 0):
+                self.rows.append((float(sm.value), pw.value / 1000.0, int(rs.value)))
+            self.stop.wait(0.01)
+
+    def __enter__(self):
+        self.thread.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop.set()
+        self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": self.smax, "reasons": ["no samples"]}
+        sm = [r[0] for r in self.rows]
+        hot = [x for x in sm if x > 0.3 * self.smax] or sm
+        reasons = sorted({k for r in self.rows for k, b in self.BITS.items() if r[2] & b})
+        return {"sm_mhz": statistics.median(hot), "sm_max_mhz": self.smax, "reasons": reasons,
+                "samples": len(self.rows), "power_w_max": max(r[1] for r in self.rows), "sampler": "nvml, 10 ms"}
+
+
+def clock_sampler(torch_device, index):
+    """NVML sampler when pynvml works, else nvidia-smi."""
+    try:
+        return NvmlClockSampler(torch_device)
+    except Exception:
+        return ClockSampler(index)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
 
@@ -1106,7 +1173,7 @@ def main():
         pb.proj_forward_pose_grad(P.plan, pose_d, pb.PROJ_LOSS_NCC, target_d, grad_d, loss_d, None, P.ws)
 
     stream = torch.cuda.current_stream()
-    clocks = ClockSampler(local).__enter__()
+    clocks = clock_sampler(dev, local).__enter__()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
