@@ -214,7 +214,8 @@ __device__ __forceinline__ bool cell_live(const Occ& o, int cx, int cy, int cz) 
 // [0, n] (1-voxel border) or [0, n + 2] (2-voxel border) so the 8 corners
 // stay inside the padded array; fractions are taken from the clamped corner
 // so that a point marginally outside the box (rounding) interpolates
-// towards the zero border.
+// towards the zero border.  The lower clamp comes with the conversion: a
+// float-to-unsigned conversion saturates, so a negative coordinate gives 0.
 struct Cell {
   int idx;
   float ax, ay, az;
@@ -222,9 +223,9 @@ struct Cell {
 };
 
 __device__ __forceinline__ Cell locate(float fx, float fy, float fz, const Geo& g) {
-  const int ix = min(max(__float2int_rd(fx), 0), g.nx);
-  const int iy = min(max(__float2int_rd(fy), 0), g.ny);
-  const int iz = min(max(__float2int_rd(fz), 0), g.nz);
+  const int ix = (int)min(__float2uint_rd(fx), (unsigned)(g.nx));
+  const int iy = (int)min(__float2uint_rd(fy), (unsigned)(g.ny));
+  const int iz = (int)min(__float2uint_rd(fz), (unsigned)(g.nz));
   Cell c;
   c.ax = fx - (float)ix;
   c.ay = fy - (float)iy;
@@ -240,9 +241,9 @@ __device__ __forceinline__ Cell locate(float fx, float fy, float fz, const Geo& 
 // along y), z slices interleaved in pairs as in the (mu, grad mu) volumes.
 template <int YF>
 __device__ __forceinline__ Cell locate_q(float fx, float fy, float fz, const Geo& g) {
-  const int ix = min(max(__float2int_rd(fx), 0), g.nx);
-  const int iy = min(max(__float2int_rd(fy), 0), g.ny);
-  const int iz = min(max(__float2int_rd(fz), 0), g.nz);
+  const int ix = (int)min(__float2uint_rd(fx), (unsigned)(g.nx));
+  const int iy = (int)min(__float2uint_rd(fy), (unsigned)(g.ny));
+  const int iz = (int)min(__float2uint_rd(fz), (unsigned)(g.nz));
   Cell c;
   c.ax = fx - (float)ix;
   c.ay = fy - (float)iy;
@@ -267,9 +268,9 @@ __device__ __forceinline__ Cell locate_q(float fx, float fy, float fz, const Geo
 template <int YF = 0>
 __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo& g, int sx = 0, int sy = 0,
                                         int szp = 0) {
-  const int ix = min(max(__float2int_rd(fx), 0), g.nx + 2);
-  const int iy = min(max(__float2int_rd(fy), 0), g.ny + 2);
-  const int iz = min(max(__float2int_rd(fz), 0), g.nz + 2);
+  const int ix = (int)min(__float2uint_rd(fx), (unsigned)(g.nx + 2));
+  const int iy = (int)min(__float2uint_rd(fy), (unsigned)(g.ny + 2));
+  const int iz = (int)min(__float2uint_rd(fz), (unsigned)(g.nz + 2));
   Cell c;
   c.ax = fx - (float)ix;
   c.ay = fy - (float)iy;
