@@ -81,6 +81,36 @@ __device__ __forceinline__ void red_add4(float4* p, float a, float b, float c, f
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
 
+// Projection of the voxel-driven back-projection pair (k_back and its exact
+// transpose k_back_adjoint share it): per instance and voxel column, the
+// homogeneous pixel coordinates with 2 added to u and v (up = u + 2, vp = v +
+// 2, folded into the instance's matrix), so that a voxel inside the image's
+// bilinear support (u in (-1, nu), v in (-1, nv)) has up, vp in (1, n + 2).
+__device__ __forceinline__ void bp_shifted(const InstTable& T, float fx, float fy, float& bu, float& bv, float& bw,
+                                           float& qz0, float& qz1, float& qz2) {
+  bw = fmaf(T.Q[5], fy, fmaf(T.Q[2], fx, T.Q[11]));
+  bu = fmaf(2.f, bw, fmaf(T.Q[3], fy, fmaf(T.Q[0], fx, T.Q[9])));
+  bv = fmaf(2.f, bw, fmaf(T.Q[4], fy, fmaf(T.Q[1], fx, T.Q[10])));
+  qz2 = T.Q[8];
+  qz0 = fmaf(2.f, qz2, T.Q[6]);
+  qz1 = fmaf(2.f, qz2, T.Q[7]);
+}
+
+// Detector cell record of (up, vp) in (1, n + 2): (floor(u) + 1, floor(v) + 1)
+// and the bilinear fractions, without float-int conversions: for 1 <= x <
+// 2^22 the sum x + (2^23 - 1/2) lies in [2^23, 2^24), where FP32 spacing is 1,
+// so it rounds to 2^23 + RN(x - 1/2), whose low mantissa bits are floor(x)
+// (floor(x) - 1 with fraction 1 at integers: the same bilinear value).  The
+// record index is then (bits(tv) - 2^23's bits - 1) * ru + (bits(tu) - ... -
+// 1), folded into koff.  __fadd_rn keeps the sum from being contracted with
+// the product that formed up.
+__device__ __forceinline__ unsigned bp_record(float up, float vp, unsigned ru, unsigned koff, float& au, float& av) {
+  const float tu = __fadd_rn(up, 8388607.5f), tv = __fadd_rn(vp, 8388607.5f);
+  au = up - (tu - 8388608.f);
+  av = vp - (tv - 8388608.f);
+  return __float_as_uint(tv) * ru + __float_as_uint(tu) - koff;
+}
+
 // ---------------------------------------------------------------- K5
 
 __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict__ inst, int n_inst, Geo g,
@@ -94,14 +124,14 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
   float acc[kZChunk];
 #pragma unroll
   for (int z = 0; z < kZChunk; ++z) acc[z] = 0.f;
-  const float fu = (float)g.nu, fvv = (float)g.nv;
+  const float ulim = (float)g.nu + 2.f, vlim = (float)g.nv + 2.f;
+  const unsigned ru = (unsigned)g.nu + 1u, koff = (0x4B000000u + 1u) * (ru + 1u);
   for (int n = 0; n < n_inst; ++n) {
     const InstTable& T = inst[n];
     if (!T.valid) continue;
-    const float bu = fmaf(T.Q[3], fy, fmaf(T.Q[0], fx, T.Q[9]));
-    const float bv = fmaf(T.Q[4], fy, fmaf(T.Q[1], fx, T.Q[10]));
-    const float bw = fmaf(T.Q[5], fy, fmaf(T.Q[2], fx, T.Q[11]));
-    const float qz0 = T.Q[6], qz1 = T.Q[7], qz2 = T.Q[8], w0 = T.w0;
+    float bu, bv, bw, qz0, qz1, qz2;
+    bp_shifted(T, fx, fy, bu, bv, bw, qz0, qz1, qz2);
+    const float w0 = T.w0;
     const float4* rec = detq + (size_t)n * (g.nu + 1) * (g.nv + 1);
 #pragma unroll
     for (int z = 0; z < kZChunk; ++z) {
@@ -109,14 +139,12 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
       const float hw = fmaf(qz2, fz, bw);
       if (!(hw > 0.f)) continue;
       const float rw = __fdividef(1.0f, hw);  // fast reciprocal (about 2 ulp), the same in k_back and k_back_adjoint
-      const float u = fmaf(qz0, fz, bu) * rw, v = fmaf(qz1, fz, bv) * rw;
-      if (!(u > -1.f && u < fu && v > -1.f && v < fvv)) continue;
-      // u in (-1, nu) and v in (-1, nv): the lower corner is in [-1, n-1],
-      // record (i0 + 1, j0 + 1)
-      const float flu = floorf(u), flv = floorf(v);
-      const int i0 = (int)flu, j0 = (int)flv;
-      const float au = u - flu, av = v - flv;
-      const float4 q = __ldg(rec + (j0 + 1) * (g.nu + 1) + (i0 + 1));
+      const float up = fmaf(qz0, fz, bu) * rw, vp = fmaf(qz1, fz, bv) * rw;
+      // u = up - 2 in (-1, nu) and v = vp - 2 in (-1, nv): record (floor(u) + 1, floor(v) + 1)
+      if (!(up > 1.f && up < ulim && vp > 1.f && vp < vlim)) continue;
+      float au, av;
+      const unsigned r = bp_record(up, vp, ru, koff, au, av);
+      const float4 q = __ldg(rec + r);
       float val = lerp(lerp(q.x, q.y, au), lerp(q.z, q.w, au), av);
       if (weight != PROJ_W_NONE) {
         const float r = w0 * rw;
@@ -376,26 +404,25 @@ __global__ void __launch_bounds__(kBpThreads) k_back_adjoint(const InstTable* __
 #pragma unroll
   for (int z = 0; z < kZChunk; ++z)
     yv[z] = (iz0 + z < g.nz) ? __ldg(y + ((size_t)(iz0 + z) * g.ny + iy) * g.nx + ix) : 0.f;
-  const float fu = (float)g.nu, fvv = (float)g.nv;
+  const float ulim = (float)g.nu + 2.f, vlim = (float)g.nv + 2.f;
+  const unsigned ru = (unsigned)g.nu + 1u, koff = (0x4B000000u + 1u) * (ru + 1u);
   for (int n = 0; n < n_inst; ++n) {
     const InstTable& T = inst[n];
     if (!T.valid) continue;
-    const float bu = fmaf(T.Q[3], fy, fmaf(T.Q[0], fx, T.Q[9]));
-    const float bv = fmaf(T.Q[4], fy, fmaf(T.Q[1], fx, T.Q[10]));
-    const float bw = fmaf(T.Q[5], fy, fmaf(T.Q[2], fx, T.Q[11]));
+    float bu, bv, bw, qz0, qz1, qz2;
+    bp_shifted(T, fx, fy, bu, bv, bw, qz0, qz1, qz2);
     float4* rec = detq + (size_t)n * (g.nu + 1) * (g.nv + 1);
 #pragma unroll
     for (int z = 0; z < kZChunk; ++z) {
       if (yv[z] == 0.f) continue;
       const float fz = (float)(iz0 + z) - g.cz;
-      const float hw = fmaf(T.Q[8], fz, bw);
+      const float hw = fmaf(qz2, fz, bw);
       if (!(hw > 0.f)) continue;
       const float rw = __fdividef(1.0f, hw);  // fast reciprocal (about 2 ulp), the same in k_back and k_back_adjoint
-      const float u = fmaf(T.Q[6], fz, bu) * rw, v = fmaf(T.Q[7], fz, bv) * rw;
-      if (!(u > -1.f && u < fu && v > -1.f && v < fvv)) continue;
-      const float flu = floorf(u), flv = floorf(v);
-      const int i0 = (int)flu, j0 = (int)flv;
-      const float au = u - flu, av = v - flv;
+      const float up = fmaf(qz0, fz, bu) * rw, vp = fmaf(qz1, fz, bv) * rw;
+      if (!(up > 1.f && up < ulim && vp > 1.f && vp < vlim)) continue;
+      float au, av;
+      const unsigned r = bp_record(up, vp, ru, koff, au, av);
       float val = yv[z];
       if (weight != PROJ_W_NONE) {
         const float r = T.w0 * rw;
@@ -404,8 +431,7 @@ __global__ void __launch_bounds__(kBpThreads) k_back_adjoint(const InstTable* __
       // the 4 corner weights go to record (i0 + 1, j0 + 1) in one vector
       // reduction; weights of corners outside the image land in border lanes
       // that k_detector_unrecord never reads
-      red_add4(rec + (j0 + 1) * (g.nu + 1) + (i0 + 1), val * (1.f - au) * (1.f - av), val * au * (1.f - av),
-               val * (1.f - au) * av, val * au * av);
+      red_add4(rec + r, val * (1.f - au) * (1.f - av), val * au * (1.f - av), val * (1.f - au) * av, val * au * av);
     }
   }
 }
