@@ -349,33 +349,6 @@ __global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ m
   }
 }
 
-// Occupancy bricks (Occ): one thread per voxel; a non-zero voxel (i, j, k)
-// is a non-zero corner of the bordered-grid cells i .. i+3 (its mu and the
-// central differences on both sides), which with the one-cell apron marks
-// the bricks holding cells i-1 .. i+4 along each axis.  Every writer stores
-// the same value 1, so the unordered stores need no atomics.
-__device__ __forceinline__ void occ_mark(unsigned char* map, int sh, int nb0, int nb1, int x0, int x1, int y0, int y1,
-                                         int z0, int z1) {
-  for (int bz = z0 >> sh; bz <= (z1 >> sh); ++bz)
-    for (int by = y0 >> sh; by <= (y1 >> sh); ++by)
-      for (int bx = x0 >> sh; bx <= (x1 >> sh); ++bx) map[(bz * nb1 + by) * nb0 + bx] = 1;
-}
-
-__global__ void k_occupancy(const float* __restrict__ mu, Geo g, unsigned char* __restrict__ occ8,
-                            unsigned char* __restrict__ occ16) {
-  const long long n = (long long)g.nx * g.ny * g.nz;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
-    if (__ldg(mu + p) == 0.f) continue;
-    const int i = (int)(p % g.nx), j = (int)((p / g.nx) % g.ny), k = (int)(p / ((long long)g.nx * g.ny));
-    const int x0 = max(i - 1, 0), x1 = min(i + 4, g.nx + 2);
-    const int y0 = max(j - 1, 0), y1 = min(j + 4, g.ny + 2);
-    const int z0 = max(k - 1, 0), z1 = min(k + 4, g.nz + 2);
-    if (occ8) occ_mark(occ8, 3, occ_bricks(g.nx, 3), occ_bricks(g.ny, 3), x0, x1, y0, y1, z0, z1);
-    if (occ16) occ_mark(occ16, 4, occ_bricks(g.nx, 4), occ_bricks(g.ny, 4), x0, x1, y0, y1, z0, z1);
-  }
-}
-
 // Cell map (Occ::cells): cell (x, y, z) of the 2-voxel-bordered grid has
 // corners x..x+1, y..y+1, z..z+1, so its bit is the OR of the non-zero bits
 // of those 8 elements: the OR of 4 rows (y, z pairs), then of bits x and x+1.
@@ -406,33 +379,71 @@ __global__ void k_cell_bits(const unsigned* __restrict__ nb, Geo g, unsigned* __
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(live, (unsigned long long)cnt);
 }
 
+// Occupancy bricks (Occ) from the cell map: a brick of 8^3 cells is marked
+// when a cell within one cell of it, i.e. in [8 b - 1, 8 b + 8] per axis
+// (clipped to the grid), has a non-zero corner.  One warp per brick: its
+// lanes take the (y, z) rows of that range (at most 100), each ORs the one or
+// two map words the x range touches, and the warp votes.  For the automatic
+// cell test the warps also add up the grid cells of the marked bricks
+// (bricks on the far faces hold fewer than 512) into cell_stat[1].
+__global__ void k_brick_maps8(const unsigned* __restrict__ cells, Geo g, unsigned char* __restrict__ occ8,
+                              unsigned long long* __restrict__ cell_stat) {
+  const int cw = cell_words(g.nx), ch = g.ny + 3;
+  const int ex = g.nx + 3, ey = g.ny + 3, ez = g.nz + 3;  // cells per axis
+  const int nb0 = occ_bricks(g.nx, 3), nb1 = occ_bricks(g.ny, 3);
+  const int n8 = nb0 * nb1 * occ_bricks(g.nz, 3);
+  const int lane = threadIdx.x & 31;
+  unsigned long long counted = 0;
+  for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < n8; b += (gridDim.x * blockDim.x) >> 5) {
+    const int bx = b % nb0, by = (b / nb0) % nb1, bz = b / (nb0 * nb1);
+    const int x0 = max(8 * bx - 1, 0), x1 = min(8 * bx + 8, ex - 1);
+    const int y0 = max(8 * by - 1, 0), y1 = min(8 * by + 8, ey - 1);
+    const int z0 = max(8 * bz - 1, 0), z1 = min(8 * bz + 8, ez - 1);
+    const int w0 = x0 >> 5, w1 = x1 >> 5;
+    // bits x0 .. x1 of the words w0 .. w1 (at most two words: the range spans <= 10 cells)
+    const unsigned m0 = (~0u << (x0 & 31)) & (w0 == w1 ? (~0u >> (31 - (x1 & 31))) : ~0u);
+    const unsigned m1 = w0 == w1 ? 0u : (~0u >> (31 - (x1 & 31)));
+    const int ny = y1 - y0 + 1, nrows = ny * (z1 - z0 + 1);
+    unsigned any = 0;
+    for (int r = lane; r < nrows; r += 32) {
+      const unsigned* row = cells + ((size_t)(z0 + r / ny) * ch + (y0 + r % ny)) * cw;
+      any |= (__ldg(row + w0) & m0) | (m1 ? (__ldg(row + w1) & m1) : 0u);
+    }
+    const bool marked = __any_sync(0xffffffffu, any != 0);
+    if (lane == 0) {
+      occ8[b] = marked ? 1 : 0;
+      if (marked) counted += (unsigned long long)min(8, ex - 8 * bx) * min(8, ey - 8 * by) * min(8, ez - 8 * bz);
+    }
+  }
+  if (lane == 0 && counted && cell_stat) atomicAdd(cell_stat + 1, counted);
+}
+
+// The 16^3 map from the 8^3 one: a 16^3 brick's cells within one cell,
+// [16 B - 1, 16 B + 16], are exactly those of its eight 8^3 sub-bricks' ranges
+// ([8 b - 1, 8 b + 8] for b = 2 B, 2 B + 1 per axis), so it is marked when
+// one of them is (sub-bricks past the grid do not exist and count as empty).
+__global__ void k_brick_maps16(const unsigned char* __restrict__ occ8, Geo g, unsigned char* __restrict__ occ16) {
+  const int a0 = occ_bricks(g.nx, 3), a1 = occ_bricks(g.ny, 3), a2 = occ_bricks(g.nz, 3);
+  const int nb0 = occ_bricks(g.nx, 4), nb1 = occ_bricks(g.ny, 4);
+  const int n16 = nb0 * nb1 * occ_bricks(g.nz, 4);
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n16; b += gridDim.x * blockDim.x) {
+    const int bx = b % nb0, by = (b / nb0) % nb1, bz = b / (nb0 * nb1);
+    unsigned char m = 0;
+    for (int k = 2 * bz; k <= min(2 * bz + 1, a2 - 1); ++k)
+      for (int j = 2 * by; j <= min(2 * by + 1, a1 - 1); ++j)
+        for (int i = 2 * bx; i <= min(2 * bx + 1, a0 - 1); ++i) m |= occ8[(k * a1 + j) * a0 + i];
+    occ16[b] = m ? 1 : 0;
+  }
+}
+
 // Automatic cell test: the cell map pays off when a fair share of the cells
 // inside the occupied 8^3 bricks has no non-zero corner (samples there are
 // left out); on a dense volume every test is spent for nothing (measured: a
-// uniformly filled volume marches about 12 % slower with the test).  One
-// block counts the grid cells of the occupied bricks (bricks on the grid's
-// far faces hold fewer than 512) and sets the flag when the live cells are at
-// most 85 % of them.
-__global__ void k_cell_decide(const unsigned char* __restrict__ occ8, Geo g, const unsigned long long* __restrict__ live,
-                              int* __restrict__ flag) {
-  __shared__ unsigned long long part[32];
-  const int ex = g.nx + 3, ey = g.ny + 3, ez = g.nz + 3;  // cells per axis
-  const int nb0 = occ_bricks(g.nx, 3), nb1 = occ_bricks(g.ny, 3), nb2 = occ_bricks(g.nz, 3);
-  unsigned long long c = 0;
-  for (int b = threadIdx.x; b < nb0 * nb1 * nb2; b += blockDim.x) {
-    if (!occ8[b]) continue;
-    const int bx = b % nb0, by = (b / nb0) % nb1, bz = b / (nb0 * nb1);
-    c += (unsigned long long)min(8, ex - 8 * bx) * min(8, ey - 8 * by) * min(8, ez - 8 * bz);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long cells = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) cells += part[w];
-    *flag = (double)*live <= 0.85 * (double)cells ? 1 : 0;
-  }
+// uniformly filled volume marches about 12 % slower with the test).  The
+// flag is set when the live cells (cell_stat[0], k_cell_bits) are at most
+// 85 % of the grid cells of the occupied bricks (cell_stat[1], k_brick_maps).
+__global__ void k_cell_decide(const unsigned long long* __restrict__ cell_stat, int* __restrict__ flag) {
+  if (threadIdx.x == 0) *flag = (double)cell_stat[0] <= 0.85 * (double)cell_stat[1] ? 1 : 0;
 }
 
 // ---------------------------------------------------------------- K2
@@ -853,12 +864,13 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
 // Per pose: sum the tile records of each of its instances in FP64 (fixed
 // order), apply the loss, convert the accumulator sums to dL/dM and
 // contract with dM/dtheta.
-__global__ void k_forward_grad_reduce(const InstTable* __restrict__ inst, const PoseTable* __restrict__ ptab,
+constexpr int kReduceThreads = 512;
+__global__ void __launch_bounds__(kReduceThreads) k_forward_grad_reduce(const InstTable* __restrict__ inst, const PoseTable* __restrict__ ptab,
                                       const int* __restrict__ pose_ptr, const int* __restrict__ pose_idx,
                                       int n_tiles, Geo g, int loss, const float* __restrict__ part,
                                       float* __restrict__ grad, float* __restrict__ loss_out,
                                       const int* __restrict__ pose_list, int n_pose) {
-  constexpr int kGroups = 5;
+  constexpr int kGroups = kReduceThreads / kRec;  // 10 groups of tiles summed side by side
   __shared__ double sp[kGroups][kRec];
   __shared__ double rec[kRec];
   const int p = pose_list ? pose_list[blockIdx.x] : (int)blockIdx.x;
@@ -1043,20 +1055,6 @@ int elementwise_grid(long long n) {
 
 }  // namespace
 
-cudaError_t launch_occupancy(const float* d_mu, Geo geo, unsigned char* d_occ8, unsigned char* d_occ16,
-                             cudaStream_t s) {
-  cudaError_t e = cudaSuccess;
-  if (d_occ8)
-    e = cudaMemsetAsync(d_occ8, 0,
-                        (size_t)occ_bricks(geo.nx, 3) * occ_bricks(geo.ny, 3) * occ_bricks(geo.nz, 3), s);
-  if (e == cudaSuccess && d_occ16)
-    e = cudaMemsetAsync(d_occ16, 0,
-                        (size_t)occ_bricks(geo.nx, 4) * occ_bricks(geo.ny, 4) * occ_bricks(geo.nz, 4), s);
-  if (e != cudaSuccess) return e;
-  k_occupancy<<<elementwise_grid((long long)geo.nx * geo.ny * geo.nz), 256, 0, s>>>(d_mu, geo, d_occ8, d_occ16);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float4* d_vol4, cudaStream_t s,
                                unsigned* d_nbits) {
   // the pitched extents (qx, qy, qz) exceed the 1-padded ones (n + 2) in every axis; blockIdx.x is the
@@ -1072,16 +1070,28 @@ cudaError_t launch_volume_bricks(const float4* d_vol4, Geo geo, float4* d_volb, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_cell_bits(const unsigned* d_nbits, Geo geo, unsigned* d_cells, const unsigned char* d_occ8,
-                             void* d_stat, cudaStream_t s) {
-  unsigned long long* live = static_cast<unsigned long long*>(d_stat);
+cudaError_t launch_cell_bits(const unsigned* d_nbits, Geo geo, unsigned* d_cells, unsigned char* d_occ8,
+                             unsigned char* d_occ16, void* d_stat, cudaStream_t s) {
+  unsigned long long* stat = static_cast<unsigned long long*>(d_stat);
   cudaError_t e = cudaMemsetAsync(d_stat, 0, kCellStatBytes, s);
   if (e != cudaSuccess) return e;
   k_cell_bits<<<elementwise_grid((long long)cell_words(geo.nx) * (geo.ny + 3) * (geo.nz + 3)), 256, 0, s>>>(
-      d_nbits, geo, d_cells, live);
+      d_nbits, geo, d_cells, stat);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_cell_decide<<<1, 1024, 0, s>>>(d_occ8, geo, live, const_cast<int*>(cell_flag_of(d_stat)));
+  if (d_occ8) {
+    const long long n8 = (long long)occ_bricks(geo.nx, 3) * occ_bricks(geo.ny, 3) * occ_bricks(geo.nz, 3);
+    k_brick_maps8<<<elementwise_grid(32 * n8), 256, 0, s>>>(d_cells, geo, d_occ8, stat);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (d_occ16) {
+      const long long n16 = (long long)occ_bricks(geo.nx, 4) * occ_bricks(geo.ny, 4) * occ_bricks(geo.nz, 4);
+      k_brick_maps16<<<elementwise_grid(n16), 256, 0, s>>>(d_occ8, geo, d_occ16);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  k_cell_decide<<<1, 32, 0, s>>>(stat, const_cast<int*>(cell_flag_of(d_stat)));
   return cudaGetLastError();
 }
 
@@ -1250,7 +1260,7 @@ cudaError_t launch_forward_grad_reduce(const InstTable* d_inst, const PoseTable*
                                        cudaStream_t s, const int* d_pose_list, int n_list) {
   const int blocks = d_pose_list ? n_list : n_pose;
   if (blocks < 1) return cudaSuccess;
-  k_forward_grad_reduce<<<blocks, 256, 0, s>>>(d_inst, d_ptab, d_pose_ptr, d_pose_idx, n_tiles, geo, loss, d_part,
+  k_forward_grad_reduce<<<blocks, kReduceThreads, 0, s>>>(d_inst, d_ptab, d_pose_ptr, d_pose_idx, n_tiles, geo, loss, d_part,
                                                d_grad, d_loss, d_pose_list, n_pose);
   return cudaGetLastError();
 }

@@ -162,17 +162,15 @@ cudaError_t launch_setup(const float* d_pose, int n_pose, const double* d_views,
 // d_nbits (optional): the non-zero bits of (mu, grad mu), [qz][qy][nbits_words(qx)] words
 cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float4* d_vol4, cudaStream_t s,
                                unsigned* d_nbits = nullptr);
-// the cell map, [nz + 3][ny + 3][cell_words(nx)] words, from the non-zero bits; d_stat (2 counters and
+// the cell map, [nz + 3][ny + 3][cell_words(nx)] words, from the non-zero bits, then from it the
+// occupancy bricks of both edges (8 and 16 cells; either map may be null); d_stat (2 counters and
 // the flag, kCellStatBytes) receives the decision of the automatic cell test (see k_cell_decide)
 constexpr int kCellStatBytes = 32;
-cudaError_t launch_cell_bits(const unsigned* d_nbits, Geo geo, unsigned* d_cells, const unsigned char* d_occ8,
-                             void* d_stat, cudaStream_t s);
+cudaError_t launch_cell_bits(const unsigned* d_nbits, Geo geo, unsigned* d_cells, unsigned char* d_occ8,
+                             unsigned char* d_occ16, void* d_stat, cudaStream_t s);
 __host__ __device__ inline const int* cell_flag_of(const void* d_stat) {
   return reinterpret_cast<const int*>(static_cast<const char*>(d_stat) + 16);
 }
-// occupancy bricks of both edges (8 and 16 cells) for the volume d_mu; either map may be null
-cudaError_t launch_occupancy(const float* d_mu, Geo geo, unsigned char* d_occ8, unsigned char* d_occ16,
-                             cudaStream_t s);
 // d_volqy: the copy of the cell records with rows along y (instances with yfast
 // set march it), or null (all march d_volq)
 cudaError_t launch_forward(const InstTable* d_inst, int n_inst, Geo geo, const float4* d_volq, const float4* d_volqy,
