@@ -74,17 +74,16 @@ struct FdkView {
 // those of the 2-voxel-bordered (mu, grad mu) grid (lower corner 0 .. n + 2
 // per axis); a brick is 2^shift cells on a side.  Byte b of map is non-zero
 // when brick b holds, or lies within one cell of, a cell with a non-zero
-// corner in (mu, grad mu), i.e. a cell within 2..4 cells of a non-zero
-// voxel.  A sample whose cell has only zero corners adds exact zeros to every
-// sum of the marches, so a ray's samples before the first and after the last
-// occupied brick it crosses can be left out without changing any result.
+// corner in (mu, grad mu).  A sample whose cell has only zero corners adds
+// exact zeros to every sum of the marches, so a ray's samples before the
+// first and after the last occupied brick it crosses can be left out without
+// changing any result.
 //
-// Within the brick range each ray's ends are then narrowed sample by sample
-// with the cell map (cells): bit (x & 31) of word (z * ch + y) * cw + (x >> 5)
-// is set when cell (x, y, z) of the same grid has a non-zero corner in
-// (mu, grad mu).  The test uses the march's own FP32 position and cell of each
-// sample, so the samples it leaves out are exactly those that read eight zero
-// corners.
+// Inside that range the fused march tests each sample's own cell in the cell
+// map (cells): bit (x & 31) of word (z * ch + y) * cw + (x >> 5) is set when
+// cell (x, y, z) has a non-zero corner.  The test uses the march's own FP32
+// position and cell of the sample, so the samples whose gathers it leaves out
+// are exactly those that read eight zero corners.
 struct Occ {
   const unsigned char* map;  // nullptr: no skipping
   int shift;                 // 3 (8-cell bricks) or 4 (16-cell bricks)

@@ -168,6 +168,17 @@ def test_bad_ops_and_null_arguments(L):
     assert L.proj_set_brick_shape(None, 0) == pb.PROJ_E_ARG
     assert L.proj_get_brick_shape(None, None) == pb.PROJ_E_ARG
     assert L.proj_autotune_back_grad(None, None, None, 0, None, None, 0, None, 1, None, None) == pb.PROJ_E_ARG
+    assert L.proj_set_skip_brick(None, 8) == pb.PROJ_E_ARG
+    assert L.proj_get_skip_brick(None, None) == pb.PROJ_E_ARG
+    assert L.proj_set_skip_cells(None, 1) == pb.PROJ_E_ARG
+    assert L.proj_get_skip_cells(None, None) == pb.PROJ_E_ARG
+    assert L.proj_autotune_march(None, None, 0, None, None, 0, None, 1, None, None, None, None) == pb.PROJ_E_ARG
+    assert L.proj_count_marched_samples(None, None, None, None, 0, None) == pb.PROJ_E_ARG
+    # the option flags alone, or together, enable no operation
+    rc, _ = create(tiny_geom(), ops=pb.PROJ_FLAG_BRICKS | pb.PROJ_FLAG_ONE_COPY)
+    assert rc == pb.PROJ_E_ARG and "non-empty" in pb.proj_last_error()
+    rc, _ = create(tiny_geom(), ops=pb.PROJ_OP_FORWARD_GRAD | 1024)            # an unknown flag bit
+    assert rc == pb.PROJ_E_ARG
 
 
 def test_valid_plan_without_a_gpu_reports_a_cuda_error(L):

@@ -151,6 +151,18 @@ def test_automatic_cell_test_follows_the_volume():
     assert dense["auto"] == dense[8]               # ... but too few for the automatic test
 
 
+def test_skip_settings_reject_invalid_values():
+    g = small_geom(n=(12, 10, 14), det=(16, 12), n_views=1)
+    P = pb.Projector(g, n_pose=1, inst_view=np.zeros(1, np.int32), inst_pose=np.zeros(1, np.int32),
+                     ops=pb.PROJ_OP_FORWARD_GRAD)
+    L = pb.lib()
+    for bad in (-1, 4, 9, 32):
+        assert L.proj_set_skip_brick(P.plan.handle, bad) == pb.PROJ_E_ARG
+    for bad in (-1, 3):
+        assert L.proj_set_skip_cells(P.plan.handle, bad) == pb.PROJ_E_ARG
+    assert pb.proj_get_skip_brick(P.plan) == 8 and pb.proj_get_skip_cells(P.plan) == pb.SKIP_CELLS_AUTO
+
+
 def test_empty_volume_marches_nothing():
     rng = np.random.default_rng(3)
     g = small_geom(n=(20, 18, 22), det=(24, 20), n_views=2)
