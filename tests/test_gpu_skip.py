@@ -89,6 +89,7 @@ def check_exact(g, mu, poses, iv, ip, rng):
     assert counts[8, 2] in (counts[8, 0], counts[8, 1])
     out = {e: counts[e, 0] for e in EDGES} | {("cells", e): counts[e, 1] for e in EDGES}
     out["auto"] = counts[8, 2]
+    res[base]["target"] = target
     return res[base], out
 
 
@@ -103,6 +104,16 @@ def test_sparse_phantom_exact_and_against_the_oracle():
     assert counts[8] < 0.8 * counts[0]                 # the phantom leaves most samples in air
     ref = oracle.forward(g, mu.astype(np.float64), poses.astype(np.float64), iv, ip)
     assert np.linalg.norm(res["proj"] - ref) <= 1e-4 * np.linalg.norm(ref)
+    # the pose gradients (equal in every skipping mode) against the oracle's analytic gradient
+    target = res["target"].astype(np.float64)
+    for kind in ("l2", "ncc"):
+        _, w = oracle.pose_loss_weights(kind, ref, target, iv, ip, 2)
+        gth, _ = oracle.forward_grad(g, mu.astype(np.float64), poses.astype(np.float64), w, iv, ip,
+                                     mode=oracle.GRAD_ANALYTIC)
+        got = res[kind][0].astype(np.float64)
+        for p in range(2):
+            for blk in (slice(0, 3), slice(3, 6)):
+                assert np.linalg.norm(got[p, blk] - gth[p, blk]) <= 1e-3 * np.linalg.norm(gth[p, blk]), (kind, p)
 
 
 @pytest.mark.parametrize("seed", range(16))
