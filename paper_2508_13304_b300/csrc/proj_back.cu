@@ -145,7 +145,9 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
       float au, av;
       const unsigned r = bp_record(up, vp, ru, koff, au, av);
       const float4 q = __ldg(rec + r);
-      float val = lerp(lerp(q.x, q.y, au), lerp(q.z, q.w, au), av);
+      // the cell's two detector columns as a pair: lerp along v, then along u
+      const float2 e = lerp2(lo2(q), hi2(q), dup2(av));
+      float val = lerp(e.x, e.y, au);
       if (weight != PROJ_W_NONE) {
         const float r = w0 * rw;
         val *= r * r;

@@ -468,9 +468,10 @@ __device__ __forceinline__ float drr_ray(const InstTable& T, const Geo& g, int i
     const float kf = (float)k;
     const Cell c = locate_q<YF>(fmaf(kf, r.dx, r.ax), fmaf(kf, r.dy, r.ay), fmaf(kf, r.dz, r.az), g);
     const float4 f0 = __ldg(volq + c.idx), f1 = __ldg(volq + c.idx + ((c.idx & 1) ? szp - 1 : 1));
-    const float c0 = lerp(lerp(f0.x, f0.y, c.ax), lerp(f0.z, f0.w, c.ax), c.ay);
-    const float c1 = lerp(lerp(f1.x, f1.y, c.ax), lerp(f1.z, f1.w, c.ax), c.ay);
-    acc += lerp(c0, c1, c.az);
+    // the two x columns of the cell as a pair: lerp along y in each face, then along z, then along x
+    const float2 ty = dup2(c.ay);
+    const float2 e = lerp2(lerp2(lo2(f0), hi2(f0), ty), lerp2(lo2(f1), hi2(f1), ty), dup2(c.az));
+    acc += lerp(e.x, e.y, c.ax);
   }
   return acc;
 }
@@ -568,8 +569,10 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
     const int sx = YF == 3 ? 1 : (yf ? 2 * g.rqy : 2), sy = YF == 3 ? 5 : (yf ? 2 : 2 * g.qx);
     const int szp = yf ? 2 * g.rqx * g.rqy : 2 * g.qx * g.qy;
     const float kbf = (float)kb;
-    // sum_k g f~_k with f~_k = f~_kb + (k - kb) D: accumulate sum g and sum (k - kb) g, combine at the end
-    float t[3] = {0.f, 0.f, 0.f};
+    // sum_k g f~_k with f~_k = f~_kb + (k - kb) D: accumulate sum g and sum (k - kb) g, combine at the end.
+    // The four channels run as two pairs, (mu, g_x) and (g_y, g_z): sums (a, s0x), (s0y, s0z), and
+    // (-, tx), (ty, tz) (the first lane of the third pair accumulates mu (k - kb), unused).
+    float2 A01 = make_float2(0.f, 0.f), A23 = A01, T01 = A01, T23 = A01;
     for (int k = r.k0; k <= r.k1; ++k) {
       const float kf = (float)k;
       const float fx = fmaf(kf, r.dx, r.ax), fy = fmaf(kf, r.dy, r.ay), fz = fmaf(kf, r.dz, r.az);
@@ -581,35 +584,34 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
       const float4 v010 = __ldg(p0 + sy), v110 = __ldg(p0 + sy + sx);
       const float4 v001 = __ldg(p0 + sz), v101 = __ldg(p0 + sz + sx);
       const float4 v011 = __ldg(p0 + sz + sy), v111 = __ldg(p0 + sz + sy + sx);
-      // trilinear weights once per sample, then 8 FMAs per channel
+      // trilinear weights once per sample, then 8 two-wide FMAs per channel pair
       const float bx = 1.f - c.ax, by = 1.f - c.ay, bz = 1.f - c.az;
       const float w00 = bx * by, w10 = c.ax * by, w01 = bx * c.ay, w11 = c.ax * c.ay;
       const float q000 = w00 * bz, q100 = w10 * bz, q010 = w01 * bz, q110 = w11 * bz;
       const float q001 = w00 * c.az, q101 = w10 * c.az, q011 = w01 * c.az, q111 = w11 * c.az;
-      auto tri = [&](float e000, float e100, float e010, float e110, float e001, float e101, float e011,
-                     float e111) {
-        float v = q000 * e000;
-        v = fmaf(q100, e100, v);
-        v = fmaf(q010, e010, v);
-        v = fmaf(q110, e110, v);
-        v = fmaf(q001, e001, v);
-        v = fmaf(q101, e101, v);
-        v = fmaf(q011, e011, v);
-        return fmaf(q111, e111, v);
+      float2 pa = mul2(dup2(q000), lo2(v000)), pb = mul2(dup2(q000), hi2(v000));  // (mu, g_x), (g_y, g_z)
+      auto corner = [&](float q, const float4& v) {
+        pa = fma2(dup2(q), lo2(v), pa);
+        pb = fma2(dup2(q), hi2(v), pb);
       };
-      const float vm = tri(v000.x, v100.x, v010.x, v110.x, v001.x, v101.x, v011.x, v111.x);
-      const float gx = tri(v000.y, v100.y, v010.y, v110.y, v001.y, v101.y, v011.y, v111.y);
-      const float gy = tri(v000.z, v100.z, v010.z, v110.z, v001.z, v101.z, v011.z, v111.z);
-      const float gz = tri(v000.w, v100.w, v010.w, v110.w, v001.w, v101.w, v011.w, v111.w);
-      const float j = kf - kbf;  // exact: |k| < 2^24
-      a += vm;
-      s0[0] += gx;
-      s0[1] += gy;
-      s0[2] += gz;
-      t[0] = fmaf(gx, j, t[0]);
-      t[1] = fmaf(gy, j, t[1]);
-      t[2] = fmaf(gz, j, t[2]);
+      corner(q100, v100);
+      corner(q010, v010);
+      corner(q110, v110);
+      corner(q001, v001);
+      corner(q101, v101);
+      corner(q011, v011);
+      corner(q111, v111);
+      const float2 j = dup2(kf - kbf);  // exact: |k| < 2^24
+      A01 = add2(A01, pa);
+      A23 = add2(A23, pb);
+      T01 = fma2(pa, j, T01);
+      T23 = fma2(pb, j, T23);
     }
+    a = A01.x;
+    s0[0] = A01.y;
+    s0[1] = A23.x;
+    s0[2] = A23.y;
+    const float t[3] = {T01.y, T23.x, T23.y};
     // centred index coordinates of sample kb
     const float fbx = fmaf(kbf, r.dx, r.ax) - (g.cx + 2.0f), fby = fmaf(kbf, r.dy, r.ay) - (g.cy + 2.0f),
                 fbz = fmaf(kbf, r.dz, r.az) - (g.cz + 2.0f);

@@ -270,4 +270,28 @@ inline int back_grad_blocks(const Geo& g, int shape) {
   return ceil_div(g.nx, kGbX) * ceil_div(g.ny, kGbY) * ceil_div(g.nz, brick_gz(shape));
 }
 
+#ifdef __CUDACC__
+// Two-wide FP32 arithmetic: sm_100 and later issue the same operation on a
+// pair of 32-bit values as one instruction (PTX .f32x2).  The interpolating
+// kernels apply it to pairs of channels that one 16-byte load leaves in
+// adjacent registers.  Element by element the results are those of the
+// scalar forms: lerp2(a, b, t).x == fmaf(t.x, b.x - a.x, a.x), add2 and
+// mul2 are rounded adds and products, fma2 fused multiply-adds.
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float2 t) {
+  float2 r;
+  asm("{\n\t.reg .b64 ra, rb, rt, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rt, {%6, %7};\n\t"
+      "sub.rn.f32x2 rd, rb, ra;\n\tfma.rn.f32x2 rd, rt, rd, ra;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(t.x), "f"(t.y));
+  return r;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 dup2(float s) { return make_float2(s, s); }
+#endif
+
 }  // namespace projk
