@@ -53,16 +53,20 @@ __global__ void k_detector_prep(const float* __restrict__ proj, int n_inst, Geo 
 // the four pixels of the bilinear cell whose lower corner is pixel
 // (x-1, y-1), (l(x-1, y-1), l(x, y-1), l(x-1, y), l(x, y)), zero outside the
 // image, so a bilinear sample anywhere in (-1, nu) x (-1, nv) reads its 4
-// corners with one 128-bit load and no edge tests.
-__global__ void k_detector_records(const float* __restrict__ proj, Geo g, float4* __restrict__ detq) {
+// corners with one 128-bit load and no edge tests.  With the FDK weight the
+// records carry the instance's factor w0^2 of W = (w0 / w')^2 (k_back applies
+// the per-voxel 1 / w'^2).
+__global__ void k_detector_records(const float* __restrict__ proj, Geo g, const InstTable* __restrict__ inst,
+                                   int weight, float4* __restrict__ detq) {
   const int ru = g.nu + 1, rv = g.nv + 1;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, in = blockIdx.z;
   if (x >= ru) return;
   const int iu = x - 1, iv = y - 1;
   const float* img = proj + (size_t)in * g.nu * g.nv;
-  detq[((size_t)in * rv + y) * ru + x] = make_float4(pix(img, g.nu, g.nv, iu, iv), pix(img, g.nu, g.nv, iu + 1, iv),
-                                                     pix(img, g.nu, g.nv, iu, iv + 1),
-                                                     pix(img, g.nu, g.nv, iu + 1, iv + 1));
+  const float w0 = inst[in].w0, f = weight != PROJ_W_NONE ? w0 * w0 : 1.f;
+  detq[((size_t)in * rv + y) * ru + x] =
+      make_float4(f * pix(img, g.nu, g.nv, iu, iv), f * pix(img, g.nu, g.nv, iu + 1, iv),
+                  f * pix(img, g.nu, g.nv, iu, iv + 1), f * pix(img, g.nu, g.nv, iu + 1, iv + 1));
 }
 
 // Pixel (i, j) = lane 0 of record (i+1, j+1), lane 1 of (i, j+1), lane 2 of
@@ -124,14 +128,13 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
   float acc[kZChunk];
 #pragma unroll
   for (int z = 0; z < kZChunk; ++z) acc[z] = 0.f;
-  const float ulim = (float)g.nu + 2.f, vlim = (float)g.nv + 2.f;
-  const unsigned ru = (unsigned)g.nu + 1u, koff = (0x4B000000u + 1u) * (ru + 1u);
+  const unsigned ru = (unsigned)g.nu + 1u, nu = (unsigned)g.nu, nv = (unsigned)g.nv;
+  const bool fdk = weight != PROJ_W_NONE;
   for (int n = 0; n < n_inst; ++n) {
     const InstTable& T = inst[n];
     if (!T.valid) continue;
     float bu, bv, bw, qz0, qz1, qz2;
     bp_shifted(T, fx, fy, bu, bv, bw, qz0, qz1, qz2);
-    const float w0 = T.w0;
     const float4* rec = detq + (size_t)n * (g.nu + 1) * (g.nv + 1);
 #pragma unroll
     for (int z = 0; z < kZChunk; ++z) {
@@ -140,19 +143,21 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
       if (!(hw > 0.f)) continue;
       const float rw = __fdividef(1.0f, hw);  // fast reciprocal (about 2 ulp), the same in k_back and k_back_adjoint
       const float up = fmaf(qz0, fz, bu) * rw, vp = fmaf(qz1, fz, bv) * rw;
-      // u = up - 2 in (-1, nu) and v = vp - 2 in (-1, nv): record (floor(u) + 1, floor(v) + 1)
-      if (!(up > 1.f && up < ulim && vp > 1.f && vp < vlim)) continue;
-      float au, av;
-      const unsigned r = bp_record(up, vp, ru, koff, au, av);
-      const float4 q = __ldg(rec + r);
+      // record (i, j) = (floor(u) + 1, floor(v) + 1) of u = up - 2, v = vp - 2 as in bp_record, and the
+      // support test on it: i <= nu and j <= nv (unsigned) hold exactly when 1 < up < nu + 2 and
+      // 1 < vp < nv + 2, but for up = nu + 2 (or vp = nv + 2) when the sum rounds to even below, where
+      // the sample is the zero border pixel with weight 1 and adds +0; every up outside [1, 2^22),
+      // negative, infinite or NaN gives an index far above nu
+      const float tu = __fadd_rn(up, 8388607.5f), tv = __fadd_rn(vp, 8388607.5f);
+      const unsigned i = __float_as_uint(tu) - 0x4B000001u, j = __float_as_uint(tv) - 0x4B000001u;
+      if (i > nu || j > nv) continue;
+      const float au = up - (tu - 8388608.f), av = vp - (tv - 8388608.f);
+      const float4 q = __ldg(rec + j * ru + i);
       // the cell's two detector columns as a pair: lerp along v, then along u
       const float2 e = lerp2(lo2(q), hi2(q), dup2(av));
-      float val = lerp(e.x, e.y, au);
-      if (weight != PROJ_W_NONE) {
-        const float r = w0 * rw;
-        val *= r * r;
-      }
-      acc[z] += val;
+      const float val = lerp(e.x, e.y, au);
+      // FDK: the record holds w0^2 l, times 1 / w'^2 here
+      acc[z] = fdk ? fmaf(val, rw * rw, acc[z]) : acc[z] + val;
     }
   }
 #pragma unroll
@@ -449,7 +454,8 @@ cudaError_t launch_detector_prep(const float* d_proj, int n_inst, Geo geo, float
 
 cudaError_t launch_back(const InstTable* d_inst, int n_inst, Geo geo, int weight, const float* d_proj,
                         float4* d_detq, float* d_vol, cudaStream_t s) {
-  k_detector_records<<<dim3(ceil_div(geo.nu + 1, 128), geo.nv + 1, n_inst), 128, 0, s>>>(d_proj, geo, d_detq);
+  k_detector_records<<<dim3(ceil_div(geo.nu + 1, 128), geo.nv + 1, n_inst), 128, 0, s>>>(d_proj, geo, d_inst, weight,
+                                                                                          d_detq);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 grid(ceil_div(geo.nx, kBpX), ceil_div(geo.ny, kBpY), ceil_div(geo.nz, kZChunk));
