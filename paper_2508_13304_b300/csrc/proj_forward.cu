@@ -464,9 +464,12 @@ __device__ __forceinline__ float drr_ray(const InstTable& T, const Geo& g, int i
   if (occ.map && !occ_clip(occ, r.ax, r.ay, r.az, r.dx, r.dy, r.dz, 1, g.nx, g.ny, g.nz, r.k0, r.k1))
     return acc;
   const int szp = 2 * g.px * g.py;
-  for (int k = r.k0; k <= r.k1; ++k) {
-    const float kf = (float)k;
-    const Cell c = locate_q<YF>(fmaf(kf, r.dx, r.ax), fmaf(kf, r.dy, r.ay), fmaf(kf, r.dz, r.az), g);
+  // the sample index as a float pair (exact: |k| < 2^24): x and y of the position in one paired FMA
+  const float2 one = dup2(1.f), d01 = make_float2(r.dx, r.dy), a01 = make_float2(r.ax, r.ay);
+  float2 kk = dup2((float)r.k0);
+  for (int k = r.k0; k <= r.k1; ++k, kk = add2(kk, one)) {
+    const float2 f01 = fma2(kk, d01, a01);
+    const Cell c = locate_q<YF>(f01.x, f01.y, fmaf(kk.x, r.dz, r.az), g);
     const float4 f0 = __ldg(volq + c.idx), f1 = __ldg(volq + c.idx + ((c.idx & 1) ? szp - 1 : 1));
     // the two x columns of the cell as a pair: lerp along y in each face, then along z, then along x
     const float2 ty = dup2(c.ay);
@@ -573,10 +576,13 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
     // The four channels run as two pairs, (mu, g_x) and (g_y, g_z): sums (a, s0x), (s0y, s0z), and
     // (-, tx), (ty, tz) (the first lane of the third pair accumulates mu (k - kb), unused).
     float2 A01 = make_float2(0.f, 0.f), A23 = A01, T01 = A01, T23 = A01;
-    for (int k = r.k0; k <= r.k1; ++k) {
-      const float kf = (float)k;
-      const float fx = fmaf(kf, r.dx, r.ax), fy = fmaf(kf, r.dy, r.ay), fz = fmaf(kf, r.dz, r.az);
-      const Cell c = locate2<YF>(fx, fy, fz, g, sx, sy, szp);
+    // the sample index as a float pair (exact: |k| < 2^24), so that x and y of the position and k - kb
+    // come from paired instructions
+    const float2 one = dup2(1.f), d01 = make_float2(r.dx, r.dy), a01 = make_float2(r.ax, r.ay), nkb = dup2(-kbf);
+    float2 kk = dup2((float)r.k0);
+    for (int k = r.k0; k <= r.k1; ++k, kk = add2(kk, one)) {
+      const float2 f01 = fma2(kk, d01, a01);
+      const Cell c = locate2<YF>(f01.x, f01.y, fmaf(kk.x, r.dz, r.az), g, sx, sy, szp);
       if (cell_test && !cell_live(occ, c.cx, c.cy, c.cz)) continue;
       const float4* p0 = vol + c.idx;
       const int sz = YF == 3 ? 25 : ((c.idx & 1) ? szp - 1 : 1);
@@ -601,7 +607,7 @@ __device__ __forceinline__ void march_tile(const InstTable* __restrict__ inst, i
       corner(q101, v101);
       corner(q011, v011);
       corner(q111, v111);
-      const float2 j = dup2(kf - kbf);  // exact: |k| < 2^24
+      const float2 j = add2(kk, nkb);
       A01 = add2(A01, pa);
       A23 = add2(A23, pb);
       T01 = fma2(pa, j, T01);
