@@ -12,6 +12,8 @@
 // lines at the same bank slots) in the views where x runs along u.  Each
 // thread projects its voxels with the instance's 3x4 matrix Q (centred voxel
 // index -> (u',v',w')), one FMA chain per voxel.
+#include <cstddef>
+
 #include "proj_internal.cuh"
 
 namespace projk {
@@ -90,14 +92,21 @@ __device__ __forceinline__ void red_add4(float4* p, float a, float b, float c, f
 // homogeneous pixel coordinates with 2 added to u and v (up = u + 2, vp = v +
 // 2, folded into the instance's matrix), so that a voxel inside the image's
 // bilinear support (u in (-1, nu), v in (-1, nv)) has up, vp in (1, n + 2).
-__device__ __forceinline__ void bp_shifted(const InstTable& T, float fx, float fy, float& bu, float& bv, float& bw,
-                                           float& qz0, float& qz1, float& qz2) {
-  bw = fmaf(T.Q[5], fy, fmaf(T.Q[2], fx, T.Q[11]));
-  bu = fmaf(2.f, bw, fmaf(T.Q[3], fy, fmaf(T.Q[0], fx, T.Q[9])));
-  bv = fmaf(2.f, bw, fmaf(T.Q[4], fy, fmaf(T.Q[1], fx, T.Q[10])));
-  qz2 = T.Q[8];
-  qz0 = fmaf(2.f, qz2, T.Q[6]);
-  qz1 = fmaf(2.f, qz2, T.Q[7]);
+// Q is read as three 16-byte loads (the tables are 256-byte aligned arrays of 160-byte entries).
+static_assert(offsetof(InstTable, Q) % 16 == 0 && sizeof(InstTable) % 16 == 0, "InstTable::Q as float4");
+// The column's values are taken at the chunk's first voxel, centred index
+// fz0, so that voxel z of the chunk is (bu, bv, bw) + z (qz0, qz1, qz2).
+__device__ __forceinline__ void bp_shifted(const InstTable& T, float fx, float fy, float fz0, float& bu, float& bv,
+                                           float& bw, float& qz0, float& qz1, float& qz2) {
+  const float4* q = reinterpret_cast<const float4*>(T.Q);
+  const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);  // Q[0..3], Q[4..7], Q[8..11]
+  qz2 = c.x;
+  qz0 = fmaf(2.f, qz2, b.z);
+  qz1 = fmaf(2.f, qz2, b.w);
+  const float w = fmaf(b.y, fy, fmaf(a.z, fx, c.w));
+  bu = fmaf(qz0, fz0, fmaf(2.f, w, fmaf(a.w, fy, fmaf(a.x, fx, c.y))));
+  bv = fmaf(qz1, fz0, fmaf(2.f, w, fmaf(b.x, fy, fmaf(a.y, fx, c.z))));
+  bw = fmaf(qz2, fz0, w);
 }
 
 // Detector cell record of (up, vp) in (1, n + 2): (floor(u) + 1, floor(v) + 1)
@@ -124,7 +133,7 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
   const int iy = blockIdx.y * kBpY + col_y();
   const int iz0 = blockIdx.z * kZChunk;
   if (ix >= g.nx || iy >= g.ny) return;
-  const float fx = (float)ix - g.cx, fy = (float)iy - g.cy;
+  const float fx = (float)ix - g.cx, fy = (float)iy - g.cy, fz0 = (float)iz0 - g.cz;
   float acc[kZChunk];
 #pragma unroll
   for (int z = 0; z < kZChunk; ++z) acc[z] = 0.f;
@@ -134,11 +143,11 @@ __global__ void __launch_bounds__(kBpThreads) k_back(const InstTable* __restrict
     const InstTable& T = inst[n];
     if (!T.valid) continue;
     float bu, bv, bw, qz0, qz1, qz2;
-    bp_shifted(T, fx, fy, bu, bv, bw, qz0, qz1, qz2);
+    bp_shifted(T, fx, fy, fz0, bu, bv, bw, qz0, qz1, qz2);
     const float4* rec = detq + (size_t)n * (g.nu + 1) * (g.nv + 1);
 #pragma unroll
     for (int z = 0; z < kZChunk; ++z) {
-      const float fz = (float)(iz0 + z) - g.cz;
+      const float fz = (float)z;
       const float hw = fmaf(qz2, fz, bw);
       if (!(hw > 0.f)) continue;
       const float rw = __fdividef(1.0f, hw);  // fast reciprocal (about 2 ulp), the same in k_back and k_back_adjoint
@@ -406,7 +415,7 @@ __global__ void __launch_bounds__(kBpThreads) k_back_adjoint(const InstTable* __
   const int iy = blockIdx.y * kBpY + (threadIdx.x >> 5);
   const int iz0 = blockIdx.z * kZChunk;
   if (ix >= g.nx || iy >= g.ny) return;
-  const float fx = (float)ix - g.cx, fy = (float)iy - g.cy;
+  const float fx = (float)ix - g.cx, fy = (float)iy - g.cy, fz0 = (float)iz0 - g.cz;
   float yv[kZChunk];
 #pragma unroll
   for (int z = 0; z < kZChunk; ++z)
@@ -417,12 +426,12 @@ __global__ void __launch_bounds__(kBpThreads) k_back_adjoint(const InstTable* __
     const InstTable& T = inst[n];
     if (!T.valid) continue;
     float bu, bv, bw, qz0, qz1, qz2;
-    bp_shifted(T, fx, fy, bu, bv, bw, qz0, qz1, qz2);
+    bp_shifted(T, fx, fy, fz0, bu, bv, bw, qz0, qz1, qz2);
     float4* rec = detq + (size_t)n * (g.nu + 1) * (g.nv + 1);
 #pragma unroll
     for (int z = 0; z < kZChunk; ++z) {
       if (yv[z] == 0.f) continue;
-      const float fz = (float)(iz0 + z) - g.cz;
+      const float fz = (float)z;
       const float hw = fmaf(qz2, fz, bw);
       if (!(hw > 0.f)) continue;
       const float rw = __fdividef(1.0f, hw);  // fast reciprocal (about 2 ulp), the same in k_back and k_back_adjoint
