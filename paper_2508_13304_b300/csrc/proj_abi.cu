@@ -437,10 +437,9 @@ int proj_set_volume(proj_plan p, const float* d_mu, void* d_ws, size_t ws_bytes,
   int rc = check_ws(p, d_ws, ws_bytes, &w);
   if (rc) return rc;
   if ((rc = check_device(p))) return rc;
-  cudaError_t e = launch_volume_prep(d_mu, p->geo, w.volq, w.vol4, (cudaStream_t)stream, w.nbits);
+  cudaError_t e = launch_volume_prep(d_mu, p->geo, w.volq, w.vol4, (cudaStream_t)stream, w.nbits, w.vol4y);
   if (e == cudaSuccess && w.cells)
     e = launch_cell_bits(w.nbits, p->geo, w.cells, w.occ8, w.occ16, w.cstat, (cudaStream_t)stream);
-  if (e == cudaSuccess && w.vol4y) e = launch_volume_yfast(w.vol4, p->geo, w.vol4y, (cudaStream_t)stream);
   if (e == cudaSuccess && w.volb) e = launch_volume_bricks(w.vol4, p->geo, w.volb, (cudaStream_t)stream);
   if (e == cudaSuccess && w.volqy) e = launch_records_yfast(w.volq, p->geo, w.volqy, (cudaStream_t)stream);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "volume preparation launch");

@@ -10,6 +10,8 @@
 // sample index k and their 8-corner gathers share cache lines.  Samples are
 // anchored at world arc length k * step from the source (k integer), so a
 // projection is a continuous function of the pose.
+#include <algorithm>
+
 #include "proj_internal.cuh"
 
 namespace projk {
@@ -305,22 +307,31 @@ __device__ __forceinline__ Cell locate2(float fx, float fy, float fz, const Geo&
 // registers: every voxel of mu is read once from DRAM (the x and y
 // neighbours come from the slice the block just loaded, through L1).  The
 // same thread writes the volq cell whose base corner is its element, where
-// that falls inside volq's extent.
+// that falls inside volq's extent.  With vol4y the block also writes its tile
+// of the copy with rows along y: each z pair of the tile is staged in shared
+// memory and written as 32 runs of 16 elements (8 y x 2 slices, contiguous in
+// that copy), so the copy costs its writes only.
 constexpr int kPrepZChunk = 32;
 
 __global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ mu, Geo g, float4* __restrict__ volq,
-                                                     float4* __restrict__ vol4, unsigned* __restrict__ nbits) {
+                                                     float4* __restrict__ vol4, float4* __restrict__ vol4y,
+                                                     unsigned* __restrict__ nbits) {
+  // [y][slice of the pair][x]: the strides (66 and 33 float4) put the 8 elements that a quarter-warp
+  // reads in the write-out (4 y x 2 slices of one x) on distinct bank groups
+  __shared__ float4 stage[8][2][33];
   auto at = [&](int a, int b, int c) -> float {
     return (a >= 0 && a < g.nx && b >= 0 && b < g.ny && c >= 0 && c < g.nz)
                ? __ldg(mu + ((size_t)c * g.ny + b) * g.nx + a)
                : 0.0f;
   };
-  const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int x = blockIdx.x * 32 + tx, y = blockIdx.y * 8 + ty;
   const int z0 = blockIdx.z * kPrepZChunk, z1 = min(g.qz, z0 + kPrepZChunk);
   const int i = x - 2, j = y - 2;  // voxel column of this element
   const bool inq = x < g.qx && y < g.qy, in4 = vol4 && inq;
+  const bool iny = x < g.rqx && y < g.rqy;
   // nbits: each warp (32 consecutive x of one row y) stores one word per z: bit = element non-zero
-  const bool row_bits = nbits && y < g.qy;  // uniform per warp
+  const bool row_bits = nbits && y < g.qy && (int)blockIdx.x < nbits_words(g.qx);  // uniform per warp
   const int x1 = x - 1, y1 = y - 1;
   const bool in1xy = volq && x1 >= 0 && x1 < g.px && y1 >= 0 && y1 < g.py;
   float m_prev = at(i, j, z0 - 3), m = at(i, j, z0 - 2);
@@ -329,7 +340,7 @@ __global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ m
     const int k = z - 2;
     const float m_next = at(i, j, k + 1);
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (inq && (vol4 || nbits)) {
+    if ((inq && (vol4 || nbits)) || (vol4y && iny)) {
       v.x = m;
       v.y = (at(i + 1, j, k) - at(i - 1, j, k)) * sx;
       v.z = (at(i, j + 1, k) - at(i, j - 1, k)) * sy;
@@ -338,7 +349,21 @@ __global__ void __launch_bounds__(256) k_volume_prep(const float* __restrict__ m
     }
     if (row_bits) {
       const unsigned b = __ballot_sync(0xffffffffu, v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f);
-      if ((threadIdx.x & 31) == 0) nbits[((size_t)z * g.qy + y) * nbits_words(g.qx) + blockIdx.x] = b;
+      if (tx == 0) nbits[((size_t)z * g.qy + y) * nbits_words(g.qx) + blockIdx.x] = b;
+    }
+    if (vol4y) {  // uniform per block; z0 and z1 are even, so every pair is complete
+      stage[ty][z & 1][tx] = v;
+      if (z & 1) {
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int e = threadIdx.x + 256 * h, xl = e >> 4, yl = (e >> 1) & 7, zz = e & 1;
+          const int xo = blockIdx.x * 32 + xl, yo = blockIdx.y * 8 + yl;
+          if (xo < g.rqx && yo < g.rqy)
+            vol4y[((((size_t)(z >> 1) * g.rqx + xo) * g.rqy + yo) << 1) + zz] = stage[yl][zz][xl];
+        }
+        __syncthreads();  // the next pair overwrites the stage
+      }
     }
     const int zz1 = z - 1;
     if (in1xy && zz1 >= 0 && zz1 < g.pz)
@@ -1064,11 +1089,12 @@ int elementwise_grid(long long n) {
 }  // namespace
 
 cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float4* d_vol4, cudaStream_t s,
-                               unsigned* d_nbits) {
-  // the pitched extents (qx, qy, qz) exceed the 1-padded ones (n + 2) in every axis; blockIdx.x is the
-  // word of a row of the non-zero bits (nbits_words(qx) = the grid's x extent)
-  dim3 grid(ceil_div(geo.qx, 32), ceil_div(geo.qy, 8), ceil_div(geo.qz, kPrepZChunk));
-  k_volume_prep<<<grid, 256, 0, s>>>(d_mu, geo, d_volq, d_vol4, d_nbits);
+                               unsigned* d_nbits, float4* d_vol4y) {
+  // the pitched extents (qx, qy, qz) exceed the 1-padded ones (n + 2) in every axis, and with the y-fast
+  // copy the grid covers its pitches (rqx, rqy) too; blocks past nbits_words(qx) store no bits
+  const int X = d_vol4y ? std::max(geo.qx, geo.rqx) : geo.qx, Y = d_vol4y ? std::max(geo.qy, geo.rqy) : geo.qy;
+  dim3 grid(ceil_div(X, 32), ceil_div(Y, 8), ceil_div(geo.qz, kPrepZChunk));
+  k_volume_prep<<<grid, 256, 0, s>>>(d_mu, geo, d_volq, d_vol4, d_vol4y, d_nbits);
   return cudaGetLastError();
 }
 
@@ -1207,12 +1233,6 @@ __global__ void k_transpose_xy(const float4* __restrict__ v, int X, int Y, int s
   }
 }
 }  // namespace
-
-cudaError_t launch_volume_yfast(const float4* d_vol4, Geo geo, float4* d_vol4y, cudaStream_t s) {
-  dim3 grid(ceil_div(geo.rqx, kTr), ceil_div(geo.rqy, kTr), geo.qz), block(kTr, 8);
-  k_transpose_xy<<<grid, block, 0, s>>>(d_vol4, geo.nx + 4, geo.ny + 4, geo.qx, geo.qy, d_vol4y, geo.rqx, geo.rqy);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_records_yfast(const float4* d_volq, Geo geo, float4* d_volqy, cudaStream_t s) {
   dim3 grid(ceil_div(geo.px, kTr), ceil_div(geo.py, kTr), record_slices(geo.nz)), block(kTr, 8);

@@ -158,9 +158,10 @@ __host__ __device__ constexpr int brick_views(int shape) { return shape >= 2 ? 1
 cudaError_t launch_setup(const float* d_pose, int n_pose, const double* d_views, const int* d_inst_view,
                          const int* d_inst_pose, int n_inst, Geo geo, InstTable* d_inst, PoseTable* d_ptab,
                          int* d_status, cudaStream_t s);
-// d_nbits (optional): the non-zero bits of (mu, grad mu), [qz][qy][nbits_words(qx)] words
+// d_nbits (optional): the non-zero bits of (mu, grad mu), [qz][qy][nbits_words(qx)] words;
+// d_vol4y (optional): the copy of (mu, grad mu) with rows along y (pitches rqx, rqy)
 cudaError_t launch_volume_prep(const float* d_mu, Geo geo, float4* d_volq, float4* d_vol4, cudaStream_t s,
-                               unsigned* d_nbits = nullptr);
+                               unsigned* d_nbits = nullptr, float4* d_vol4y = nullptr);
 // the cell map, [nz + 3][ny + 3][cell_words(nx)] words, from the non-zero bits, then from it the
 // occupancy bricks of both edges (8 and 16 cells; either map may be null); d_stat (2 counters and
 // the flag, kCellStatBytes) receives the decision of the automatic cell test (see k_cell_decide)
@@ -198,8 +199,7 @@ cudaError_t launch_gather_probe(const InstTable* d_inst, int n_inst, Geo geo, co
 __host__ __device__ constexpr int vb_n(int n) { return (n + 6) >> 2; }  // ceil((n + 3) / 4) bricks per axis
 constexpr int kVbElems = 128;
 cudaError_t launch_volume_bricks(const float4* d_vol4, Geo geo, float4* d_volb, cudaStream_t s);
-// y-fast copy of the pitched (mu, grad mu) volume (tiled transpose of every z slice)
-cudaError_t launch_volume_yfast(const float4* d_vol4, Geo geo, float4* d_vol4y, cudaStream_t s);
+// copy of the DRR march's cell records with rows along y (tiled transpose of every z slice)
 cudaError_t launch_records_yfast(const float4* d_volq, Geo geo, float4* d_volqy, cudaStream_t s);
 // d_pose_list: optional [n_list] poses to reduce (-1 = skip); nullptr = all n_pose
 cudaError_t launch_forward_grad_reduce(const InstTable* d_inst, const PoseTable* d_ptab, int n_pose,
