@@ -353,7 +353,8 @@ __global__ void __launch_bounds__(kBpThreads, GZ <= 8 ? 4 : 3)
   }
 }
 
-// Per pose: FP64 sum over bricks (fixed order) of its instances' records,
+// Per pose: fixed-order sum over bricks of its instances' records (each of
+// 20 groups of bricks with the two-sum FP32 accumulation, the groups in FP64),
 // conversion to dL/dM and contraction with dM/dtheta.
 __global__ void k_back_grad_reduce(const PoseTable* __restrict__ ptab, const int* __restrict__ pose_ptr,
                                    const int* __restrict__ pose_idx, int n_inst, int n_blocks, Geo g,
@@ -368,9 +369,10 @@ __global__ void k_back_grad_reduce(const PoseTable* __restrict__ ptab, const int
     const int n = pose_idx[e];
     if (t < kGroups * 12) {
       const int q = t % 12, grp = t / 12;
-      double s = 0.0;
-      for (int b = grp; b < n_blocks; b += kGroups) s += (double)part[((size_t)n * n_blocks + b) * 12 + q];
-      sp[grp][q] = s;
+      float hi = 0.f, lo = 0.f;
+#pragma unroll 4
+      for (int b = grp; b < n_blocks; b += kGroups) sum2_add(hi, lo, part[((size_t)n * n_blocks + b) * 12 + q]);
+      sp[grp][q] = (double)hi + (double)lo;
     }
     __syncthreads();
     if (t < 12) {

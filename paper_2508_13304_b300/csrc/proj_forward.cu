@@ -894,9 +894,10 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
   }
 }
 
-// Per pose: sum the tile records of each of its instances in FP64 (fixed
-// order), apply the loss, convert the accumulator sums to dL/dM and
-// contract with dM/dtheta.
+// Per pose: sum the tile records of each of its instances in a fixed order
+// (each of 10 groups of tiles with the two-sum FP32 accumulation, the groups
+// and everything after in FP64), apply the loss, convert the accumulator sums
+// to dL/dM and contract with dM/dtheta.
 constexpr int kReduceThreads = 512;
 __global__ void __launch_bounds__(kReduceThreads) k_forward_grad_reduce(const InstTable* __restrict__ inst, const PoseTable* __restrict__ ptab,
                                       const int* __restrict__ pose_ptr, const int* __restrict__ pose_idx,
@@ -918,9 +919,10 @@ __global__ void __launch_bounds__(kReduceThreads) k_forward_grad_reduce(const In
     const int n = pose_idx[e];
     if (t < kGroups * kRec) {
       const int q = t % kRec, grp = t / kRec;
-      double s = 0.0;
-      for (int tile = grp; tile < n_tiles; tile += kGroups) s += (double)part[((size_t)n * n_tiles + tile) * kRec + q];
-      sp[grp][q] = s;
+      float hi = 0.f, lo = 0.f;
+#pragma unroll 4
+      for (int tile = grp; tile < n_tiles; tile += kGroups) sum2_add(hi, lo, part[((size_t)n * n_tiles + tile) * kRec + q]);
+      sp[grp][q] = (double)hi + (double)lo;
     }
     __syncthreads();
     if (t < kRec) {

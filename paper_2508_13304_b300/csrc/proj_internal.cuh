@@ -292,6 +292,18 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float2 dup2(float s) { return make_float2(s, s); }
+
+// Error-free FP32 accumulation (Knuth's two-sum): the running sum is hi + lo,
+// lo collecting the exact rounding error of every add, so a fixed-order sum
+// of FP32 values keeps about 48 significant bits.  The reductions use it in
+// place of FP64 adds, which run at a small fraction of the FP32 rate here.
+__device__ __forceinline__ void sum2_add(float& hi, float& lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
 #endif
 
 }  // namespace projk
