@@ -895,24 +895,25 @@ __global__ void __launch_bounds__(kMarchThreads, 4)
 }
 
 // Per pose: sum the tile records of each of its instances in a fixed order
-// (each of 10 groups of tiles with the two-sum FP32 accumulation, the groups
-// and everything after in FP64), apply the loss, convert the accumulator sums
-// to dL/dM and contract with dM/dtheta.
-constexpr int kReduceThreads = 512;
+// (each of 21 groups of tiles with the two-sum FP32 accumulation, the groups
+// and everything after in FP64), apply the loss (thread q < 12 keeps the sum
+// of component q), convert the accumulator sums to dL/dM and contract with
+// dM/dtheta.
+constexpr int kReduceThreads = 1024;
 __global__ void __launch_bounds__(kReduceThreads) k_forward_grad_reduce(const InstTable* __restrict__ inst, const PoseTable* __restrict__ ptab,
                                       const int* __restrict__ pose_ptr, const int* __restrict__ pose_idx,
                                       int n_tiles, Geo g, int loss, const float* __restrict__ part,
                                       float* __restrict__ grad, float* __restrict__ loss_out,
                                       const int* __restrict__ pose_list, int n_pose) {
-  constexpr int kGroups = kReduceThreads / kRec;  // 10 groups of tiles summed side by side
+  constexpr int kGroups = kReduceThreads / kRec;  // 21 groups of tiles summed side by side
   __shared__ double sp[kGroups][kRec];
   __shared__ double rec[kRec];
+  __shared__ double accs[12];
   const int p = pose_list ? pose_list[blockIdx.x] : (int)blockIdx.x;
   if (p < 0 || p >= n_pose) return;  // empty slot (or an index the march reported)
   const int t = threadIdx.x;
-  double acc[12];
-  double L = 0.0;
-  for (int q = 0; q < 12; ++q) acc[q] = 0.0;
+  double acc = 0.0;  // component t of the 12 (threads 0..11)
+  double L = 0.0;    // thread 0
   const int e0 = pose_ptr[p], e1 = pose_ptr[p + 1];
   const double np = (double)(e1 - e0);
   for (int e = e0; e < e1; ++e) {
@@ -931,7 +932,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_forward_grad_reduce(const In
       rec[t] = s;
     }
     __syncthreads();
-    if (t == 0 && inst[n].valid) {
+    // no barrier after this: the next instance writes sp, and rec only after its first barrier
+    if (t < 12 && inst[n].valid) {
       if (loss == PROJ_LOSS_NCC) {
         const double N = (double)g.nu * g.nv;
         const double ma = rec[kRecMom] / N, mb = rec[kRecMom + 3] / N;
@@ -941,20 +943,18 @@ __global__ void __launch_bounds__(kReduceThreads) k_forward_grad_reduce(const In
         if (Va > 0.0 && Vb > 0.0) {
           const double r = 1.0 / sqrt(Va * Vb);
           const double c2 = A * r / Va;
-          for (int q = 0; q < 12; ++q) {
-            const double gq = r * (rec[kRecBG + q] - mb * rec[kRecG + q]) -
-                              c2 * (rec[kRecAG + q] - ma * rec[kRecG + q]);
-            acc[q] -= gq / np;
-          }
-          L -= A * r / np;
+          const double gq = r * (rec[kRecBG + t] - mb * rec[kRecG + t]) - c2 * (rec[kRecAG + t] - ma * rec[kRecG + t]);
+          acc -= gq / np;
+          if (t == 0) L -= A * r / np;
         }
       } else {
-        for (int q = 0; q < 12; ++q) acc[q] += rec[kRecG + q];
-        if (loss == PROJ_LOSS_L2) L += rec[kRecLoss];
+        acc += rec[kRecG + t];
+        if (t == 0 && loss == PROJ_LOSS_L2) L += rec[kRecLoss];
       }
     }
-    __syncthreads();
   }
+  if (t < 12) accs[t] = acc;
+  __syncthreads();
   if (t != 0) return;
   const PoseTable& P = ptab[p];
   float* out = grad + 6 * p;
@@ -963,12 +963,12 @@ __global__ void __launch_bounds__(kReduceThreads) k_forward_grad_reduce(const In
     if (loss_out) loss_out[p] = 0.f;
     return;
   }
-  // acc[0..2] = S0_b, acc[3 + 3b + c] = sum g_b f~_c.  T[b][c] = sum g_b r'_c.
+  // accs[0..2] = S0_b, accs[3 + 3b + c] = sum g_b f~_c.  T[b][c] = sum g_b r'_c.
   const double off[3] = {g.offx, g.offy, g.offz};
   const double vox[3] = {g.vx, g.vy, g.vz};
   double Tm[9];
   for (int b = 0; b < 3; ++b)
-    for (int c = 0; c < 3; ++c) Tm[3 * b + c] = off[c] * acc[b] + vox[c] * acc[3 + 3 * b + c];
+    for (int c = 0; c < 3; ++c) Tm[3 * b + c] = off[c] * accs[b] + vox[c] * accs[3 + 3 * b + c];
   double gM[12];
   for (int a = 0; a < 3; ++a) {
     for (int b = 0; b < 3; ++b) {
@@ -976,7 +976,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_forward_grad_reduce(const In
       for (int c = 0; c < 3; ++c) s += P.R[3 * a + c] * Tm[3 * b + c];
       gM[4 * a + b] = s;
     }
-    gM[4 * a + 3] = -(P.R[3 * a] * acc[0] + P.R[3 * a + 1] * acc[1] + P.R[3 * a + 2] * acc[2]);
+    gM[4 * a + 3] = -(P.R[3 * a] * accs[0] + P.R[3 * a + 1] * accs[1] + P.R[3 * a + 2] * accs[2]);
   }
   for (int a = 0; a < 3; ++a) out[a] = (float)gM[4 * a + 3];
   for (int j = 0; j < 3; ++j) {
