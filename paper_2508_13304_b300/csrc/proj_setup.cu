@@ -135,9 +135,12 @@ __global__ void k_setup(const float* __restrict__ pose, int n_pose, const double
 cudaError_t launch_setup(const float* d_pose, int n_pose, const double* d_views, const int* d_inst_view,
                          const int* d_inst_pose, int n_inst, Geo geo, InstTable* d_inst, PoseTable* d_ptab,
                          int* d_status, cudaStream_t s) {
+  // one thread per instance runs a long dependent chain of FP64 operations (FP64 runs at a small
+  // fraction of the FP32 rate here): blocks of 8 threads spread the instances over many SMs
+  constexpr int kSetupThreads = 8;
   const int n = n_pose > n_inst ? n_pose : n_inst;
-  k_setup<<<ceil_div(n, 128), 128, 0, s>>>(d_pose, n_pose, d_views, d_inst_view, d_inst_pose, n_inst, geo, d_inst,
-                                           d_ptab, d_status);
+  k_setup<<<ceil_div(n, kSetupThreads), kSetupThreads, 0, s>>>(d_pose, n_pose, d_views, d_inst_view, d_inst_pose,
+                                                               n_inst, geo, d_inst, d_ptab, d_status);
   return cudaGetLastError();
 }
 
