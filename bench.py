@@ -43,10 +43,10 @@ L2_FLUSH_BYTES = 256 << 20
 # one-pass metrics.  NCU_SOURCE_SHA16 is the hash (kernel_source_sha16) of
 # the march's sources they were taken on; when the built sources hash
 # differently the line reports them as null.
-NCU_SOURCE_SHA16 = "942c2746640f3cf3"
-NCU_L1_WAVEFRONT_PCT = 59.6
-NCU_ISSUE_ACTIVE_PCT = 56.0
-TRAFFIC_PER_LAUNCH = 78.89e6  # 70.21 MB read + 8.69 MB written
+NCU_SOURCE_SHA16 = "c9f6b15863013dad"
+NCU_L1_WAVEFRONT_PCT = 58.7
+NCU_ISSUE_ACTIVE_PCT = 55.9
+TRAFFIC_PER_LAUNCH = 78.98e6  # 70.19 MB read + 8.79 MB written
 MARCH_SOURCES = ("paper_2508_13304_b300/csrc/proj_forward.cu", "paper_2508_13304_b300/csrc/proj_internal.cuh")
 
 
@@ -959,7 +959,10 @@ CONV_LAYERS = ((64, 32, 64), (32, 64, 128), (16, 128, 128), (8, 128, 128), (4, 1
 
 def conv_layers(pb, torch, dev, flush, bf16_peak, B=256):
     """The network's 3x3 stride-2 convolutions (bias + ReLU, BF16 out): im2col
-    + GEMM against the implicit-GEMM kernel that gathers the patches itself."""
+    + GEMM against the implicit-GEMM kernel that gathers the patches itself,
+    and their input gradients: GEMM + col2im against the implicit GEMM (which
+    multiplies 9 taps per input pixel, about 2.25 of them non-zero, so its
+    useful rate is quoted)."""
     out = []
     gen = torch.Generator(device=dev)
     gen.manual_seed(8)
@@ -979,12 +982,30 @@ def conv_layers(pb, torch, dev, flush, bf16_peak, B=256):
         ms_e = _event_ms(torch, explicit, flush, reps=5)
         ms_i = _event_ms(torch, lambda: pb.pn_conv3x3s2_bf16(x, B, H, H, C, w, Co, bias=bias, relu=True, y16=y),
                          flush, reps=5)
+        # input gradient (ReLU mask of x): GEMM into the FP32 column matrix + col2im, against the implicit GEMM
+        wT = torch.empty((K, Co), device=dev, dtype=torch.bfloat16)
+        pb.pn_transpose_bf16(w, Co, K, wT, Co)
+        wt = torch.empty((C, 9 * Co), device=dev, dtype=torch.bfloat16)
+        pb.pn_conv_dgrad_weights(w, Co, C, wt)
+        dcol = torch.empty((M, K), device=dev)
+        dx = torch.empty((B, H, H, C), device=dev, dtype=torch.bfloat16)
+
+        def dgrad_explicit():
+            pb.pn_gemm_bf16(M, K, Co, y, Co, wT, Co, D32=dcol)
+            pb.pn_col2im_3x3s2(dcol, B, H, H, C, K, mask=x, dx16=dx)
+
+        ms_de = _event_ms(torch, dgrad_explicit, flush, reps=5)
+        ms_di = _event_ms(torch, lambda: pb.pn_conv3x3s2_dgrad_bf16(y, B, H, H, C, wt, Co, mask=x, dx16=dx),
+                          flush, reps=5)
         fl = 2.0 * M * Co * K
         out.append({"input": "%dx%dx%dx%d" % (B, H, H, C), "cout": Co, "gemm_MNK": [M, Co, K],
                     "im2col_gemm_ms": ms_e, "implicit_ms": ms_i, "implicit_tflops": fl / (ms_i * 1e-3) / 1e12,
                     "implicit_frac_of_bf16_peak": fl / (ms_i * 1e-3) / 1e12 / bf16_peak,
-                    "col_matrix_bytes_avoided": M * K * 2})
-        del x, w, col, y
+                    "col_matrix_bytes_avoided": M * K * 2,
+                    "dgrad_gemm_col2im_ms": ms_de, "dgrad_implicit_ms": ms_di,
+                    "dgrad_implicit_tflops_useful": fl / (ms_di * 1e-3) / 1e12,
+                    "dgrad_fp32_col_matrix_bytes_avoided": M * K * 4})
+        del x, w, col, y, wT, wt, dcol, dx
     return out
 
 

@@ -116,6 +116,30 @@ int pn_to_bf16(const float *src, long long n, void *dst, proj_stream stream);
 int pn_conv3x3s2_bf16(const void *x, int B, int H, int W, int C, const void *w, int cout, const float *bias,
                       int relu, float *y32, void *y16, proj_stream stream);
 
+/* Input gradient of pn_conv3x3s2_bf16 as an implicit GEMM on the tensor
+ * cores, the adjoint of the convolution's patch gather without a column
+ * matrix: dx[b][iy][ix][c] = sum over taps (ky, kx) and output channels o of
+ * dy[b][oy][ox][o] w[o][(ky * 3 + kx) C + c], over the (oy, ox) with
+ * 2 oy - 1 + ky = iy and 2 ox - 1 + kx = ix inside the output grid.  The
+ * kernel gathers each 128 x 64 tile of dy rows (zero for a tap with no such
+ * output pixel) into shared memory; FP32 accumulation.
+ *   dy     BF16 NHWC [B][Ho][Wo][cout], Ho = (H + 1) / 2, Wo = (W + 1) / 2,
+ *          cout a multiple of 8, 16-byte aligned.
+ *   wt     BF16 [C][9 cout], k = (ky * 3 + kx) cout + o: the weights
+ *          rearranged by pn_conv_dgrad_weights, 16-byte aligned.
+ *   mask   BF16 NHWC [B][H][W][C] or NULL: dx is zeroed where mask <= 0
+ *          (ReLU backward of the layer that produced the convolution's x).
+ *   dx32, dx16  outputs [B][H][W][C] (FP32 / BF16; at least one).
+ * Errors: PROJ_E_ARG (shapes, alignment, cout not a multiple of 8),
+ * PROJ_E_CUDA.  Waits are bounded as in pn_gemm_bf16 (pn_status). */
+int pn_conv3x3s2_dgrad_bf16(const void *dy, int B, int H, int W, int C, const void *wt, int cout, const void *mask,
+                            float *dx32, void *dx16, proj_stream stream);
+
+/* wt[c][(ky * 3 + kx) cout + o] = w[o][(ky * 3 + kx) C + c]: the weights of
+ * pn_conv3x3s2_dgrad_bf16 from those of the convolution (BF16, no padding
+ * columns: w is [cout][9 C]). */
+int pn_conv_dgrad_weights(const void *w, int cout, int C, void *wt, proj_stream stream);
+
 /* Synchronise the stream, return and clear the status word of the current
  * device: 0 = clean; bit 1: a TMA stage never filled, bit 2: an
  * accumulator never completed, bit 4: a stage was never released (each

@@ -99,6 +99,8 @@ _SIGS = {
     "pn_im2col_3x3s2": [_P, _I, _I, _I, _I, _I, _P, _P],
     "pn_conv3x3s2_bf16": [_P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _P, _P],
     "pn_col2im_3x3s2": [_P, _I, _I, _I, _I, _I, _P, _P, _P, _P],
+    "pn_conv3x3s2_dgrad_bf16": [_P, _I, _I, _I, _I, _P, _I, _P, _P, _P, _P],
+    "pn_conv_dgrad_weights": [_P, _I, _I, _P, _P],
     "pn_transpose_bf16": [_P, _I, _I, _P, _I, _P],
     "pn_colsum_scratch_floats": [_I, _I],
     "pn_colsum_bf16": [_P, _I, _I, _I, _P, _P, _P],
@@ -605,6 +607,21 @@ def pn_conv3x3s2_bf16(x, B, H, W, C, w, cout, bias=None, relu=False, y32=None, y
                                    _f32(bias, cout, "bias", allow_none=True), 1 if relu else 0,
                                    _f32(y32, B * Ho * Wo * cout, "y32", allow_none=True),
                                    _bf(y16, B * Ho * Wo * cout, "y16", allow_none=True), _stream(stream)))
+
+
+def pn_conv3x3s2_dgrad_bf16(dy, B, H, W, C, wt, cout, mask=None, dx32=None, dx16=None, stream=None):
+    """Implicit-GEMM input gradient of pn_conv3x3s2_bf16 (see include/posenet.h)."""
+    Ho, Wo = (H + 1) // 2, (W + 1) // 2
+    n = B * H * W * C
+    _check(lib().pn_conv3x3s2_dgrad_bf16(_bf(dy, B * Ho * Wo * cout, "dy"), B, H, W, C, _bf(wt, C * 9 * cout, "wt"),
+                                         int(cout), _bf(mask, n, "mask", allow_none=True),
+                                         _f32(dx32, n, "dx32", allow_none=True), _bf(dx16, n, "dx16", allow_none=True),
+                                         _stream(stream)))
+
+
+def pn_conv_dgrad_weights(w, cout, C, wt, stream=None):
+    _check(lib().pn_conv_dgrad_weights(_bf(w, cout * 9 * C, "w"), int(cout), int(C), _bf(wt, C * 9 * cout, "wt"),
+                                       _stream(stream)))
 
 
 def pn_im2col_3x3s2(x, B, H, W, C, kp, col, stream=None):

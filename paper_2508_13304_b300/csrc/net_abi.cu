@@ -219,6 +219,45 @@ int pn_conv3x3s2_bf16(const void* x, int B, int H, int W, int C, const void* w, 
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "implicit convolution launch");
 }
 
+int pn_conv3x3s2_dgrad_bf16(const void* dy, int B, int H, int W, int C, const void* wt, int cout, const void* mask,
+                            float* dx32, void* dx16, proj_stream stream) {
+  if (!dy || !wt || (!dx32 && !dx16)) return fail(PROJ_E_ARG, "pn_conv3x3s2_dgrad_bf16: NULL input, weights or output");
+  if (B < 1 || H < 1 || W < 1 || C < 1) return fail(PROJ_E_ARG, "pn_conv3x3s2_dgrad_bf16: empty shape");
+  if (cout < 8 || cout % 8)
+    return fail(PROJ_E_ARG, "pn_conv3x3s2_dgrad_bf16: cout = %d must be a positive multiple of 8", cout);
+  if (!aligned16(dy) || !aligned16(wt)) return fail(PROJ_E_ARG, "pn_conv3x3s2_dgrad_bf16: dy and wt must be 16-byte aligned");
+  const long long M = (long long)B * H * W;
+  if (M > 0x7fffffffLL || M * C > (1LL << 40)) return fail(PROJ_E_ARG, "pn_conv3x3s2_dgrad_bf16: shape too large");
+  int* status = status_word();
+  if (!status) return fail(PROJ_E_CUDA, "pn_conv3x3s2_dgrad_bf16: no device status word");
+  const int bn = bn_for(C);
+  CUtensorMap tw;
+  int rc = make_map(&tw, wt, C, 9 * cout, 9 * cout, bn);
+  if (rc) return rc;
+  GemmEpi epi;
+  epi.bias = nullptr;
+  epi.mask = static_cast<const __nv_bfloat16*>(mask);
+  epi.ldm = C;
+  epi.relu = 0;
+  epi.d32 = dx32;
+  epi.d16 = static_cast<__nv_bfloat16*>(dx16);
+  epi.ldd = C;
+  epi.part = nullptr;
+  epi.wait_ns = g_wait_ns;
+  epi.stall_tma = 0;
+  cudaError_t e = launch_conv_dgrad_implicit(static_cast<const __nv_bfloat16*>(dy), B, H, W, cout, tw, C, bn, epi,
+                                             status, (cudaStream_t)stream);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "implicit input-gradient launch");
+}
+
+int pn_conv_dgrad_weights(const void* w, int cout, int C, void* wt, proj_stream stream) {
+  if (!w || !wt) return fail(PROJ_E_ARG, "pn_conv_dgrad_weights: NULL argument");
+  if (cout < 1 || C < 1) return fail(PROJ_E_ARG, "pn_conv_dgrad_weights: empty shape");
+  cudaError_t e = launch_conv_dgrad_weights(static_cast<const __nv_bfloat16*>(w), cout, C,
+                                            static_cast<__nv_bfloat16*>(wt), (cudaStream_t)stream);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "dgrad weights launch");
+}
+
 int pn_im2col_3x3s2(const void* x, int B, int H, int W, int C, int kp, void* col, proj_stream stream) {
   if (!x || !col) return fail(PROJ_E_ARG, "pn_im2col_3x3s2: NULL argument");
   if (B < 1 || H < 1 || W < 1 || C < 1) return fail(PROJ_E_ARG, "pn_im2col_3x3s2: empty shape");

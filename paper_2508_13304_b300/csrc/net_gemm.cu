@@ -668,7 +668,11 @@ cudaError_t launch_pair_persistent(const CUtensorMap& ta, const CUtensorMap& tb,
 // memory: warps 0-3 gather each 128 x 64 A stage straight from the
 // activation, one output pixel (tile row) per thread, as eight 16-byte
 // cp.async copies placed at their 128-byte-swizzled positions (zero fill for
-// taps in the padding and for rows past M).  The weights [Cout][9 C] arrive
+// taps in the padding and for rows past M).  DGRAD = true runs the input
+// gradient of that convolution the same way: a row is an input pixel (iy,
+// ix), and tap (ky, kx) reads the output gradient at ((iy + 1 - ky) / 2,
+// (ix + 1 - kx) / 2) where both are integers inside the output grid (zero
+// otherwise), against the weights rearranged to [C][9 cout].  The weights [Cout][9 C] arrive
 // by TMA as in k_gemm_bf16 (warp 4), one lane of warp 5 issues the MMAs, and
 // warps 0-3 run the same epilogue.  K runs tap-major, k = tap * C + c, as in
 // k_im2col, so the accumulation order and the results equal those of im2col
@@ -687,9 +691,11 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <int BN>
+// x: the gathered tensor, [B][SH][SW][C]; rows of the GEMM run over the grid [B][OH][OW] (forward: the
+// output pixels, SH = H, OH = (H + 1) / 2; DGRAD: the input pixels, SH = Ho, OH = H).
+template <int BN, bool DGRAD>
 __global__ void __launch_bounds__(kConvThreads, 1)
-    k_conv3x3s2_implicit(const __nv_bfloat16* __restrict__ x, int H, int W, int C,
+    k_conv3x3s2_implicit(const __nv_bfloat16* __restrict__ x, int SH, int SW, int C, int OH, int OW,
                          const __grid_constant__ CUtensorMap tb, int M, int N, GemmEpi epi, int* status) {
   constexpr uint32_t kBytesA = kBM * kBK * 2, kBytesB = BN * kBK * 2;
   constexpr int kAhead = kStages - 1;  // stages of copies a gathering thread keeps in flight
@@ -708,7 +714,6 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
   const int nkb = (9 * C + kBK - 1) / kBK;
-  const int Ho = (H + 1) / 2, Wo = (W + 1) / 2;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -734,9 +739,11 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     const int t = threadIdx.x;  // row of the A tile
     const int m = m0 + t;
     const bool row_ok = m < M;
-    const int wo = row_ok ? m % Wo : 0, ho = row_ok ? (m / Wo) % Ho : 0, b = row_ok ? m / (Wo * Ho) : 0;
-    const int hi0 = 2 * ho - 1, wi0 = 2 * wo - 1;
-    const __nv_bfloat16* xb = x + (size_t)b * H * W * C;
+    const int wo = row_ok ? m % OW : 0, ho = row_ok ? (m / OW) % OH : 0, b = row_ok ? m / (OW * OH) : 0;
+    // forward: source pixel (2 ho - 1 + ky, 2 wo - 1 + kx); DGRAD: twice the source pixel is (ho + 1 - ky,
+    // wo + 1 - kx)
+    const int hi0 = DGRAD ? ho + 1 : 2 * ho - 1, wi0 = DGRAD ? wo + 1 : 2 * wo - 1;
+    const __nv_bfloat16* xb = x + (size_t)b * SH * SW * C;
     const uint32_t row_off = (uint32_t)t * 128u, swz = (uint32_t)(t & 7);
     int i = 0;
     for (; i < nkb; ++i) {
@@ -750,9 +757,19 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       const uint32_t dst = sA + s * kBytesA + row_off;
 #pragma unroll
       for (int j = 0; j < kBK / 8; ++j) {  // 16-byte chunk j of the row: k .. k + 7 of tap `tap`
-        const int hi = hi0 + tap / 3, wi = wi0 + tap % 3;
-        const bool ok = row_ok && tap < 9 && hi >= 0 && hi < H && wi >= 0 && wi < W;
-        cp_async16(dst + (((uint32_t)j ^ swz) << 4), ok ? xb + ((size_t)hi * W + wi) * C + c : x, ok ? 16u : 0u);
+        int hi, wi;
+        bool ok;
+        if (DGRAD) {
+          const int h2 = hi0 - tap / 3, w2 = wi0 - tap % 3;
+          hi = h2 >> 1;
+          wi = w2 >> 1;
+          ok = row_ok && tap < 9 && h2 >= 0 && !(h2 & 1) && hi < SH && w2 >= 0 && !(w2 & 1) && wi < SW;
+        } else {
+          hi = hi0 + tap / 3;
+          wi = wi0 + tap % 3;
+          ok = row_ok && tap < 9 && hi >= 0 && hi < SH && wi >= 0 && wi < SW;
+        }
+        cp_async16(dst + (((uint32_t)j ^ swz) << 4), ok ? xb + ((size_t)hi * SW + wi) * C + c : x, ok ? 16u : 0u);
         c += 8;
         if (c == C) {
           c = 0;
@@ -816,17 +833,21 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   }
 }
 
-template <int BN>
+// forward: x [B][H][W][C], rows = output pixels; dgrad: x = the output gradient [B][Ho][Wo][C] (C = the
+// convolution's cout), rows = the B x H x W input pixels
+template <int BN, bool DGRAD>
 cudaError_t launch_conv_bn(const __nv_bfloat16* x, int B, int H, int W, int C, const CUtensorMap& tb, int N,
                            const GemmEpi& epi, int* status, cudaStream_t s) {
   const size_t smem = gemm_smem_bytes(BN);
   cudaError_t e =
-      cudaFuncSetAttribute(k_conv3x3s2_implicit<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_conv3x3s2_implicit<BN, DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long M = (long long)B * ((H + 1) / 2) * ((W + 1) / 2);
+  const int Ho = (H + 1) / 2, Wo = (W + 1) / 2;
+  const int SH = DGRAD ? Ho : H, SW = DGRAD ? Wo : W, OH = DGRAD ? H : Ho, OW = DGRAD ? W : Wo;
+  const long long M = (long long)B * OH * OW;
   if (M > 0x7fffffffLL) return cudaErrorInvalidValue;
   dim3 grid((unsigned)((M + kBM - 1) / kBM), (N + BN - 1) / BN, 1);
-  k_conv3x3s2_implicit<BN><<<grid, kConvThreads, smem, s>>>(x, H, W, C, tb, (int)M, N, epi, status);
+  k_conv3x3s2_implicit<BN, DGRAD><<<grid, kConvThreads, smem, s>>>(x, SH, SW, C, OH, OW, tb, (int)M, N, epi, status);
   return cudaGetLastError();
 }
 
@@ -852,10 +873,21 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int
 cudaError_t launch_conv_implicit(const __nv_bfloat16* x, int B, int H, int W, int C, const CUtensorMap& tw, int cout,
                                  int bn, const GemmEpi& epi, int* status, cudaStream_t s) {
   switch (bn) {
-    case 32: return launch_conv_bn<32>(x, B, H, W, C, tw, cout, epi, status, s);
-    case 64: return launch_conv_bn<64>(x, B, H, W, C, tw, cout, epi, status, s);
-    case 128: return launch_conv_bn<128>(x, B, H, W, C, tw, cout, epi, status, s);
-    case 256: return launch_conv_bn<256>(x, B, H, W, C, tw, cout, epi, status, s);
+    case 32: return launch_conv_bn<32, false>(x, B, H, W, C, tw, cout, epi, status, s);
+    case 64: return launch_conv_bn<64, false>(x, B, H, W, C, tw, cout, epi, status, s);
+    case 128: return launch_conv_bn<128, false>(x, B, H, W, C, tw, cout, epi, status, s);
+    case 256: return launch_conv_bn<256, false>(x, B, H, W, C, tw, cout, epi, status, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_conv_dgrad_implicit(const __nv_bfloat16* dy, int B, int H, int W, int cout, const CUtensorMap& twt,
+                                       int C, int bn, const GemmEpi& epi, int* status, cudaStream_t s) {
+  switch (bn) {
+    case 32: return launch_conv_bn<32, true>(dy, B, H, W, cout, twt, C, epi, status, s);
+    case 64: return launch_conv_bn<64, true>(dy, B, H, W, cout, twt, C, epi, status, s);
+    case 128: return launch_conv_bn<128, true>(dy, B, H, W, cout, twt, C, epi, status, s);
+    case 256: return launch_conv_bn<256, true>(dy, B, H, W, cout, twt, C, epi, status, s);
     default: return cudaErrorInvalidValue;
   }
 }

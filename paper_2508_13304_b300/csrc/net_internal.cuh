@@ -45,6 +45,13 @@ cudaError_t launch_split_reduce(const float* part, int split, int M, int N, cons
 // ([cout][9 C], boxes of bn rows), output through epi (rows = output pixels, columns = output channels)
 cudaError_t launch_conv_implicit(const __nv_bfloat16* x, int B, int H, int W, int C, const CUtensorMap& tw, int cout,
                                  int bn, const GemmEpi& epi, int* status, cudaStream_t s);
+// its input gradient as an implicit GEMM: dy [B][Ho][Wo][cout] (cout % 8 == 0), weights by the tensor map
+// twt ([C][9 cout], k = tap * cout + o, boxes of bn rows), output through epi (rows = the B x H x W input
+// pixels, columns = the C input channels)
+cudaError_t launch_conv_dgrad_implicit(const __nv_bfloat16* dy, int B, int H, int W, int cout, const CUtensorMap& twt,
+                                       int C, int bn, const GemmEpi& epi, int* status, cudaStream_t s);
+// wt[c][tap * cout + o] = w[o][tap * C + c]: the weights of the input-gradient GEMM
+cudaError_t launch_conv_dgrad_weights(const __nv_bfloat16* w, int cout, int C, __nv_bfloat16* wt, cudaStream_t s);
 
 cudaError_t launch_im2col(const __nv_bfloat16* x, int B, int H, int W, int C, int kp, __nv_bfloat16* col,
                           cudaStream_t s);

@@ -200,6 +200,17 @@ __global__ void k_to_bf16(const float* __restrict__ src, long long n, __nv_bfloa
     dst[i] = __float2bfloat16_rn(src[i]);
 }
 
+// Weights of the input-gradient GEMM: wt[c][tap * cout + o] = w[o][tap * C + c], one thread per element.
+__global__ void k_dgrad_weights(const __nv_bfloat16* __restrict__ w, int cout, int C, __nv_bfloat16* __restrict__ wt) {
+  const long long n = 9LL * cout * C;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int o = (int)(i % cout);
+    const long long r = i / cout;
+    const int tap = (int)(r % 9), c = (int)(r / 9);
+    wt[i] = w[((long long)o * 9 + tap) * C + c];
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_im2col(const __nv_bfloat16* x, int B, int H, int W, int C, int kp, __nv_bfloat16* col,
@@ -255,6 +266,11 @@ cudaError_t launch_mse(const float* y, int B, int n_out, int ldy, const float* t
 
 cudaError_t launch_to_bf16(const float* src, long long n, __nv_bfloat16* dst, cudaStream_t s) {
   k_to_bf16<<<grid_for(n, 256), 256, 0, s>>>(src, n, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conv_dgrad_weights(const __nv_bfloat16* w, int cout, int C, __nv_bfloat16* wt, cudaStream_t s) {
+  k_dgrad_weights<<<grid_for(9LL * cout * C, 256), 256, 0, s>>>(w, cout, C, wt);
   return cudaGetLastError();
 }
 

@@ -14,8 +14,10 @@ translations / t_range, rotations / r_range).  Loss: mean squared error.
 Every forward and backward step runs in the library's kernels: implicit-
 GEMM convolutions (the tensor-core kernel gathers the 3x3 patches itself;
 bias and ReLU fused) forward for layers whose input has a multiple of 8
-channels and at least 8192 output pixels, im2col + GEMM for the others; GEMM + col2im (ReLU mask fused)
-for the input gradients; im2col, transposes + split-K GEMM for the weight
+channels and at least 8192 output pixels, im2col + GEMM for the others; the
+input gradients as implicit GEMMs too (the kernel gathers the output
+gradient's rows per input pixel and tap; ReLU mask fused), or GEMM + col2im
+with implicit=False; im2col, transposes + split-K GEMM for the weight
 gradients; column sums for the bias gradients.  Parameters are FP32 masters updated by Adam
 (a few torch elementwise operations, as in the registration loop) and
 converted to BF16 (and transposed) for the GEMMs after every update.
@@ -29,7 +31,7 @@ import numpy as np
 import torch
 
 from . import (PROJ_OP_FORWARD, Projector, pn_col2im_3x3s2, pn_colsum_bf16, pn_colsum_scratch_floats,
-               pn_conv3x3s2_bf16, pn_gemm_bf16, pn_gemm_split_hint, pn_im2col_3x3s2, pn_mse_loss, pn_prepare_images,
+               pn_conv3x3s2_bf16, pn_conv3x3s2_dgrad_bf16, pn_conv_dgrad_weights, pn_gemm_bf16, pn_gemm_split_hint, pn_im2col_3x3s2, pn_mse_loss, pn_prepare_images,
                pn_to_bf16, pn_transpose_bf16, proj_forward)
 
 BF = torch.bfloat16
@@ -84,6 +86,8 @@ class PoseNet:
             L["d"] = torch.empty((M, L["cout"]), device=d, dtype=BF)       # gradient w.r.t. pre-activation
             L["wb"] = torch.empty((L["cout"], L["kp"]), device=d, dtype=BF)
             L["wbT"] = torch.empty((L["kp"], L["cout"]), device=d, dtype=BF)
+            if L["kp"] == 9 * L["cin"] and L["cout"] % 8 == 0:  # weights of the implicit input gradient
+                L["wd"] = torch.empty((L["cin"], 9 * L["cout"]), device=d, dtype=BF)
             L["gw"] = torch.zeros_like(L["w"])
             L["gb"] = torch.zeros_like(L["b"])
             L["split"] = pn_gemm_split_hint(L["cout"], L["kp"], L["Mp"])
@@ -127,6 +131,8 @@ class PoseNet:
             pn_to_bf16(P["w"], P["wb"])
             rows, cols = P["wb"].shape
             pn_transpose_bf16(P["wb"], rows, cols, P["wbT"], rows)
+            if "wd" in P:
+                pn_conv_dgrad_weights(P["wb"], P["cout"], P["cin"], P["wd"])
 
     # ---------------------------------------------------------------- passes
     def forward(self, x=None):
@@ -193,7 +199,11 @@ class PoseNet:
                 L["col_ready"] = True
             self._wgrad(L["d"], L["M"], L["cout"], L["col"], L["kp"], L["gw"], L["split"])
             pn_colsum_bf16(L["d"], L["M"], L["cout"], L["cout"], L["gb"], self.cs)
-            if i > 0:
+            if i > 0 and self.implicit and "wd" in L:
+                P = self.layers[i - 1]
+                pn_conv3x3s2_dgrad_bf16(L["d"], B, L["H"], L["H"], L["cin"], L["wd"], L["cout"], mask=P["a"],
+                                        dx16=P["d"])
+            elif i > 0:
                 P = self.layers[i - 1]
                 dcol = self.dcol[:L["M"] * L["kp"]]
                 pn_gemm_bf16(L["M"], L["kp"], L["cout"], L["d"], L["cout"], L["wbT"], L["cout"], D32=dcol)
