@@ -110,12 +110,24 @@ __global__ void k_colsum_part(const __nv_bfloat16* __restrict__ y, int M, int N,
   }
 }
 
-__global__ void k_colsum_final(const float* __restrict__ part, int n_part, int N, float* __restrict__ out) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int q = 0; q < n_part; ++q) s += part[(size_t)q * N + c];
-    out[c] = (float)s;
+// Column sums, stage 2: one block per column sums the n_part partials in a
+// fixed order (thread t the partials t, t + 256, ..., then a shared-memory
+// tree), in FP64; a column per thread made one long dependent chain of FP64
+// adds, which run at a small fraction of the FP32 rate here.
+constexpr int kColsumFinalThreads = 256;
+__global__ void __launch_bounds__(kColsumFinalThreads) k_colsum_final(const float* __restrict__ part, int n_part, int N,
+                                                                     float* __restrict__ out) {
+  __shared__ double red[kColsumFinalThreads];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int q = threadIdx.x; q < n_part; q += kColsumFinalThreads) s += part[(size_t)q * N + c];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = kColsumFinalThreads / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) out[c] = (float)red[0];
 }
 
 // One block per (image, view): box-average by `factor` into shared memory,
@@ -243,7 +255,7 @@ cudaError_t launch_colsum(const __nv_bfloat16* y, int M, int N, int ld, float* p
   k_colsum_part<<<n_part, 256, 0, s>>>(y, M, N, ld, rows, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_colsum_final<<<(N + 255) / 256, 256, 0, s>>>(part, n_part, N, out);
+  k_colsum_final<<<N, kColsumFinalThreads, 0, s>>>(part, n_part, N, out);
   return cudaGetLastError();
 }
 
