@@ -140,6 +140,16 @@ int pn_conv3x3s2_dgrad_bf16(const void *dy, int B, int H, int W, int C, const vo
  * columns: w is [cout][9 C]). */
 int pn_conv_dgrad_weights(const void *w, int cout, int C, void *wt, proj_stream stream);
 
+/* One Adam step on n FP32 elements (flat arrays, the whole network in one
+ * launch): m = b1 m + a1 g; v = b2 v + a2 g^2; p = decay p - step m /
+ * (sqrt(v) + eps), with a1 = 1 - b1 and a2 = 1 - b2 (passed separately so
+ * that they carry full FP32 precision), step = lr sqrt(1 - b2^t) /
+ * (1 - b1^t) and decay = 1 - lr wd from the caller; p16 (BF16, n elements)
+ * or NULL receives the updated p rounded to BF16.  Errors: PROJ_E_ARG,
+ * PROJ_E_CUDA. */
+int pn_adam_step(float *p, const float *g, float *m, float *v, long long n, float step, float b1, float a1, float b2,
+                 float a2, float eps, float decay, void *p16, proj_stream stream);
+
 /* Synchronise the stream, return and clear the status word of the current
  * device: 0 = clean; bit 1: a TMA stage never filled, bit 2: an
  * accumulator never completed, bit 4: a stage was never released (each

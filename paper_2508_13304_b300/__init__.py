@@ -101,6 +101,7 @@ _SIGS = {
     "pn_col2im_3x3s2": [_P, _I, _I, _I, _I, _I, _P, _P, _P, _P],
     "pn_conv3x3s2_dgrad_bf16": [_P, _I, _I, _I, _I, _P, _I, _P, _P, _P, _P],
     "pn_conv_dgrad_weights": [_P, _I, _I, _P, _P],
+    "pn_adam_step": [_P, _P, _P, _P, ctypes.c_longlong] + [ctypes.c_float] * 7 + [_P, _P],
     "pn_transpose_bf16": [_P, _I, _I, _P, _I, _P],
     "pn_colsum_scratch_floats": [_I, _I],
     "pn_colsum_bf16": [_P, _I, _I, _I, _P, _P, _P],
@@ -622,6 +623,14 @@ def pn_conv3x3s2_dgrad_bf16(dy, B, H, W, C, wt, cout, mask=None, dx32=None, dx16
 def pn_conv_dgrad_weights(w, cout, C, wt, stream=None):
     _check(lib().pn_conv_dgrad_weights(_bf(w, cout * 9 * C, "w"), int(cout), int(C), _bf(wt, C * 9 * cout, "wt"),
                                        _stream(stream)))
+
+
+def pn_adam_step(p, g, m, v, step, b1, b2, eps, decay=1.0, p16=None, stream=None):
+    """One Adam step on flat FP32 tensors p, g, m, v (see include/posenet.h)."""
+    n = p.numel()
+    _check(lib().pn_adam_step(_f32(p, n, "p"), _f32(g, n, "g"), _f32(m, n, "m"), _f32(v, n, "v"), n, float(step),
+                              float(b1), 1.0 - float(b1), float(b2), 1.0 - float(b2), float(eps), float(decay),
+                              _bf(p16, n, "p16", allow_none=True), _stream(stream)))
 
 
 def pn_im2col_3x3s2(x, B, H, W, C, kp, col, stream=None):

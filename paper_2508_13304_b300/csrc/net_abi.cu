@@ -327,6 +327,14 @@ int pn_to_bf16(const float* src, long long n, void* dst, proj_stream stream) {
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "conversion launch");
 }
 
+int pn_adam_step(float* p, const float* g, float* m, float* v, long long n, float step, float b1, float a1, float b2,
+                 float a2, float eps, float decay, void* p16, proj_stream stream) {
+  if (!p || !g || !m || !v || n < 1) return fail(PROJ_E_ARG, "pn_adam_step: bad argument");
+  cudaError_t e = launch_adam(p, g, m, v, n, step, b1, a1, b2, a2, eps, decay, static_cast<__nv_bfloat16*>(p16),
+                              (cudaStream_t)stream);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "adam launch");
+}
+
 int pn_status(proj_stream stream, int* status) {
   if (!status) return fail(PROJ_E_ARG, "pn_status: NULL argument");
   int* w = status_word();

@@ -50,6 +50,9 @@ cudaError_t launch_conv_implicit(const __nv_bfloat16* x, int B, int H, int W, in
 // pixels, columns = the C input channels)
 cudaError_t launch_conv_dgrad_implicit(const __nv_bfloat16* dy, int B, int H, int W, int cout, const CUtensorMap& twt,
                                        int C, int bn, const GemmEpi& epi, int* status, cudaStream_t s);
+// one Adam step on flat FP32 arrays (and the BF16 copy of p when p16 is not null)
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float step, float b1, float a1,
+                        float b2, float a2, float eps, float decay, __nv_bfloat16* p16, cudaStream_t s);
 // wt[c][tap * cout + o] = w[o][tap * C + c]: the weights of the input-gradient GEMM
 cudaError_t launch_conv_dgrad_weights(const __nv_bfloat16* w, int cout, int C, __nv_bfloat16* wt, cudaStream_t s);
 

@@ -212,6 +212,22 @@ __global__ void k_to_bf16(const float* __restrict__ src, long long n, __nv_bfloa
     dst[i] = __float2bfloat16_rn(src[i]);
 }
 
+// Adam on flat FP32 arrays, and the BF16 copy of the updated weights.
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       long long n, float step, float b1, float a1, float b2, float a2, float eps, float decay,
+                       __nv_bfloat16* __restrict__ p16) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + a1 * gi;
+    const float vi = b2 * v[i] + a2 * gi * gi;
+    const float pi = p[i] * decay - step * mi / (sqrtf(vi) + eps);
+    m[i] = mi;
+    v[i] = vi;
+    p[i] = pi;
+    if (p16) p16[i] = __float2bfloat16_rn(pi);
+  }
+}
+
 // Weights of the input-gradient GEMM: wt[c][tap * cout + o] = w[o][tap * C + c], one thread per element.
 __global__ void k_dgrad_weights(const __nv_bfloat16* __restrict__ w, int cout, int C, __nv_bfloat16* __restrict__ wt) {
   const long long n = 9LL * cout * C;
@@ -283,6 +299,12 @@ cudaError_t launch_to_bf16(const float* src, long long n, __nv_bfloat16* dst, cu
 
 cudaError_t launch_conv_dgrad_weights(const __nv_bfloat16* w, int cout, int C, __nv_bfloat16* wt, cudaStream_t s) {
   k_dgrad_weights<<<grid_for(9LL * cout * C, 256), 256, 0, s>>>(w, cout, C, wt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float step, float b1, float a1,
+                        float b2, float a2, float eps, float decay, __nv_bfloat16* p16, cudaStream_t s) {
+  k_adam<<<grid_for(n, 256), 256, 0, s>>>(p, g, m, v, n, step, b1, a1, b2, a2, eps, decay, p16);
   return cudaGetLastError();
 }
 

@@ -18,9 +18,9 @@ channels and at least 8192 output pixels, im2col + GEMM for the others; the
 input gradients as implicit GEMMs too (the kernel gathers the output
 gradient's rows per input pixel and tap; ReLU mask fused), or GEMM + col2im
 with implicit=False; im2col, transposes + split-K GEMM for the weight
-gradients; column sums for the bias gradients.  Parameters are FP32 masters updated by Adam
-(a few torch elementwise operations, as in the registration loop) and
-converted to BF16 (and transposed) for the GEMMs after every update.
+gradients; column sums for the bias gradients.  Parameters are FP32 masters in one flat
+buffer, updated by Adam in one launch that also writes their BF16 copies
+(pn_adam_step), then transposed for the GEMMs after every update.
 """
 from __future__ import annotations
 
@@ -31,7 +31,7 @@ import numpy as np
 import torch
 
 from . import (PROJ_OP_FORWARD, Projector, pn_col2im_3x3s2, pn_colsum_bf16, pn_colsum_scratch_floats,
-               pn_conv3x3s2_bf16, pn_conv3x3s2_dgrad_bf16, pn_conv_dgrad_weights, pn_gemm_bf16, pn_gemm_split_hint, pn_im2col_3x3s2, pn_mse_loss, pn_prepare_images,
+               pn_adam_step, pn_conv3x3s2_bf16, pn_conv3x3s2_dgrad_bf16, pn_conv_dgrad_weights, pn_gemm_bf16, pn_gemm_split_hint, pn_im2col_3x3s2, pn_mse_loss, pn_prepare_images,
                pn_to_bf16, pn_transpose_bf16, proj_forward)
 
 BF = torch.bfloat16
@@ -74,8 +74,35 @@ class PoseNet:
         self.refresh()
 
     # ---------------------------------------------------------------- buffers
+    def _flatten(self):
+        """Master weights, their gradients and their BF16 copies as views of three
+        flat buffers (each tensor at a multiple of 8 elements, so every view is
+        16-byte aligned for the tensor maps), so that one launch updates them all
+        (pn_adam_step) and one converts them (pn_to_bf16)."""
+        d = self.dev
+        ts = [P[k] for P in self.layers + self.fc for k in ("w", "b")]
+        offs, n = [], 0
+        for t in ts:
+            offs.append(n)
+            n += _r8(t.numel())
+        self.flat_p = torch.zeros(n, device=d)
+        self.flat_g = torch.zeros(n, device=d)
+        self.flat_b16 = torch.zeros(n, device=d, dtype=BF)
+        i = 0
+        for P in self.layers + self.fc:
+            for k in ("w", "b"):
+                t, o = P[k], offs[i]
+                i += 1
+                view = self.flat_p[o:o + t.numel()].view(t.shape)
+                view.copy_(t)
+                P[k] = view
+                P["g" + k] = self.flat_g[o:o + t.numel()].view(t.shape)
+                if k == "w":
+                    P["wb"] = self.flat_b16[o:o + t.numel()].view(t.shape)
+
     def _alloc(self):
         B, d = self.B, self.dev
+        self._flatten()
         self.x = torch.zeros((B, self.hw, self.hw, self.n_views), device=d, dtype=BF)
         biggest_t, biggest_dcol, biggest_part = 0, 0, 0
         for L in self.layers:
@@ -84,12 +111,9 @@ class PoseNet:
             L["col"] = torch.empty((M, L["kp"]), device=d, dtype=BF)
             L["a"] = torch.empty((M, L["cout"]), device=d, dtype=BF)       # post-ReLU output, NHWC
             L["d"] = torch.empty((M, L["cout"]), device=d, dtype=BF)       # gradient w.r.t. pre-activation
-            L["wb"] = torch.empty((L["cout"], L["kp"]), device=d, dtype=BF)
             L["wbT"] = torch.empty((L["kp"], L["cout"]), device=d, dtype=BF)
             if L["kp"] == 9 * L["cin"] and L["cout"] % 8 == 0:  # weights of the implicit input gradient
                 L["wd"] = torch.empty((L["cin"], 9 * L["cout"]), device=d, dtype=BF)
-            L["gw"] = torch.zeros_like(L["w"])
-            L["gb"] = torch.zeros_like(L["b"])
             L["split"] = pn_gemm_split_hint(L["cout"], L["kp"], L["Mp"])
             biggest_t = max(biggest_t, L["kp"] * L["Mp"], L["cout"] * L["Mp"])
             biggest_dcol = max(biggest_dcol, M * L["kp"])
@@ -97,10 +121,7 @@ class PoseNet:
         Bp = _r8(B)
         self.Bp = Bp
         for F in self.fc:
-            F["wb"] = torch.empty((F["n"], F["n_in"]), device=d, dtype=BF)
             F["wbT"] = torch.empty((F["n_in"], F["n"]), device=d, dtype=BF)
-            F["gw"] = torch.zeros_like(F["w"])
-            F["gb"] = torch.zeros_like(F["b"])
             F["split"] = pn_gemm_split_hint(F["n"], F["n_in"], Bp)
             biggest_t = max(biggest_t, F["n"] * Bp, F["n_in"] * Bp)
             biggest_part = max(biggest_part, F["split"] * F["n"] * F["n_in"])
@@ -125,10 +146,12 @@ class PoseNet:
     def grads(self):
         return [t for L in self.layers for t in (L["gw"], L["gb"])] + [t for F in self.fc for t in (F["gw"], F["gb"])]
 
-    def refresh(self):
-        """BF16 copies (and transposes) of the FP32 weights for the GEMMs."""
+    def refresh(self, convert=True):
+        """BF16 copies (and transposes) of the FP32 weights for the GEMMs;
+        convert=False when pn_adam_step has written the BF16 copies already."""
+        if convert:
+            pn_to_bf16(self.flat_p, self.flat_b16)
         for P in self.layers + self.fc:
-            pn_to_bf16(P["w"], P["wb"])
             rows, cols = P["wb"].shape
             pn_transpose_bf16(P["wb"], rows, cols, P["wbT"], rows)
             if "wd" in P:
@@ -225,26 +248,26 @@ class PoseNet:
 
 
 class AdamW:
-    """Adam on a list of FP32 tensors (decoupled weight decay optional)."""
+    """Adam (bias-corrected, decoupled weight decay optional) on a network's
+    flat FP32 master weights, one launch per step (pn_adam_step), which also
+    writes the BF16 copies the GEMMs read."""
 
-    def __init__(self, params, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, wd=0.0):
-        self.p = params
-        self.m = [torch.zeros_like(t) for t in params]
-        self.v = [torch.zeros_like(t) for t in params]
+    def __init__(self, net, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, wd=0.0):
+        self.net = net
+        self.m = torch.zeros_like(net.flat_p)
+        self.v = torch.zeros_like(net.flat_p)
         self.lr, self.b1, self.b2, self.eps, self.wd = lr, betas[0], betas[1], eps, wd
         self.t = 0
 
-    def step(self, grads, lr=None):
+    def step(self, lr=None):
+        """One update from the gradients in net.flat_g; then net.refresh(convert=False)."""
         self.t += 1
         lr = self.lr if lr is None else lr
         c1 = 1 - self.b1 ** self.t
         c2 = 1 - self.b2 ** self.t
-        for p, g, m, v in zip(self.p, grads, self.m, self.v):
-            m.mul_(self.b1).add_(g, alpha=1 - self.b1)
-            v.mul_(self.b2).addcmul_(g, g, value=1 - self.b2)
-            if self.wd:
-                p.mul_(1 - lr * self.wd)
-            p.addcdiv_(m, v.sqrt().add_(self.eps), value=-lr * math.sqrt(c2) / c1)
+        n = self.net
+        pn_adam_step(n.flat_p, n.flat_g, self.m, self.v, lr * math.sqrt(c2) / c1, self.b1, self.b2, self.eps,
+                     1 - lr * self.wd, n.flat_b16)
 
 
 class DrrSource:
@@ -285,7 +308,7 @@ class DrrSource:
 
 def train(net, source, n_samples, lr=1e-3, lr_final=1e-5, log_every=0, log=print):
     """Adam with cosine decay over n_samples DRRs; returns the loss history."""
-    opt = AdamW(net.params, lr=lr)
+    opt = AdamW(net, lr=lr)
     target = torch.empty((net.B, 6), device=net.dev)
     steps = max(1, n_samples // net.B)
     hist = []
@@ -296,8 +319,8 @@ def train(net, source, n_samples, lr=1e-3, lr_final=1e-5, log_every=0, log=print
         net.loss_grad(target)
         net.backward()
         k = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * s / steps))
-        opt.step(net.grads, lr=k)
-        net.refresh()
+        opt.step(lr=k)
+        net.refresh(convert=False)
         hist.append(net.loss.clone())
         if log_every and (s + 1) % log_every == 0:
             log("step %d/%d loss %.5f (%.1f s)" % (s + 1, steps, float(torch.stack(hist[-log_every:]).mean()),

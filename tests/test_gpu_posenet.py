@@ -351,6 +351,33 @@ def test_conv_implicit_dgrad_rejects_bad_arguments():
         pb.pn_conv3x3s2_dgrad_bf16(dy16, 1, 8, 8, 16, wt16, 16)
 
 
+def test_adam_step_matches_numpy():
+    """pn_adam_step: three bias-corrected Adam steps with decoupled weight decay
+    on a flat FP32 array (odd length) against numpy in FP64 (FP32 rounding of
+    each operation: rel <= 1e-6), and the BF16 copy of the result."""
+    rng = np.random.default_rng(31)
+    n = 1001
+    p0 = rng.standard_normal(n)
+    p = torch.from_numpy(p0.astype(np.float32)).cuda()
+    m = torch.zeros(n, device="cuda")
+    v = torch.zeros(n, device="cuda")
+    p16 = torch.empty(n, device="cuda", dtype=torch.bfloat16)
+    lr, b1, b2, eps, wd = 1e-2, 0.9, 0.999, 1e-8, 0.01
+    P, M, V = p.cpu().numpy().astype(np.float64), np.zeros(n), np.zeros(n)
+    for t in range(1, 4):
+        g = rng.standard_normal(n)
+        step = lr * np.sqrt(1 - b2 ** t) / (1 - b1 ** t)
+        pb.pn_adam_step(p, torch.from_numpy(g.astype(np.float32)).cuda(), m, v, step, b1, b2, eps, 1 - lr * wd, p16)
+        g32 = g.astype(np.float32).astype(np.float64)
+        M = b1 * M + (1 - b1) * g32
+        V = b2 * V + (1 - b2) * g32 * g32
+        P = P * (1 - lr * wd) - step * M / (np.sqrt(V) + eps)
+    torch.cuda.synchronize()
+    assert rel(p.cpu().numpy(), P) <= 1e-6
+    assert rel(m.cpu().numpy(), M) <= 1e-6 and rel(v.cpu().numpy(), V) <= 1e-6
+    assert torch.equal(p16, p.bfloat16())
+
+
 def test_prepare_and_mse():
     rng = np.random.default_rng(12)
     n_img, n_views, nu, nv, f = 5, 2, 96, 72, 3
