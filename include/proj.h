@@ -419,6 +419,24 @@ int proj_fdk_filter(proj_plan plan, const float *d_proj, float scale, float *d_o
 int proj_sharpness(proj_plan plan, const float *d_vol, float *d_loss, float *d_grad, void *d_ws, size_t ws_bytes,
                    proj_stream stream);
 
+/* One Adam step on n poses (the optimiser of the registration and
+ * motion-compensation loops, Sec. II-D.3), in one launch, no plan needed.
+ * For each pose i with d_active[i] != 0 (every pose when d_active is NULL):
+ * t_i += 1; per parameter j: m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * pose -= lr[j] (m / (1 - b1^t_i)) / (sqrt(v / (1 - b2^t_i)) + eps).
+ * Inactive poses keep pose, m, v and t_i, so a pose's bias correction counts
+ * only its own updates.
+ *   d_pose, d_grad, d_m, d_v  [n][6] FP32 (device); d_t  [n] FP32 step
+ *   counts (device, start at 0); d_active  [n] bytes (device) or NULL;
+ *   lr  6 step sizes (host memory, copied into the launch); b1, b2, eps
+ *   FP32 (1 - b1 and 1 - b2 are formed from those FP32 values).
+ * Asynchronous on stream, no allocation, capturable in a CUDA graph.
+ * Errors: PROJ_E_ARG (NULL pointers, n < 0, b1 or b2 outside [0, 1),
+ * eps < 0), PROJ_E_CUDA. */
+int proj_pose_adam(float *d_pose, const float *d_grad, float *d_m, float *d_v, float *d_t,
+                   const unsigned char *d_active, int n, const float *lr, float b1, float b2, float eps,
+                   proj_stream stream);
+
 /* Synchronise the stream, read and clear the workspace status word.
  * *status receives the PROJ_STATUS_* bits (may be NULL).  Returns PROJ_OK,
  * PROJ_E_DEVICE when a bit was set, or PROJ_E_CUDA. */

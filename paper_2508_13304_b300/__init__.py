@@ -72,6 +72,7 @@ _SIGS = {
                                       _P, _P, _I, _P, _P, _P, _P],
     "proj_fdk_filter": [_P, _P, ctypes.c_float, _P, _P],
     "proj_sharpness": [_P, _P, _P, _P, _P, _SZ, _P],
+    "proj_pose_adam": [_P, _P, _P, _P, _P, _P, _I, ctypes.POINTER(ctypes.c_float)] + [ctypes.c_float] * 3 + [_P],
     "proj_gather_probe": [_P, _P, _P, _SZ, _P],
     "proj_set_warp_shape": [_P, _I],
     "proj_get_warp_shape": [_P, ctypes.POINTER(_I)],
@@ -378,6 +379,18 @@ def proj_sharpness(plan: Plan, vol, loss, grad=None, ws=None, stream=None):
                                 _ptr(loss, torch.float32, 1, "loss"),
                                 _ptr(grad, torch.float32, plan.vol_numel, "grad", allow_none=True), p, nb,
                                 _stream(stream)))
+
+
+def proj_pose_adam(pose, grad, m, v, t, active, lr, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    """One Adam step on [n][6] poses in one launch (include/proj.h):
+    m, v [n][6] and t [n] (step counts) FP32 state; active [n] bool or None."""
+    import torch
+    n = pose.shape[0]
+    lr6 = (ctypes.c_float * 6)(*[float(x) for x in lr])
+    _check(lib().proj_pose_adam(_ptr(pose, torch.float32, 6 * n, "pose"), _ptr(grad, torch.float32, 6 * n, "grad"),
+                                _ptr(m, torch.float32, 6 * n, "m"), _ptr(v, torch.float32, 6 * n, "v"),
+                                _ptr(t, torch.float32, n, "t"), _ptr(active, torch.bool, n, "active", allow_none=True),
+                                int(n), lr6, float(b1), float(b2), float(eps), _stream(stream)))
 
 
 WARP_WIDTHS = (2, 4, 8, 16)

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "proj_internal.cuh"
+#include "proj_optim.cuh"
 
 using namespace projk;
 
@@ -893,6 +894,25 @@ int proj_sharpness(proj_plan p, const float* d_vol, float* d_loss, float* d_grad
   double* stats = part + 2 * (size_t)sharpness_blocks(p->geo);
   cudaError_t e = launch_sharpness(d_vol, p->geo, m, part, stats, d_loss, d_grad, (cudaStream_t)stream);
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "sharpness launch");
+}
+
+int proj_pose_adam(float* d_pose, const float* d_grad, float* d_m, float* d_v, float* d_t,
+                   const unsigned char* d_active, int n, const float* lr, float b1, float b2, float eps,
+                   proj_stream stream) {
+  if (n < 0) return fail(PROJ_E_ARG, "proj_pose_adam: n = %d", n);
+  if (n == 0) return PROJ_OK;
+  if (!d_pose || !d_grad || !d_m || !d_v || !d_t || !lr) return fail(PROJ_E_ARG, "proj_pose_adam: NULL argument");
+  if (!(b1 >= 0.f && b1 < 1.f && b2 >= 0.f && b2 < 1.f && eps >= 0.f))
+    return fail(PROJ_E_ARG, "proj_pose_adam: need 0 <= b1, b2 < 1 and eps >= 0");
+  PoseAdam h;
+  for (int j = 0; j < 6; ++j) h.lr[j] = lr[j];
+  h.b1 = b1;
+  h.a1 = (float)(1.0 - (double)b1);
+  h.b2 = b2;
+  h.a2 = (float)(1.0 - (double)b2);
+  h.eps = eps;
+  cudaError_t e = launch_pose_adam(d_pose, d_grad, d_m, d_v, d_t, d_active, n, h, (cudaStream_t)stream);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "pose Adam launch");
 }
 
 }  // extern "C"

@@ -7,8 +7,8 @@ changes by less than 1e-5 or the NCC exceeds 0.999).
 Batched: every start pose (candidate) is a pose of one plan, all candidates
 advance together, one fused launch per iteration; a converged candidate
 keeps its pose (masked update).  Plain: the same loop with one candidate per
-launch.  The Adam update is a few elementwise torch operations on an
-[n, 6] tensor; its step counter lives on the device, so whole iterations
+launch.  The Adam update is one launch on the [n, 6] pose tensor
+(proj_pose_adam); its step counters live on the device, so whole iterations
 (pose-gradient launches, stopping test, Adam step) can be captured in a CUDA
 graph and replayed (graph_steps > 0): the host then looks at the stopping
 state once per replay instead of once per iteration.  The trajectories are
@@ -23,31 +23,27 @@ import time
 import numpy as np
 import torch
 
-from . import PROJ_LOSS_NCC, PROJ_OP_FORWARD_GRAD, Projector, proj_forward_pose_grad, proj_set_volume
+from . import (PROJ_LOSS_NCC, PROJ_OP_FORWARD_GRAD, Projector, proj_forward_pose_grad, proj_pose_adam,
+               proj_set_volume)
 
 
 class Adam:
-    """Adam on an [n, 6] pose tensor with per-parameter step sizes."""
+    """Adam on an [n, 6] pose tensor with per-parameter step sizes, one launch
+    per step (proj_pose_adam)."""
 
     def __init__(self, n, lr, betas=(0.9, 0.999), eps=1e-8, device="cuda"):
-        self.lr = torch.as_tensor(lr, dtype=torch.float32, device=device).reshape(1, 6)
+        self.lr = [float(x) for x in np.broadcast_to(np.asarray(lr, dtype=np.float64), (6,))]
         self.b1, self.b2 = betas
         self.eps = eps
         self.m = torch.zeros((n, 6), device=device)
         self.v = torch.zeros((n, 6), device=device)
         # step count of each pose, on the device: a pose's bias correction counts only its own
         # updates, so a start that joins a running batch later follows its own trajectory
-        self.t = torch.zeros((n, 1), dtype=torch.float32, device=device)
+        self.t = torch.zeros(n, dtype=torch.float32, device=device)
 
     def step(self, pose, grad, active):
-        a = active.float().reshape(-1, 1)
-        self.t.add_(a)
-        tc = self.t.clamp(min=1.0)              # rows never updated have m = v = 0
-        self.m.mul_(1 - a * (1 - self.b1)).add_(a * (1 - self.b1) * grad)
-        self.v.mul_(1 - a * (1 - self.b2)).add_(a * (1 - self.b2) * grad * grad)
-        mh = self.m / (1 - torch.pow(self.b1, tc))
-        vh = self.v / (1 - torch.pow(self.b2, tc))
-        pose.sub_(a * self.lr * mh / (torch.sqrt(vh) + self.eps))
+        """Update the rows of pose whose active flag is set (active: [n] bool, or None for all)."""
+        proj_pose_adam(pose, grad, self.m, self.v, self.t, active, self.lr, self.b1, self.b2, self.eps)
 
 
 def paper_step_sizes():

@@ -213,3 +213,12 @@ def test_c_program_uses_the_abi_without_python(tmp_path, L):
                     "-Wl,-rpath," + libdir, "-o", exe], check=True)
     out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stdout + out.stderr
+
+
+def test_pose_adam_checks_its_arguments_on_the_host():
+    lr = (ctypes.c_float * 6)(*([1.0] * 6))
+    f = pb.lib().proj_pose_adam
+    assert f(None, None, None, None, None, None, 0, lr, 0.9, 0.999, 1e-8, None) == pb.PROJ_OK   # nothing to do
+    assert f(None, None, None, None, None, None, 1, lr, 0.9, 0.999, 1e-8, None) == pb.PROJ_E_ARG
+    assert "NULL" in pb.proj_last_error()
+    assert f(None, None, None, None, None, None, -1, lr, 0.9, 0.999, 1e-8, None) == pb.PROJ_E_ARG
