@@ -437,6 +437,46 @@ int proj_pose_adam(float *d_pose, const float *d_grad, float *d_m, float *d_v, f
                    const unsigned char *d_active, int n, const float *lr, float b1, float b2, float eps,
                    proj_stream stream);
 
+/* Parameters of proj_registration_step. */
+typedef struct {
+  float lr[6];           /* Adam step sizes per pose parameter (mm, rad) */
+  float b1, b2, eps;     /* Adam moments and epsilon (FP32 values) */
+  float ncc_stop;        /* a start stops when -loss >= ncc_stop (loss = -NCC) ... */
+  float dloss_stop;      /* ... or |loss - previous loss| < dloss_stop ... */
+  long long max_iter;    /* ... or after max_iter updates */
+  float tol_mm, tol_deg; /* hit tolerance against the truth: every |translation error| <= tol_mm and
+                            every |rotation error| <= tol_deg */
+} proj_reg_params;
+
+/* The bookkeeping of one iteration of a multi-start registration (Sec.
+ * II-D.3), after proj_forward_pose_grad(_list) has written the loss and
+ * gradient of the listed starts, in one launch (one block):
+ *   1. the starts in d_slots (n_slots entries, -1 = empty) are "listed";
+ *   2. for each listed start i: if d_truth is given and pose i is within
+ *      the tolerance of truth row i (or of row 0 when n_truth = 1),
+ *      *d_hit_any = 1; the start stops (d_alive[i] = 0) when its loss meets
+ *      a stopping rule; a start still alive counts the update in
+ *      d_iters[i] and takes one Adam step (as proj_pose_adam); its loss is
+ *      kept in d_last[i] for the next loss-change test;
+ *   3. every slot that is empty or holds a stopped start takes the next
+ *      start in order (*d_next, then *d_next + 1, ...) while starts remain,
+ *      else becomes -1; *d_next advances by the starts taken.
+ * Running every start at once: n_slots = n, d_slots = 0 .. n - 1, *d_next =
+ * n (slots of stopped starts just empty).
+ *   d_pose, d_grad [n][6], d_loss, d_last, d_t [n] FP32; d_m, d_v [n][6]
+ *   FP32 (Adam state, zero at the start); d_alive [n] bytes (1 at the
+ *   start); d_iters [n] int64; d_slots [n_slots] int32; d_next 1 int64;
+ *   d_truth [n_truth][6] or NULL; d_hit_any 1 byte (needed with a truth);
+ *   d_listed [n] bytes of scratch; prm host memory (copied into the launch).
+ * Asynchronous, no allocation, capturable.  Errors: PROJ_E_ARG (NULL
+ * pointers, negative sizes, n_truth not 1 or n, b1 or b2 outside [0, 1),
+ * eps < 0), PROJ_E_CUDA. */
+int proj_registration_step(int n, int n_slots, float *d_pose, const float *d_grad, const float *d_loss, float *d_last,
+                           float *d_m, float *d_v, float *d_t, unsigned char *d_alive, long long *d_iters,
+                           int *d_slots, long long *d_next, const float *d_truth, int n_truth,
+                           unsigned char *d_hit_any, unsigned char *d_listed, const proj_reg_params *prm,
+                           proj_stream stream);
+
 /* Synchronise the stream, read and clear the workspace status word.
  * *status receives the PROJ_STATUS_* bits (may be NULL).  Returns PROJ_OK,
  * PROJ_E_DEVICE when a bit was set, or PROJ_E_CUDA. */

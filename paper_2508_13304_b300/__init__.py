@@ -73,6 +73,7 @@ _SIGS = {
     "proj_fdk_filter": [_P, _P, ctypes.c_float, _P, _P],
     "proj_sharpness": [_P, _P, _P, _P, _P, _SZ, _P],
     "proj_pose_adam": [_P, _P, _P, _P, _P, _P, _I, ctypes.POINTER(ctypes.c_float)] + [ctypes.c_float] * 3 + [_P],
+    "proj_registration_step": [_I, _I] + [_P] * 12 + [_I, _P, _P, _P, _P],
     "proj_gather_probe": [_P, _P, _P, _SZ, _P],
     "proj_set_warp_shape": [_P, _I],
     "proj_get_warp_shape": [_P, ctypes.POINTER(_I)],
@@ -391,6 +392,37 @@ def proj_pose_adam(pose, grad, m, v, t, active, lr, b1=0.9, b2=0.999, eps=1e-8, 
                                 _ptr(m, torch.float32, 6 * n, "m"), _ptr(v, torch.float32, 6 * n, "v"),
                                 _ptr(t, torch.float32, n, "t"), _ptr(active, torch.bool, n, "active", allow_none=True),
                                 int(n), lr6, float(b1), float(b2), float(eps), _stream(stream)))
+
+
+class RegParams(ctypes.Structure):
+    """proj_reg_params of include/proj.h."""
+    _fields_ = [("lr", ctypes.c_float * 6), ("b1", ctypes.c_float), ("b2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("ncc_stop", ctypes.c_float), ("dloss_stop", ctypes.c_float), ("max_iter", ctypes.c_longlong),
+                ("tol_mm", ctypes.c_float), ("tol_deg", ctypes.c_float)]
+
+
+def reg_params(lr, b1=0.9, b2=0.999, eps=1e-8, ncc_stop=0.999, dloss_stop=1e-5, max_iter=1 << 62, tol=(0.5, 0.5)):
+    return RegParams((ctypes.c_float * 6)(*[float(x) for x in lr]), b1, b2, eps, ncc_stop, dloss_stop,
+                     int(max_iter), float(tol[0]), float(tol[1]))
+
+
+def proj_registration_step(pose, grad, loss, last, m, v, t, alive, iters, slots, nxt, truth, hit_any, listed,
+                           params, stream=None):
+    """One iteration's bookkeeping of a multi-start registration in one launch
+    (include/proj.h): hit test, stopping test, masked Adam step, refill of the
+    slots of stopped starts.  params: a RegParams (reg_params())."""
+    import torch
+    n, ns = pose.shape[0], slots.numel()
+    n_truth = 0 if truth is None else truth.numel() // 6
+    _check(lib().proj_registration_step(
+        int(n), int(ns), _ptr(pose, torch.float32, 6 * n, "pose"), _ptr(grad, torch.float32, 6 * n, "grad"),
+        _ptr(loss, torch.float32, n, "loss"), _ptr(last, torch.float32, n, "last"),
+        _ptr(m, torch.float32, 6 * n, "m"), _ptr(v, torch.float32, 6 * n, "v"), _ptr(t, torch.float32, n, "t"),
+        _ptr(alive, torch.bool, n, "alive"), _ptr(iters, torch.int64, n, "iters"),
+        _ptr(slots, torch.int32, ns, "slots"), _ptr(nxt, torch.int64, 1, "next"),
+        _ptr(truth, torch.float32, None, "truth", allow_none=True), int(n_truth),
+        _ptr(hit_any, torch.bool, 1, "hit_any", allow_none=True), _ptr(listed, torch.bool, None, "listed"),
+        ctypes.byref(params), _stream(stream)))
 
 
 WARP_WIDTHS = (2, 4, 8, 16)

@@ -915,6 +915,54 @@ int proj_pose_adam(float* d_pose, const float* d_grad, float* d_m, float* d_v, f
   return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "pose Adam launch");
 }
 
+int proj_registration_step(int n, int n_slots, float* d_pose, const float* d_grad, const float* d_loss, float* d_last,
+                           float* d_m, float* d_v, float* d_t, unsigned char* d_alive, long long* d_iters,
+                           int* d_slots, long long* d_next, const float* d_truth, int n_truth,
+                           unsigned char* d_hit_any, unsigned char* d_listed, const proj_reg_params* prm,
+                           proj_stream stream) {
+  if (n < 0 || n_slots < 0) return fail(PROJ_E_ARG, "proj_registration_step: n = %d, n_slots = %d", n, n_slots);
+  if (n == 0 || n_slots == 0) return PROJ_OK;
+  if (!d_pose || !d_grad || !d_loss || !d_last || !d_m || !d_v || !d_t || !d_alive || !d_iters || !d_slots ||
+      !d_next || !d_listed || !prm)
+    return fail(PROJ_E_ARG, "proj_registration_step: NULL argument");
+  if (d_truth && (n_truth != 1 && n_truth != n))
+    return fail(PROJ_E_ARG, "proj_registration_step: n_truth = %d must be 1 or n = %d", n_truth, n);
+  if (d_truth && !d_hit_any) return fail(PROJ_E_ARG, "proj_registration_step: a truth needs d_hit_any");
+  if (!(prm->b1 >= 0.f && prm->b1 < 1.f && prm->b2 >= 0.f && prm->b2 < 1.f && prm->eps >= 0.f))
+    return fail(PROJ_E_ARG, "proj_registration_step: need 0 <= b1, b2 < 1 and eps >= 0");
+  RegStep r;
+  r.n = n;
+  r.n_slots = n_slots;
+  r.pose = d_pose;
+  r.grad = d_grad;
+  r.loss = d_loss;
+  r.last = d_last;
+  r.m = d_m;
+  r.v = d_v;
+  r.t = d_t;
+  r.alive = d_alive;
+  r.iters = d_iters;
+  r.slots = d_slots;
+  r.next = d_next;
+  r.truth = d_truth;
+  r.n_truth = n_truth;
+  r.hit_any = d_hit_any;
+  r.listed = d_listed;
+  r.ncc_stop = prm->ncc_stop;
+  r.dloss_stop = prm->dloss_stop;
+  r.tol_mm = prm->tol_mm;
+  r.tol_deg = prm->tol_deg;
+  r.max_iter = prm->max_iter;
+  for (int j = 0; j < 6; ++j) r.adam.lr[j] = prm->lr[j];
+  r.adam.b1 = prm->b1;
+  r.adam.a1 = (float)(1.0 - (double)prm->b1);
+  r.adam.b2 = prm->b2;
+  r.adam.a2 = (float)(1.0 - (double)prm->b2);
+  r.adam.eps = prm->eps;
+  cudaError_t e = launch_registration_step(r, (cudaStream_t)stream);
+  return e == cudaSuccess ? PROJ_OK : cuda_fail(e, "registration step launch");
+}
+
 }  // extern "C"
 
 struct proj_batch_s {

@@ -7,8 +7,10 @@ changes by less than 1e-5 or the NCC exceeds 0.999).
 Batched: every start pose (candidate) is a pose of one plan, all candidates
 advance together, one fused launch per iteration; a converged candidate
 keeps its pose (masked update).  Plain: the same loop with one candidate per
-launch.  The Adam update is one launch on the [n, 6] pose tensor
-(proj_pose_adam); its step counters live on the device, so whole iterations
+launch.  The bookkeeping of an iteration (hit test against a known truth,
+stopping test, masked Adam step, refill of the slots of stopped starts) is
+one launch (proj_registration_step); the Adam step counters live on the
+device, so whole iterations
 (pose-gradient launches, stopping test, Adam step) can be captured in a CUDA
 graph and replayed (graph_steps > 0): the host then looks at the stopping
 state once per replay instead of once per iteration.  The trajectories are
@@ -24,7 +26,7 @@ import numpy as np
 import torch
 
 from . import (PROJ_LOSS_NCC, PROJ_OP_FORWARD_GRAD, Projector, proj_forward_pose_grad, proj_pose_adam,
-               proj_set_volume)
+               proj_registration_step, proj_set_volume, reg_params)
 
 
 class Adam:
@@ -94,21 +96,21 @@ def register(geom, mu, target, init_poses, max_iter=200, lr=None, ncc_stop=0.999
     iters = torch.zeros(n, dtype=torch.int64, device=device)
     hit_any = torch.zeros((), dtype=torch.bool, device=device)
     views = [(pose[grp[0]:grp[-1] + 1], grad[grp[0]:grp[-1] + 1], loss[grp[0]:grp[-1] + 1]) for grp in groups]
+    tp = None
     if true_pose is not None:
-        tp = torch.as_tensor(np.asarray(true_pose, dtype=np.float32), device=device).reshape(-1, 6)
+        tp = torch.as_tensor(np.asarray(true_pose, dtype=np.float32), device=device).reshape(-1, 6).contiguous()
+    # every start in a slot of its own; a stopped start's slot just empties (no start waits)
+    slots = torch.arange(n, dtype=torch.int32, device=device)
+    nxt = torch.full((), n, dtype=torch.int64, device=device)
+    listed = torch.zeros(n, dtype=torch.bool, device=device)
+    params = reg_params(opt.lr, opt.b1, opt.b2, opt.eps, ncc_stop, dloss_stop, max_iter, tol)
 
     def iteration():
         for (pg, g_out, l_out), P in zip(views, projs):
             proj_forward_pose_grad(P.plan, pg, PROJ_LOSS_NCC, tgt, g_out, l_out, None, P.ws)
-        if true_pose is not None:
-            d = (pose - tp).abs()
-            hit = (d[:, :3].amax(1) <= tol[0]) & (torch.rad2deg(d[:, 3:]).amax(1) <= tol[1])
-            hit_any.logical_or_(hit.any())
-        done = (-loss >= ncc_stop) | ((last - loss).abs() < dloss_stop)
-        active.logical_and_(~done)
-        iters.add_(active)
-        opt.step(pose, grad, active)
-        last.copy_(loss)
+        # hit test, stopping test, masked Adam step, loss history: one launch
+        proj_registration_step(pose, grad, loss, last, opt.m, opt.v, opt.t, active, iters, slots, nxt, tp,
+                               hit_any if tp is not None else None, listed, params)
 
     first_hit = None
     torch.cuda.synchronize()
@@ -171,32 +173,18 @@ def register_waves(geom, mu, target, init_poses, wave, max_iter=200, lr=None, nc
     slots = torch.arange(B, dtype=torch.int32, device=device)    # pose of each slot, -1 = empty
     nxt = torch.full((), B, dtype=torch.int64, device=device)    # next start to begin
     hit_any = torch.zeros((), dtype=torch.bool, device=device)
-    listed_buf = torch.zeros(n + 1, dtype=torch.bool, device=device)
+    listed = torch.zeros(n, dtype=torch.bool, device=device)
+    tp = None
     if true_pose is not None:
-        tp = torch.as_tensor(np.asarray(true_pose, dtype=np.float32), device=device).reshape(-1, 6)
+        tp = torch.as_tensor(np.asarray(true_pose, dtype=np.float32), device=device).reshape(-1, 6).contiguous()
+    params = reg_params(opt.lr, opt.b1, opt.b2, opt.eps, ncc_stop, dloss_stop, max_iter, tol)
 
     def iteration():
         proj_forward_pose_grad_list(P.plan, pose, slots, PROJ_LOSS_NCC, tgt, grad, loss, None, P.ws)
-        sl = slots.long()
-        listed_buf.zero_()
-        listed_buf.index_fill_(0, torch.where(sl >= 0, sl, n), True)
-        listed = listed_buf[:n]
-        if true_pose is not None:
-            d = (pose - tp).abs()
-            hit = listed & (d[:, :3].amax(1) <= tol[0]) & (torch.rad2deg(d[:, 3:]).amax(1) <= tol[1])
-            hit_any.logical_or_(hit.any())
-        done = listed & ((-loss >= ncc_stop) | ((last - loss).abs() < dloss_stop) | (iters >= max_iter))
-        alive.logical_and_(~done)
-        upd = alive & listed
-        iters.add_(upd)
-        opt.step(pose, grad, upd)
-        last.copy_(torch.where(listed, loss, last))
-        # refill the slots of stopped starts (and empty ones) with the next starts, in order
-        free = (sl < 0) | ~alive[sl.clamp(min=0)]
-        cand = nxt + torch.cumsum(free.long(), 0) - 1
-        take = free & (cand < n)
-        slots.copy_(torch.where(take, cand, torch.where(free, torch.full_like(cand, -1), sl)).int())
-        nxt.add_(take.long().sum())
+        # hit test, stopping test, masked Adam step, loss history and the refill of the slots of stopped
+        # starts with the next starts in order: one launch
+        proj_registration_step(pose, grad, loss, last, opt.m, opt.v, opt.t, alive, iters, slots, nxt, tp,
+                               hit_any if tp is not None else None, listed, params)
 
     first_hit = None
     torch.cuda.synchronize()

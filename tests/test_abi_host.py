@@ -222,3 +222,13 @@ def test_pose_adam_checks_its_arguments_on_the_host():
     assert f(None, None, None, None, None, None, 1, lr, 0.9, 0.999, 1e-8, None) == pb.PROJ_E_ARG
     assert "NULL" in pb.proj_last_error()
     assert f(None, None, None, None, None, None, -1, lr, 0.9, 0.999, 1e-8, None) == pb.PROJ_E_ARG
+
+
+def test_registration_step_checks_its_arguments_on_the_host():
+    f = pb.lib().proj_registration_step
+    prm = pb.reg_params([1.0] * 6)
+    nul = [None] * 12
+    assert f(0, 0, *nul, 0, None, None, ctypes.byref(prm), None) == pb.PROJ_OK        # nothing to do
+    assert f(2, 2, *nul, 0, None, None, ctypes.byref(prm), None) == pb.PROJ_E_ARG
+    assert "NULL" in pb.proj_last_error()
+    assert f(-1, 2, *nul, 0, None, None, ctypes.byref(prm), None) == pb.PROJ_E_ARG
