@@ -414,6 +414,8 @@ def proj_registration_step(pose, grad, loss, last, m, v, t, alive, iters, slots,
     import torch
     n, ns = pose.shape[0], slots.numel()
     n_truth = 0 if truth is None else truth.numel() // 6
+    if truth is not None and truth.numel() not in (6, 6 * n):
+        raise ValueError("truth must hold 1 or n = %d poses" % n)
     _check(lib().proj_registration_step(
         int(n), int(ns), _ptr(pose, torch.float32, 6 * n, "pose"), _ptr(grad, torch.float32, 6 * n, "grad"),
         _ptr(loss, torch.float32, n, "loss"), _ptr(last, torch.float32, n, "last"),
@@ -421,7 +423,7 @@ def proj_registration_step(pose, grad, loss, last, m, v, t, alive, iters, slots,
         _ptr(alive, torch.bool, n, "alive"), _ptr(iters, torch.int64, n, "iters"),
         _ptr(slots, torch.int32, ns, "slots"), _ptr(nxt, torch.int64, 1, "next"),
         _ptr(truth, torch.float32, None, "truth", allow_none=True), int(n_truth),
-        _ptr(hit_any, torch.bool, 1, "hit_any", allow_none=True), _ptr(listed, torch.bool, None, "listed"),
+        _ptr(hit_any, torch.bool, 1, "hit_any", allow_none=True), _ptr(listed, torch.bool, n, "listed"),
         ctypes.byref(params), _stream(stream)))
 
 
