@@ -1411,10 +1411,10 @@ def main():
                         "losses copied out every step; step k+1's copies overlap step k's compute; no L2 flush "
                         "between steps (the two 285 MB (mu, grad mu) copies exceed L2)",
                 "serial_value": world * args.n_cand / (em_serial * 1e-3), "serial_ms_per_step": em_serial},
-        # per step and rank: k_volume_prep, k_transpose_xy (the y-fast copy), k_cell_bits, k_brick_maps8,
+        # per step and rank: k_volume_prep (both (mu, grad mu) copies), k_cell_bits, k_brick_maps8,
         # k_brick_maps16, k_cell_decide (proj_set_volume, plus one memset of the cell-test counters), k_setup,
         # k_forward_grad, k_forward_grad_reduce (proj_forward_pose_grad)
-        "gpu_launches": 9 * args.steps * world,
+        "gpu_launches": 8 * args.steps * world,
         "clocks": clk,
         "wall_s_timed_region": wall,
     }
