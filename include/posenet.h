@@ -121,8 +121,11 @@ int pn_conv3x3s2_bf16(const void *x, int B, int H, int W, int C, const void *w, 
  * matrix: dx[b][iy][ix][c] = sum over taps (ky, kx) and output channels o of
  * dy[b][oy][ox][o] w[o][(ky * 3 + kx) C + c], over the (oy, ox) with
  * 2 oy - 1 + ky = iy and 2 ox - 1 + kx = ix inside the output grid.  The
- * kernel gathers each 128 x 64 tile of dy rows (zero for a tap with no such
- * output pixel) into shared memory; FP32 accumulation.
+ * kernel gathers each 128 x 64 tile of dy rows into shared memory; FP32
+ * accumulation.  With cout a multiple of 64 the input pixels run in their
+ * four parity classes (iy mod 2, ix mod 2), each over only the 1, 2 or 4
+ * taps that reach an output pixel; else every pixel runs over all 9 taps
+ * (zero rows for the taps with no output pixel).
  *   dy     BF16 NHWC [B][Ho][Wo][cout], Ho = (H + 1) / 2, Wo = (W + 1) / 2,
  *          cout a multiple of 8, 16-byte aligned.
  *   wt     BF16 [C][9 cout], k = (ky * 3 + kx) cout + o: the weights

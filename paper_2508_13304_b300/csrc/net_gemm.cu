@@ -136,11 +136,14 @@ __device__ __forceinline__ float epi_value(float acc, int row, int col, const Ge
 
 // Epilogue of one CTA: its 128 TMEM lanes are rows m0..m0+127 of D, its BN
 // columns are n0..; each warp reads its 32 lanes 16 columns at a time.
+// out_row >= 0 stores this lane's row as row out_row of D (and of the mask)
+// instead, for GEMMs whose rows are a permutation of D's.
 template <int BN>
 __device__ __forceinline__ void epilogue(uint32_t tmem_d, int m0, int n0, int M, int N, int z, const GemmEpi& epi,
-                                         int quarter) {
+                                         int quarter, int out_row = -1) {
   const int lane = threadIdx.x & 31;
-  const int row = m0 + quarter * 32 + lane;  // a warp reads TMEM lanes 32 * (warp id mod 4) ...
+  const int lrow = m0 + quarter * 32 + lane;  // a warp reads TMEM lanes 32 * (warp id mod 4) ...
+  const int row = out_row >= 0 ? out_row : lrow;
   const uint32_t lane_base = tmem_d + (static_cast<uint32_t>(quarter * 32) << 16);
 #pragma unroll 1
   for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -148,7 +151,7 @@ __device__ __forceinline__ void epilogue(uint32_t tmem_d, int m0, int n0, int M,
     __syncwarp();  // tcgen05.ld is warp-collective
     tmem_ld16(lane_base + c0, v);
     const int col0 = n0 + c0;
-    if (row >= M || col0 >= N) continue;
+    if (lrow >= M || col0 >= N) continue;
     const int nval = min(16, N - col0);
     if (epi.part) {
       float* dst = epi.part + ((size_t)z * M + row) * N + col0;
@@ -668,7 +671,7 @@ cudaError_t launch_pair_persistent(const CUtensorMap& ta, const CUtensorMap& tb,
 // memory: warps 0-3 gather each 128 x 64 A stage straight from the
 // activation, one output pixel (tile row) per thread, as eight 16-byte
 // cp.async copies placed at their 128-byte-swizzled positions (zero fill for
-// taps in the padding and for rows past M).  DGRAD = true runs the input
+// taps in the padding and for rows past M).  MODE 1 and 2 run the input
 // gradient of that convolution the same way: a row is an input pixel (iy,
 // ix), and tap (ky, kx) reads the output gradient at ((iy + 1 - ky) / 2,
 // (ix + 1 - kx) / 2) where both are integers inside the output grid (zero
@@ -691,12 +694,20 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// x: the gathered tensor, [B][SH][SW][C]; rows of the GEMM run over the grid [B][OH][OW] (forward: the
-// output pixels, SH = H, OH = (H + 1) / 2; DGRAD: the input pixels, SH = Ho, OH = H).
-template <int BN, bool DGRAD>
+// x: the gathered tensor, [B][SH][SW][C]; rows of the GEMM run over the grid [B][OH][OW] (MODE 0, the
+// forward convolution: the output pixels, SH = H, OH = (H + 1) / 2; MODE 1, its input gradient: the
+// input pixels, SH = Ho, OH = H, every row over all 9 taps).  MODE 2 is the input gradient by parity
+// class: a block's rows are input pixels (iy, ix) of one class (iy mod 2, ix mod 2) = (py, px), for
+// which only taps ky = 1 (py = 0) or ky in {0, 2} (py = 1), likewise kx, have an output pixel, so the
+// K loop runs over those 1, 2 or 4 taps only (C a multiple of 64: a K block never straddles taps);
+// M is then the batch size, the classes' tiles follow one another in blockIdx.x (ctile: the tile
+// counts of classes 0, 0-1, 0-2, 0-3), and the epilogue stores each row at its pixel's position.
+template <int BN, int MODE>
 __global__ void __launch_bounds__(kConvThreads, 1)
     k_conv3x3s2_implicit(const __nv_bfloat16* __restrict__ x, int SH, int SW, int C, int OH, int OW,
-                         const __grid_constant__ CUtensorMap tb, int M, int N, GemmEpi epi, int* status) {
+                         const __grid_constant__ CUtensorMap tb, int M, int N, GemmEpi epi, int* status,
+                         int4 ctile) {
+  constexpr bool DGRAD = MODE != 0;
   constexpr uint32_t kBytesA = kBM * kBK * 2, kBytesB = BN * kBK * 2;
   constexpr int kAhead = kStages - 1;  // stages of copies a gathering thread keeps in flight
   extern __shared__ uint8_t smem_raw[];
@@ -712,8 +723,29 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   const uint32_t done = bars + 8u * (2 * kStages);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-  const int nkb = (9 * C + kBK - 1) / kBK;
+  const int n0 = blockIdx.y * BN;
+  int m0 = blockIdx.x * kBM, Mrows = M, nkb = (9 * C + kBK - 1) / kBK;
+  int py = 0, px = 0, Hc = OH, Wc = OW, cpt = 1;
+  if (MODE == 2) {  // uniform per block: the tile's parity class and its K blocks
+    const int bx = blockIdx.x;
+    const int cls = bx < ctile.x ? 0 : (bx < ctile.y ? 1 : (bx < ctile.z ? 2 : 3));
+    const int first = cls == 0 ? 0 : (cls == 1 ? ctile.x : (cls == 2 ? ctile.y : ctile.z));
+    py = cls >> 1;
+    px = cls & 1;
+    Hc = (OH + 1 - py) >> 1;
+    Wc = (OW + 1 - px) >> 1;
+    m0 = (bx - first) * kBM;
+    Mrows = M * Hc * Wc;
+    cpt = C / kBK;
+    nkb = (1 + py) * (1 + px) * cpt;
+  }
+  // MODE 2: K block i is channels c .. c + 63 of tap (ky, kx)
+  auto class_tap = [&](int i, int& ky, int& kx, int& c) {
+    const int j = i / cpt, ntx = 1 + px, kyi = j / ntx, kxi = j - kyi * ntx;
+    c = (i - j * cpt) * kBK;
+    ky = py ? 2 * kyi : 1;
+    kx = px ? 2 * kxi : 1;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -735,10 +767,20 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   const uint32_t tmem_d = *tmem_slot;
   int fail = 0;
 
+  int out_row = -1;  // MODE 2: this thread's row of the output
   if (warp < 4) {
     const int t = threadIdx.x;  // row of the A tile
     const int m = m0 + t;
-    const bool row_ok = m < M;
+    const bool row_ok = m < Mrows;
+    int iy = 0, ix = 0;
+    const __nv_bfloat16* xc = x;
+    if (MODE == 2 && row_ok) {
+      const int jx = m % Wc, jy = (m / Wc) % Hc, bc = m / (Wc * Hc);
+      iy = 2 * jy + py;
+      ix = 2 * jx + px;
+      out_row = (bc * OH + iy) * OW + ix;
+      xc = x + (size_t)bc * SH * SW * C;
+    }
     const int wo = row_ok ? m % OW : 0, ho = row_ok ? (m / OW) % OH : 0, b = row_ok ? m / (OW * OH) : 0;
     // forward: source pixel (2 ho - 1 + ky, 2 wo - 1 + kx); DGRAD: twice the source pixel is (ho + 1 - ky,
     // wo + 1 - kx)
@@ -752,11 +794,20 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         fail = kStatusTimeoutFree;
         break;
       }
+      const uint32_t dst = sA + s * kBytesA + row_off;
+      if (MODE == 2) {
+        int ky, kx, c;
+        class_tap(i, ky, kx, c);
+        const int oy = (iy + 1 - ky) >> 1, ox = (ix + 1 - kx) >> 1;  // exact: the class has the parity
+        const bool ok = row_ok && oy < SH && ox < SW;
+        const __nv_bfloat16* src = ok ? xc + ((size_t)oy * SW + ox) * C + c : x;
+#pragma unroll
+        for (int j = 0; j < kBK / 8; ++j) cp_async16(dst + (((uint32_t)j ^ swz) << 4), ok ? src + 8 * j : x, ok ? 16u : 0u);
+      }
       const int k = i * kBK;
       int tap = k / C, c = k - tap * C;
-      const uint32_t dst = sA + s * kBytesA + row_off;
 #pragma unroll
-      for (int j = 0; j < kBK / 8; ++j) {  // 16-byte chunk j of the row: k .. k + 7 of tap `tap`
+      for (int j = 0; j < (MODE == 2 ? 0 : kBK / 8); ++j) {  // 16-byte chunk j of the row: k .. k + 7 of tap `tap`
         int hi, wi;
         bool ok;
         if (DGRAD) {
@@ -796,7 +847,13 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         break;
       }
       mbar_expect_tx(full(s), kBytesB);
-      tma_load_2d(sB + s * kBytesB, &tb, full(s), i * kBK, n0);
+      int kcol = i * kBK;
+      if (MODE == 2) {
+        int ky, kx, c;
+        class_tap(i, ky, kx, c);
+        kcol = (ky * 3 + kx) * C + c;
+      }
+      tma_load_2d(sB + s * kBytesB, &tb, full(s), kcol, n0);
     }
   } else if (warp == 5 && lane == 0) {
     constexpr uint32_t idesc = idesc_bf16(BN);
@@ -822,7 +879,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   const bool any_fail = __syncthreads_or(fail != 0 || !ok) != 0;
   tc_fence_after();
 
-  if (!any_fail && warp < 4) epilogue<BN>(tmem_d, m0, n0, M, N, 0, epi, warp);
+  if (!any_fail && warp < 4) epilogue<BN>(tmem_d, m0, n0, Mrows, N, 0, epi, warp, out_row);
 
   tc_fence_before();
   __syncthreads();
@@ -833,21 +890,40 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   }
 }
 
-// forward: x [B][H][W][C], rows = output pixels; dgrad: x = the output gradient [B][Ho][Wo][C] (C = the
-// convolution's cout), rows = the B x H x W input pixels
-template <int BN, bool DGRAD>
+// MODE 0 (forward): x [B][H][W][C], rows = output pixels; MODE 1 / 2 (input gradient): x = the output
+// gradient [B][Ho][Wo][C] (C = the convolution's cout), rows = the B x H x W input pixels (MODE 2 in
+// parity classes, C a multiple of 64)
+template <int BN, int MODE>
 cudaError_t launch_conv_bn(const __nv_bfloat16* x, int B, int H, int W, int C, const CUtensorMap& tb, int N,
                            const GemmEpi& epi, int* status, cudaStream_t s) {
   const size_t smem = gemm_smem_bytes(BN);
   cudaError_t e =
-      cudaFuncSetAttribute(k_conv3x3s2_implicit<BN, DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_conv3x3s2_implicit<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  constexpr bool DGRAD = MODE != 0;
   const int Ho = (H + 1) / 2, Wo = (W + 1) / 2;
   const int SH = DGRAD ? Ho : H, SW = DGRAD ? Wo : W, OH = DGRAD ? H : Ho, OW = DGRAD ? W : Wo;
   const long long M = (long long)B * OH * OW;
   if (M > 0x7fffffffLL) return cudaErrorInvalidValue;
-  dim3 grid((unsigned)((M + kBM - 1) / kBM), (N + BN - 1) / BN, 1);
-  k_conv3x3s2_implicit<BN, DGRAD><<<grid, kConvThreads, smem, s>>>(x, SH, SW, C, OH, OW, tb, (int)M, N, epi, status);
+  int4 ctile = make_int4(0, 0, 0, 0);
+  long long blocks = (M + kBM - 1) / kBM;
+  int m_arg = (int)M;
+  if (MODE == 2) {
+    if (C % kBK) return cudaErrorInvalidValue;
+    long long acc = 0, cum[4];
+    for (int c = 0; c < 4; ++c) {
+      const long long rows = (long long)B * ((H + 1 - (c >> 1)) / 2) * ((W + 1 - (c & 1)) / 2);
+      acc += (rows + kBM - 1) / kBM;
+      cum[c] = acc;
+    }
+    ctile = make_int4((int)cum[0], (int)cum[1], (int)cum[2], (int)cum[3]);
+    blocks = acc;
+    m_arg = B;
+  }
+  if (blocks < 1) return cudaSuccess;
+  dim3 grid((unsigned)blocks, (N + BN - 1) / BN, 1);
+  k_conv3x3s2_implicit<BN, MODE><<<grid, kConvThreads, smem, s>>>(x, SH, SW, C, OH, OW, tb, m_arg, N, epi, status,
+                                                                  ctile);
   return cudaGetLastError();
 }
 
@@ -873,21 +949,32 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int
 cudaError_t launch_conv_implicit(const __nv_bfloat16* x, int B, int H, int W, int C, const CUtensorMap& tw, int cout,
                                  int bn, const GemmEpi& epi, int* status, cudaStream_t s) {
   switch (bn) {
-    case 32: return launch_conv_bn<32, false>(x, B, H, W, C, tw, cout, epi, status, s);
-    case 64: return launch_conv_bn<64, false>(x, B, H, W, C, tw, cout, epi, status, s);
-    case 128: return launch_conv_bn<128, false>(x, B, H, W, C, tw, cout, epi, status, s);
-    case 256: return launch_conv_bn<256, false>(x, B, H, W, C, tw, cout, epi, status, s);
+    case 32: return launch_conv_bn<32, 0>(x, B, H, W, C, tw, cout, epi, status, s);
+    case 64: return launch_conv_bn<64, 0>(x, B, H, W, C, tw, cout, epi, status, s);
+    case 128: return launch_conv_bn<128, 0>(x, B, H, W, C, tw, cout, epi, status, s);
+    case 256: return launch_conv_bn<256, 0>(x, B, H, W, C, tw, cout, epi, status, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_conv_dgrad_implicit(const __nv_bfloat16* dy, int B, int H, int W, int cout, const CUtensorMap& twt,
                                        int C, int bn, const GemmEpi& epi, int* status, cudaStream_t s) {
+  // by parity class (each input pixel only over the taps that reach an output pixel) when a K block of
+  // 64 channels never straddles two taps; else every input pixel over all 9 taps
+  if (cout % kBK == 0) {
+    switch (bn) {
+      case 32: return launch_conv_bn<32, 2>(dy, B, H, W, cout, twt, C, epi, status, s);
+      case 64: return launch_conv_bn<64, 2>(dy, B, H, W, cout, twt, C, epi, status, s);
+      case 128: return launch_conv_bn<128, 2>(dy, B, H, W, cout, twt, C, epi, status, s);
+      case 256: return launch_conv_bn<256, 2>(dy, B, H, W, cout, twt, C, epi, status, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (bn) {
-    case 32: return launch_conv_bn<32, true>(dy, B, H, W, cout, twt, C, epi, status, s);
-    case 64: return launch_conv_bn<64, true>(dy, B, H, W, cout, twt, C, epi, status, s);
-    case 128: return launch_conv_bn<128, true>(dy, B, H, W, cout, twt, C, epi, status, s);
-    case 256: return launch_conv_bn<256, true>(dy, B, H, W, cout, twt, C, epi, status, s);
+    case 32: return launch_conv_bn<32, 1>(dy, B, H, W, cout, twt, C, epi, status, s);
+    case 64: return launch_conv_bn<64, 1>(dy, B, H, W, cout, twt, C, epi, status, s);
+    case 128: return launch_conv_bn<128, 1>(dy, B, H, W, cout, twt, C, epi, status, s);
+    case 256: return launch_conv_bn<256, 1>(dy, B, H, W, cout, twt, C, epi, status, s);
     default: return cudaErrorInvalidValue;
   }
 }
